@@ -1,0 +1,798 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct FP64 CPU reference for the hot
+ * path of "Xabclib: A Fully Auto-tuned Sparse Iterative Solver" (Katagiri et
+ * al.): CRS sparse matrix-vector multiply inside the restarted Krylov solvers
+ * GMRES(m) and BiCGStab, the restart-frequency rule (Eq. 1, Fig. 2, Sec. 4.3),
+ * and the pieces the GPU library adds around them (FP32-inside-FP64 iterative
+ * refinement, matrix features, and a small MLP with analytic gradients).
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and
+ * the benchmark's CPU-baseline / reference arm may load it.  The CUDA library
+ * never calls it and shares no code, header, table or helper with it.
+ *
+ * Style rules followed throughout:
+ *   - one loop per mathematical sum, ascending index order, no blocking,
+ *     fusion or reordering beyond what the stated definition says;
+ *   - FP64 everywhere except where a routine's whole point is FP32 arithmetic
+ *     (the inner solve of the mixed-precision refinement), which says so;
+ *   - CRS is 0-based: rowptr[n+1], col[nnz], val[nnz], columns ascending.
+ *
+ * Return codes match the library's meaning: 0 ok, -4 not converged within the
+ * iteration limit, -5 numerical breakdown.
+ *
+ * Parity pins (which independent facts each routine is checked against) are
+ * listed in the test files; every routine here has at least one.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ENOCONV (-4)
+#define ORC_EBREAKDOWN (-5)
+
+/* ------------------------------------------------------------------------ */
+/* Sparse matrix-vector products                                              */
+/* ------------------------------------------------------------------------ */
+
+/* General CRS SpMV, y = alpha*A*x + beta*y (Sec. 3.2.2; CRS format Sec. 4.2).
+ * For each row i: s = sum over k in [rowptr[i], rowptr[i+1]) of val[k]*x[col[k]],
+ * accumulated in ascending k.  beta == 0 means y is not read (BLAS rule). */
+void orc_spmv(int n, const int *rowptr, const int *col, const double *val,
+              double alpha, const double *x, double beta, double *y)
+{
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++)
+            s += val[k] * x[col[k]];
+        y[i] = (beta == 0.0) ? alpha * s : alpha * s + beta * y[i];
+    }
+}
+
+/* Symmetric SpMV from upper-triangle storage (Sec. 4.2: "the lower part of the
+ * matrix is not stored"; S1-S3 of Sec. 3.2.2).  Each stored (i, j, u) with
+ * j >= i contributes u*x[j] to row i and, when j != i, u*x[i] to row j, i.e.
+ * y = alpha*(U + U^T - diag(U))*x + beta*y. */
+void orc_spmv_sym(int n, const int *rowptr, const int *col, const double *val,
+                  double alpha, const double *x, double beta, double *y)
+{
+    double *t = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int i = 0; i < n; i++) {
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            int j = col[k];
+            t[i] += val[k] * x[j];
+            if (j != i)
+                t[j] += val[k] * x[i];
+        }
+    }
+    for (int i = 0; i < n; i++)
+        y[i] = (beta == 0.0) ? alpha * t[i] : alpha * t[i] + beta * y[i];
+    free(t);
+}
+
+/* FP32 CRS SpMV with FP32 accumulation (the inner product of the mixed
+ * precision refinement: matrix, vector and sum all single precision). */
+void orc_spmv_f32(int n, const int *rowptr, const int *col, const float *val,
+                  float alpha, const float *x, float beta, float *y)
+{
+    for (int i = 0; i < n; i++) {
+        float s = 0.0f;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++)
+            s += val[k] * x[col[k]];
+        y[i] = (beta == 0.0f) ? alpha * s : alpha * s + beta * y[i];
+    }
+}
+
+/* Dense y = A x, A row-major m x n.  Used only to pin the sparse routines. */
+void orc_dense_matvec(int m, int n, const double *A, const double *x, double *y)
+{
+    for (int i = 0; i < m; i++) {
+        double s = 0.0;
+        for (int j = 0; j < n; j++)
+            s += A[(size_t)i * n + j] * x[j];
+        y[i] = s;
+    }
+}
+
+/* Dense LU with partial pivoting, solves A z = b in place (A row-major n x n
+ * is overwritten by its factors, b by z).  Returns 0, or -1 if a pivot is 0.
+ * Textbook Gaussian elimination; used only to pin the Krylov solvers. */
+int orc_lu_solve(int n, double *A, double *b)
+{
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = fabs(A[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double v = fabs(A[(size_t)i * n + k]);
+            if (v > best) { best = v; p = i; }
+        }
+        if (best == 0.0)
+            return -1;
+        if (p != k) {
+            for (int j = 0; j < n; j++) {
+                double t = A[(size_t)k * n + j];
+                A[(size_t)k * n + j] = A[(size_t)p * n + j];
+                A[(size_t)p * n + j] = t;
+            }
+            double t = b[k]; b[k] = b[p]; b[p] = t;
+        }
+        for (int i = k + 1; i < n; i++) {
+            double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            A[(size_t)i * n + k] = l;
+            for (int j = k + 1; j < n; j++)
+                A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = b[i];
+        for (int j = i + 1; j < n; j++)
+            s -= A[(size_t)i * n + j] * b[j];
+        b[i] = s / A[(size_t)i * n + i];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector helpers (plain loops)                                              */
+/* ------------------------------------------------------------------------ */
+
+static double dot(int n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; i++)
+        s += a[i] * b[i];
+    return s;
+}
+
+static double nrm2(int n, const double *a) { return sqrt(dot(n, a, a)); }
+
+/* matvec by storage kind: 0 = general CRS, 1 = symmetric upper CRS */
+static void matvec(int kind, int n, const int *rp, const int *ci, const double *v,
+                   const double *x, double *y)
+{
+    if (kind == 1)
+        orc_spmv_sym(n, rp, ci, v, 1.0, x, 0.0, y);
+    else
+        orc_spmv(n, rp, ci, v, 1.0, x, 0.0, y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restart-frequency auto-tuning (Sec. 3.2.1, Eq. 1; Fig. 2; Sec. 4.3)       */
+/* ------------------------------------------------------------------------ */
+
+/* MM ratio of Eq. (1): R(s,t) = max{r(z)} / min{r(z)} over z = s-t+1 .. s.
+ * r is indexed 1-based as in the paper (r[z-1] holds r(z)).  Requires
+ * 1 <= t <= s.  A zero minimum gives +inf. */
+double orc_mm_ratio(const double *r, int s, int t)
+{
+    double mx = r[s - t], mn = r[s - t];
+    for (int z = s - t + 1; z <= s; z++) {
+        double v = r[z - 1];
+        if (v > mx) mx = v;
+        if (v < mn) mn = v;
+    }
+    return (mn == 0.0) ? INFINITY : mx / mn;
+}
+
+/* The judgement of OpenATI_DAFRT: over the I samples SAMP(1..I), a small MM
+ * ratio means stagnation, so IRT = 1 ("increase the restart frequency") when
+ * R(I, I) < theta, else IRT = 0.  theta is a library parameter (the paper
+ * passes it through IATPARAM/RATPARAM without giving a value). */
+int orc_dafrt(int I, const double *samp, double theta)
+{
+    return orc_mm_ratio(samp, I, I) < theta ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Arnoldi with modified Gram-Schmidt (Sec. 3.2.2, "MGS: the default")       */
+/* ------------------------------------------------------------------------ */
+
+/* k steps of Arnoldi from v1 = v0/||v0||.  V is (m+1) x n (row j = v_{j+1}),
+ * H is (m+1) x m row-major, both zero-filled here.  MGS per step j:
+ * w = A v_j; for i = 1..j: h_ij = (w, v_i), w -= h_ij v_i; h_{j+1,j} = ||w||.
+ * Stops early on breakdown (h_{j+1,j} == 0).  Returns the number of steps. */
+int orc_arnoldi(int n, int kind, const int *rp, const int *ci, const double *v,
+                const double *v0, int m, double *V, double *H)
+{
+    memset(V, 0, sizeof(double) * (size_t)(m + 1) * n);
+    memset(H, 0, sizeof(double) * (size_t)(m + 1) * m);
+    double b = nrm2(n, v0);
+    for (int i = 0; i < n; i++)
+        V[i] = v0[i] / b;
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    int steps = 0;
+    for (int j = 0; j < m; j++) {
+        matvec(kind, n, rp, ci, v, V + (size_t)j * n, w);
+        for (int i = 0; i <= j; i++) {
+            double h = dot(n, w, V + (size_t)i * n);
+            H[(size_t)i * m + j] = h;
+            for (int q = 0; q < n; q++)
+                w[q] -= h * V[(size_t)i * n + q];
+        }
+        double hn = nrm2(n, w);
+        H[(size_t)(j + 1) * m + j] = hn;
+        steps = j + 1;
+        if (hn == 0.0)
+            break;
+        for (int q = 0; q < n; q++)
+            V[(size_t)(j + 1) * n + q] = w[q] / hn;
+    }
+    free(w);
+    return steps;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restarted GMRES(m) (Saad & Schultz; listed in Sec. 2.2, run in Sec. 4.3)  */
+/* ------------------------------------------------------------------------ */
+
+/* Breakdown threshold: after MGS, w is (in exact arithmetic) the component of
+ * A v_j orthogonal to the basis, and ||A v_j||^2 = sum_i h_ij^2 + h_{j+1,j}^2.
+ * A "happy" breakdown is declared when h_{j+1,j} <= 1e-14 of that length. */
+#define ORC_BREAKDOWN_REL 1e-14
+
+/*
+ * GMRES(m) with MGS Arnoldi and Givens-rotation least squares, no
+ * preconditioner, x in: initial guess, out: iterate.
+ *
+ *   kind:     0 general CRS, 1 symmetric upper CRS
+ *   m:        initial restart length;  m_max: cap for the restart rule
+ *   tol:      stop when ||b - A x|| / ||b|| <= tol (true residual)
+ *   maxiter:  limit on Arnoldi steps (SpMVs inside cycles)
+ *   dafrt:    1 = apply the restart-frequency rule: the true residual at every
+ *             restart is a sample (Sec. 4.3: "in every restarting"); each time
+ *             `window` samples are gathered (Fig. 2's judgement period I) the
+ *             MM-ratio judgement runs, m += dm when it says IRT = 1 (Sec. 4.3:
+ *             MSIZE+5), and the sample count resets (Fig. 2: K = 0).
+ *   theta:    DAFRT threshold
+ *
+ * Fault convergence (Sec. 3.1, 3.3.2): each cycle stops on the implicit
+ * residual |g_{k+1}|/||b|| <= tau.  If the true residual computed at the next
+ * restart still exceeds tol, the cycle's claim was false: the fault counter
+ * is incremented and the implicit threshold is narrowed, tau *= tol/res_true.
+ *
+ * iinfo: [0] iterations, [1] restarts (cycles completed), [2] final m,
+ *        [3] fault-convergence events.
+ * dinfo: [0] last implicit relative residual, [1] true relative residual.
+ * hist/mhist (may be NULL): true relative residual at the start of each cycle
+ *        and the restart length m that cycle runs with, up to hist_cap entries.
+ */
+int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
+              const double *b, double *x, int m, int m_max, double tol,
+              int maxiter, int dafrt, double theta, int window, int dm,
+              int *iinfo, double *dinfo, double *hist, int *mhist, int hist_cap)
+{
+    if (m_max < m) m_max = m;
+    int iters = 0, restarts = 0, faults = 0, K = 0, claimed = 0, status = ORC_OK;
+    double tau = tol, res_impl = 0.0, res_true = 0.0;
+    double bnorm = nrm2(n, b);
+    iinfo[0] = iinfo[1] = iinfo[3] = 0;
+    iinfo[2] = m;
+    if (bnorm == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        dinfo[0] = dinfo[1] = 0.0;
+        return ORC_OK;
+    }
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double *V = (double *)malloc(sizeof(double) * (size_t)(m_max + 1) * n);
+    double *H = (double *)malloc(sizeof(double) * (size_t)(m_max + 1) * m_max);
+    double *cs = (double *)malloc(sizeof(double) * (size_t)m_max);
+    double *sn = (double *)malloc(sizeof(double) * (size_t)m_max);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m_max + 1));
+    double *y = (double *)malloc(sizeof(double) * (size_t)m_max);
+    double *samp = (double *)malloc(sizeof(double) * (size_t)(window > 0 ? window : 1));
+
+    for (;;) {
+        /* r = b - A x, true residual */
+        matvec(kind, n, rp, ci, va, x, r);
+        for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+        double beta = nrm2(n, r);
+        res_true = beta / bnorm;
+        if (hist && restarts < hist_cap) { hist[restarts] = res_true; mhist[restarts] = m; }
+        if (res_true <= tol) { status = ORC_OK; break; }
+        if (iters >= maxiter) { status = ORC_ENOCONV; break; }
+        if (claimed) { faults++; tau *= tol / res_true; }
+        claimed = 0;
+        if (dafrt && restarts > 0 && window > 0) {
+            samp[K++] = res_true;
+            if (K == window) {
+                if (orc_dafrt(window, samp, theta)) {
+                    m += dm;
+                    if (m > m_max) m = m_max;
+                }
+                K = 0;
+            }
+        }
+        if (mhist && restarts < hist_cap) mhist[restarts] = m; /* m this cycle uses */
+        /* one cycle */
+        for (int i = 0; i < n; i++) V[i] = r[i] / beta;
+        for (int i = 0; i <= m; i++) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0, broke = 0;
+        for (int j = 0; j < m; j++) {
+            iters++;
+            matvec(kind, n, rp, ci, va, V + (size_t)j * n, w);
+            double len2 = 0.0;
+            for (int i = 0; i <= j; i++) {
+                double h = dot(n, w, V + (size_t)i * n);
+                H[(size_t)i * m_max + j] = h;
+                len2 += h * h;
+                for (int q = 0; q < n; q++)
+                    w[q] -= h * V[(size_t)i * n + q];
+            }
+            double hn = nrm2(n, w);
+            H[(size_t)(j + 1) * m_max + j] = hn;
+            len2 += hn * hn;
+            /* previous rotations on column j */
+            for (int i = 0; i < j; i++) {
+                double a = H[(size_t)i * m_max + j], c = H[(size_t)(i + 1) * m_max + j];
+                H[(size_t)i * m_max + j] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m_max + j] = -sn[i] * a + cs[i] * c;
+            }
+            /* new rotation zeroing h_{j+1,j} */
+            double a = H[(size_t)j * m_max + j];
+            double rr = hypot(a, hn);
+            if (rr == 0.0) { status = ORC_EBREAKDOWN; k = j; broke = 2; break; }
+            cs[j] = a / rr;
+            sn[j] = hn / rr;
+            H[(size_t)j * m_max + j] = rr;
+            H[(size_t)(j + 1) * m_max + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            res_impl = fabs(g[j + 1]) / bnorm;
+            k = j + 1;
+            if (hn <= ORC_BREAKDOWN_REL * sqrt(len2)) { broke = 1; break; }
+            for (int q = 0; q < n; q++)
+                V[(size_t)(j + 1) * n + q] = w[q] / hn;
+            if (res_impl <= tau) { claimed = 1; break; }
+            if (iters >= maxiter) break;
+        }
+        if (broke == 2) break;
+        if (broke == 1) claimed = 1;
+        /* back substitution R y = g, then x += V y */
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int q = i + 1; q < k; q++)
+                s -= H[(size_t)i * m_max + q] * y[q];
+            y[i] = s / H[(size_t)i * m_max + i];
+        }
+        for (int i = 0; i < k; i++)
+            for (int q = 0; q < n; q++)
+                x[q] += y[i] * V[(size_t)i * n + q];
+        restarts++;
+    }
+    iinfo[0] = iters;
+    iinfo[1] = restarts;
+    iinfo[2] = m;
+    iinfo[3] = faults;
+    dinfo[0] = res_impl;
+    dinfo[1] = res_true;
+    free(r); free(w); free(V); free(H); free(cs); free(sn); free(g); free(y); free(samp);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BiCGStab (van der Vorst), no preconditioner (listed in Sec. 2.2, run in   */
+/* Sec. 4.3).                                                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One BiCGStab iteration (two SpMVs):
+ *   rho' = (rhat, r); beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v)
+ *   v = A p; alpha = rho' / (rhat, v); s = r - alpha v
+ *   if ||s||/||b|| <= tau: x += alpha p, stop
+ *   t = A s; omega = (t, s)/(t, t); x += alpha p + omega s; r = s - omega t
+ *   rho = rho'; stop if ||r||/||b|| <= tau
+ * Breakdown (status -5) when rho', (rhat, v) or (t, t) is exactly zero, or omega
+ * is zero without convergence.  The true residual is checked after every
+ * claimed convergence; a false claim (fault convergence, Sec. 3.3.2) restarts
+ * the recurrence from the true residual with tau *= tol/res_true.
+ * iinfo: [0] iterations, [1] recurrence restarts, [3] fault events.
+ * dinfo: [0] last recursive relative residual, [1] true relative residual.
+ */
+int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va,
+                 const double *b, double *x, double tol, int maxiter,
+                 int *iinfo, double *dinfo)
+{
+    int iters = 0, restarts = 0, faults = 0, claimed = 0, status = ORC_OK;
+    double tau = tol, res_rec = 0.0, res_true = 0.0;
+    double bnorm = nrm2(n, b);
+    iinfo[0] = iinfo[1] = iinfo[2] = iinfo[3] = 0;
+    if (bnorm == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        dinfo[0] = dinfo[1] = 0.0;
+        return ORC_OK;
+    }
+    size_t bytes = sizeof(double) * (size_t)n;
+    double *r = (double *)malloc(bytes), *rh = (double *)malloc(bytes);
+    double *p = (double *)malloc(bytes), *v = (double *)malloc(bytes);
+    double *s = (double *)malloc(bytes), *t = (double *)malloc(bytes);
+    for (;;) {
+        matvec(kind, n, rp, ci, va, x, r);
+        for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+        res_true = nrm2(n, r) / bnorm;
+        if (res_true <= tol) { status = ORC_OK; break; }
+        if (iters >= maxiter) { status = ORC_ENOCONV; break; }
+        if (claimed) { faults++; tau *= tol / res_true; restarts++; }
+        else if (iters > 0) restarts++;
+        claimed = 0;
+        for (int i = 0; i < n; i++) { rh[i] = r[i]; p[i] = 0.0; v[i] = 0.0; }
+        double rho = 1.0, alpha = 1.0, omega = 1.0;
+        int broke = 0;
+        while (iters < maxiter) {
+            iters++;
+            double rho1 = dot(n, rh, r);
+            if (rho1 == 0.0) { broke = 1; break; }
+            double beta = (rho1 / rho) * (alpha / omega);
+            for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+            matvec(kind, n, rp, ci, va, p, v);
+            double sigma = dot(n, rh, v);
+            if (sigma == 0.0) { broke = 1; break; }
+            alpha = rho1 / sigma;
+            for (int i = 0; i < n; i++) s[i] = r[i] - alpha * v[i];
+            double sn = nrm2(n, s) / bnorm;
+            if (sn <= tau) {
+                for (int i = 0; i < n; i++) x[i] += alpha * p[i];
+                res_rec = sn;
+                claimed = 1;
+                break;
+            }
+            matvec(kind, n, rp, ci, va, s, t);
+            double tt = dot(n, t, t);
+            if (tt == 0.0) { broke = 1; break; }
+            omega = dot(n, t, s) / tt;
+            for (int i = 0; i < n; i++) x[i] += alpha * p[i] + omega * s[i];
+            for (int i = 0; i < n; i++) r[i] = s[i] - omega * t[i];
+            rho = rho1;
+            res_rec = nrm2(n, r) / bnorm;
+            if (res_rec <= tau) { claimed = 1; break; }
+            if (omega == 0.0) { broke = 1; break; }
+        }
+        if (broke) {
+            matvec(kind, n, rp, ci, va, x, r);
+            for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+            res_true = nrm2(n, r) / bnorm;
+            status = (res_true <= tol) ? ORC_OK : ORC_EBREAKDOWN;
+            break;
+        }
+    }
+    iinfo[0] = iters;
+    iinfo[1] = restarts;
+    iinfo[3] = faults;
+    dinfo[0] = res_rec;
+    dinfo[1] = res_true;
+    free(r); free(rh); free(p); free(v); free(s); free(t);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32-inside-FP64 iterative refinement with GMRES(m) as the inner solver.   */
+/* The paper's accuracy policy deliberately avoids refinement (Sec. 3.3.1);  */
+/* this is the library's precision extension, written as the textbook        */
+/* refinement loop: r = b - A x (FP64); solve A d = r/||r|| approximately in */
+/* FP32; x += ||r|| d (FP64).                                                */
+/* ------------------------------------------------------------------------ */
+
+static float sdot(int n, const float *a, const float *b)
+{
+    float s = 0.0f;
+    for (int i = 0; i < n; i++)
+        s += a[i] * b[i];
+    return s;
+}
+
+/* Inner FP32 GMRES(m) from d = 0 on A32 d = r32: SpMV, basis and inner
+ * products (accumulated) in FP32; Hessenberg, Givens rotations and the small
+ * least-squares solve in FP64; d += V y in FP32.  Stops when the implicit
+ * residual relative to ||r32|| is <= tol_in or after maxit steps.
+ * Returns the number of Arnoldi steps taken (status -5 on breakdown is folded
+ * into an early return; the outer loop tests the true residual anyway). */
+int orc_gmres_f32_inner(int n, const int *rp, const int *ci, const float *va,
+                        const float *r32, float *d, int m, double tol_in, int maxit)
+{
+    int iters = 0;
+    double rb = sqrt((double)sdot(n, r32, r32));
+    for (int i = 0; i < n; i++) d[i] = 0.0f;
+    if (rb == 0.0) return 0;
+    float *rin = (float *)malloc(sizeof(float) * (size_t)n);
+    float *w = (float *)malloc(sizeof(float) * (size_t)n);
+    float *V = (float *)malloc(sizeof(float) * (size_t)(m + 1) * n);
+    double *H = (double *)malloc(sizeof(double) * (size_t)(m + 1) * m);
+    double *cs = (double *)malloc(sizeof(double) * (size_t)m);
+    double *sn = (double *)malloc(sizeof(double) * (size_t)m);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *y = (double *)malloc(sizeof(double) * (size_t)m);
+    int done = 0;
+    while (!done && iters < maxit) {
+        orc_spmv_f32(n, rp, ci, va, 1.0f, d, 0.0f, rin);
+        for (int i = 0; i < n; i++) rin[i] = r32[i] - rin[i];
+        double beta = sqrt((double)sdot(n, rin, rin));
+        if (beta / rb <= tol_in || beta == 0.0) break;
+        for (int i = 0; i < n; i++) V[i] = (float)(rin[i] / beta);
+        for (int i = 0; i <= m; i++) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; j++) {
+            iters++;
+            orc_spmv_f32(n, rp, ci, va, 1.0f, V + (size_t)j * n, 0.0f, w);
+            double len2 = 0.0;
+            for (int i = 0; i <= j; i++) {
+                double h = (double)sdot(n, w, V + (size_t)i * n);
+                H[(size_t)i * m + j] = h;
+                len2 += h * h;
+                float hf = (float)h;
+                for (int q = 0; q < n; q++)
+                    w[q] -= hf * V[(size_t)i * n + q];
+            }
+            double hn = sqrt((double)sdot(n, w, w));
+            len2 += hn * hn;
+            H[(size_t)(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; i++) {
+                double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[(size_t)j * m + j];
+            double rr = hypot(a, hn);
+            if (rr == 0.0) { done = 1; break; }
+            cs[j] = a / rr;
+            sn[j] = hn / rr;
+            H[(size_t)j * m + j] = rr;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            k = j + 1;
+            if (hn <= ORC_BREAKDOWN_REL * sqrt(len2)) { done = 1; break; }
+            for (int q = 0; q < n; q++)
+                V[(size_t)(j + 1) * n + q] = (float)((double)w[q] / hn);
+            if (fabs(g[j + 1]) / rb <= tol_in) { done = 1; break; }
+            if (iters >= maxit) break;
+        }
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int q = i + 1; q < k; q++)
+                s -= H[(size_t)i * m + q] * y[q];
+            y[i] = s / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < k; i++) {
+            float yi = (float)y[i];
+            for (int q = 0; q < n; q++)
+                d[q] += yi * V[(size_t)i * n + q];
+        }
+    }
+    free(rin); free(w); free(V); free(H); free(cs); free(sn); free(g); free(y);
+    return iters;
+}
+
+/*
+ * Mixed-precision refinement: outer loop in FP64 on the FP64 matrix, inner
+ * FP32 GMRES(m) on float(A).  Stagnation guard: if the outer residual fails to
+ * halve twice in a row, the remaining work is handed to FP64 GMRES(m) from the
+ * current x (iinfo[5] = 1 records that).
+ * iinfo: [0] total inner iterations, [1] outer iterations, [4] FP64 fallback
+ *        iterations, [5] fallback flag.   dinfo: [1] true relative residual.
+ */
+int orc_gmres_ir(int n, const int *rp, const int *ci, const double *va,
+                 const double *b, double *x, int m, double tol, double tol_in,
+                 int maxit_in, int max_outer, int *iinfo, double *dinfo)
+{
+    for (int i = 0; i < 6; i++) iinfo[i] = 0;
+    dinfo[0] = dinfo[1] = 0.0;
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        return ORC_OK;
+    }
+    int nnz = rp[n];
+    float *va32 = (float *)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    for (int k = 0; k < nnz; k++) va32[k] = (float)va[k];
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    float *r32 = (float *)malloc(sizeof(float) * (size_t)n);
+    float *d = (float *)malloc(sizeof(float) * (size_t)n);
+    int status = ORC_OK, outer = 0, slow = 0, inner_total = 0;
+    double prev = INFINITY, res = 0.0;
+    for (;;) {
+        orc_spmv(n, rp, ci, va, 1.0, x, 0.0, r);
+        for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+        double rn = nrm2(n, r);
+        res = rn / bnorm;
+        if (res <= tol) { status = ORC_OK; break; }
+        if (outer >= max_outer) { status = ORC_ENOCONV; break; }
+        slow = (rn > 0.5 * prev) ? slow + 1 : 0;
+        if (slow >= 2) {
+            int ii[4]; double dd[2];
+            status = orc_gmres(n, 0, rp, ci, va, b, x, m, m, tol, 1 << 30, 0, 0.0, 0, 0,
+                               ii, dd, NULL, NULL, 0);
+            iinfo[4] = ii[0];
+            iinfo[5] = 1;
+            res = dd[1];
+            break;
+        }
+        prev = rn;
+        for (int i = 0; i < n; i++) r32[i] = (float)(r[i] / rn);
+        inner_total += orc_gmres_f32_inner(n, rp, ci, va32, r32, d, m, tol_in, maxit_in);
+        for (int i = 0; i < n; i++) x[i] += rn * (double)d[i];
+        outer++;
+    }
+    iinfo[0] = inner_total;
+    iinfo[1] = outer;
+    dinfo[1] = res;
+    free(va32); free(r); free(r32); free(d);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matrix features (inputs of the learned tuner)                             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * raw[0] n, raw[1] nnz, raw[2] mean row length, raw[3] population variance of
+ * row lengths, raw[4] max row length, raw[5] bandwidth max |i - j| over stored
+ * entries, raw[6] symmetry flag: 1 when stored as upper triangle (sym_upper),
+ * else 1 iff pattern and values equal their transpose exactly.
+ * feat[8] (network input): ln(1+n), ln(1+nnz), ln(1+mean), ln(1+var),
+ * ln(1+max), ln(1+bandwidth), sym, ln(1+max) - ln(1+mean).
+ */
+void orc_features(int n, const int *rp, const int *ci, const double *va,
+                  int sym_upper, double *raw, double *feat)
+{
+    int nnz = rp[n];
+    double mean = n > 0 ? (double)nnz / n : 0.0;
+    double var = 0.0, mx = 0.0, bw = 0.0;
+    for (int i = 0; i < n; i++) {
+        double L = rp[i + 1] - rp[i];
+        var += (L - mean) * (L - mean);
+        if (L > mx) mx = L;
+        for (int k = rp[i]; k < rp[i + 1]; k++) {
+            double d = fabs((double)(ci[k] - i));
+            if (d > bw) bw = d;
+        }
+    }
+    var = n > 0 ? var / n : 0.0;
+    int sym = 1;
+    if (!sym_upper) {
+        /* every (i, j, v) must have a stored (j, i, v): search row j */
+        for (int i = 0; i < n && sym; i++) {
+            for (int k = rp[i]; k < rp[i + 1] && sym; k++) {
+                int j = ci[k], found = 0;
+                for (int q = rp[j]; q < rp[j + 1]; q++)
+                    if (ci[q] == i) { found = (va[q] == va[k]); break; }
+                if (!found) sym = 0;
+            }
+        }
+    }
+    raw[0] = n; raw[1] = nnz; raw[2] = mean; raw[3] = var; raw[4] = mx; raw[5] = bw;
+    raw[6] = sym;
+    feat[0] = log1p((double)n);
+    feat[1] = log1p((double)nnz);
+    feat[2] = log1p(mean);
+    feat[3] = log1p(var);
+    feat[4] = log1p(mx);
+    feat[5] = log1p(bw);
+    feat[6] = sym;
+    feat[7] = log1p(mx) - log1p(mean);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tuner MLP: d_in -> h1 (ReLU) -> h2 (ReLU) -> sum(heads) logits,           */
+/* softmax cross-entropy per head, Adam.  FP64 reference of the GPU's FP32   */
+/* kernels.  Parameter blob: W1[h1][d_in], b1[h1], W2[h2][h1], b2[h2],       */
+/* W3[o][h2], b3[o], o = sum of head sizes.                                  */
+/* ------------------------------------------------------------------------ */
+
+static void mlp_layer(const double *W, const double *bias, int out, int in,
+                      const double *a, double *z)
+{
+    for (int o = 0; o < out; o++) {
+        double s = bias[o];
+        for (int i = 0; i < in; i++)
+            s += W[(size_t)o * in + i] * a[i];
+        z[o] = s;
+    }
+}
+
+void orc_mlp_forward(const double *P, int d_in, int h1, int h2, int o,
+                     const double *X, int B, double *logits)
+{
+    const double *W1 = P, *b1 = W1 + (size_t)h1 * d_in, *W2 = b1 + h1,
+                 *b2 = W2 + (size_t)h2 * h1, *W3 = b2 + h2, *b3 = W3 + (size_t)o * h2;
+    double *a1 = (double *)malloc(sizeof(double) * (size_t)h1);
+    double *a2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    for (int s = 0; s < B; s++) {
+        mlp_layer(W1, b1, h1, d_in, X + (size_t)s * d_in, a1);
+        for (int i = 0; i < h1; i++) a1[i] = a1[i] > 0.0 ? a1[i] : 0.0;
+        mlp_layer(W2, b2, h2, h1, a1, a2);
+        for (int i = 0; i < h2; i++) a2[i] = a2[i] > 0.0 ? a2[i] : 0.0;
+        mlp_layer(W3, b3, o, h2, a2, logits + (size_t)s * o);
+    }
+    free(a1); free(a2);
+}
+
+/* Loss = (1/B) sum_s sum_heads -log softmax(logits_head)[label], and its
+ * gradient with respect to every parameter (grad has the blob's layout).
+ * heads[h] is the size of head h; labels is B x nh.  Returns the loss. */
+double orc_mlp_loss_grad(const double *P, int d_in, int h1, int h2, int nh,
+                         const int *heads, const double *X, const int *labels,
+                         int B, double *grad)
+{
+    int o = 0;
+    for (int h = 0; h < nh; h++) o += heads[h];
+    size_t np = (size_t)h1 * d_in + h1 + (size_t)h2 * h1 + h2 + (size_t)o * h2 + o;
+    memset(grad, 0, sizeof(double) * np);
+    const double *W1 = P, *b1 = W1 + (size_t)h1 * d_in, *W2 = b1 + h1,
+                 *b2 = W2 + (size_t)h2 * h1, *W3 = b2 + h2, *b3 = W3 + (size_t)o * h2;
+    double *gW1 = grad, *gb1 = gW1 + (size_t)h1 * d_in, *gW2 = gb1 + h1,
+           *gb2 = gW2 + (size_t)h2 * h1, *gW3 = gb2 + h2, *gb3 = gW3 + (size_t)o * h2;
+    (void)b3;
+    double *z1 = (double *)malloc(sizeof(double) * (size_t)h1);
+    double *a1 = (double *)malloc(sizeof(double) * (size_t)h1);
+    double *z2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    double *a2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    double *z3 = (double *)malloc(sizeof(double) * (size_t)o);
+    double *d3 = (double *)malloc(sizeof(double) * (size_t)o);
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    double *d1 = (double *)malloc(sizeof(double) * (size_t)h1);
+    double loss = 0.0;
+    for (int s = 0; s < B; s++) {
+        const double *x = X + (size_t)s * d_in;
+        mlp_layer(W1, b1, h1, d_in, x, z1);
+        for (int i = 0; i < h1; i++) a1[i] = z1[i] > 0.0 ? z1[i] : 0.0;
+        mlp_layer(W2, b2, h2, h1, a1, z2);
+        for (int i = 0; i < h2; i++) a2[i] = z2[i] > 0.0 ? z2[i] : 0.0;
+        mlp_layer(W3, P + ((size_t)h1 * d_in + h1 + (size_t)h2 * h1 + h2 + (size_t)o * h2),
+                  o, h2, a2, z3);
+        /* softmax cross-entropy per head: dL/dz = (softmax - onehot) / B */
+        int off = 0;
+        for (int h = 0; h < nh; h++) {
+            int K = heads[h];
+            double mx = z3[off];
+            for (int c = 1; c < K; c++) if (z3[off + c] > mx) mx = z3[off + c];
+            double se = 0.0;
+            for (int c = 0; c < K; c++) se += exp(z3[off + c] - mx);
+            int lab = labels[(size_t)s * nh + h];
+            loss += -(z3[off + lab] - mx - log(se)) / B;
+            for (int c = 0; c < K; c++)
+                d3[off + c] = (exp(z3[off + c] - mx) / se - (c == lab ? 1.0 : 0.0)) / B;
+            off += K;
+        }
+        for (int q = 0; q < o; q++) {
+            gb3[q] += d3[q];
+            for (int i = 0; i < h2; i++) gW3[(size_t)q * h2 + i] += d3[q] * a2[i];
+        }
+        for (int i = 0; i < h2; i++) {
+            double s2 = 0.0;
+            for (int q = 0; q < o; q++) s2 += W3[(size_t)q * h2 + i] * d3[q];
+            d2[i] = z2[i] > 0.0 ? s2 : 0.0;
+        }
+        for (int q = 0; q < h2; q++) {
+            gb2[q] += d2[q];
+            for (int i = 0; i < h1; i++) gW2[(size_t)q * h1 + i] += d2[q] * a1[i];
+        }
+        for (int i = 0; i < h1; i++) {
+            double s1 = 0.0;
+            for (int q = 0; q < h2; q++) s1 += W2[(size_t)q * h1 + i] * d2[q];
+            d1[i] = z1[i] > 0.0 ? s1 : 0.0;
+        }
+        for (int q = 0; q < h1; q++) {
+            gb1[q] += d1[q];
+            for (int i = 0; i < d_in; i++) gW1[(size_t)q * d_in + i] += d1[q] * x[i];
+        }
+    }
+    free(z1); free(a1); free(z2); free(a2); free(z3); free(d3); free(d2); free(d1);
+    return loss;
+}
+
+/* Adam (Kingma & Ba), step t >= 1:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */
+void orc_adam(double *P, const double *G, double *M, double *Vv, int np, int t,
+              double lr, double b1, double b2, double eps)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (int i = 0; i < np; i++) {
+        M[i] = b1 * M[i] + (1.0 - b1) * G[i];
+        Vv[i] = b2 * Vv[i] + (1.0 - b2) * G[i] * G[i];
+        P[i] -= lr * (M[i] / c1) / (sqrt(Vv[i] / c2) + eps);
+    }
+}
