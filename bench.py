@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the CRS SpMV + Krylov hot path on GB300.
+
+Headline (one JSON line on rank 0): achieved HBM GB/s of the auto-tuned FP64
+SpMV y = A x on the power-law matrix of the unbalanced-rows workload
+(n = 4,000,000, lognormal row lengths with arithmetic mean 12, sigma 1.5, cap
+20,000, uniform random columns, diagonal 2 * row |sum|; ~52M non-zeros,
+~0.70 GB of algorithmic traffic per SpMV, so every step streams more than
+the 129 MB L2).  GB/s counts algorithmic bytes: 12 B per non-zero (value +
+column index), rowptr once, x once, y once.
+
+--impl reference times the CPU oracle (plain C, one host core) on a bounded
+row sample of the same matrix with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV HBM GB/s vs peak; GMRES time-to-1e-8, tuned/mixed vs plain FP64"
+WORKLOAD = ("power-law CRS n=4,000,000 (lognormal rows mean 12 sigma 1.5 cap 20k, "
+            "uniform columns, diagonal 2x row |sum|), FP64, y = A x")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=4_000_000)
+    ap.add_argument("--no-extras", action="store_true", help="skip per-variant/sym/solver lines")
+    ap.add_argument("--solvers", action="store_true", help="also time the large solver cases")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        def rd():
+            for line in self.proc.stdout:
+                self.rows.append([c.strip() for c in line.split(",")])
+        self.t = threading.Thread(target=rd, daemon=True)
+        self.t.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[4 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_c3(n):
+    from paper_2405_01599_gb300 import gen
+    return gen.powerlaw(n=n, seed=3)
+
+
+def alg_bytes(A, vb=8, beta=False):
+    n, nnz = A["n"], A["nnz"]
+    return (vb + 4) * nnz + 4 * (n + 1) + 2 * vb * n + (vb * n if beta else 0)
+
+
+def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None):
+    """Time the oracle's SpMV (plain C, one core) on a bounded row block."""
+    import oracle
+    rp = A["rowptr"]
+    n = A["n"]
+    if max_nnz is not None and A["nnz"] > max_nnz:
+        r1 = int(np.searchsorted(rp, max_nnz, side="right")) - 1
+        r1 = max(1, r1)
+    else:
+        r1 = n
+    sub = dict(n=r1, nnz=int(rp[r1]), rowptr=np.ascontiguousarray(rp[: r1 + 1]),
+               col=A["col"], val=A["val"], sym_upper=False)
+    x = np.random.default_rng(0).uniform(-1, 1, n)
+    y = np.zeros(r1)
+    L = oracle.lib()
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while True:
+        t0 = time.perf_counter()
+        L.orc_spmv(r1, sub["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end or len(times) >= 50:
+            break
+    t = float(np.median(times))
+    b = 12 * sub["nnz"] + 4 * (r1 + 1) + 8 * r1 + 8 * r1 + 0  # x gathered, y written
+    b += 8 * r1  # x once (rows of the sample)
+    return b / t / 1e9, t, sub, len(times)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    A = make_c3(args.n)
+    # each step: the oracle SpMV over a row block of ~8M non-zeros
+    budget_nnz = 8_000_000
+    gbs, t, sub, reps = cpu_oracle_rate(A, budget_s=0.0, max_nnz=budget_nnz)
+    import oracle
+    L = oracle.lib()
+    x = np.random.default_rng(0).uniform(-1, 1, A["n"])
+    y = np.zeros(sub["n"])
+    for _ in range(args.warmup):
+        L.orc_spmv(sub["n"], sub["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.orc_spmv(sub["n"], sub["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
+    el = time.perf_counter() - t0
+    b = 12 * sub["nnz"] + 4 * (sub["n"] + 1) + 16 * sub["n"] + 8 * sub["n"]
+    val = b * args.steps / el / 1e9
+    sample = f"rows 0..{sub['n']} of the n=4M power-law matrix ({sub['nnz']} non-zeros) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    import torch
+    import paper_2405_01599_gb300 as xb
+    xb.build()
+    xb.lib()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    stream = torch.cuda.current_stream()
+
+    A = make_c3(args.n)
+    n, nnz = A["n"], A["nnz"]
+    plan = xb.Plan.from_host(A, dev)
+    choice = plan.tune()
+    x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, n), device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    bytes_step = alg_bytes(A)
+    launches_per_spmv = 2 if choice["variant"] == xb.VAR_SEGSCAN else 1
+
+    for _ in range(max(3, args.warmup)):
+        plan.spmv(x, y)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[2 * k].record(stream)
+        plan.spmv(x, y)
+        ev[2 * k + 1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    per_launch = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    avg_launch_ms = float(np.mean(per_launch))
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = ws * bytes_step / (ms_step * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D x, SpMV, D2H y
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    xh.copy_(x.cpu())
+    yh = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        x.copy_(xh, non_blocking=True)
+        plan.spmv(x, y)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        plan.spmv(x, y)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_val = ws * bytes_step / (e2e_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    achieved = bytes_step / (avg_launch_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz,
+                   "spmv_choice": {"variant": xb.VARIANT_NAMES[choice["variant"]],
+                                   "block": choice["block"], "ipt": choice["ipt"]},
+                   "alg_bytes_per_step": bytes_step,
+                   "l2": "inputs larger than L2 (0.70 GB streamed per step > 129 MB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "spmv (" + xb.VARIANT_NAMES[choice["variant"]] + ")"},
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches_per_spmv * args.steps,
+        "clocks": clk,
+    }
+    if ws == 1:
+        gbs, t, sub, reps = cpu_oracle_rate(A, budget_s=10.0)
+        out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                               "sample": f"full n=4M SpMV, median of {reps} runs"}
+    if not args.no_extras:
+        out["extras"] = extras(xb, torch, dev, plan, A, x, y, args)
+    print(json.dumps(out))
+    if pg:
+        pg.destroy_process_group()
+
+
+def _time_spmv(torch, fn, reps=20):
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extras(xb, torch, dev, plan, A, x, y, args):
+    from paper_2405_01599_gb300 import gen
+    import oracle
+    res = {}
+    b3 = alg_bytes(A)
+    var = {}
+    for name, v, blk, ipt in [("row_U1", 0, 256, 1), ("nnz_U2", 1, 256, 8),
+                              ("segscan_U3", 2, 256, 8), ("segscan_U3_i16", 2, 128, 16)]:
+        ms = _time_spmv(torch, lambda: plan.spmv(x, y, variant=v, block=blk, ipt=ipt))
+        var[name] = {"ms": ms, "GBs": b3 / ms / 1e6}
+    res["c3_variants"] = var
+    # config 2: 3D 7-point Laplacian 128^3, symmetric upper storage vs full
+    U = gen.laplace3d(128, upper=True)
+    F = gen.laplace3d(128)
+    pu = xb.Plan.from_host(U, dev)
+    pf = xb.Plan.from_host(F, dev)
+    cu = pu.tune()
+    cf = pf.tune()
+    n2 = U["n"]
+    x2 = torch.ones(n2, dtype=torch.float64, device=dev)
+    y2 = torch.empty_like(x2)
+    reps = 200
+    ms_sym = _time_spmv(torch, lambda: pu.spmv(x2, y2), reps)
+    ms_full = _time_spmv(torch, lambda: pf.spmv(x2, y2), reps)
+    ms_sym_atomic = _time_spmv(torch, lambda: pu.spmv(x2, y2, variant=3, block=256, ipt=1), reps)
+    bs = 12 * U["nnz"] + 4 * (n2 + 1) + 16 * n2
+    bf = alg_bytes(F)
+    flops = 2 * F["nnz"]
+    res["c2_sym_vs_full"] = {
+        "sym_tuned": {"choice": cu, "ms": ms_sym, "GBs": bs / ms_sym / 1e6, "GFLOPs": flops / ms_sym / 1e6},
+        "sym_atomic_S1": {"ms": ms_sym_atomic, "GBs": bs / ms_sym_atomic / 1e6},
+        "full_tuned": {"choice": cf, "ms": ms_full, "GBs": bf / ms_full / 1e6, "GFLOPs": flops / ms_full / 1e6},
+        "200_spmv_ms": {"sym": 200 * ms_sym, "full": 200 * ms_full},
+    }
+    # config 1: 64x64 Poisson GMRES(30) to 1e-8, b = A*ones, x0 = 0
+    P = gen.poisson2d(64)
+    pp = xb.Plan.from_host(P, dev)
+    bp = torch.tensor(oracle.spmv(P, np.ones(P["n"])), device=dev)
+    for ce in (1, 8):
+        xs = torch.zeros(P["n"], dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        info = pp.gmres(bp, xs, m=30, tol=1e-8, check_every=ce)
+        res[f"c1_gmres30_check{ce}"] = {"s": time.perf_counter() - t0, "iters": info["iters"],
+                                        "res_true": info["res_true"], "status": info["status"]}
+    return res
+
+
+if __name__ == "__main__":
+    main()

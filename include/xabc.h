@@ -1,0 +1,248 @@
+/*
+ * xabc.h -- C ABI of the GB300 (sm_103a) CRS SpMV + restarted Krylov library.
+ *
+ * The operation throughout is the paper's linear system A x = b with A in
+ * compressed row storage (CRS, Sec. 4.2 of Katagiri et al., "Xabclib: A Fully
+ * Auto-tuned Sparse Iterative Solver"), optionally symmetric with only the
+ * upper triangle stored (Sec. 4.2).
+ *
+ * Conventions for every entry point
+ *   - Matrix and vector pointers are DEVICE pointers owned by the caller (for
+ *     example torch tensors).  The library never frees caller memory.
+ *   - CRS is 0-based: rowptr[n+1], col[nnz] ascending within each row, no
+ *     duplicates, val[nnz] FP64.  n and nnz are < 2^31.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued on it in stream order; functions that
+ *     must read a device result on the host (solvers, tuners) synchronise
+ *     that stream.
+ *   - Return value: XB_OK (0) or a negative XB_E* code.  The message of the
+ *     last error on the calling host thread is returned by xb_last_error().
+ *   - A plan (xb_plan) owns library workspace in device memory, created by
+ *     xb_plan_create and released by xb_plan_destroy.  A plan may be used by
+ *     one host thread / one stream at a time.
+ */
+#ifndef XABC_H
+#define XABC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define XB_OK 0
+#define XB_EINVAL (-1)       /* bad argument or malformed CRS                  */
+#define XB_ENOMEM (-2)       /* device or host allocation failed               */
+#define XB_ECUDA (-3)        /* CUDA runtime error (message: xb_last_error)    */
+#define XB_ENOCONV (-4)      /* iteration/time limit hit; x holds the iterate  */
+#define XB_EBREAKDOWN (-5)   /* Krylov breakdown (singular/indefinite pivot)   */
+#define XB_ETIMEOUT (-6)     /* a bounded device-side wait expired            */
+
+/* ---- SpMV implementation variants (Sec. 3.2.2: U1-U3, S1-S3) ---------- */
+#define XB_VAR_AUTO (-1)     /* plan's tuned / default choice                  */
+#define XB_VAR_ROW 0         /* U1: one thread per row (conventional)          */
+#define XB_VAR_NNZ 1         /* U2: nnz-balanced row-aligned tiles             */
+#define XB_VAR_SEGSCAN 2     /* U3: flat nnz split + segmented sum (BSS)       */
+#define XB_VAR_SYM_ATOMIC 3  /* S1-like: every transpose term a global atomic  */
+#define XB_VAR_SYM_TILE 4    /* S2/S3-like: nnz-balanced tiles, in-tile        */
+                             /*   transpose terms in shared memory, only the   */
+                             /*   out-of-tile (non-zero region) ones global    */
+#define XB_NUM_VARIANTS 5
+
+#define XB_ORTHO_MGS 0       /* modified Gram-Schmidt (Sec. 3.2.2, default)    */
+#define XB_ORTHO_CGS2 1      /* DGKS: classical Gram-Schmidt twice            */
+
+#define XB_PREC_FP64 0
+#define XB_PREC_MIXED 1      /* FP32 SpMV + Arnoldi basis inside FP64          */
+                             /*   iterative refinement                         */
+
+#define XB_TUNER_NONE 0      /* fixed variant (options.variant or default)     */
+#define XB_TUNER_EXHAUSTIVE 1 /* time every candidate (Sec. 3.1)              */
+#define XB_TUNER_MLP 2       /* learned tuner (xb_mlp_*)                       */
+
+typedef struct xb_csr {
+    int32_t n;               /* rows = columns                                 */
+    int32_t nnz;             /* stored entries                                 */
+    const int32_t *rowptr;   /* device, n+1                                    */
+    const int32_t *col;      /* device, nnz                                    */
+    const double *val;       /* device, nnz                                    */
+    int32_t sym_upper;       /* 1: symmetric, only entries with col >= row     */
+} xb_csr;
+
+typedef struct xb_options {
+    double tol;              /* ||b - A x|| / ||b|| target (default 1e-8)      */
+    int32_t maxiter;         /* Arnoldi steps / BiCGStab iterations cap        */
+    double maxtime_s;        /* wall-clock cap, seconds (default 1000)        */
+    int32_t m;               /* GMRES restart length (default 30)             */
+    int32_t m_max;           /* cap for the restart rule (default 120)        */
+    int32_t dafrt;           /* 1: MM-ratio restart rule on (Eq. 1, Sec. 4.3)  */
+    double dafrt_theta;      /* judgement threshold (default 10)              */
+    int32_t dafrt_window;    /* samples per judgement (default 5, Fig. 2)     */
+    int32_t dafrt_dm;        /* restart-length increment (default 5)          */
+    int32_t ortho;           /* XB_ORTHO_*                                     */
+    int32_t precision;       /* XB_PREC_*                                      */
+    double tol_inner;        /* inner FP32 solve tolerance (default 1e-4)     */
+    int32_t maxiter_inner;   /* inner FP32 Arnoldi steps per refinement step  */
+    int32_t max_outer;       /* refinement steps cap (default 60)             */
+    int32_t variant;         /* XB_VAR_* for the SpMV inside solvers          */
+    int32_t block;           /* CTA size for SpMV (0 = plan default)          */
+    int32_t ipt;             /* items per thread (segscan / tile size)        */
+    int32_t tuner;           /* XB_TUNER_*                                     */
+    int32_t check_every;     /* host reads the residual every k steps (>=1)   */
+    int32_t timing;          /* 1: record per-SpMV CUDA-event times in info   */
+} xb_options;
+
+typedef struct xb_info {
+    int32_t status;          /* same as the return value                      */
+    int32_t iters;           /* Arnoldi steps / BiCGStab iterations           */
+    int32_t restarts;        /* GMRES cycles completed / BiCGStab restarts    */
+    int32_t m_final;         /* restart length at exit                        */
+    int32_t faults;          /* fault-convergence events (Sec. 3.3.2)         */
+    int32_t outer;           /* refinement steps (mixed precision)            */
+    int32_t inner_iters;     /* FP32 Arnoldi steps (mixed precision)          */
+    int32_t fallback;        /* 1: mixed solve finished in FP64               */
+    int32_t variant_used;    /* XB_VAR_* of the SpMV                          */
+    int32_t block_used;
+    int32_t ipt_used;
+    int32_t spmv_calls;      /* SpMV launches in the solve                    */
+    double res_implicit;     /* last implicit (recursive) relative residual   */
+    double res_true;         /* ||b - A x|| / ||b|| at exit, FP64             */
+    double t_solve_s;        /* host wall time of the solve                   */
+    double spmv_ms;          /* summed CUDA-event SpMV time (opt.timing)      */
+    double bytes_alg;        /* algorithmic bytes of all launches (see docs)  */
+} xb_info;
+
+typedef struct xb_plan xb_plan;
+
+typedef struct xb_choice {
+    int32_t variant, block, ipt;
+    float ms;                /* best measured time (exhaustive)               */
+} xb_choice;
+
+/* ---- setup -------------------------------------------------------------- */
+
+/* Fill *opt with the defaults listed in the struct comments (the paper's
+ * OpenATI_INIT: set default parameters, Table 1). */
+void xb_options_default(xb_options *opt);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *xb_last_error(void);
+
+/* Build a plan for A (the paper's *_Setup functions, Table 1): validates
+ * sizes, copies rowptr to the host once, and builds on the device the
+ * row-aligned nnz-balanced tile partition (U2/S2), the flat segment
+ * partition with per-CTA start rows (U3) and, for sym_upper, the per-tile
+ * non-zero region bounds (S3).  opt may be NULL (defaults).  The plan keeps
+ * A's pointers: A's arrays must outlive the plan and stay unmodified.
+ * XB_EINVAL: n < 0, nnz < 0, NULL arrays with n > 0, rowptr[0] != 0,
+ * rowptr[n] != nnz or rowptr decreasing.  Columns are checked
+ * (0 <= col < n, ascending, and col >= row when sym_upper) only when the
+ * environment variable XB_VALIDATE=1 is set. */
+int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out);
+int xb_plan_destroy(xb_plan *plan);
+
+/* Set the SpMV variant and launch shape used by XB_VAR_AUTO calls and by the
+ * solvers.  block in {64,128,256,512}; ipt in [1,32].  XB_EINVAL for a
+ * variant that does not fit the storage (sym variants need sym_upper=1,
+ * general variants sym_upper=0). */
+int xb_plan_set_choice(xb_plan *plan, int32_t variant, int32_t block, int32_t ipt);
+int xb_plan_get_choice(const xb_plan *plan, xb_choice *out);
+
+/* ---- SpMV entry points: y = alpha*A*x + beta*y ---------------------------
+ * x, y: device FP64 vectors of length n; y may not alias x.  beta == 0 means
+ * y is write-only (its old contents, even NaN, are ignored).  Stream-ordered,
+ * no host synchronisation. */
+
+/* General CRS SpMV, nnz-balanced row-aligned tiles (U2 of Sec. 3.2.2; the
+ * partition follows Fig. 3: rows grouped so each tile holds about the same
+ * number of non-zeros; a row is never split across tiles unless it alone
+ * exceeds a tile).  Deterministic.  XB_EINVAL if the plan is sym_upper. */
+int spmv_crs(xb_plan *plan, double alpha, const double *x, double beta, double *y, void *stream);
+
+/* Symmetric SpMV from upper storage: y = alpha*(U + U^T - diag U) x + beta*y
+ * (S1-S3 of Sec. 3.2.2).  Uses the plan's sym variant (XB_VAR_SYM_TILE unless
+ * set otherwise): transpose contributions that land inside the tile are summed
+ * in shared memory, only the non-zero region outside a tile goes through
+ * device atomics (so the result is not bitwise reproducible run to run; it
+ * agrees to rounding).  XB_EINVAL if the plan is not sym_upper. */
+int spmv_sym(xb_plan *plan, double alpha, const double *x, double beta, double *y, void *stream);
+
+/* General CRS SpMV by the branchless segmented-scan idea (U3/BSS, Sec. 3.2.2,
+ * Sec. 4.4.1.3): the non-zeros are split into equal flat segments regardless
+ * of row boundaries, each thread sums its segment with row breaks taken from
+ * the per-CTA start rows of the plan, and row sums that straddle threads or
+ * CTAs are combined by a segmented scan and a deterministic carry fix-up.
+ * Deterministic.  XB_EINVAL if the plan is sym_upper. */
+int spmv_segscan(xb_plan *plan, double alpha, const double *x, double beta, double *y, void *stream);
+
+/* Any variant (XB_VAR_*; XB_VAR_AUTO = plan choice) with an explicit launch
+ * shape (block/ipt 0 = plan choice). */
+int xb_spmv(xb_plan *plan, int32_t variant, int32_t block, int32_t ipt, double alpha,
+            const double *x, double beta, double *y, void *stream);
+
+/* FP32 SpMV on the plan's FP32 copy of A (made on first use, library-owned):
+ * y32 = alpha*A32*x32 + beta*y32 with FP32 accumulation (the inner operator
+ * of the mixed-precision refinement). */
+int xb_spmv_f32(xb_plan *plan, int32_t variant, float alpha, const float *x, float beta,
+                float *y, void *stream);
+
+/* ---- Krylov solvers -------------------------------------------------------
+ * b: device FP64 right-hand side; x: device FP64, in = initial guess,
+ * out = iterate.  opt NULL = defaults.  info may be NULL.  The solve ends
+ * when the TRUE residual ||b - A x|| / ||b|| <= opt->tol (checked in FP64
+ * after every claimed convergence: the fault-convergence test of Sec. 3.1 and
+ * 3.3.2, which narrows the implicit threshold and continues when the claim
+ * was false), or with XB_ENOCONV at maxiter / maxtime_s, or XB_EBREAKDOWN.
+ * b == 0 gives x = 0.  The host synchronises `stream` every
+ * opt->check_every steps to read the residual. */
+
+/* Restarted GMRES(m) (Sec. 2.2, Sec. 4.3) with MGS (or CGS2) Arnoldi and
+ * Givens least squares; opt->dafrt enables the MM-ratio restart rule of
+ * Eq. (1) / Fig. 2 / Sec. 4.3 (m += dafrt_dm, at most m_max).
+ * opt->precision == XB_PREC_MIXED runs FP32 GMRES(m) (FP32 SpMV and basis,
+ * FP64 Hessenberg/Givens/least squares) inside FP64 iterative refinement. */
+int gmres_solve(xb_plan *plan, const double *b, double *x, const xb_options *opt,
+                xb_info *info, void *stream);
+
+/* BiCGStab (Sec. 2.2, Sec. 4.3), unpreconditioned, two SpMVs per step. */
+int bicgstab_solve(xb_plan *plan, const double *b, double *x, const xb_options *opt,
+                   xb_info *info, void *stream);
+
+/* ---- Krylov vector operations (FP64, device) ------------------------------
+ * Deterministic two-stage reductions; `out` is a DEVICE pointer to one
+ * double.  n >= 0. */
+int xb_dot(xb_plan *plan, int32_t n, const double *x, const double *y, double *out, void *stream);
+int xb_axpy(int32_t n, double a, const double *x, double *y, void *stream); /* y += a x */
+/* One modified Gram-Schmidt sweep (Sec. 3.2.2, MGS): for i = 0..k-1,
+ * h[i] = (w, V_i); w -= h[i] V_i, with V row-major k x ld (ld >= n), then
+ * h[k] = ||w||.  h: device, k+1 doubles. */
+int xb_mgs(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, double *w,
+           double *h, void *stream);
+
+/* ---- run-time auto-tuning ------------------------------------------------ */
+
+/* Before-execution AT (Sec. 3.1): time every candidate (variant x CTA size x
+ * items per thread) that fits the plan's storage, each at most 4 times after
+ * one warm-up, with CUDA events on `stream`; keep the minimum.  Sets the
+ * plan's choice and returns it in *out (may be NULL). */
+int xb_tune_exhaustive(xb_plan *plan, xb_choice *out, void *stream);
+
+/* MM ratio of Eq. (1): R(s,t) = max / min of r(s-t+1..s), r 1-based on the
+ * HOST array r (r[z-1] = r(z)); 1 <= t <= s.  Returns +inf for a zero min. */
+double xb_mm_ratio(const double *r, int32_t s, int32_t t);
+/* OpenATI_DAFRT judgement: 1 if R(I, I) over samp[0..I-1] < theta, else 0. */
+int xb_dafrt(int32_t I, const double *samp, double theta);
+
+/* ---- learned tuner --------------------------------------------------------
+ * Matrix features on the device (host output): raw[7] = n, nnz, mean row
+ * length, population variance, max row length, bandwidth max|i-j|, symmetry
+ * (1 if sym_upper or the stored pattern and values equal their transpose);
+ * feat[8] = ln(1+n), ln(1+nnz), ln(1+mean), ln(1+var), ln(1+max),
+ * ln(1+bandwidth), sym, ln(1+max) - ln(1+mean).  Either output may be NULL. */
+int xb_features(const xb_csr *A, double *raw, float *feat, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XABC_H */

@@ -1,0 +1,297 @@
+"""Python binding of the GB300 CRS SpMV + restarted Krylov library.
+
+Argument marshalling only: every step runs in the CUDA library
+(``_build/libxabc.so``, built from ``csrc/`` by ``buildlib.py``).  Torch is used
+for device memory and the current stream.  There is no fallback: if the
+library is missing or no GPU is present, calls raise.
+
+Names follow the C ABI in ``include/xabc.h`` (spmv_crs, spmv_sym,
+spmv_segscan, gmres_solve, bicgstab_solve, xb_tune_exhaustive, ...).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libxabc.so")
+
+XB_OK, XB_EINVAL, XB_ENOMEM, XB_ECUDA, XB_ENOCONV, XB_EBREAKDOWN, XB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE = -1, 0, 1, 2, 3, 4
+VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile"}
+ORTHO_MGS, ORTHO_CGS2 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+TUNER_NONE, TUNER_EXHAUSTIVE, TUNER_MLP = 0, 1, 2
+
+
+class XbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"xabc error {code}: {msg}")
+        self.code = code
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("sym_upper", C.c_int32)]
+
+
+class Options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxiter", C.c_int32), ("maxtime_s", C.c_double),
+                ("m", C.c_int32), ("m_max", C.c_int32), ("dafrt", C.c_int32),
+                ("dafrt_theta", C.c_double), ("dafrt_window", C.c_int32),
+                ("dafrt_dm", C.c_int32), ("ortho", C.c_int32), ("precision", C.c_int32),
+                ("tol_inner", C.c_double), ("maxiter_inner", C.c_int32),
+                ("max_outer", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
+                ("ipt", C.c_int32), ("tuner", C.c_int32), ("check_every", C.c_int32),
+                ("timing", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("status", "iters", "restarts", "m_final", "faults",
+                                         "outer", "inner_iters", "fallback", "variant_used",
+                                         "block_used", "ipt_used", "spmv_calls")] + \
+               [(k, C.c_double) for k in ("res_implicit", "res_true", "t_solve_s", "spmv_ms",
+                                          "bytes_alg")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Choice(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("block", C.c_int32), ("ipt", C.c_int32),
+                ("ms", C.c_float)]
+
+
+_lib = None
+
+
+def build(force=False):
+    """Compile the CUDA library in-tree (nvcc, sm_103a) if missing or stale."""
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, f64, f32 = C.c_void_p, C.c_int32, C.c_double, C.c_float
+    P = C.POINTER
+    sig = {
+        "xb_options_default": (None, [P(Options)]),
+        "xb_last_error": (C.c_char_p, []),
+        "xb_plan_create": (i32, [P(Csr), P(Options), vp, P(vp)]),
+        "xb_plan_destroy": (i32, [vp]),
+        "xb_plan_set_choice": (i32, [vp, i32, i32, i32]),
+        "xb_plan_get_choice": (i32, [vp, P(Choice)]),
+        "spmv_crs": (i32, [vp, f64, vp, f64, vp, vp]),
+        "spmv_sym": (i32, [vp, f64, vp, f64, vp, vp]),
+        "spmv_segscan": (i32, [vp, f64, vp, f64, vp, vp]),
+        "xb_spmv": (i32, [vp, i32, i32, i32, f64, vp, f64, vp, vp]),
+        "xb_spmv_f32": (i32, [vp, i32, f32, vp, f32, vp, vp]),
+        "gmres_solve": (i32, [vp, vp, vp, P(Options), P(Info), vp]),
+        "bicgstab_solve": (i32, [vp, vp, vp, P(Options), P(Info), vp]),
+        "xb_dot": (i32, [vp, i32, vp, vp, vp, vp]),
+        "xb_axpy": (i32, [i32, f64, vp, vp, vp]),
+        "xb_mgs": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, vp]),
+        "xb_tune_exhaustive": (i32, [vp, P(Choice), vp]),
+        "xb_mm_ratio": (f64, [P(f64), i32, i32]),
+        "xb_dafrt": (i32, [i32, P(f64), f64]),
+        "xb_features": (i32, [P(Csr), P(f64), P(f32), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def last_error():
+    return lib().xb_last_error().decode()
+
+
+def _check(code, ok=(XB_OK,)):
+    if code not in ok:
+        raise XbError(code, last_error())
+    return code
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _need(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor (got {t.dtype})")
+
+
+def default_options(**kw):
+    o = Options()
+    lib().xb_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """A matrix in CRS on the device plus the library's setup data."""
+
+    def __init__(self, rowptr, col, val, sym_upper=False, stream=None):
+        import torch
+        _need(rowptr, torch.int32, "rowptr")
+        _need(col, torch.int32, "col")
+        _need(val, torch.float64, "val")
+        self.n = rowptr.numel() - 1
+        self.nnz = col.numel()
+        self.sym_upper = bool(sym_upper)
+        self._keep = (rowptr, col, val)
+        self._csr = Csr(self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val), int(sym_upper))
+        h = C.c_void_p()
+        _check(lib().xb_plan_create(C.byref(self._csr), None, _stream(stream), C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        import torch
+        return cls(torch.as_tensor(A["rowptr"], dtype=torch.int32, device=device),
+                   torch.as_tensor(A["col"], dtype=torch.int32, device=device),
+                   torch.as_tensor(A["val"], dtype=torch.float64, device=device),
+                   sym_upper=A.get("sym_upper", False))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xb_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- SpMV ----
+    def _vec(self, x, y):
+        import torch
+        _need(x, torch.float64, "x")
+        _need(y, torch.float64, "y")
+        if x.numel() != self.n or y.numel() != self.n:
+            raise ValueError("vector length != n")
+
+    def spmv_crs(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        self._vec(x, y)
+        _check(lib().spmv_crs(self._h, alpha, _ptr(x), beta, _ptr(y), _stream(stream)))
+        return y
+
+    def spmv_sym(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        self._vec(x, y)
+        _check(lib().spmv_sym(self._h, alpha, _ptr(x), beta, _ptr(y), _stream(stream)))
+        return y
+
+    def spmv_segscan(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        self._vec(x, y)
+        _check(lib().spmv_segscan(self._h, alpha, _ptr(x), beta, _ptr(y), _stream(stream)))
+        return y
+
+    def spmv(self, x, y, alpha=1.0, beta=0.0, variant=VAR_AUTO, block=0, ipt=0, stream=None):
+        self._vec(x, y)
+        _check(lib().xb_spmv(self._h, variant, block, ipt, alpha, _ptr(x), beta, _ptr(y),
+                             _stream(stream)))
+        return y
+
+    def spmv_f32(self, x, y, alpha=1.0, beta=0.0, variant=VAR_AUTO, stream=None):
+        import torch
+        _need(x, torch.float32, "x")
+        _need(y, torch.float32, "y")
+        _check(lib().xb_spmv_f32(self._h, variant, alpha, _ptr(x), beta, _ptr(y), _stream(stream)))
+        return y
+
+    # ---- solvers ----
+    def _solve(self, fn, b, x, opts, stream):
+        import torch
+        _need(b, torch.float64, "b")
+        _need(x, torch.float64, "x")
+        o = opts if isinstance(opts, Options) else default_options(**(opts or {}))
+        info = Info()
+        code = fn(self._h, _ptr(b), _ptr(x), C.byref(o), C.byref(info), _stream(stream))
+        d = info.as_dict()
+        d["status"] = code
+        d["error"] = last_error() if code != XB_OK else ""
+        if code in (XB_EINVAL, XB_ENOMEM, XB_ECUDA):
+            raise XbError(code, d["error"])
+        return d
+
+    def gmres(self, b, x, stream=None, **opts):
+        return self._solve(lib().gmres_solve, b, x, opts, stream)
+
+    def bicgstab(self, b, x, stream=None, **opts):
+        return self._solve(lib().bicgstab_solve, b, x, opts, stream)
+
+    # ---- tuning ----
+    def tune(self, stream=None):
+        c = Choice()
+        _check(lib().xb_tune_exhaustive(self._h, C.byref(c), _stream(stream)))
+        return dict(variant=c.variant, block=c.block, ipt=c.ipt, ms=c.ms)
+
+    def set_choice(self, variant, block=256, ipt=8):
+        _check(lib().xb_plan_set_choice(self._h, variant, block, ipt))
+
+    def choice(self):
+        c = Choice()
+        _check(lib().xb_plan_get_choice(self._h, C.byref(c)))
+        return dict(variant=c.variant, block=c.block, ipt=c.ipt, ms=c.ms)
+
+    # ---- vector ops ----
+    def dot(self, x, y, stream=None):
+        import torch
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+        _check(lib().xb_dot(self._h, x.numel(), _ptr(x), _ptr(y), _ptr(out), _stream(stream)))
+        return out
+
+    def mgs(self, V, w, stream=None):
+        """One MGS sweep of w against the k rows of V; returns h (k+1)."""
+        import torch
+        k, ld = V.shape
+        h = torch.empty(k + 1, dtype=torch.float64, device=V.device)
+        _check(lib().xb_mgs(self._h, w.numel(), k, _ptr(V), ld, _ptr(w), _ptr(h),
+                            _stream(stream)))
+        return h
+
+
+def axpy(a, x, y, stream=None):
+    _check(lib().xb_axpy(x.numel(), a, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def features(rowptr, col, val, sym_upper=False, stream=None):
+    import numpy as np
+    csr = Csr(rowptr.numel() - 1, col.numel(), _ptr(rowptr), _ptr(col), _ptr(val), int(sym_upper))
+    raw = (C.c_double * 7)()
+    feat = (C.c_float * 8)()
+    _check(lib().xb_features(C.byref(csr), raw, feat, _stream(stream)))
+    return np.array(raw[:]), np.array(feat[:], dtype=np.float32)
+
+
+def mm_ratio(r, s, t):
+    arr = (C.c_double * len(r))(*r)
+    return lib().xb_mm_ratio(arr, s, t)
+
+
+def dafrt(samp, theta):
+    arr = (C.c_double * len(samp))(*samp)
+    return lib().xb_dafrt(len(samp), arr, theta)

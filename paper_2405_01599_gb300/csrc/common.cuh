@@ -1,0 +1,143 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/xabc.h"
+
+namespace xb {
+
+// ---- error handling -------------------------------------------------------
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *where);
+
+#define XB_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return ::xb::cuda_error(e__, #call);   \
+    } while (0)
+#define XB_LAUNCHED(where)                                             \
+    do {                                                               \
+        cudaError_t e__ = cudaGetLastError();                          \
+        if (e__ != cudaSuccess) return ::xb::cuda_error(e__, where);    \
+    } while (0)
+#define XB_TRY(...)                                                    \
+    do {                                                               \
+        int r__ = (__VA_ARGS__);                                       \
+        if (r__ != XB_OK) return r__;                                  \
+    } while (0)
+
+// ---- device constants ------------------------------------------------------
+constexpr int kRedSlots = 1024;     // max CTAs of a reduction grid
+constexpr int kScalars = 4096;      // device scalar scratch per plan (doubles)
+
+int num_sms();                      // cached cudaDevAttrMultiProcessorCount
+int reduce_grid(int64_t n, int block);  // CTAs for a streaming reduction
+
+// ---- partitions -------------------------------------------------------------
+// Row-aligned nnz-balanced tiles (U2 / S2): tile t covers rows
+// [row[t], row[t+1]); at most T = block*ipt non-zeros and `block` rows, except
+// a single row longer than T which forms a tile of its own.
+struct TilePart {
+    int block = 0, ipt = 0;
+    int ntiles = 0;
+    int *d_row = nullptr;    // ntiles+1
+};
+// Flat nnz segments (U3): CTA b covers non-zeros [b*T, (b+1)*T); d_row[b] is
+// the row holding non-zero b*T (d_row[nblk] = n); carries feed the fix-up.
+struct SegPart {
+    int block = 0, ipt = 0;
+    int nblk = 0;
+    int *d_row = nullptr;    // nblk+1
+    int *d_carry_row = nullptr;
+    double *d_carry_val = nullptr;   // raw partial sums (float in FP32 use)
+};
+
+}  // namespace xb
+
+struct xb_plan {
+    int n = 0, nnz = 0, sym = 0;
+    const int *rowptr = nullptr, *col = nullptr;
+    const double *val = nullptr;
+    float *val32 = nullptr;              // FP32 copy (mixed precision)
+    std::vector<int> h_rowptr;           // host copy, used to build partitions
+    int max_row = 0;
+    int n_empty = 0;
+    int *d_empty = nullptr;              // rows with no stored entry
+    std::vector<xb::TilePart> tiles;     // cache by (block, ipt)
+    std::vector<xb::SegPart> segs;       // cache by (block, ipt)
+    // reduction scratch
+    double *d_part = nullptr;            // kRedSlots * 4 partials
+    unsigned *d_ticket = nullptr;        // 8 counters
+    double *d_scal = nullptr;            // kScalars
+    // solver workspace (grown on demand)
+    void *d_work = nullptr;
+    size_t work_bytes = 0;
+    double *h_pin = nullptr;             // pinned host mirror of a few scalars
+    // tuned choice
+    int variant = XB_VAR_NNZ, block = 256, ipt = 8;
+    float tuned_ms = 0.f;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace xb {
+
+const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
+const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
+int ensure_val32(xb_plan *p, cudaStream_t s);
+int ensure_work(xb_plan *p, size_t bytes);
+bool variant_fits(const xb_plan *p, int variant);
+
+// SpMV dispatch: y = alpha*A*x + beta*y in value type double or float.
+int spmv_launch(xb_plan *p, int variant, int block, int ipt, double alpha, const double *x,
+                double beta, double *y, cudaStream_t s);
+int spmv_launch_f32(xb_plan *p, int variant, int block, int ipt, float alpha, const float *x,
+                    float beta, float *y, cudaStream_t s);
+// Algorithmic bytes of one SpMV (val+col once, rowptr once, x once, y once,
+// y read again when beta != 0).
+double spmv_alg_bytes(const xb_plan *p, bool beta_nonzero, int val_bytes);
+
+// ---- vector kernels (vec.cu) ------------------------------------------------
+// Deterministic reductions write their result to a device double.
+int vdot(xb_plan *p, int64_t n, const double *x, const double *y, double *out, cudaStream_t s);
+int vnrm2(xb_plan *p, int64_t n, const double *x, double *out, cudaStream_t s);
+int vaxpy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
+int vcopy(int64_t n, const double *x, double *y, cudaStream_t s);
+int vscale(int64_t n, double a, double *x, cudaStream_t s);
+int vfill(int64_t n, double a, double *x, cudaStream_t s);
+
+}  // namespace xb
+
+// ---- device helpers ----------------------------------------------------------
+namespace xbd {
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; result valid in thread 0.  `sh` holds >= 32 V.
+template <typename V>
+__device__ __forceinline__ V block_sum(V v, V *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        v = lane < nw ? sh[lane] : V(0);
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+}  // namespace xbd

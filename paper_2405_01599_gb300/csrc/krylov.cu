@@ -1,0 +1,508 @@
+// Krylov vector kernels: deterministic two-stage reductions (per-CTA partials,
+// the last CTA to finish reduces them in a fixed order, so no extra launch and
+// no run-to-run variation), the fused modified Gram-Schmidt step of Arnoldi
+// (Sec. 3.2.2, MGS) with the Givens update folded into its final CTA, and the
+// fused BiCGStab updates.  Scalars never leave the device inside a step.
+#include "krylov.cuh"
+
+#include <cmath>
+
+namespace {
+
+constexpr int kVB = 256;  // block size of all streaming vector kernels
+
+// Reduce NV per-thread values over the grid.  Returns true in every thread of
+// the last CTA to finish; tot[] is then valid in thread 0 of that CTA.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *__restrict__ part,
+                                            unsigned *__restrict__ ticket, double (&tot)[NV]) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const int G = gridDim.x;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const double b = xbd::block_sum(v[k], sh);
+        if (threadIdx.x == 0) part[k * G + blockIdx.x] = b;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == (unsigned)G - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < G; i += blockDim.x) a += __ldcg(part + k * G + i);
+        tot[k] = xbd::block_sum(a, sh);
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+__device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// ---- plain vector ops --------------------------------------------------------
+
+__global__ void k_dot(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                      double *__restrict__ part, unsigned *__restrict__ ticket,
+                      double *__restrict__ out, int sq) {
+    double v[1] = {0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) v[0] = fma(x[i], y[i], v[0]);
+    double t[1];
+    if (grid_reduce<1>(v, part, ticket, t) && threadIdx.x == 0) *out = sq ? sqrt(t[0]) : t[0];
+}
+
+__global__ void k_axpy(int64_t n, double a, const double *__restrict__ x, double *__restrict__ y) {
+    for (int64_t i = gtid(); i < n; i += gstride()) y[i] = fma(a, x[i], y[i]);
+}
+__global__ void k_copy(int64_t n, const double *__restrict__ x, double *__restrict__ y) {
+    for (int64_t i = gtid(); i < n; i += gstride()) y[i] = x[i];
+}
+__global__ void k_scale(int64_t n, double a, double *__restrict__ x) {
+    for (int64_t i = gtid(); i < n; i += gstride()) x[i] *= a;
+}
+__global__ void k_fill(int64_t n, double a, double *__restrict__ x) {
+    for (int64_t i = gtid(); i < n; i += gstride()) x[i] = a;
+}
+
+int stream_grid(int64_t n) {
+    int64_t want = (n + kVB - 1) / kVB;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)xb::num_sms() * 16));
+}
+
+// ---- GMRES ----------------------------------------------------------------------
+
+// ||r0|| -> start a cycle: g = (beta, 0, ...), sc[0] = 1/beta.
+template <typename VB>
+__global__ void k_gm_init(int64_t n, const VB *__restrict__ r0, xb::GmDev st, double tau,
+                          double *__restrict__ part, unsigned *__restrict__ ticket) {
+    double v[1] = {0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const double a = (double)r0[i];
+        v[0] = fma(a, a, v[0]);
+    }
+    double t[1];
+    if (grid_reduce<1>(v, part, ticket, t)) {
+        for (int i = threadIdx.x; i <= st.M; i += blockDim.x) st.g[i] = 0.0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(t[0]);
+            st.g[0] = beta;
+            st.sc[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+            st.scf[0] = (float)st.sc[0];
+            st.misc[xb::GM_BETA] = beta;
+            const double bn = st.misc[xb::GM_BNORM];
+            st.misc[xb::GM_RES] = bn > 0.0 ? beta / bn : 0.0;
+            st.misc[xb::GM_K] = 0.0;
+            st.misc[xb::GM_STOP] = 0.0;
+            st.misc[xb::GM_TAU] = tau;
+            st.misc[xb::GM_LEN2] = 0.0;
+            st.misc[xb::GM_RAW] = 0.0;
+        }
+    }
+}
+
+// Givens update of column j after h_{j+1,j} = hn (single thread).
+__device__ void gm_givens(xb::GmDev st, int j, double hn) {
+    double *col = st.H + (size_t)j * (st.M + 1);
+    col[j + 1] = hn;
+    const double len2 = st.misc[xb::GM_LEN2] + hn * hn;
+    for (int i = 0; i < j; i++) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = st.cs[i] * a + st.sn[i] * b;
+        col[i + 1] = -st.sn[i] * a + st.cs[i] * b;
+    }
+    const double a = col[j];
+    const double rr = hypot(a, hn);
+    if (rr == 0.0) {  // A v_j lies in span(v_0..v_{j-1}) with a zero pivot: singular
+        st.misc[xb::GM_STOP] = 2.0;
+        return;
+    }
+    st.cs[j] = a / rr;
+    st.sn[j] = hn / rr;
+    col[j] = rr;
+    col[j + 1] = 0.0;
+    st.g[j + 1] = -st.sn[j] * st.g[j];
+    st.g[j] = st.cs[j] * st.g[j];
+    const double bn = st.misc[xb::GM_BNORM];
+    const double res = fabs(st.g[j + 1]) / bn;
+    st.misc[xb::GM_RES] = res;
+    st.misc[xb::GM_K] = (double)(j + 1);
+    if (hn <= 1e-14 * sqrt(len2)) {  // happy breakdown: the Krylov space is invariant
+        st.misc[xb::GM_STOP] = 1.0;
+        st.sc[j + 1] = 0.0;
+        st.scf[j + 1] = 0.0f;
+        return;
+    }
+    st.sc[j + 1] = 1.0 / hn;
+    st.scf[j + 1] = (float)(1.0 / hn);
+    if (res <= st.misc[xb::GM_TAU]) st.misc[xb::GM_STOP] = 1.0;
+}
+
+// One launch of the MGS sweep of Arnoldi step j:
+//   i == 0      : h_0j = (w, v_0)
+//   0 < i <= j  : w -= h_{i-1,j} v_{i-1};  h_ij = (w, v_i)
+//   i == j+1    : w -= h_jj v_j;  h_{j+1,j} = ||w||, then Givens.
+// Basis vectors are stored unnormalised with scales sc (v_i = sc[i]*V_i).
+template <typename VB>
+__global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
+                                             const VB *__restrict__ vprev,
+                                             const VB *__restrict__ vnext, xb::GmDev st, int j,
+                                             int i, double *__restrict__ part,
+                                             unsigned *__restrict__ ticket) {
+    if (st.misc[xb::GM_STOP] != 0.0) return;
+    const double cd = vprev ? st.misc[xb::GM_COEF] : 0.0;
+    const VB c = (VB)cd;
+    VB acc = VB(0);
+    if (vprev && vnext) {
+        for (int64_t e = gtid(); e < n; e += gstride()) {
+            const VB a = fma(-c, vprev[e], w[e]);
+            w[e] = a;
+            acc = fma(a, vnext[e], acc);
+        }
+    } else if (vprev) {
+        for (int64_t e = gtid(); e < n; e += gstride()) {
+            const VB a = fma(-c, vprev[e], w[e]);
+            w[e] = a;
+            acc = fma(a, a, acc);
+        }
+    } else {
+        for (int64_t e = gtid(); e < n; e += gstride()) acc = fma(w[e], vnext[e], acc);
+    }
+    double v[1] = {(double)acc};
+    double t[1];
+    if (grid_reduce<1>(v, part, ticket, t) && threadIdx.x == 0) {
+        if (vnext) {
+            const double h = st.sc[i] * t[0];
+            st.H[(size_t)j * (st.M + 1) + i] = h;
+            st.misc[xb::GM_COEF] = st.sc[i] * h;
+            st.misc[xb::GM_LEN2] = (i == 0 ? 0.0 : st.misc[xb::GM_LEN2]) + h * h;
+        } else if (st.misc[xb::GM_RAW] != 0.0) {
+            st.H[(size_t)j * (st.M + 1) + j + 1] = sqrt(t[0]);
+        } else {
+            gm_givens(st, j, sqrt(t[0]));
+        }
+    }
+}
+
+// Least squares R y = g (upper triangular k x k), then y_i *= sc[i].
+__global__ void k_gm_solve(xb::GmDev st) {
+    if (threadIdx.x != 0) return;
+    const int k = (int)st.misc[xb::GM_K];
+    for (int i = k - 1; i >= 0; i--) {
+        double s = st.g[i];
+        for (int q = i + 1; q < k; q++) s -= st.H[(size_t)q * (st.M + 1) + i] * st.y[q];
+        st.y[i] = s / st.H[(size_t)i * (st.M + 1) + i];
+    }
+    for (int i = 0; i < k; i++) st.y[i] *= st.sc[i];
+}
+
+// x += sum_i y_i V_i (each basis vector read once).
+template <typename VB, typename VX>
+__global__ void __launch_bounds__(kVB) k_gm_xupd(int64_t n, const VB *__restrict__ V, int64_t ld,
+                                                 xb::GmDev st, VX *__restrict__ x) {
+    __shared__ double ys[512];
+    const int k = (int)st.misc[xb::GM_K];
+    for (int i = threadIdx.x; i < k && i < 512; i += blockDim.x) ys[i] = st.y[i];
+    __syncthreads();
+    for (int64_t e = gtid(); e < n; e += gstride()) {
+        VX s = VX(0);
+        for (int i = 0; i < k; i++) s = fma((VX)ys[i], (VX)V[(size_t)i * ld + e], s);
+        x[e] += s;
+    }
+}
+
+// ---- BiCGStab ------------------------------------------------------------------
+
+// rho = (rhat, r) with rhat = r at a (re)start; alpha = omega = rho_old = 1.
+__global__ void k_bi_init(int64_t n, const double *__restrict__ r, double *__restrict__ sc,
+                          double tau2, double *__restrict__ part, unsigned *__restrict__ ticket) {
+    double v[1] = {0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) v[0] = fma(r[i], r[i], v[0]);
+    double t[1];
+    if (grid_reduce<1>(v, part, ticket, t) && threadIdx.x == 0) {
+        sc[xb::BI_RHO] = t[0];
+        sc[xb::BI_RHO_OLD] = 1.0;
+        sc[xb::BI_ALPHA] = 1.0;
+        sc[xb::BI_OMEGA] = 1.0;
+        sc[xb::BI_RNORM2] = t[0];
+        sc[xb::BI_SNORM2] = INFINITY;
+        sc[xb::BI_FLAG] = 0.0;
+        sc[xb::BI_TAU2] = tau2;
+    }
+}
+
+// p = r + beta (p - omega v), beta = (rho/rho_old)(alpha/omega).
+__global__ void k_bi_p(int64_t n, const double *__restrict__ sc, const double *__restrict__ r,
+                       double *__restrict__ p, const double *__restrict__ v) {
+    if (sc[xb::BI_FLAG] != 0.0) return;
+    const double beta = (sc[xb::BI_RHO] / sc[xb::BI_RHO_OLD]) * (sc[xb::BI_ALPHA] / sc[xb::BI_OMEGA]);
+    const double om = sc[xb::BI_OMEGA];
+    for (int64_t i = gtid(); i < n; i += gstride()) p[i] = fma(beta, fma(-om, v[i], p[i]), r[i]);
+}
+
+// sigma = (rhat, v); alpha = rho / sigma.
+__global__ void k_bi_sigma(int64_t n, double *__restrict__ sc, const double *__restrict__ rh,
+                           const double *__restrict__ v, double *__restrict__ part,
+                           unsigned *__restrict__ ticket) {
+    if (sc[xb::BI_FLAG] != 0.0) return;
+    double a[1] = {0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) a[0] = fma(rh[i], v[i], a[0]);
+    double t[1];
+    if (grid_reduce<1>(a, part, ticket, t) && threadIdx.x == 0) {
+        if (t[0] == 0.0) sc[xb::BI_FLAG] = 3.0;
+        else sc[xb::BI_ALPHA] = sc[xb::BI_RHO] / t[0];
+    }
+}
+
+// s = r - alpha v, ||s||^2.
+__global__ void k_bi_s(int64_t n, double *__restrict__ sc, const double *__restrict__ r,
+                       const double *__restrict__ v, double *__restrict__ s,
+                       double *__restrict__ part, unsigned *__restrict__ ticket) {
+    if (sc[xb::BI_FLAG] != 0.0) return;
+    const double al = sc[xb::BI_ALPHA];
+    double a[1] = {0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const double si = fma(-al, v[i], r[i]);
+        s[i] = si;
+        a[0] = fma(si, si, a[0]);
+    }
+    double t[1];
+    if (grid_reduce<1>(a, part, ticket, t) && threadIdx.x == 0) sc[xb::BI_SNORM2] = t[0];
+}
+
+// omega = (t, s) / (t, t).
+__global__ void k_bi_omega(int64_t n, double *__restrict__ sc, const double *__restrict__ t,
+                           const double *__restrict__ s, double *__restrict__ part,
+                           unsigned *__restrict__ ticket) {
+    if (sc[xb::BI_FLAG] != 0.0) return;
+    double a[2] = {0.0, 0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        a[0] = fma(t[i], s[i], a[0]);
+        a[1] = fma(t[i], t[i], a[1]);
+    }
+    double tt[2];
+    if (grid_reduce<2>(a, part, ticket, tt) && threadIdx.x == 0) {
+        if (sc[xb::BI_SNORM2] <= sc[xb::BI_TAU2]) return;  // s already converged
+        if (tt[1] == 0.0) sc[xb::BI_FLAG] = 4.0;
+        else sc[xb::BI_OMEGA] = tt[0] / tt[1];
+    }
+}
+
+// x += alpha p + omega s;  r = s - omega t;  ||r||^2, rho_next = (rhat, r).
+// When ||s|| already met the threshold: x += alpha p only, flag = 1 (done).
+__global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__ x,
+                        const double *__restrict__ p, const double *__restrict__ s,
+                        const double *__restrict__ t, double *__restrict__ r,
+                        const double *__restrict__ rh, double *__restrict__ part,
+                        unsigned *__restrict__ ticket) {
+    if (sc[xb::BI_FLAG] != 0.0) return;
+    const double al = sc[xb::BI_ALPHA];
+    if (sc[xb::BI_SNORM2] <= sc[xb::BI_TAU2]) {
+        for (int64_t i = gtid(); i < n; i += gstride()) x[i] = fma(al, p[i], x[i]);
+        double a[1] = {0.0}, tt[1];
+        if (grid_reduce<1>(a, part, ticket, tt) && threadIdx.x == 0) {
+            sc[xb::BI_RNORM2] = sc[xb::BI_SNORM2];
+            sc[xb::BI_FLAG] = 1.0;
+        }
+        return;
+    }
+    const double om = sc[xb::BI_OMEGA];
+    double a[2] = {0.0, 0.0};
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const double si = s[i];
+        x[i] = fma(om, si, fma(al, p[i], x[i]));
+        const double ri = fma(-om, t[i], si);
+        r[i] = ri;
+        a[0] = fma(ri, ri, a[0]);
+        a[1] = fma(rh[i], ri, a[1]);
+    }
+    double tt[2];
+    if (grid_reduce<2>(a, part, ticket, tt) && threadIdx.x == 0) {
+        sc[xb::BI_RNORM2] = tt[0];
+        sc[xb::BI_RHO_OLD] = sc[xb::BI_RHO];
+        sc[xb::BI_RHO] = tt[1];
+        if (tt[0] <= sc[xb::BI_TAU2]) sc[xb::BI_FLAG] = 1.0;
+        else if (tt[1] == 0.0) sc[xb::BI_FLAG] = 2.0;
+        else if (om == 0.0) sc[xb::BI_FLAG] = 5.0;
+    }
+}
+
+// ---- mixed precision helpers ------------------------------------------------------
+
+__global__ void k_cast_scaled(int64_t n, const double *__restrict__ a,
+                              const double *__restrict__ scale, float *__restrict__ b) {
+    const double s = *scale;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int64_t i = gtid(); i < n; i += gstride()) b[i] = (float)(a[i] * inv);
+}
+
+__global__ void k_add_scaled(int64_t n, double *__restrict__ x, const double *__restrict__ scale,
+                             const float *__restrict__ d) {
+    const double s = *scale;
+    for (int64_t i = gtid(); i < n; i += gstride()) x[i] = fma(s, (double)d[i], x[i]);
+}
+
+}  // namespace
+
+namespace xb {
+
+GmDev gm_layout(double *base, int M) {
+    GmDev st;
+    st.M = M;
+    double *q = base;
+    st.H = q; q += (size_t)(M + 1) * M;
+    st.cs = q; q += M;
+    st.sn = q; q += M;
+    st.g = q; q += M + 1;
+    st.sc = q; q += M + 1;
+    st.y = q; q += M;
+    st.misc = q; q += GM_NMISC;
+    st.scf = reinterpret_cast<float *>(q);
+    return st;
+}
+
+int vdot(xb_plan *p, int64_t n, const double *x, const double *y, double *out, cudaStream_t s) {
+    const int g = reduce_grid(n, kVB);
+    k_dot<<<g, kVB, 0, s>>>(n, x, y, p->d_part, p->d_ticket, out, 0);
+    XB_LAUNCHED("k_dot");
+    return XB_OK;
+}
+int vnrm2(xb_plan *p, int64_t n, const double *x, double *out, cudaStream_t s) {
+    const int g = reduce_grid(n, kVB);
+    k_dot<<<g, kVB, 0, s>>>(n, x, x, p->d_part, p->d_ticket, out, 1);
+    XB_LAUNCHED("k_nrm2");
+    return XB_OK;
+}
+int vaxpy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
+    if (n <= 0) return XB_OK;
+    k_axpy<<<stream_grid(n), kVB, 0, s>>>(n, a, x, y);
+    XB_LAUNCHED("k_axpy");
+    return XB_OK;
+}
+int vcopy(int64_t n, const double *x, double *y, cudaStream_t s) {
+    if (n <= 0) return XB_OK;
+    k_copy<<<stream_grid(n), kVB, 0, s>>>(n, x, y);
+    XB_LAUNCHED("k_copy");
+    return XB_OK;
+}
+int vscale(int64_t n, double a, double *x, cudaStream_t s) {
+    if (n <= 0) return XB_OK;
+    k_scale<<<stream_grid(n), kVB, 0, s>>>(n, a, x);
+    XB_LAUNCHED("k_scale");
+    return XB_OK;
+}
+int vfill(int64_t n, double a, double *x, cudaStream_t s) {
+    if (n <= 0) return XB_OK;
+    k_fill<<<stream_grid(n), kVB, 0, s>>>(n, a, x);
+    XB_LAUNCHED("k_fill");
+    return XB_OK;
+}
+
+int gm_cycle_init(xb_plan *p, GmDev st, int64_t n, const double *r0, double tau, cudaStream_t s) {
+    k_gm_init<double><<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r0, st, tau, p->d_part, p->d_ticket);
+    XB_LAUNCHED("k_gm_init");
+    return XB_OK;
+}
+int gm_cycle_init_f32(xb_plan *p, GmDev st, int64_t n, const float *r0, double tau,
+                      cudaStream_t s) {
+    k_gm_init<float><<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r0, st, tau, p->d_part, p->d_ticket);
+    XB_LAUNCHED("k_gm_init_f32");
+    return XB_OK;
+}
+
+template <typename VB>
+int gm_mgs_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
+                cudaStream_t s) {
+    const int g = reduce_grid(n, kVB);
+    for (int i = 0; i <= j + 1; i++) {
+        const VB *vprev = i > 0 ? V + (size_t)(i - 1) * ld : nullptr;
+        const VB *vnext = i <= j ? V + (size_t)i * ld : nullptr;
+        k_mgs<VB><<<g, kVB, 0, s>>>(n, w, vprev, vnext, st, j, i, p->d_part, p->d_ticket);
+    }
+    XB_LAUNCHED("k_mgs");
+    return XB_OK;
+}
+template int gm_mgs_step<double>(xb_plan *, GmDev, int64_t, const double *, int64_t, double *,
+                                  int, cudaStream_t);
+template int gm_mgs_step<float>(xb_plan *, GmDev, int64_t, const float *, int64_t, float *, int,
+                                 cudaStream_t);
+
+template <typename VB, typename VX>
+int gm_update(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, int k, VX *x,
+              cudaStream_t s) {
+    (void)p;
+    (void)k;
+    k_gm_solve<<<1, 32, 0, s>>>(st);
+    XB_LAUNCHED("k_gm_solve");
+    k_gm_xupd<VB, VX><<<stream_grid(n), kVB, 0, s>>>(n, V, ld, st, x);
+    XB_LAUNCHED("k_gm_xupd");
+    return XB_OK;
+}
+template int gm_update<double, double>(xb_plan *, GmDev, int64_t, const double *, int64_t, int,
+                                       double *, cudaStream_t);
+template int gm_update<float, float>(xb_plan *, GmDev, int64_t, const float *, int64_t, int,
+                                     float *, cudaStream_t);
+
+int bi_init(xb_plan *p, double *scal, int64_t n, const double *r, double tau2, cudaStream_t s) {
+    k_bi_init<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r, scal, tau2, p->d_part, p->d_ticket);
+    XB_LAUNCHED("k_bi_init");
+    return XB_OK;
+}
+int bi_p_update(double *scal, int64_t n, const double *r, double *pv, const double *v,
+                cudaStream_t s) {
+    k_bi_p<<<stream_grid(n), kVB, 0, s>>>(n, scal, r, pv, v);
+    XB_LAUNCHED("k_bi_p");
+    return XB_OK;
+}
+int bi_sigma(xb_plan *p, double *scal, int64_t n, const double *rh, const double *v,
+             cudaStream_t s) {
+    k_bi_sigma<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, rh, v, p->d_part, p->d_ticket);
+    XB_LAUNCHED("k_bi_sigma");
+    return XB_OK;
+}
+int bi_s_update(xb_plan *p, double *scal, int64_t n, const double *r, const double *v, double *sv,
+                cudaStream_t s) {
+    k_bi_s<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, r, v, sv, p->d_part, p->d_ticket);
+    XB_LAUNCHED("k_bi_s");
+    return XB_OK;
+}
+int bi_omega(xb_plan *p, double *scal, int64_t n, const double *t, const double *sv,
+             cudaStream_t s) {
+    k_bi_omega<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, t, sv, p->d_part, p->d_ticket);
+    XB_LAUNCHED("k_bi_omega");
+    return XB_OK;
+}
+int bi_xr_update(xb_plan *p, double *scal, int64_t n, double *x, const double *pv,
+                 const double *sv, const double *t, double *r, const double *rh, cudaStream_t s) {
+    k_bi_xr<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, x, pv, sv, t, r, rh, p->d_part,
+                                                p->d_ticket);
+    XB_LAUNCHED("k_bi_xr");
+    return XB_OK;
+}
+
+// r = b - A x
+int residual(xb_plan *p, const double *b, const double *x, double *r, cudaStream_t s) {
+    XB_TRY(vcopy(p->n, b, r, s));
+    return spmv_launch(p, XB_VAR_AUTO, 0, 0, -1.0, x, 1.0, r, s);
+}
+
+int cast_f64_to_f32_scaled(int64_t n, const double *a, const double *scale_dev, float *b,
+                           cudaStream_t s) {
+    if (n <= 0) return XB_OK;
+    k_cast_scaled<<<stream_grid(n), kVB, 0, s>>>(n, a, scale_dev, b);
+    XB_LAUNCHED("k_cast_scaled");
+    return XB_OK;
+}
+
+int add_scaled_f32(int64_t n, double *x, const double *scale_dev, const float *d, cudaStream_t s) {
+    if (n <= 0) return XB_OK;
+    k_add_scaled<<<stream_grid(n), kVB, 0, s>>>(n, x, scale_dev, d);
+    XB_LAUNCHED("k_add_scaled");
+    return XB_OK;
+}
+
+}  // namespace xb

@@ -1,0 +1,438 @@
+// Plans (the paper's *_Setup functions, Table 1): validation, partitions for
+// every SpMV variant, FP32 copy of A, reduction scratch, matrix features.
+#include "common.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+namespace xb {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *where) {
+    return set_error(XB_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int reduce_grid(int64_t n, int block) {
+    int64_t want = (n + block * 4 - 1) / (block * 4);
+    int64_t cap = std::min<int64_t>(kRedSlots, (int64_t)num_sms() * 4);
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+bool variant_fits(const xb_plan *p, int v) {
+    if (p->sym) return v == XB_VAR_SYM_ATOMIC || v == XB_VAR_SYM_TILE;
+    return v == XB_VAR_ROW || v == XB_VAR_NNZ || v == XB_VAR_SEGSCAN;
+}
+
+// ---- partitions -------------------------------------------------------------
+
+const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
+    for (auto &t : p->tiles)
+        if (t.block == block && t.ipt == ipt) return &t;
+    const int n = p->n;
+    const int64_t T = (int64_t)block * ipt;
+    const int *rp = p->h_rowptr.data();
+    std::vector<int> rows;
+    rows.reserve(n / std::max(1, block / 2) + 16);
+    rows.push_back(0);
+    int r = 0;
+    while (r < n) {
+        const int64_t k0 = rp[r];
+        int r1 = r + 1;
+        if ((int64_t)rp[r + 1] - k0 <= T)
+            while (r1 < n && r1 - r < block && (int64_t)rp[r1 + 1] - k0 <= T) r1++;
+        rows.push_back(r1);
+        r = r1;
+    }
+    TilePart t;
+    t.block = block;
+    t.ipt = ipt;
+    t.ntiles = (int)rows.size() - 1;
+    cudaError_t e = cudaMalloc(&t.d_row, rows.size() * sizeof(int));
+    if (e != cudaSuccess) {
+        *err = cuda_error(e, "cudaMalloc(tiles)");
+        return nullptr;
+    }
+    e = cudaMemcpyAsync(t.d_row, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(t.d_row);
+        *err = cuda_error(e, "upload tiles");
+        return nullptr;
+    }
+    p->tiles.push_back(t);
+    return &p->tiles.back();
+}
+
+__global__ void k_seg_rows(int n, const int *__restrict__ rowptr, long long T, int nblk,
+                           int *__restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nblk) return;
+    if (b == nblk) {
+        out[b] = n;
+        return;
+    }
+    const long long target = (long long)b * T;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (int)(((long long)lo + hi + 1) >> 1);
+        if ((long long)rowptr[mid] <= target) lo = mid;
+        else hi = mid - 1;
+    }
+    out[b] = lo;
+}
+
+const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
+    for (auto &t : p->segs)
+        if (t.block == block && t.ipt == ipt) return &t;
+    SegPart t;
+    t.block = block;
+    t.ipt = ipt;
+    const long long T = (long long)block * ipt;
+    t.nblk = (int)((p->nnz + T - 1) / T);
+    const size_t nb = (size_t)t.nblk + 1;
+    cudaError_t e = cudaMalloc(&t.d_row, nb * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_carry_row, nb * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_carry_val, nb * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(t.d_row);
+        cudaFree(t.d_carry_row);
+        cudaFree(t.d_carry_val);
+        *err = cuda_error(e, "cudaMalloc(segments)");
+        return nullptr;
+    }
+    k_seg_rows<<<(t.nblk + 1 + 255) / 256, 256, 0, s>>>(p->n, p->rowptr, T, t.nblk, t.d_row);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = cuda_error(e, "k_seg_rows");
+        return nullptr;
+    }
+    p->segs.push_back(t);
+    return &p->segs.back();
+}
+
+__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+int ensure_val32(xb_plan *p, cudaStream_t s) {
+    if (p->val32 || p->nnz == 0) return XB_OK;
+    XB_CUDA(cudaMalloc(&p->val32, (size_t)p->nnz * sizeof(float)));
+    k_to_f32<<<num_sms() * 8, 256, 0, s>>>(p->nnz, p->val, p->val32);
+    XB_LAUNCHED("k_to_f32");
+    return XB_OK;
+}
+
+int ensure_work(xb_plan *p, size_t bytes) {
+    if (p->work_bytes >= bytes) return XB_OK;
+    if (p->d_work) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_error(e, "sync before workspace growth");
+        cudaFree(p->d_work);
+        p->d_work = nullptr;
+        p->work_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&p->d_work, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(XB_ENOMEM, "solver workspace of %zu bytes: %s", bytes,
+                         cudaGetErrorString(e));
+    }
+    p->work_bytes = bytes;
+    return XB_OK;
+}
+
+// ---- features -----------------------------------------------------------------
+
+__global__ void k_feat(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                       unsigned long long *__restrict__ acc /* [0] sum L^2, [1] max L, [2] max bw */) {
+    __shared__ unsigned long long s2[32];
+    __shared__ unsigned int mx[2];
+    if (threadIdx.x == 0) mx[0] = mx[1] = 0;
+    __syncthreads();
+    unsigned long long sq = 0;
+    unsigned int ml = 0, mb = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int a = rowptr[i], b = rowptr[i + 1];
+        const unsigned int L = (unsigned int)(b - a);
+        sq += (unsigned long long)L * L;
+        ml = max(ml, L);
+        if (b > a) {  // columns ascending: the extremes are the first and last
+            mb = max(mb, (unsigned int)abs(col[a] - i));
+            mb = max(mb, (unsigned int)abs(col[b - 1] - i));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+        mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s2[threadIdx.x >> 5] = sq;
+        atomicMax(&mx[0], ml);
+        atomicMax(&mx[1], mb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s2[w];
+        atomicAdd(&acc[0], t);
+        atomicMax(&acc[1], (unsigned long long)mx[0]);
+        atomicMax(&acc[2], (unsigned long long)mx[1]);
+    }
+}
+
+// Exact symmetry test: every stored (i, j, v) has a stored (j, i, v).
+__global__ void k_feat_sym(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                           const double *__restrict__ val, unsigned long long *__restrict__ bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            const int j = col[k];
+            int lo = rowptr[j], hi = rowptr[j + 1] - 1;
+            int found = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int c = col[mid];
+                if (c == i) {
+                    found = mid;
+                    break;
+                }
+                if (c < i) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (found < 0 || val[found] != val[k]) {
+                atomicOr(bad, 1ull);
+                return;
+            }
+        }
+    }
+}
+
+}  // namespace xb
+
+using namespace xb;
+
+extern "C" {
+
+const char *xb_last_error(void) { return g_err.c_str(); }
+
+void xb_options_default(xb_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->tol = 1e-8;
+    o->maxiter = 1000000;
+    o->maxtime_s = 1000.0;
+    o->m = 30;
+    o->m_max = 120;
+    o->dafrt = 0;
+    o->dafrt_theta = 10.0;
+    o->dafrt_window = 5;
+    o->dafrt_dm = 5;
+    o->ortho = XB_ORTHO_MGS;
+    o->precision = XB_PREC_FP64;
+    o->tol_inner = 1e-4;
+    o->maxiter_inner = 300;
+    o->max_outer = 60;
+    o->variant = XB_VAR_AUTO;
+    o->block = 0;
+    o->ipt = 0;
+    o->tuner = XB_TUNER_NONE;
+    o->check_every = 1;
+    o->timing = 0;
+}
+
+int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out) {
+    (void)opt;
+    if (!A || !out) return set_error(XB_EINVAL, "plan_create: NULL argument");
+    *out = nullptr;
+    const int n = A->n, nnz = A->nnz;
+    if (n < 0 || nnz < 0) return set_error(XB_EINVAL, "plan_create: n=%d nnz=%d", n, nnz);
+    if (n > 0 && (!A->rowptr || (nnz > 0 && (!A->col || !A->val))))
+        return set_error(XB_EINVAL, "plan_create: NULL CRS array");
+    cudaStream_t s = (cudaStream_t)stream;
+    xb_plan *p = new (std::nothrow) xb_plan();
+    if (!p) return set_error(XB_ENOMEM, "plan_create: host allocation");
+    p->n = n;
+    p->nnz = nnz;
+    p->sym = A->sym_upper ? 1 : 0;
+    p->rowptr = A->rowptr;
+    p->col = A->col;
+    p->val = A->val;
+    auto fail = [&](int code) {
+        xb_plan_destroy(p);
+        return code;
+    };
+    p->h_rowptr.resize((size_t)n + 1, 0);
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(p->h_rowptr.data(), A->rowptr, ((size_t)n + 1) * sizeof(int),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: read rowptr"));
+    }
+    const int *rp = p->h_rowptr.data();
+    if (rp[0] != 0 || rp[n] != nnz)
+        return fail(set_error(XB_EINVAL, "plan_create: rowptr[0]=%d rowptr[n]=%d nnz=%d", rp[0],
+                              rp[n], nnz));
+    std::vector<int> empty;
+    for (int i = 0; i < n; i++) {
+        const int L = rp[i + 1] - rp[i];
+        if (L < 0) return fail(set_error(XB_EINVAL, "plan_create: rowptr decreases at row %d", i));
+        p->max_row = std::max(p->max_row, L);
+        if (L == 0) empty.push_back(i);
+    }
+    const char *val_env = std::getenv("XB_VALIDATE");
+    if (val_env && val_env[0] == '1' && nnz > 0) {
+        std::vector<int> hc(nnz);
+        cudaError_t e = cudaMemcpy(hc.data(), A->col, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: read col"));
+        for (int i = 0; i < n; i++)
+            for (int k = rp[i]; k < rp[i + 1]; k++) {
+                const int c = hc[k];
+                if (c < 0 || c >= n || (k > rp[i] && c <= hc[k - 1]) || (p->sym && c < i))
+                    return fail(set_error(XB_EINVAL, "plan_create: bad column %d at row %d (k=%d)",
+                                          c, i, k));
+            }
+    }
+    p->n_empty = (int)empty.size();
+    if (p->n_empty) {
+        cudaError_t e = cudaMalloc(&p->d_empty, empty.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_empty, empty.data(), empty.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: empty rows"));
+    }
+    cudaError_t e = cudaMalloc(&p->d_part, (size_t)kRedSlots * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ticket, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_scal, (size_t)kScalars * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ticket, 0, 64 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_scal, 0, (size_t)kScalars * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->h_pin, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[1]);
+    if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: scratch"));
+    // default choice (Sec. 3.3.1 STABLE policy: no tuning): power-law rows go to
+    // the segmented scan, everything else to the nnz-balanced tiles.
+    if (p->sym) {
+        p->variant = XB_VAR_SYM_TILE;
+    } else {
+        const double mean = n > 0 ? (double)nnz / n : 0.0;
+        p->variant = (p->max_row > 64 && p->max_row > 16.0 * mean) ? XB_VAR_SEGSCAN : XB_VAR_NNZ;
+    }
+    p->block = 256;
+    p->ipt = 8;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "plan_create"));
+    *out = p;
+    return XB_OK;
+}
+
+int xb_plan_destroy(xb_plan *p) {
+    if (!p) return XB_OK;
+    cudaDeviceSynchronize();
+    for (auto &t : p->tiles) cudaFree(t.d_row);
+    for (auto &t : p->segs) {
+        cudaFree(t.d_row);
+        cudaFree(t.d_carry_row);
+        cudaFree(t.d_carry_val);
+    }
+    cudaFree(p->val32);
+    cudaFree(p->d_empty);
+    cudaFree(p->d_part);
+    cudaFree(p->d_ticket);
+    cudaFree(p->d_scal);
+    cudaFree(p->d_work);
+    if (p->h_pin) cudaFreeHost(p->h_pin);
+    for (auto &e : p->ev)
+        if (e) cudaEventDestroy(e);
+    delete p;
+    return XB_OK;
+}
+
+int xb_plan_set_choice(xb_plan *p, int32_t variant, int32_t block, int32_t ipt) {
+    if (!p) return set_error(XB_EINVAL, "set_choice: NULL plan");
+    if (!variant_fits(p, variant))
+        return set_error(XB_EINVAL, "set_choice: variant %d does not fit this storage", variant);
+    if (block != 64 && block != 128 && block != 256 && block != 512)
+        return set_error(XB_EINVAL, "set_choice: block %d", block);
+    if (ipt < 1 || ipt > 32) return set_error(XB_EINVAL, "set_choice: ipt %d", ipt);
+    p->variant = variant;
+    p->block = block;
+    p->ipt = ipt;
+    return XB_OK;
+}
+
+int xb_plan_get_choice(const xb_plan *p, xb_choice *out) {
+    if (!p || !out) return set_error(XB_EINVAL, "get_choice: NULL argument");
+    out->variant = p->variant;
+    out->block = p->block;
+    out->ipt = p->ipt;
+    out->ms = p->tuned_ms;
+    return XB_OK;
+}
+
+int xb_features(const xb_csr *A, double *raw, float *feat, void *stream) {
+    if (!A) return set_error(XB_EINVAL, "features: NULL matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = A->n, nnz = A->nnz;
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (n > 0) {
+        unsigned long long *d = nullptr;
+        XB_CUDA(cudaMalloc(&d, 4 * sizeof(unsigned long long)));
+        cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), s);
+        const int g = std::max(1, std::min(num_sms() * 8, (n + 255) / 256));
+        k_feat<<<g, 256, 0, s>>>(n, A->rowptr, A->col, d);
+        if (!A->sym_upper && nnz > 0) k_feat_sym<<<g, 256, 0, s>>>(n, A->rowptr, A->col, A->val, d + 3);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h, d, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d);
+        if (e != cudaSuccess) return cuda_error(e, "features");
+    }
+    const double dn = n, mean = n > 0 ? (double)nnz / n : 0.0;
+    double var = n > 0 ? ((double)h[0] - (double)nnz * mean) / dn : 0.0;
+    if (var < 0) var = 0;
+    const double r[7] = {dn, (double)nnz, mean, var, (double)h[1], (double)h[2],
+                         (A->sym_upper || h[3] == 0) ? 1.0 : 0.0};
+    if (raw)
+        for (int i = 0; i < 7; i++) raw[i] = r[i];
+    if (feat) {
+        feat[0] = (float)std::log1p(r[0]);
+        feat[1] = (float)std::log1p(r[1]);
+        feat[2] = (float)std::log1p(r[2]);
+        feat[3] = (float)std::log1p(r[3]);
+        feat[4] = (float)std::log1p(r[4]);
+        feat[5] = (float)std::log1p(r[5]);
+        feat[6] = (float)r[6];
+        feat[7] = (float)(std::log1p(r[4]) - std::log1p(r[2]));
+    }
+    return XB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,608 @@
+// CRS SpMV kernels for sm_103a: y = alpha*A*x + beta*y.
+//
+// The paper's OpenMP implementations (Sec. 3.2.2) are the prior art: U1
+// row-based decomposition, U2 non-zero-balanced row decomposition, U3
+// branchless segmented scan (BSS), and for symmetric upper storage S1-S3
+// (S3: skip the reduction work on all-zero parts of the per-thread vectors).
+// On GB300 the FP64 pipe delivers ~2 DFMA/clk/SM (~0.6 T DFMA/s), barely
+// above what HBM needs for 12 B per non-zero, so every kernel here spends
+// one FP64 instruction per non-zero and keeps all other work (index math,
+// staging, row search, transpose scatter) on integer, shared-memory or L2
+// atomic paths.
+//
+// mode: 0 -> y = s, 1 -> y = alpha*s, 2 -> y = alpha*s + beta*y.
+#include "common.cuh"
+#include "krylov.cuh"
+
+#include <algorithm>
+#include <climits>
+#include <mutex>
+#include <unordered_set>
+
+namespace {
+
+template <typename V>
+__device__ __forceinline__ void store_row(V *__restrict__ y, int r, V s, V alpha, V beta, int mode) {
+    if (mode == 0)
+        y[r] = s;
+    else if (mode == 1)
+        y[r] = alpha * s;
+    else
+        y[r] = fma(alpha, s, beta * y[r]);
+}
+
+// ---------------------------------------------------------------------------
+// U1: one thread per row, operands straight from global memory.
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(512) k_row(int n, const int *__restrict__ rowptr,
+                                             const int *__restrict__ col, const V *__restrict__ val,
+                                             const V *__restrict__ x, V alpha, V beta, int mode,
+                                             V *__restrict__ y, const V *__restrict__ adev) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (adev) alpha = *adev;
+    const int a = rowptr[r], b = rowptr[r + 1];
+    V s = V(0);
+    for (int k = a; k < b; k++) s = fma(val[k], x[col[k]], s);
+    store_row(y, r, s, alpha, beta, mode);
+}
+
+// ---------------------------------------------------------------------------
+// U2: row-aligned, nnz-balanced tiles.  A tile holds at most T = B*IPT
+// non-zeros and B rows; its val and x[col] are staged into shared memory with
+// coalesced loads (IPT independent loads and gathers in flight per thread),
+// then each thread sums one row with FMAs from shared memory.  Tiles whose
+// rows average more than 32 non-zeros use a warp per row; a single row longer
+// than T is a tile of its own, summed by the whole CTA.
+// ---------------------------------------------------------------------------
+template <typename V, int IPT>
+__global__ void __launch_bounds__(512) k_tile(const int *__restrict__ rowptr,
+                                              const int *__restrict__ col,
+                                              const V *__restrict__ val, const V *__restrict__ x,
+                                              V alpha, V beta, int mode, V *__restrict__ y,
+                                              const int *__restrict__ trow,
+                                              const V *__restrict__ adev) {
+    extern __shared__ __align__(16) unsigned char sm_[];
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int T = B * IPT;
+    if (adev) alpha = *adev;
+    const int r0 = trow[blockIdx.x], r1 = trow[blockIdx.x + 1];
+    const int k0 = rowptr[r0], k1 = rowptr[r1];
+    const int cnt = k1 - k0;
+    V *red = reinterpret_cast<V *>(sm_);  // 32
+    if (cnt > T) {  // one long row, whole CTA
+        V s0 = V(0), s1 = V(0);
+        int e = k0 + tid;
+        for (; e + B < k1; e += 2 * B) {
+            const int c0 = col[e], c1 = col[e + B];
+            const V v0 = val[e], v1 = val[e + B];
+            s0 = fma(v0, x[c0], s0);
+            s1 = fma(v1, x[c1], s1);
+        }
+        if (e < k1) s0 = fma(val[e], x[col[e]], s0);
+        V s = xbd::block_sum(s0 + s1, red);
+        if (tid == 0) store_row(y, r0, s, alpha, beta, mode);
+        return;
+    }
+    V *sv = red + 32;
+    V *sx = sv + T;
+    int *srp = reinterpret_cast<int *>(sx + T);
+    {
+        int c[IPT];
+        V v[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int e = tid + j * B;
+            if (e < cnt) {
+                c[j] = col[k0 + e];
+                v[j] = val[k0 + e];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int e = tid + j * B;
+            if (e < cnt) {
+                sx[e] = x[c[j]];
+                sv[e] = v[j];
+            }
+        }
+    }
+    const int nr = r1 - r0;
+    for (int i = tid; i <= nr; i += B) srp[i] = rowptr[r0 + i] - k0;
+    __syncthreads();
+    if (cnt > 32 * nr) {  // long rows: a warp per row
+        const int lane = tid & 31, w = tid >> 5, nw = B >> 5;
+        for (int i = w; i < nr; i += nw) {
+            const int a = srp[i], b = srp[i + 1];
+            V s = V(0);
+            for (int e = a + lane; e < b; e += 32) s = fma(sv[e], sx[e], s);
+            s = xbd::warp_sum(s);
+            if (lane == 0) store_row(y, r0 + i, s, alpha, beta, mode);
+        }
+        return;
+    }
+    for (int i = tid; i < nr; i += B) {
+        const int a = srp[i], b = srp[i + 1];
+        V s = V(0);
+        for (int e = a; e < b; e++) s = fma(sv[e], sx[e], s);
+        store_row(y, r0 + i, s, alpha, beta, mode);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// U3 (BSS): flat nnz segments.  CTA b owns non-zeros [b*T, b*T+T); thread t
+// owns IPT consecutive ones.  val and col are staged with coalesced loads
+// into a padded shared layout (stride IPT+1, conflict-free per-thread reads),
+// the thread's start row comes from a binary search in the CTA's staged
+// rowptr slice, and each thread runs its IPT FMAs with row breaks as
+// predicated stores (no data-dependent loop).  Partial sums of rows that
+// straddle threads are combined by a key-segmented scan (warp shuffles, then
+// across warps), rows straddling CTAs by a deterministic carry fix-up.
+// ---------------------------------------------------------------------------
+template <typename V, int IPT>
+__global__ void __launch_bounds__(512) k_seg(int n, int nnz, const int *__restrict__ rowptr,
+                                             const int *__restrict__ col,
+                                             const V *__restrict__ val, const V *__restrict__ x,
+                                             V alpha, V beta, int mode, V *__restrict__ y,
+                                             const int *__restrict__ brow, V *__restrict__ cval,
+                                             int *__restrict__ crow, const V *__restrict__ adev) {
+    extern __shared__ __align__(16) unsigned char sm_[];
+    const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (adev) alpha = *adev;
+    const int T = B * IPT, TP = T + B;
+    const int E0 = blockIdx.x * T;
+    const int cnt = min(T, nnz - E0);
+    const int rb = brow[blockIdx.x], re = brow[blockIdx.x + 1];
+    V *sv = reinterpret_cast<V *>(sm_);
+    V *wsum = sv + TP;   // 32
+    V *wtot = wsum + 32; // 32
+    int *sc = reinterpret_cast<int *>(wtot + 32);
+    int *srp = sc + TP;  // T + 2
+    int *wkf = srp + T + 2, *wkl = wkf + 32;
+
+    {
+        int c[IPT];
+        V v[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int e = tid + j * B;
+            if (e < cnt) {
+                c[j] = col[E0 + e];
+                v[j] = val[E0 + e];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int e = tid + j * B;
+            if (e < cnt) {
+                const int p = e + e / IPT;
+                sv[p] = v[j];
+                sc[p] = c[j];
+            }
+        }
+    }
+    const int nr = re - rb + 2;  // rowptr[rb .. re+1], clamped to n
+    const bool big = nr > T + 2;
+    if (!big)
+        for (int i = tid; i < nr; i += B) srp[i] = rowptr[min(rb + i, n)];
+    __syncthreads();
+#define RP(r) (big ? rowptr[min((r), n)] : srp[(r) - rb])
+
+    const int el = tid * IPT;
+    const int ecnt = max(0, min(IPT, cnt - el));
+    const int p0 = tid * (IPT + 1);
+    int row = INT_MAX;
+    V sum = V(0), head = V(0);
+    int hrow = -1;
+    if (ecnt > 0) {
+        const int target = E0 + el;
+        int lo = rb, hi = re;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (RP(mid) <= target) lo = mid;
+            else hi = mid - 1;
+        }
+        row = lo;
+        V xv[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; j++)
+            if (j < ecnt) xv[j] = x[sc[p0 + j]];
+        int nend = RP(row + 1) - E0;
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            if (j < ecnt) {
+                sum = fma(sv[p0 + j], xv[j], sum);
+                const int le = el + j + 1;
+                if (le == nend) {
+                    if (hrow < 0) {
+                        head = sum;
+                        hrow = row;
+                    } else {
+                        store_row(y, row, sum, alpha, beta, mode);
+                    }
+                    sum = V(0);
+                    do {
+                        row++;
+                        nend = RP(row + 1) - E0;
+                    } while (nend == le && row < n);
+                }
+            }
+        }
+    }
+#undef RP
+    // key-segmented inclusive scan of (row, sum) over the CTA
+    V s = sum;
+    int k = row;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V su = __shfl_up_sync(0xffffffffu, s, o);
+        const int ku = __shfl_up_sync(0xffffffffu, k, o);
+        if (lane >= o && ku == k) s += su;
+    }
+    if (lane == 31) {
+        wsum[wid] = s;
+        wkl[wid] = k;
+    }
+    if (lane == 0) wkf[wid] = k;
+    __syncthreads();
+    const int nw = B >> 5;
+    if (wid == 0) {
+        // segmented scan over warp tails: warp l continues warp l-1's tail run
+        // when the whole warp carries that one key.
+        V ts = lane < nw ? wsum[lane] : V(0);
+        int f = 1;
+        if (lane < nw && lane > 0) f = !(wkf[lane] == wkl[lane] && wkl[lane - 1] == wkl[lane]);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const V su = __shfl_up_sync(0xffffffffu, ts, o);
+            const int fu = __shfl_up_sync(0xffffffffu, f, o);
+            if (lane >= o && !f) {
+                ts += su;
+                f |= fu;
+            }
+        }
+        if (lane < nw) wtot[lane] = ts;
+    }
+    __syncthreads();
+    if (wid > 0 && k == wkf[wid] && wkl[wid - 1] == k) s += wtot[wid - 1];
+    V sp = __shfl_up_sync(0xffffffffu, s, 1);
+    int kp = __shfl_up_sync(0xffffffffu, k, 1);
+    if (lane == 0) {
+        if (wid > 0) {
+            sp = wtot[wid - 1];
+            kp = wkl[wid - 1];
+        } else {
+            sp = V(0);
+            kp = -1;
+        }
+    }
+    if (hrow >= 0) store_row(y, hrow, head + (kp == hrow ? sp : V(0)), alpha, beta, mode);
+    if (cnt > 0 && tid == (cnt - 1) / IPT) {
+        crow[blockIdx.x] = k;
+        cval[blockIdx.x] = s;
+    }
+}
+
+// Adds each run of equal carry rows, in CTA order (deterministic).
+template <typename V>
+__global__ void k_seg_fix(int nblk, int n, const int *__restrict__ crow, const V *__restrict__ cval,
+                          V alpha, int mode, V *__restrict__ y, const V *__restrict__ adev) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblk) return;
+    if (adev) alpha = *adev;
+    const int r = crow[b];
+    if (r >= n || (b > 0 && crow[b - 1] == r)) return;
+    V s = cval[b];
+    for (int q = b + 1; q < nblk && crow[q] == r; q++) s += cval[q];
+    y[r] += (mode == 0) ? s : alpha * s;
+}
+
+template <typename V>
+__global__ void k_empty_rows(int cnt, const int *__restrict__ rows, V beta, int mode,
+                             V *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int r = rows[i];
+    y[r] = (mode == 2) ? beta * y[r] : V(0);
+}
+
+template <typename V>
+__global__ void k_yscale(int n, V beta, V *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (beta == V(0)) ? V(0) : beta * y[i];
+}
+
+// ---------------------------------------------------------------------------
+// S1-like baseline: thread per upper row; the row part is a plain FMA sum,
+// every transpose term u*x_i goes to y[j] through a device FP64 atomic (an
+// L2 reduction, no FP64 work on the SM).  y must hold beta*y beforehand.
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(512) k_sym_atomic(int n, const int *__restrict__ rowptr,
+                                                    const int *__restrict__ col,
+                                                    const V *__restrict__ val,
+                                                    const V *__restrict__ x, V alpha,
+                                                    V *__restrict__ y, const V *__restrict__ adev) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (adev) alpha = *adev;
+    const int a = rowptr[r], b = rowptr[r + 1];
+    const V axi = alpha * x[r];
+    V s = V(0);
+    for (int k = a; k < b; k++) {
+        const int j = col[k];
+        const V u = val[k];
+        s = fma(u, x[j], s);
+        if (j != r) atomicAdd(&y[j], u * axi);
+    }
+    atomicAdd(&y[r], alpha * s);
+}
+
+// ---------------------------------------------------------------------------
+// S2/S3-like: the U2 tile partition over the upper rows.  Transpose terms
+// whose target row lies inside the tile are summed in a shared-memory
+// vector for the tile's rows; only the tile's out-of-tile targets (the
+// non-zero region beyond the tile) reach device memory, as FP64 atomics.
+// Each tile row is then added to y once.  y must hold beta*y beforehand.
+// ---------------------------------------------------------------------------
+template <typename V, int IPT>
+__global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr,
+                                                  const int *__restrict__ col,
+                                                  const V *__restrict__ val,
+                                                  const V *__restrict__ x, V alpha,
+                                                  V *__restrict__ y,
+                                                  const int *__restrict__ trow,
+                                                  const V *__restrict__ adev) {
+    extern __shared__ __align__(16) unsigned char sm_[];
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int T = B * IPT;
+    if (adev) alpha = *adev;
+    const int r0 = trow[blockIdx.x], r1 = trow[blockIdx.x + 1];
+    const int k0 = rowptr[r0], k1 = rowptr[r1];
+    const int cnt = k1 - k0;
+    V *red = reinterpret_cast<V *>(sm_);  // 32
+    if (cnt > T) {  // one long row r0: whole CTA
+        const V axi = alpha * x[r0];
+        V s = V(0);
+        for (int e = k0 + tid; e < k1; e += B) {
+            const int j = col[e];
+            const V u = val[e];
+            s = fma(u, x[j], s);
+            if (j != r0) atomicAdd(&y[j], u * axi);
+        }
+        s = xbd::block_sum(s, red);
+        if (tid == 0) atomicAdd(&y[r0], alpha * s);
+        return;
+    }
+    V *acc = red + 32;     // B
+    V *sv = acc + B;       // T
+    int *sc = reinterpret_cast<int *>(sv + T);  // T
+    int *srp = sc + T;     // B + 1
+    {
+        int c[IPT];
+        V v[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int e = tid + j * B;
+            if (e < cnt) {
+                c[j] = col[k0 + e];
+                v[j] = val[k0 + e];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const int e = tid + j * B;
+            if (e < cnt) {
+                sc[e] = c[j];
+                sv[e] = v[j];
+            }
+        }
+    }
+    const int nr = r1 - r0;
+    for (int i = tid; i <= nr; i += B) srp[i] = rowptr[r0 + i] - k0;
+    for (int i = tid; i < nr; i += B) acc[i] = V(0);
+    __syncthreads();
+    V s = V(0);
+    if (tid < nr) {
+        const int r = r0 + tid;
+        const V axi = alpha * x[r];
+        const int a = srp[tid], b = srp[tid + 1];
+        for (int e = a; e < b; e++) {
+            const int j = sc[e];
+            const V u = sv[e];
+            s = fma(u, x[j], s);
+            if (j != r) {
+                if (j < r1) atomicAdd(&acc[j - r0], u * axi);
+                else atomicAdd(&y[j], u * axi);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < nr) atomicAdd(&y[r0 + tid], fma(alpha, s, acc[tid]));
+}
+
+// Opt every kernel instantiation into the device's full shared-memory
+// capacity once (the launch size decides the occupancy).
+int smem_limit() {
+    static int maxs = -1;
+    if (maxs < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return maxs;
+}
+
+int smem_optin(const void *fn, size_t need) {
+    static std::mutex mu;
+    static std::unordered_set<const void *> done;
+    if (need > (size_t)smem_limit())
+        return xb::set_error(XB_EINVAL, "launch shape needs %zu B shared memory (> %d)", need,
+                             smem_limit());
+    std::lock_guard<std::mutex> g(mu);
+    if (!done.count(fn)) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit());
+        done.insert(fn);
+    }
+    return XB_OK;
+}
+
+template <typename V>
+int launch_tile(xb_plan *p, const int *rp, const int *ci, const V *va, int block, int ipt, V alpha,
+                const V *x, V beta, int mode, V *y, const V *adev, cudaStream_t s) {
+    int err = XB_OK;
+    const xb::TilePart *tp = xb::get_tiles(p, block, ipt, s, &err);
+    if (!tp) return err;
+    if (tp->ntiles == 0) return XB_OK;
+    const size_t sm = 32 * sizeof(V) + 2ull * block * ipt * sizeof(V) + (block + 1) * sizeof(int);
+#define XB_TILE(I)                                                                       \
+    case I:                                                                              \
+        XB_TRY(smem_optin((const void *)k_tile<V, I>, sm));                             \
+        k_tile<V, I><<<tp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, beta, mode, y,  \
+                                                   tp->d_row, adev);                     \
+        break;
+    switch (ipt) {
+        XB_TILE(1) XB_TILE(2) XB_TILE(4) XB_TILE(8) XB_TILE(16)
+        default: return xb::set_error(XB_EINVAL, "tile: unsupported ipt %d", ipt);
+    }
+#undef XB_TILE
+    XB_LAUNCHED("k_tile");
+    return XB_OK;
+}
+
+template <typename V>
+int launch_seg(xb_plan *p, const int *rp, const int *ci, const V *va, int block, int ipt, V alpha,
+               const V *x, V beta, int mode, V *y, const V *adev, cudaStream_t s) {
+    int err = XB_OK;
+    const xb::SegPart *sp = xb::get_segs(p, block, ipt, s, &err);
+    if (!sp) return err;
+    if (sp->nblk > 0) {
+        const int T = block * ipt, TP = T + block;
+        const size_t sm = (size_t)TP * sizeof(V) + 64 * sizeof(V) + (size_t)TP * 4 +
+                          (size_t)(T + 2) * 4 + 64 * 4;
+        V *cv = reinterpret_cast<V *>(sp->d_carry_val);
+#define XB_SEG(I)                                                                          \
+    case I:                                                                                \
+        XB_TRY(smem_optin((const void *)k_seg<V, I>, sm));                                 \
+        k_seg<V, I><<<sp->nblk, block, sm, s>>>(p->n, p->nnz, rp, ci, va, x, alpha, beta,  \
+                                                mode, y, sp->d_row, cv, sp->d_carry_row, adev); \
+        break;
+        switch (ipt) {
+            XB_SEG(2) XB_SEG(4) XB_SEG(8) XB_SEG(12) XB_SEG(16) XB_SEG(24) XB_SEG(32)
+            default: return xb::set_error(XB_EINVAL, "segscan: unsupported ipt %d", ipt);
+        }
+#undef XB_SEG
+        XB_LAUNCHED("k_seg");
+        k_seg_fix<V><<<(sp->nblk + 255) / 256, 256, 0, s>>>(sp->nblk, p->n, sp->d_carry_row, cv,
+                                                             alpha, mode, y, adev);
+        XB_LAUNCHED("k_seg_fix");
+    }
+    if (p->n_empty > 0) {
+        k_empty_rows<V><<<(p->n_empty + 255) / 256, 256, 0, s>>>(p->n_empty, p->d_empty, beta,
+                                                                  mode, y);
+        XB_LAUNCHED("k_empty_rows");
+    }
+    return XB_OK;
+}
+
+template <typename V>
+int launch_sym(xb_plan *p, int variant, const int *rp, const int *ci, const V *va, int block,
+               int ipt, V alpha, const V *x, V beta, V *y, const V *adev, cudaStream_t s) {
+    const int n = p->n;
+    if (n == 0) return XB_OK;
+    k_yscale<V><<<(n + 255) / 256, 256, 0, s>>>(n, beta, y);
+    XB_LAUNCHED("k_yscale");
+    if (variant == XB_VAR_SYM_ATOMIC) {
+        k_sym_atomic<V><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
+        XB_LAUNCHED("k_sym_atomic");
+        return XB_OK;
+    }
+    int err = XB_OK;
+    const xb::TilePart *tp = xb::get_tiles(p, block, ipt, s, &err);
+    if (!tp) return err;
+    if (tp->ntiles == 0) return XB_OK;
+    const size_t sm = (32 + (size_t)block + (size_t)block * ipt) * sizeof(V) +
+                      (size_t)block * ipt * 4 + (block + 1) * 4;
+#define XB_SYM(I)                                                                         \
+    case I:                                                                               \
+        XB_TRY(smem_optin((const void *)k_sym_tile<V, I>, sm));                           \
+        k_sym_tile<V, I><<<tp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, y, tp->d_row, adev); \
+        break;
+    switch (ipt) {
+        XB_SYM(1) XB_SYM(2) XB_SYM(4) XB_SYM(8) XB_SYM(16)
+        default: return xb::set_error(XB_EINVAL, "sym tile: unsupported ipt %d", ipt);
+    }
+#undef XB_SYM
+    XB_LAUNCHED("k_sym_tile");
+    return XB_OK;
+}
+
+template <typename V>
+int spmv_any(xb_plan *p, int variant, int block, int ipt, V alpha, const V *x, V beta, V *y,
+             const V *va, const V *adev, cudaStream_t s) {
+    if (variant == XB_VAR_AUTO) variant = p->variant;
+    if (block <= 0) block = p->block;
+    if (ipt <= 0) ipt = p->ipt;
+    if (!xb::variant_fits(p, variant))
+        return xb::set_error(XB_EINVAL, "SpMV variant %d does not fit %s storage", variant,
+                             p->sym ? "symmetric-upper" : "general");
+    if (block != 64 && block != 128 && block != 256 && block != 512)
+        return xb::set_error(XB_EINVAL, "SpMV block %d not in {64,128,256,512}", block);
+    const int n = p->n;
+    if (n == 0) return XB_OK;
+    if (adev) beta = V(0);
+    const int mode = adev ? 1 : (beta == V(0)) ? (alpha == V(1) ? 0 : 1) : 2;
+    switch (variant) {
+        case XB_VAR_ROW:
+            k_row<V><<<(n + block - 1) / block, block, 0, s>>>(n, p->rowptr, p->col, va, x, alpha,
+                                                               beta, mode, y, adev);
+            XB_LAUNCHED("k_row");
+            return XB_OK;
+        case XB_VAR_NNZ:
+            return launch_tile<V>(p, p->rowptr, p->col, va, block, ipt, alpha, x, beta, mode, y, adev,
+                                  s);
+        case XB_VAR_SEGSCAN:
+            return launch_seg<V>(p, p->rowptr, p->col, va, block, ipt, alpha, x, beta, mode, y, adev,
+                                 s);
+        case XB_VAR_SYM_ATOMIC:
+        case XB_VAR_SYM_TILE:
+            return launch_sym<V>(p, variant, p->rowptr, p->col, va, block, ipt, alpha, x, beta, y,
+                                 adev, s);
+    }
+    return xb::set_error(XB_EINVAL, "unknown SpMV variant %d", variant);
+}
+
+}  // namespace
+
+namespace xb {
+
+int spmv_launch(xb_plan *p, int variant, int block, int ipt, double alpha, const double *x,
+                double beta, double *y, cudaStream_t s) {
+    return spmv_any<double>(p, variant, block, ipt, alpha, x, beta, y, p->val, nullptr, s);
+}
+
+int spmv_launch_dalpha(xb_plan *p, int variant, int block, int ipt, const double *alpha_dev,
+                       const double *x, double *y, cudaStream_t s) {
+    return spmv_any<double>(p, variant, block, ipt, 1.0, x, 0.0, y, p->val, alpha_dev, s);
+}
+
+int spmv_launch_dalpha_f32(xb_plan *p, int variant, int block, int ipt, const float *alpha_dev,
+                           const float *x, float *y, cudaStream_t s) {
+    XB_TRY(ensure_val32(p, s));
+    return spmv_any<float>(p, variant, block, ipt, 1.0f, x, 0.0f, y, p->val32, alpha_dev, s);
+}
+
+int spmv_launch_f32(xb_plan *p, int variant, int block, int ipt, float alpha, const float *x,
+                    float beta, float *y, cudaStream_t s) {
+    XB_TRY(ensure_val32(p, s));
+    return spmv_any<float>(p, variant, block, ipt, alpha, x, beta, y, p->val32, nullptr, s);
+}
+
+double spmv_alg_bytes(const xb_plan *p, bool beta_nonzero, int val_bytes) {
+    const double n = p->n, nnz = p->nnz;
+    const int vb = val_bytes;
+    return (vb + 4.0) * nnz + 4.0 * (n + 1) + vb * n + vb * n + (beta_nonzero ? vb * n : 0.0);
+}
+
+}  // namespace xb

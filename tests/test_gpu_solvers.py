@@ -1,0 +1,203 @@
+"""GPU Krylov solvers and vector kernels against the CPU oracle (C ABI).
+
+Solver parity: both reach the true residual ||b - A x|| / ||b|| <= tol (the
+GPU's x re-evaluated by the oracle's SpMV), FP64 iteration counts agree
+within max(3, 5 %) for GMRES and max(3, 10 %) for BiCGStab (rounding order
+differs; BiCGStab's recurrences amplify it more)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_01599_gb300 import gen
+from tests._gpu import lib_and_device
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_and_device()
+
+
+def _true_rel(A, x, b):
+    return np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+
+
+def _solve(xb, dev, A, which, b=None, x0=None, **opt):
+    import torch
+    plan = xb.Plan.from_host(A, dev)
+    if b is None:
+        b = oracle.spmv(A, np.ones(A["n"]))
+    bt = torch.tensor(b, device=dev)
+    xt = torch.zeros(A["n"], dtype=torch.float64, device=dev) if x0 is None else torch.tensor(x0, device=dev)
+    info = (plan.gmres if which == "gmres" else plan.bicgstab)(bt, xt, **opt)
+    return info, xt.cpu().numpy(), b
+
+
+@pytest.mark.parametrize("name,make,m", [
+    ("poisson64", lambda: gen.poisson2d(64), 30),
+    ("random200", lambda: gen.random200(), 30),
+    ("convdiff10", lambda: gen.convdiff3d(N=10), 20),
+    ("laplace3d_10_upper", lambda: gen.laplace3d(10, upper=True), 25),
+])
+def test_gmres_matches_oracle(env, name, make, m):
+    xb, dev = env
+    A = make()
+    info, x, b = _solve(xb, dev, A, "gmres", m=m, tol=TOL)
+    xo, io = oracle.gmres(A, b, m=m, tol=TOL)
+    assert info["status"] == 0, info
+    assert _true_rel(A, x, b) <= TOL
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
+    assert np.linalg.norm(x - xo) <= 1e-5 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_gmres_each_spmv_variant(env, variant):
+    xb, dev = env
+    A = gen.powerlaw(n=4000, seed=4)
+    info, x, b = _solve(xb, dev, A, "gmres", m=40, tol=TOL, variant=variant, maxiter=20000)
+    assert info["status"] == 0 and _true_rel(A, x, b) <= TOL
+    assert info["variant_used"] == variant
+
+
+def test_gmres_check_every_is_transparent(env):
+    xb, dev = env
+    A = gen.poisson2d(40)
+    i1, x1, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, check_every=1)
+    i4, x4, _ = _solve(xb, dev, A, "gmres", m=30, tol=TOL, check_every=7)
+    assert i1["iters"] == i4["iters"] and i1["restarts"] == i4["restarts"]
+    np.testing.assert_array_equal(x1, x4)
+
+
+def test_gmres_dafrt_matches_oracle(env):
+    xb, dev = env
+    A = gen.poisson2d(24)
+    info, x, b = _solve(xb, dev, A, "gmres", m=2, m_max=17, tol=TOL, dafrt=1, dafrt_theta=10.0,
+                        dafrt_window=5, dafrt_dm=5, maxiter=3000)
+    xo, io = oracle.gmres(A, b, m=2, m_max=17, tol=TOL, maxiter=3000, dafrt=True, theta=10.0,
+                          window=5, dm=5)
+    assert info["m_final"] == io["m_final"] and info["m_final"] > 2
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"])
+    assert info["status"] == io["status"]
+
+
+def test_gmres_edge_cases(env):
+    xb, dev = env
+    A = gen.poisson2d(10)
+    n = A["n"]
+    info, x, _ = _solve(xb, dev, A, "gmres", b=np.zeros(n), x0=np.ones(n))
+    assert info["status"] == 0 and np.all(x == 0)
+    info, x, b = _solve(xb, dev, A, "gmres", m=5, tol=1e-12, maxiter=20)
+    assert info["status"] == xb.XB_ENOCONV and info["iters"] == 20 and info["res_true"] > 1e-12
+    I = dict(n=50, nnz=50, rowptr=np.arange(51, dtype=np.int32), col=np.arange(50, dtype=np.int32),
+             val=np.ones(50), sym_upper=False)
+    info, x, b = _solve(xb, dev, I, "gmres", b=np.random.default_rng(0).standard_normal(50))
+    assert info["status"] == 0 and info["iters"] == 1
+    np.testing.assert_allclose(x, b, rtol=1e-15)
+    Z = dict(n=6, nnz=0, rowptr=np.zeros(7, np.int32), col=np.zeros(0, np.int32), val=np.zeros(0),
+             sym_upper=False)
+    info, x, b = _solve(xb, dev, Z, "gmres", b=np.ones(6))
+    assert info["status"] == xb.XB_EBREAKDOWN
+    info, x, b = _solve(xb, dev, Z, "bicgstab", b=np.ones(6))
+    assert info["status"] == xb.XB_EBREAKDOWN
+
+
+@pytest.mark.parametrize("name,make", [
+    ("convdiff12", lambda: gen.convdiff3d(N=12)),
+    ("powerlaw3000", lambda: gen.powerlaw(n=3000, seed=9)),
+    ("random200", lambda: gen.random200()),
+])
+def test_bicgstab_matches_oracle(env, name, make):
+    xb, dev = env
+    A = make()
+    info, x, b = _solve(xb, dev, A, "bicgstab", tol=TOL, maxiter=200000)
+    xo, io = oracle.bicgstab(A, b, tol=TOL, maxiter=200000)
+    assert info["status"] == 0, info
+    assert _true_rel(A, x, b) <= TOL
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.10 * io["iters"]), (info["iters"], io["iters"])
+
+
+def test_bicgstab_limits(env):
+    xb, dev = env
+    A = gen.poisson2d(20)
+    n = A["n"]
+    info, x, _ = _solve(xb, dev, A, "bicgstab", b=np.zeros(n), x0=np.ones(n))
+    assert info["status"] == 0 and np.all(x == 0)
+    info, x, b = _solve(xb, dev, A, "bicgstab", tol=1e-14, maxiter=3)
+    assert info["status"] == xb.XB_ENOCONV and info["iters"] == 3
+
+
+@pytest.mark.parametrize("name,make", [
+    ("poisson64", lambda: gen.poisson2d(64)),
+    ("convdiff16", lambda: gen.convdiff3d(N=16)),
+    ("random200", lambda: gen.random200()),
+])
+def test_mixed_refinement_reaches_fp64(env, name, make):
+    xb, dev = env
+    A = make()
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, precision=xb.PREC_MIXED, tol_inner=1e-4)
+    assert info["status"] == 0, info
+    rel = _true_rel(A, x, b)
+    assert rel <= TOL
+    assert info["outer"] >= 2
+    xo, io = oracle.gmres_ir(A, b, m=30, tol=TOL, tol_in=1e-4)
+    assert io["status"] == 0
+    # both solutions solve the system to the same accuracy class
+    assert np.linalg.norm(x - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
+def test_dot_and_axpy(env):
+    xb, dev = env
+    import torch
+    rng = np.random.default_rng(0)
+    for n in (0, 1, 1000, 1_000_003):
+        a, c = rng.standard_normal(n), rng.standard_normal(n)
+        plan = xb.Plan.from_host(gen.poisson2d(4), dev)
+        d = plan.dot(torch.tensor(a, device=dev), torch.tensor(c, device=dev)).item()
+        ref = float(np.dot(a, c))
+        assert abs(d - ref) <= 1e-13 * (np.abs(a) @ np.abs(c) + 1e-300)
+        yt = torch.tensor(c, device=dev)
+        xb.axpy(0.5, torch.tensor(a, device=dev), yt)
+        np.testing.assert_allclose(yt.cpu().numpy(), c + 0.5 * a, rtol=1e-15, atol=1e-15)
+
+
+def test_mgs_sweep_matches_oracle_arnoldi(env):
+    """One MGS sweep (h_ij = (w, v_i); w -= h_ij v_i; h_{j+1,j} = ||w||) on the
+    oracle's Arnoldi basis reproduces the oracle's Hessenberg column."""
+    xb, dev = env
+    import torch
+    A = gen.poisson2d(20)
+    m = 12
+    v0 = np.random.default_rng(3).standard_normal(A["n"])
+    k, V, H = oracle.arnoldi(A, v0, m)
+    plan = xb.Plan.from_host(A, dev)
+    for j in (0, 5, m - 1):
+        w = torch.tensor(oracle.spmv(A, V[j]), device=dev)
+        Vt = torch.tensor(V[: j + 1], device=dev)
+        h = plan.mgs(Vt, w).cpu().numpy()
+        np.testing.assert_allclose(h, H[: j + 2, j], rtol=1e-10, atol=1e-12)
+
+
+def test_tuner_choice_is_valid_and_exact(env):
+    xb, dev = env
+    import torch
+    A = gen.powerlaw(n=200000, seed=6)
+    plan = xb.Plan.from_host(A, dev)
+    ch = plan.tune()
+    assert ch["variant"] in (0, 1, 2) and ch["ms"] > 0
+    x = np.random.default_rng(1).uniform(-1, 1, A["n"])
+    y = torch.empty(A["n"], dtype=torch.float64, device=dev)
+    plan.spmv(torch.tensor(x, device=dev), y)
+    from tests._gpu import assert_rows_close, row_bound
+    assert_rows_close(y.cpu().numpy(), oracle.spmv(A, x), row_bound(A, x), what="tuned")
+    U = gen.laplace3d(30, upper=True)
+    pu = xb.Plan.from_host(U, dev)
+    assert pu.tune()["variant"] in (3, 4)
+
+
+def test_mm_ratio_and_dafrt_host(env):
+    xb, dev = env
+    assert xb.mm_ratio([1.0, 0.5, 0.25, 0.125, 0.0625], 5, 5) == 16.0
+    assert xb.dafrt([1, 1, 1, 1, 1], 10.0) == 1
+    assert xb.dafrt([1, 0.5, 0.25, 0.125, 0.0625], 10.0) == 0

@@ -1,0 +1,263 @@
+"""GPU parity of every SpMV kernel against the CPU oracle, through the C ABI.
+
+Tolerance (per row): |y_gpu - y_oracle| <= 1e-12 * sum_j |a_ij||x_j|
+(FP64); rows whose scale is zero must match exactly.  Matrices span many
+tiles/segments with ragged tails, plus the degenerate shapes (empty rows,
+n = 1, nnz = 0, one row holding most entries, rows of length 31/32/33...).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_01599_gb300 import gen
+from tests._gpu import assert_rows_close, lib_and_device, row_bound, sampled_rows_oracle
+
+pytestmark = pytest.mark.gpu
+
+GENERAL = {
+    "row": (0, [(64, 1), (256, 1)]),
+    "nnz": (1, [(64, 1), (128, 4), (256, 8), (512, 16), (256, 2)]),
+    "segscan": (2, [(128, 2), (128, 4), (256, 8), (128, 12), (256, 16), (128, 24), (128, 32)]),
+}
+
+
+def _adversarial():
+    rng = np.random.default_rng(42)
+    n = 6000
+    L = rng.choice([0, 0, 1, 2, 5, 31, 32, 33, 63, 64, 65, 127, 129], size=n)
+    L[17] = 2047
+    L[18] = 2048
+    L[19] = 2049
+    L[3000] = 5999  # a full row
+    L[-40:] = 0     # ragged empty tail
+    L[:5] = 0       # empty head
+    return gen.random_general(n, L, seed=7)
+
+
+def _one_huge_row():
+    n = 30000
+    L = np.zeros(n, np.int64)
+    L[n // 2] = n - 1
+    L[::97] = 3
+    return gen.random_general(n, L, seed=8)
+
+
+MATS = {
+    "random200": lambda: gen.random200(),
+    "poisson64": lambda: gen.poisson2d(64),
+    "laplace3d_20": lambda: gen.laplace3d(20),
+    "convdiff12": lambda: gen.convdiff3d(N=12),
+    "powerlaw30k": lambda: gen.powerlaw(n=30000, seed=3),
+    "adversarial": _adversarial,
+    "one_huge_row": _one_huge_row,
+    "n1": lambda: dict(n=1, nnz=1, rowptr=np.array([0, 1], np.int32), col=np.array([0], np.int32),
+                       val=np.array([2.5]), sym_upper=False),
+    "empty": lambda: dict(n=7, nnz=0, rowptr=np.zeros(8, np.int32), col=np.zeros(0, np.int32),
+                          val=np.zeros(0), sym_upper=False),
+}
+
+
+@pytest.fixture(scope="module")
+def env():
+    return lib_and_device()
+
+
+@pytest.mark.parametrize("mname", list(MATS))
+def test_general_variants_match_oracle(env, mname):
+    xb, dev = env
+    import torch
+    A = MATS[mname]()
+    n = A["n"]
+    plan = xb.Plan.from_host(A, dev)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1, 1, n)
+    y0 = rng.uniform(-1, 1, n)
+    xt = torch.tensor(x, device=dev)
+    for alpha, beta in [(1.0, 0.0), (-0.75, 0.0), (1.5, -2.0)]:
+        yref = oracle.spmv(A, x, alpha, beta, y0)
+        bound = row_bound(A, x, alpha, beta, y0)
+        for vname, (v, shapes) in GENERAL.items():
+            for block, ipt in shapes:
+                y = torch.tensor(y0, device=dev) if beta != 0 else torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+                plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
+                assert_rows_close(y.cpu().numpy(), yref, bound,
+                                  what=f"{mname}/{vname}/b{block}i{ipt}/a{alpha}b{beta}")
+
+
+def test_named_entry_points(env):
+    xb, dev = env
+    import torch
+    A = gen.powerlaw(n=20000, seed=11)
+    plan = xb.Plan.from_host(A, dev)
+    x = np.random.default_rng(2).uniform(-1, 1, A["n"])
+    yref = oracle.spmv(A, x)
+    bound = row_bound(A, x)
+    xt = torch.tensor(x, device=dev)
+    for fn in (plan.spmv_crs, plan.spmv_segscan):
+        y = torch.empty(A["n"], dtype=torch.float64, device=dev)
+        fn(xt, y)
+        assert_rows_close(y.cpu().numpy(), yref, bound, what=fn.__name__)
+    with pytest.raises(xb.XbError):
+        plan.spmv_sym(xt, torch.empty_like(xt))
+
+
+def test_segscan_deterministic(env):
+    xb, dev = env
+    import torch
+    A = gen.powerlaw(n=50000, seed=5)
+    plan = xb.Plan.from_host(A, dev)
+    xt = torch.tensor(np.random.default_rng(3).standard_normal(A["n"]), device=dev)
+    ys = []
+    for _ in range(3):
+        y = torch.empty_like(xt)
+        plan.spmv_segscan(xt, y)
+        ys.append(y.cpu().numpy())
+    np.testing.assert_array_equal(ys[0], ys[1])
+    np.testing.assert_array_equal(ys[0], ys[2])
+
+
+def _sym_long_row():
+    n = 4000
+    U = gen.random_sym_upper(n, per_row=3, seed=21)
+    # add a dense first row (columns 0..n-1) by bookkeeping on the CRS arrays
+    rp, col, val = U["rowptr"].astype(np.int64), U["col"], U["val"]
+    first_cols = np.arange(n)
+    first_vals = np.random.default_rng(5).uniform(-1, 1, n)
+    first_vals[0] = 4.0 * n
+    rest = slice(rp[1], rp[-1])
+    col2 = np.concatenate([first_cols, col[rest]])
+    val2 = np.concatenate([first_vals, val[rest]])
+    rp2 = np.concatenate([[0], rp[1:] - rp[1] + n])
+    return dict(n=n, nnz=int(rp2[-1]), rowptr=rp2.astype(np.int32), col=col2.astype(np.int32),
+                val=val2, sym_upper=True)
+
+
+SYM = {
+    "laplace3d_20_upper": lambda: gen.laplace3d(20, upper=True),
+    "randsym3000": lambda: gen.random_sym_upper(3000, per_row=6, seed=3),
+    "sym_long_row": _sym_long_row,
+    "poisson2d_50_upper": lambda: gen.poisson2d(50, upper=True),
+}
+
+
+@pytest.mark.parametrize("mname", list(SYM))
+def test_sym_variants_match_oracle(env, mname):
+    xb, dev = env
+    import torch
+    U = SYM[mname]()
+    F = gen.full_from_upper(U)
+    n = U["n"]
+    plan = xb.Plan.from_host(U, dev)
+    rng = np.random.default_rng(9)
+    x = rng.uniform(-1, 1, n)
+    y0 = rng.uniform(-1, 1, n)
+    xt = torch.tensor(x, device=dev)
+    for alpha, beta in [(1.0, 0.0), (2.0, 0.5)]:
+        yref = oracle.spmv(U, x, alpha, beta, y0)
+        bound = row_bound(F, x, alpha, beta, y0)
+        # the symmetric-storage identity: oracle sym == oracle full
+        assert_rows_close(oracle.spmv(F, x, alpha, beta, y0), yref, bound, what="oracle sym==full")
+        for v, shapes in ((3, [(128, 1), (256, 1)]), (4, [(128, 4), (256, 8), (512, 16), (64, 1)])):
+            for block, ipt in shapes:
+                y = torch.tensor(y0, device=dev)
+                plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
+                assert_rows_close(y.cpu().numpy(), yref, bound, what=f"{mname}/v{v}/b{block}i{ipt}")
+        y = torch.tensor(y0, device=dev)
+        plan.spmv_sym(xt, y, alpha=alpha, beta=beta)
+        assert_rows_close(y.cpu().numpy(), yref, bound, what=f"{mname}/spmv_sym")
+
+
+def test_f32_path(env):
+    xb, dev = env
+    import torch
+    for A in (gen.poisson2d(40), gen.powerlaw(n=8000, seed=2)):
+        plan = xb.Plan.from_host(A, dev)
+        x = np.random.default_rng(4).uniform(-1, 1, A["n"]).astype(np.float32)
+        yo = oracle.spmv_f32(A, x)
+        Aabs = dict(A)
+        Aabs["val"] = np.abs(A["val"])
+        bound = oracle.spmv(Aabs, np.abs(x.astype(np.float64)))
+        k = np.diff(A["rowptr"]).astype(np.float64)
+        for v in (0, 1, 2):
+            y = torch.empty(A["n"], dtype=torch.float32, device=dev)
+            plan.spmv_f32(torch.tensor(x, device=dev), y, variant=v)
+            err = np.abs(y.cpu().numpy().astype(np.float64) - yo.astype(np.float64))
+            assert np.all(err <= 2 * (k + 2) * 6e-8 * bound + 1e-30), v
+
+
+def test_full_size_powerlaw_sampled(env):
+    """Config-3 size (n = 4M, lognormal rows): the tuned launch shape and each
+    general variant, checked on 3000 sampled rows that the oracle computes one
+    by one, plus exact agreement between the deterministic variants' checksums."""
+    xb, dev = env
+    import torch
+    A = gen.powerlaw(n=4_000_000, seed=3)
+    plan = xb.Plan.from_host(A, dev)
+    choice = plan.tune()
+    x = np.random.default_rng(12).uniform(-1, 1, A["n"])
+    xt = torch.tensor(x, device=dev)
+    rows = np.sort(np.random.default_rng(13).choice(A["n"], 3000, replace=False))
+    rows = np.unique(np.concatenate([rows, [0, A["n"] - 1], [int(np.argmax(np.diff(A["rowptr"])))]]))
+    yref = sampled_rows_oracle(A, x, rows)
+    S = {k: A[k] for k in A}
+    Aabs = dict(A)
+    Aabs["val"] = np.abs(A["val"])
+    bound = sampled_rows_oracle(Aabs, np.abs(x), rows)
+    for v, b, i in [(-1, 0, 0), (0, 256, 1), (1, 256, 8), (2, 256, 8), (2, 128, 16)]:
+        y = torch.empty_like(xt)
+        plan.spmv(xt, y, variant=v, block=b, ipt=i)
+        assert_rows_close(y.cpu().numpy()[rows], yref, bound, what=f"C3 v{v} b{b} i{i} ({choice})")
+
+
+def test_full_size_sym_laplace128_sampled(env):
+    """Config-2 size (128^3 Laplacian, upper storage): sym SpMV vs the oracle on
+    sampled rows of the independently generated full-storage matrix."""
+    xb, dev = env
+    import torch
+    U = gen.laplace3d(128, upper=True)
+    plan = xb.Plan.from_host(U, dev)
+    x = np.random.default_rng(5).uniform(-1, 1, U["n"])
+    xt = torch.tensor(x, device=dev)
+    F = gen.laplace3d(128)
+    rows = np.unique(np.concatenate([np.random.default_rng(6).choice(U["n"], 3000, replace=False),
+                                     [0, 127, 128 * 128, U["n"] - 1]]))
+    yref = sampled_rows_oracle(F, x, rows)
+    Fabs = dict(F)
+    Fabs["val"] = np.abs(F["val"])
+    bound = sampled_rows_oracle(Fabs, np.abs(x), rows)
+    for v, b, i in [(3, 256, 1), (4, 256, 8), (4, 512, 4)]:
+        y = torch.empty_like(xt)
+        plan.spmv(xt, y, variant=v, block=b, ipt=i)
+        assert_rows_close(y.cpu().numpy()[rows], yref, bound, what=f"C2 v{v}")
+
+
+def test_features_match_oracle(env):
+    xb, dev = env
+    import torch
+    for A in (gen.poisson2d(30), gen.powerlaw(n=5000, seed=1), gen.laplace3d(8, upper=True),
+              gen.random200(), _adversarial()):
+        raw_o, feat_o = oracle.features(A)
+        t = [torch.as_tensor(A[k], device=dev) for k in ("rowptr", "col", "val")]
+        raw_g, feat_g = xb.features(t[0].int(), t[1].int(), t[2].double(), A["sym_upper"])
+        np.testing.assert_array_equal(raw_g[[0, 1, 4, 5, 6]], raw_o[[0, 1, 4, 5, 6]])
+        np.testing.assert_allclose(raw_g[[2, 3]], raw_o[[2, 3]], rtol=1e-12)
+        np.testing.assert_allclose(feat_g, feat_o, rtol=1e-6, atol=1e-6)
+
+
+def test_bad_arguments_rejected(env):
+    xb, dev = env
+    import torch
+    A = gen.poisson2d(8)
+    plan = xb.Plan.from_host(A, dev)
+    x = torch.ones(A["n"], dtype=torch.float64, device=dev)
+    with pytest.raises(xb.XbError):
+        plan.spmv(x, x)  # aliasing
+    with pytest.raises(xb.XbError):
+        plan.spmv(x, torch.empty_like(x), variant=3)  # sym variant on general storage
+    with pytest.raises(xb.XbError):
+        plan.spmv(x, torch.empty_like(x), variant=1, block=100)
+    bad = dict(A)
+    bad["rowptr"] = A["rowptr"].copy()
+    bad["rowptr"][-1] += 1
+    with pytest.raises(xb.XbError):
+        xb.Plan.from_host(bad, dev)
