@@ -176,6 +176,26 @@ int spmv_sym(xb_plan *plan, double alpha, const double *x, double beta, double *
  * Deterministic.  XB_EINVAL if the plan is sym_upper. */
 int spmv_segscan(xb_plan *plan, double alpha, const double *x, double beta, double *y, void *stream);
 
+/* Allocation-free variant of spmv_segscan (the paper has no counterpart).
+ * For callers that cannot allocate device memory -- their device memory is
+ * owned by another allocator, or an allocation's implicit synchronisation is
+ * not allowed where they call -- and therefore cannot create a plan either.
+ * Takes the CRS arrays directly (device pointers, same rules as xb_csr with
+ * sym_upper = 0) and computes y = alpha*A*x + beta*y with the U3 kernels at a
+ * fixed shape of 256 threads x 8 non-zeros per thread.  Its scratch (16 bytes
+ * per 2048 non-zeros) lives in one 4 MiB array compiled into the library,
+ * which every GPU that loads the library holds until the process exits; it
+ * calls no cudaMalloc/cudaFree.  Limit: nnz <= 262,142 * 2048 (about 5.4e8);
+ * larger inputs return XB_EINVAL with that limit in the message.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (for example
+ * on two streams) race and must be serialised by the caller.  The result
+ * equals spmv_segscan at the same shape, bit for bit. */
+int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
+                         const double *val, double alpha, const double *x, double beta,
+                         double *y, void *stream);
+
 /* Any variant (XB_VAR_*; XB_VAR_AUTO = plan choice) with an explicit launch
  * shape (block/ipt 0 = plan choice). */
 int xb_spmv(xb_plan *plan, int32_t variant, int32_t block, int32_t ipt, double alpha,

@@ -606,3 +606,118 @@ double spmv_alg_bytes(const xb_plan *p, bool beta_nonzero, int val_bytes) {
 }
 
 }  // namespace xb
+
+// ---------------------------------------------------------------------------
+// Allocation-free segmented-scan SpMV.
+//
+// Some callers cannot call cudaMalloc at all: applications whose device
+// memory is entirely owned by another allocator (a framework that reserves
+// the free HBM at start-up and hands out sub-buffers), and code on a path
+// where an allocation's implicit device synchronisation and latency are not
+// allowed.  Such callers cannot create an xb_plan either, since a plan owns
+// device workspace.  spmv_segscan_noalloc runs the same U3 kernels with their
+// scratch (per-CTA start rows and carries) in one file-scope device array
+// instead of plan memory.  Every GPU that loads the library holds that array
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNaBlock = 256;
+constexpr int kNaIpt = 8;
+constexpr size_t kNaScratchBytes = size_t(4) << 20;  // 4 MiB
+// per CTA: start row (int) + carry row (int) + carry value (double)
+constexpr long long kNaMaxCtas = (long long)(kNaScratchBytes / 16) - 1;
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaScratchBytes];
+
+// Row holding non-zero b*T for each CTA b (last entry n).
+__global__ void k_na_rows(int n, const int *__restrict__ rowptr, long long T, int nblk,
+                          int *__restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nblk) return;
+    if (b == nblk) {
+        out[b] = n;
+        return;
+    }
+    const long long target = (long long)b * T;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (int)(((long long)lo + hi + 1) >> 1);
+        if ((long long)rowptr[mid] <= target) lo = mid;
+        else hi = mid - 1;
+    }
+    out[b] = lo;
+}
+
+// Rows without stored entries get beta*y (or 0); no other row is touched.
+__global__ void k_na_empty(int n, const int *__restrict__ rowptr, double beta, int mode,
+                           double *__restrict__ y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n || rowptr[r] != rowptr[r + 1]) return;
+    y[r] = (mode == 2) ? beta * y[r] : 0.0;
+}
+
+// Device address of the scratch array, looked up once per device.
+int na_scratch(unsigned char **out) {
+    static std::mutex mu;
+    static unsigned char *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return xb::cuda_error(e, "spmv_segscan_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess)
+            return xb::cuda_error(e, "spmv_segscan_noalloc: cudaGetSymbolAddress(scratch)");
+        addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = addr[dev];
+    return XB_OK;
+}
+
+}  // namespace
+
+extern "C" int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr,
+                                    const int32_t *col, const double *val, double alpha,
+                                    const double *x, double beta, double *y, void *stream) {
+    if (n < 0 || nnz < 0) return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: n=%d nnz=%d", n, nnz);
+    if (n == 0) return XB_OK;
+    if (!rowptr || !x || !y || (nnz > 0 && (!col || !val)))
+        return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: NULL array");
+    if ((const void *)x == (const void *)y)
+        return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: x and y must not alias");
+    const long long T = (long long)kNaBlock * kNaIpt;
+    const long long nblk = ((long long)nnz + T - 1) / T;
+    if (nblk + 1 > kNaMaxCtas)
+        return xb::set_error(XB_EINVAL,
+                             "spmv_segscan_noalloc: nnz=%d needs %lld scratch slots; the built-in "
+                             "scratch holds %lld (nnz <= %lld)", nnz, nblk + 1, kNaMaxCtas,
+                             (kNaMaxCtas - 1) * T);
+    unsigned char *base = nullptr;
+    XB_TRY(na_scratch(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int mode = (beta == 0.0) ? (alpha == 1.0 ? 0 : 1) : 2;
+    int *brow = reinterpret_cast<int *>(base);
+    int *crow = brow + (nblk + 1);
+    double *cval = reinterpret_cast<double *>(base + 8 * (size_t)(nblk + 1));
+    if (nblk > 0) {
+        k_na_rows<<<(int)((nblk + 1 + 255) / 256), 256, 0, s>>>(n, rowptr, T, (int)nblk, brow);
+        XB_LAUNCHED("k_na_rows");
+        const int TP = (int)T + kNaBlock;
+        const size_t sm = (size_t)TP * sizeof(double) + 64 * sizeof(double) + (size_t)TP * 4 +
+                          (size_t)(T + 2) * 4 + 64 * 4;
+        XB_TRY(smem_optin((const void *)k_seg<double, kNaIpt>, sm));
+        k_seg<double, kNaIpt><<<(int)nblk, kNaBlock, sm, s>>>(n, nnz, rowptr, col, val, x, alpha,
+                                                              beta, mode, y, brow, cval, crow,
+                                                              nullptr);
+        XB_LAUNCHED("k_seg (noalloc)");
+        k_seg_fix<double><<<(int)((nblk + 255) / 256), 256, 0, s>>>((int)nblk, n, crow, cval,
+                                                                     alpha, mode, y, nullptr);
+        XB_LAUNCHED("k_seg_fix (noalloc)");
+    }
+    k_na_empty<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, beta, mode, y);
+    XB_LAUNCHED("k_na_empty");
+    return XB_OK;
+}
