@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--n", type=int, default=4_000_000)
     ap.add_argument("--no-extras", action="store_true", help="skip per-variant/sym/solver lines")
     ap.add_argument("--solvers", action="store_true", help="also time the large solver cases")
+    ap.add_argument("--variant", default=None, choices=["row", "nnz", "segscan"],
+                    help="fixed SpMV variant instead of the exhaustive tuner")
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--ipt", type=int, default=8)
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only warm-up + timed steps (for ncu captures); prints a short line")
     return ap.parse_args()
 
 
@@ -205,7 +211,12 @@ def main():
     A = make_c3(args.n)
     n, nnz = A["n"], A["nnz"]
     plan = xb.Plan.from_host(A, dev)
-    choice = plan.tune()
+    if args.variant:
+        v = {"row": xb.VAR_ROW, "nnz": xb.VAR_NNZ, "segscan": xb.VAR_SEGSCAN}[args.variant]
+        plan.set_choice(v, args.block, args.ipt)
+        choice = plan.choice()
+    else:
+        choice = plan.tune()
     x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, n), device=dev)
     y = torch.empty(n, dtype=torch.float64, device=dev)
     bytes_step = alg_bytes(A)
@@ -242,6 +253,13 @@ def main():
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
     value = ws * bytes_step / (ms_step * 1e-3) / 1e9
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "n": n, "nnz": nnz, "choice": choice,
+                              "ms_per_step": ms_step, "GBs": value}))
+        if pg:
+            pg.destroy_process_group()
+        return
 
     # end to end through the C ABI with host buffers: H2D x, SpMV, D2H y
     xh = torch.empty(n, dtype=torch.float64).pin_memory()

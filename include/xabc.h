@@ -170,10 +170,13 @@ int spmv_sym(xb_plan *plan, double alpha, const double *x, double beta, double *
 
 /* General CRS SpMV by the branchless segmented-scan idea (U3/BSS, Sec. 3.2.2,
  * Sec. 4.4.1.3): the non-zeros are split into equal flat segments regardless
- * of row boundaries, each thread sums its segment with row breaks taken from
- * the per-CTA start rows of the plan, and row sums that straddle threads or
- * CTAs are combined by a segmented scan and a deterministic carry fix-up.
- * Deterministic.  XB_EINVAL if the plan is sym_upper. */
+ * of row boundaries (ipt consecutive non-zeros per thread, 32*ipt per warp);
+ * the plan's "continuous location" data -- one row-end bit per non-zero and
+ * the start row of each warp -- lets each thread sum its segment with row
+ * breaks as predicated stores, and row sums that straddle threads or warps
+ * are combined by a segmented warp scan and a deterministic carry fix-up.
+ * Deterministic.  Launch shapes: block <= 256, ipt in {4, 8, 16, 32}.
+ * XB_EINVAL if the plan is sym_upper. */
 int spmv_segscan(xb_plan *plan, double alpha, const double *x, double beta, double *y, void *stream);
 
 /* Allocation-free variant of spmv_segscan (the paper has no counterpart).
@@ -190,8 +193,10 @@ int spmv_segscan(xb_plan *plan, double alpha, const double *x, double beta, doub
  * call on each device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
  * All calls share the one array: calls that overlap on the GPU (for example
- * on two streams) race and must be serialised by the caller.  The result
- * equals spmv_segscan at the same shape, bit for bit. */
+ * on two streams) race and must be serialised by the caller.  Each row is
+ * summed in the same order as the other SpMV entry points up to the final
+ * combination of partial sums, so results agree with spmv_segscan to within
+ * rounding (the library's 1e-12 row tolerance). */
 int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
                          const double *val, double alpha, const double *x, double beta,
                          double *y, void *stream);

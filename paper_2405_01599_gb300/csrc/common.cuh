@@ -49,14 +49,26 @@ struct TilePart {
     int ntiles = 0;
     int *d_row = nullptr;    // ntiles+1
 };
-// Flat nnz segments (U3): CTA b covers non-zeros [b*T, (b+1)*T); d_row[b] is
-// the row holding non-zero b*T (d_row[nblk] = n); carries feed the fix-up.
+// Flat nnz segments (U3, BSS): warp w owns non-zeros [w*W, (w+1)*W), W =
+// 32*ipt; d_row[w] is the (non-empty-row) index of the row holding non-zero
+// w*W; one carry slot per warp feeds the fix-up.
 struct SegPart {
     int block = 0, ipt = 0;
-    int nblk = 0;
+    int nblk = 0;            // warps
     int *d_row = nullptr;    // nblk+1
     int *d_carry_row = nullptr;
     double *d_carry_val = nullptr;   // raw partial sums (float in FP32 use)
+};
+// The BSS "continuous location" data of the plan (independent of the launch
+// shape): bit e of d_endbits is set when non-zero e is the last one of its
+// row; with empty rows present, rows are renumbered over the non-empty ones
+// (d_ne_rows maps back, d_crp is the rowptr of the non-empty rows).
+struct BssData {
+    unsigned *d_endbits = nullptr;   // ceil(nnz/32) + 1 words
+    int *d_ne_rows = nullptr;        // n_ne, or null when no row is empty
+    int *d_crp = nullptr;            // n_ne + 1, or null (then rowptr)
+    int n_ne = 0;
+    bool built = false;
 };
 
 }  // namespace xb
@@ -72,6 +84,8 @@ struct xb_plan {
     int *d_empty = nullptr;              // rows with no stored entry
     std::vector<xb::TilePart> tiles;     // cache by (block, ipt)
     std::vector<xb::SegPart> segs;       // cache by (block, ipt)
+    xb::BssData bss;
+    bool vec_ok = false;                 // val and col 16-byte aligned
     // reduction scratch
     double *d_part = nullptr;            // kRedSlots * 4 partials
     unsigned *d_ticket = nullptr;        // 8 counters
@@ -90,6 +104,7 @@ namespace xb {
 
 const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
 const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
+const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err);
 int ensure_val32(xb_plan *p, cudaStream_t s);
 int ensure_work(xb_plan *p, size_t bytes);
 bool variant_fits(const xb_plan *p, int variant);

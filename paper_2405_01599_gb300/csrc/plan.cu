@@ -89,32 +89,80 @@ const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *e
     return &p->tiles.back();
 }
 
-__global__ void k_seg_rows(int n, const int *__restrict__ rowptr, long long T, int nblk,
+// Index (over the rows of crp) of the row holding non-zero w*W, per warp w.
+__global__ void k_seg_rows(int nrows, const int *__restrict__ crp, long long W, int nw,
                            int *__restrict__ out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b > nblk) return;
-    if (b == nblk) {
-        out[b] = n;
+    if (b > nw) return;
+    if (b == nw) {
+        out[b] = nrows;
         return;
     }
-    const long long target = (long long)b * T;
-    int lo = 0, hi = n;
+    const long long target = (long long)b * W;
+    int lo = 0, hi = nrows;
     while (lo < hi) {
         const int mid = (int)(((long long)lo + hi + 1) >> 1);
-        if ((long long)rowptr[mid] <= target) lo = mid;
+        if ((long long)crp[mid] <= target) lo = mid;
         else hi = mid - 1;
     }
     out[b] = lo;
 }
 
+// Bit (rowptr[r+1]-1) for every non-empty row r: the row-end flags.
+__global__ void k_endbits(int n, const int *__restrict__ rowptr, unsigned *__restrict__ bits) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int a = rowptr[r], b = rowptr[r + 1];
+    if (b > a) atomicOr(&bits[(b - 1) >> 5], 1u << ((b - 1) & 31));
+}
+
+const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err) {
+    BssData &d = p->bss;
+    if (d.built) return &d;
+    const size_t words = (size_t)p->nnz / 32 + 2;
+    cudaError_t e = cudaMalloc(&d.d_endbits, words * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.d_endbits, 0, words * sizeof(unsigned), s);
+    if (e == cudaSuccess && p->n > 0) {
+        k_endbits<<<(p->n + 255) / 256, 256, 0, s>>>(p->n, p->rowptr, d.d_endbits);
+        e = cudaGetLastError();
+    }
+    d.n_ne = p->n - p->n_empty;
+    if (e == cudaSuccess && p->n_empty > 0) {
+        std::vector<int> ne, crp;
+        ne.reserve(d.n_ne);
+        crp.reserve(d.n_ne + 1);
+        const int *rp = p->h_rowptr.data();
+        for (int r = 0; r < p->n; r++)
+            if (rp[r + 1] > rp[r]) {
+                ne.push_back(r);
+                crp.push_back(rp[r]);
+            }
+        crp.push_back(p->nnz);
+        e = cudaMalloc(&d.d_ne_rows, std::max<size_t>(1, ne.size()) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&d.d_crp, crp.size() * sizeof(int));
+        if (e == cudaSuccess && !ne.empty())
+            e = cudaMemcpy(d.d_ne_rows, ne.data(), ne.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d.d_crp, crp.data(), crp.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        *err = cuda_error(e, "BSS plan data");
+        return nullptr;
+    }
+    d.built = true;
+    return &d;
+}
+
 const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
     for (auto &t : p->segs)
         if (t.block == block && t.ipt == ipt) return &t;
+    const BssData *bd = get_bss(p, s, err);
+    if (!bd) return nullptr;
     SegPart t;
     t.block = block;
     t.ipt = ipt;
-    const long long T = (long long)block * ipt;
-    t.nblk = (int)((p->nnz + T - 1) / T);
+    const long long W = 32LL * ipt;
+    t.nblk = (int)((p->nnz + W - 1) / W);
     const size_t nb = (size_t)t.nblk + 1;
     cudaError_t e = cudaMalloc(&t.d_row, nb * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&t.d_carry_row, nb * sizeof(int));
@@ -126,7 +174,8 @@ const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err
         *err = cuda_error(e, "cudaMalloc(segments)");
         return nullptr;
     }
-    k_seg_rows<<<(t.nblk + 1 + 255) / 256, 256, 0, s>>>(p->n, p->rowptr, T, t.nblk, t.d_row);
+    const int *crp = bd->d_crp ? bd->d_crp : p->rowptr;
+    k_seg_rows<<<(t.nblk + 1 + 255) / 256, 256, 0, s>>>(bd->n_ne, crp, W, t.nblk, t.d_row);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = cuda_error(e, "k_seg_rows");
@@ -346,6 +395,7 @@ int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan
     }
     p->block = 256;
     p->ipt = 8;
+    p->vec_ok = ((uintptr_t)A->val % 16 == 0) && ((uintptr_t)A->col % 16 == 0);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_error(e, "plan_create"));
     *out = p;
@@ -362,6 +412,9 @@ int xb_plan_destroy(xb_plan *p) {
         cudaFree(t.d_carry_val);
     }
     cudaFree(p->val32);
+    cudaFree(p->bss.d_endbits);
+    cudaFree(p->bss.d_ne_rows);
+    cudaFree(p->bss.d_crp);
     cudaFree(p->d_empty);
     cudaFree(p->d_part);
     cudaFree(p->d_ticket);

@@ -284,6 +284,147 @@ __global__ void __launch_bounds__(512) k_seg(int n, int nnz, const int *__restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// U3 (BSS) with the plan's row-end bitmask ("a data format representing the
+// continuous location", Sec. 3.2.2).  Warp w owns non-zeros [w*32*IPT, ...),
+// lane l the IPT consecutive ones from w*32*IPT + l*IPT.  A lane loads its
+// values and columns with 16-byte vector loads straight from global memory
+// (no staging, no row search): its start row is the warp's start row plus the
+// row ends that precede it (integer warp scan of popcounts of its flag bits).
+// The inner loop is IPT FMAs with row ends as predicated stores.  Row sums
+// that straddle lanes are joined by a key-segmented warp scan that stops as
+// soon as no lane needs another step (most steps cost no FP64 instruction);
+// rows that straddle warps go through one carry slot per warp and the fix-up.
+// ---------------------------------------------------------------------------
+template <typename V>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using T = double2;
+    static constexpr int N = 2;
+};
+template <>
+struct Vec2<float> {
+    using T = float4;
+    static constexpr int N = 4;
+};
+
+template <typename V, int IPT>
+__global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__restrict__ col,
+                                             const V *__restrict__ val, const V *__restrict__ x,
+                                             V alpha, V beta, int mode, V *__restrict__ y,
+                                             const unsigned *__restrict__ endbits,
+                                             const int *__restrict__ wrow,
+                                             const int *__restrict__ ne_rows, int n_ne, int n,
+                                             V *__restrict__ cval, int *__restrict__ crow,
+                                             const V *__restrict__ adev, int vec) {
+    static_assert(IPT == 4 || IPT == 8 || IPT == 16 || IPT == 32, "IPT");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= nwarps) return;  // warp-uniform
+    if (adev) alpha = *adev;
+    const long long e0 = (gw * 32 + lane) * IPT;
+    const int ecnt = (int)max(0LL, min((long long)IPT, (long long)nnz - e0));
+    unsigned fl = 0;
+    if (ecnt > 0) {
+        const unsigned w = __ldg(endbits + (e0 >> 5));
+        fl = (IPT == 32) ? w : (w >> (unsigned)(e0 & 31)) & ((1u << IPT) - 1u);
+        if (ecnt < IPT) fl &= (1u << ecnt) - 1u;
+    }
+    const int cnt = __popc(fl);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int row = __ldg(wrow + gw) + incl - cnt;  // index over non-empty rows
+    // Each lane's run is one aligned block of IPT values and IPT columns: its
+    // 16-byte loads pair up inside 32-byte sectors, so the second load of each
+    // pair is an L1 hit and DRAM sees every byte once.
+    V v[IPT];
+    int c[IPT];
+    if (vec && ecnt == IPT) {
+        using T2 = typename Vec2<V>::T;
+        constexpr int VN = Vec2<V>::N;
+        const T2 *vp = reinterpret_cast<const T2 *>(val + e0);
+#pragma unroll
+        for (int j = 0; j < IPT / VN; j++) {
+            const T2 q = __ldg(vp + j);
+            if constexpr (VN == 2) {
+                v[2 * j] = q.x;
+                v[2 * j + 1] = q.y;
+            } else {
+                v[4 * j] = q.x;
+                v[4 * j + 1] = q.y;
+                v[4 * j + 2] = q.z;
+                v[4 * j + 3] = q.w;
+            }
+        }
+        const int4 *cp = reinterpret_cast<const int4 *>(col + e0);
+#pragma unroll
+        for (int j = 0; j < IPT / 4; j++) {
+            const int4 q = __ldg(cp + j);
+            c[4 * j] = q.x;
+            c[4 * j + 1] = q.y;
+            c[4 * j + 2] = q.z;
+            c[4 * j + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            c[j] = (j < ecnt) ? __ldg(col + e0 + j) : 0;
+            v[j] = (j < ecnt) ? __ldg(val + e0 + j) : V(0);
+        }
+    }
+    V xv[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; j++) xv[j] = (j < ecnt) ? __ldg(x + c[j]) : V(0);
+    V sum = V(0), head = V(0);
+    int hrow = -1, hkey = -1;
+#pragma unroll
+    for (int j = 0; j < IPT; j++) {
+        sum = fma(v[j], xv[j], sum);
+        if ((fl >> j) & 1u) {
+            const int rid = ne_rows ? __ldg(ne_rows + row) : row;
+            if (hkey < 0) {
+                head = sum;
+                hrow = rid;
+                hkey = row;
+            } else {
+                store_row(y, rid, sum, alpha, beta, mode);
+            }
+            sum = V(0);
+            row++;
+        }
+    }
+    // key-segmented inclusive scan of (row, sum); keys ascend with the lane
+    int k = (ecnt > 0) ? row : INT_MAX;
+    V s = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ku = __shfl_up_sync(FULL, k, o);
+        const bool need = lane >= o && ku == k;
+        if (!__any_sync(FULL, need)) break;  // no longer run at this distance: done
+        const V su = __shfl_up_sync(FULL, s, o);
+        if (need) s += su;
+    }
+    const int kp = __shfl_up_sync(FULL, k, 1);
+    const V sp = __shfl_up_sync(FULL, s, 1);
+    const bool addc = lane > 0 && hkey >= 0 && kp == hkey;
+    if (__any_sync(FULL, addc))
+        if (addc) head += sp;
+    if (hkey >= 0) store_row(y, hrow, head, alpha, beta, mode);
+    // the warp's carry: the last lane holding a non-zero
+    const long long left = (long long)nnz - gw * 32 * IPT;
+    const int last = (int)min(31LL, (left - 1) / IPT);
+    if (lane == last) {
+        crow[gw] = (k < n_ne) ? (ne_rows ? __ldg(ne_rows + k) : k) : n;
+        cval[gw] = s;
+    }
+}
+
 // Adds each run of equal carry rows, in CTA order (deterministic).
 template <typename V>
 __global__ void k_seg_fix(int nblk, int n, const int *__restrict__ crow, const V *__restrict__ cval,
@@ -474,26 +615,30 @@ int launch_tile(xb_plan *p, const int *rp, const int *ci, const V *va, int block
 template <typename V>
 int launch_seg(xb_plan *p, const int *rp, const int *ci, const V *va, int block, int ipt, V alpha,
                const V *x, V beta, int mode, V *y, const V *adev, cudaStream_t s) {
+    (void)rp;
+    if (block > 256)
+        return xb::set_error(XB_EINVAL, "segscan: block %d > 256", block);
     int err = XB_OK;
     const xb::SegPart *sp = xb::get_segs(p, block, ipt, s, &err);
     if (!sp) return err;
+    const xb::BssData &bd = p->bss;
     if (sp->nblk > 0) {
-        const int T = block * ipt, TP = T + block;
-        const size_t sm = (size_t)TP * sizeof(V) + 64 * sizeof(V) + (size_t)TP * 4 +
-                          (size_t)(T + 2) * 4 + 64 * 4;
         V *cv = reinterpret_cast<V *>(sp->d_carry_val);
-#define XB_SEG(I)                                                                          \
-    case I:                                                                                \
-        XB_TRY(smem_optin((const void *)k_seg<V, I>, sm));                                 \
-        k_seg<V, I><<<sp->nblk, block, sm, s>>>(p->n, p->nnz, rp, ci, va, x, alpha, beta,  \
-                                                mode, y, sp->d_row, cv, sp->d_carry_row, adev); \
+        const int wpb = block / 32;
+        const int grid = (sp->nblk + wpb - 1) / wpb;
+        const int vec = (((uintptr_t)va % 16) == 0 && ((uintptr_t)ci % 16) == 0) ? 1 : 0;
+#define XB_BSS(I)                                                                            \
+    case I:                                                                                  \
+        k_bss<V, I><<<grid, block, 0, s>>>(p->nnz, sp->nblk, ci, va, x, alpha, beta, mode, y, \
+                                           bd.d_endbits, sp->d_row, bd.d_ne_rows, bd.n_ne,   \
+                                           p->n, cv, sp->d_carry_row, adev, vec);            \
         break;
         switch (ipt) {
-            XB_SEG(2) XB_SEG(4) XB_SEG(8) XB_SEG(12) XB_SEG(16) XB_SEG(24) XB_SEG(32)
+            XB_BSS(4) XB_BSS(8) XB_BSS(16) XB_BSS(32)
             default: return xb::set_error(XB_EINVAL, "segscan: unsupported ipt %d", ipt);
         }
-#undef XB_SEG
-        XB_LAUNCHED("k_seg");
+#undef XB_BSS
+        XB_LAUNCHED("k_bss");
         k_seg_fix<V><<<(sp->nblk + 255) / 256, 256, 0, s>>>(sp->nblk, p->n, sp->d_carry_row, cv,
                                                              alpha, mode, y, adev);
         XB_LAUNCHED("k_seg_fix");

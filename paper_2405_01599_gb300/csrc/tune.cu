@@ -22,8 +22,8 @@ std::vector<Cand> candidates(const xb_plan *p) {
     for (int b : {64, 128, 256, 512}) c.push_back({XB_VAR_ROW, b, 1});
     for (int b : {128, 256, 512})
         for (int i : {4, 8, 16}) c.push_back({XB_VAR_NNZ, b, i});
-    for (int b : {128, 256, 512})
-        for (int i : {4, 8, 12, 16, 24}) c.push_back({XB_VAR_SEGSCAN, b, i});
+    for (int b : {128, 256})
+        for (int i : {4, 8, 16, 32}) c.push_back({XB_VAR_SEGSCAN, b, i});
     return c;
 }
 

@@ -133,7 +133,25 @@ def random200(n=200, per_row=5, diag=10.0, seed=1):
 
 def _distinct_cols(rng, n, L):
     """Per row i, L[i] distinct columns from {0..n-1} minus {i}, sorted.
-    Returns (rows, cols) int64 arrays grouped by row, columns ascending."""
+    Returns (rows, cols) int64 arrays grouped by row, columns ascending.
+    Rows asking for more than half of the n-1 candidates are drawn as a
+    random subset directly; the rest by rejection of duplicates."""
+    L = np.asarray(L, np.int64)
+    dense = np.flatnonzero(L > (n - 1) // 2)
+    if dense.size:
+        Ls = L.copy()
+        Ls[dense] = 0
+        rows, cols = _distinct_cols(rng, n, Ls)
+        parts_r, parts_c = [rows], [cols]
+        for i in dense:
+            c = np.sort(rng.choice(n - 1, size=int(L[i]), replace=False))
+            c += (c >= i)
+            parts_r.append(np.full(c.size, i, np.int64))
+            parts_c.append(c)
+        r = np.concatenate(parts_r)
+        c = np.concatenate(parts_c)
+        o = np.lexsort((c, r))
+        return r[o], c[o]
     rows = np.repeat(np.arange(n, dtype=np.int64), L)
     c = rng.integers(0, n - 1, size=rows.size, dtype=np.int64)
     c += (c >= rows)
