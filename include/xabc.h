@@ -253,6 +253,11 @@ int xb_mgs(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, dou
  * plan's choice and returns it in *out (may be NULL). */
 int xb_tune_exhaustive(xb_plan *plan, xb_choice *out, void *stream);
 
+/* The sweep behind xb_tune_exhaustive: every candidate that fits, with its
+ * best time, written to the HOST array out (at most cap entries); *count
+ * receives the number of candidates timed.  Does not change the plan. */
+int xb_tune_sweep(xb_plan *plan, xb_choice *out, int32_t cap, int32_t *count, void *stream);
+
 /* MM ratio of Eq. (1): R(s,t) = max / min of r(s-t+1..s), r 1-based on the
  * HOST array r (r[z-1] = r(z)); 1 <= t <= s.  Returns +inf for a zero min. */
 double xb_mm_ratio(const double *r, int32_t s, int32_t t);
@@ -266,6 +271,53 @@ int xb_dafrt(int32_t I, const double *samp, double theta);
  * feat[8] = ln(1+n), ln(1+nnz), ln(1+mean), ln(1+var), ln(1+max),
  * ln(1+bandwidth), sym, ln(1+max) - ln(1+mean).  Either output may be NULL. */
 int xb_features(const xb_csr *A, double *raw, float *feat, void *stream);
+
+/* ---- learned tuner: MLP with hand-written training and inference kernels --
+ * d_in -> h1 (ReLU) -> h2 (ReLU) -> sum(heads) logits, one softmax
+ * cross-entropy per head; FP32 parameters on the device.  Inputs are
+ * standardised by (x - mu) / sd (identity until xb_mlp_set_norm).  Parameter
+ * blob layout: W1[h1][d_in], b1[h1], W2[h2][h1], b2[h2], W3[o][h2], b3[o],
+ * o = sum(heads).  Every batch reduction is a fixed-order loop, so results
+ * are deterministic.  d_in <= 16, nheads <= 8, each head >= 2 classes. */
+typedef struct xb_mlp xb_mlp;
+int xb_mlp_create(int32_t d_in, int32_t h1, int32_t h2, int32_t nheads, const int32_t *heads,
+                  uint64_t seed, xb_mlp **out);
+int xb_mlp_destroy(xb_mlp *m);
+int64_t xb_mlp_param_count(const xb_mlp *m);
+/* Parameters host <-> device (host pointer, param_count floats). */
+int xb_mlp_get_params(const xb_mlp *m, float *host);
+int xb_mlp_set_params(xb_mlp *m, const float *host);
+/* Input standardisation (host arrays of d_in floats, sd > 0). */
+int xb_mlp_set_norm(xb_mlp *m, const float *mu, const float *sd);
+/* Forward: X device [B][d_in] FP32 -> logits device [B][o]. */
+int xb_mlp_forward(xb_mlp *m, const float *X, int32_t B, float *logits, void *stream);
+/* Mean over the batch of the summed per-head softmax cross-entropy, and its
+ * gradient (kept in the model for xb_mlp_adam; copied to the DEVICE array
+ * grad_out when it is not NULL).  labels: device [B][nheads].  *loss: host. */
+int xb_mlp_loss_grad(xb_mlp *m, const float *X, const int32_t *labels, int32_t B, float *loss,
+                     float *grad_out, void *stream);
+/* One Adam step (Kingma & Ba; t counts from 1) with the stored gradient. */
+int xb_mlp_adam(xb_mlp *m, int32_t t, float lr, float b1, float b2, float eps, void *stream);
+/* Minibatch Adam training on device data X [N][d_in], labels [N][nheads]:
+ * `epochs` passes in a seeded shuffled order; *final_loss (host, may be
+ * NULL) receives the full-set loss after training. */
+int xb_mlp_train(xb_mlp *m, const float *X, const int32_t *labels, int32_t N, int32_t epochs,
+                 int32_t batch, float lr, uint64_t seed, float *final_loss, void *stream);
+/* Argmax per head: out_host [B][nheads]. */
+int xb_mlp_predict(xb_mlp *m, const float *X, int32_t B, int32_t *out_host, void *stream);
+/* Binary model file (header, standardisation, parameters). */
+int xb_mlp_save(const xb_mlp *m, const char *path);
+int xb_mlp_load(const char *path, xb_mlp **out);
+
+/* Learned run-time tuning: features of A (xb_features) through the model,
+ * whose heads are (variant: 5 classes XB_VAR_0..4, CTA size: 64/128/256/512,
+ * items per thread: 1/4/8/16/32, GMRES restart m: 10/20/30/50/80/120).  The
+ * arg-max over the choices that fit the plan's storage and the variant's
+ * supported shapes becomes the plan's choice (returned in *out); *m_out (may
+ * be NULL) receives the predicted restart length.  A must be the matrix the
+ * plan was built on. */
+int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, int32_t *m_out,
+                void *stream);
 
 #ifdef __cplusplus
 }

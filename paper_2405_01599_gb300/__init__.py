@@ -102,6 +102,21 @@ def lib():
         "xb_mm_ratio": (f64, [P(f64), i32, i32]),
         "xb_dafrt": (i32, [i32, P(f64), f64]),
         "xb_features": (i32, [P(Csr), P(f64), P(f32), vp]),
+        "xb_tune_sweep": (i32, [vp, P(Choice), i32, P(i32), vp]),
+        "xb_tune_mlp": (i32, [vp, P(Csr), vp, P(Choice), P(i32), vp]),
+        "xb_mlp_create": (i32, [i32, i32, i32, i32, P(i32), C.c_uint64, P(vp)]),
+        "xb_mlp_destroy": (i32, [vp]),
+        "xb_mlp_param_count": (C.c_int64, [vp]),
+        "xb_mlp_get_params": (i32, [vp, P(f32)]),
+        "xb_mlp_set_params": (i32, [vp, P(f32)]),
+        "xb_mlp_set_norm": (i32, [vp, P(f32), P(f32)]),
+        "xb_mlp_forward": (i32, [vp, vp, i32, vp, vp]),
+        "xb_mlp_loss_grad": (i32, [vp, vp, vp, i32, P(f32), vp, vp]),
+        "xb_mlp_adam": (i32, [vp, i32, f32, f32, f32, f32, vp]),
+        "xb_mlp_train": (i32, [vp, vp, vp, i32, i32, i32, f32, C.c_uint64, P(f32), vp]),
+        "xb_mlp_predict": (i32, [vp, vp, i32, P(i32), vp]),
+        "xb_mlp_save": (i32, [vp, C.c_char_p]),
+        "xb_mlp_load": (i32, [C.c_char_p, P(vp)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -256,6 +271,23 @@ class Plan:
         _check(lib().xb_plan_get_choice(self._h, C.byref(c)))
         return dict(variant=c.variant, block=c.block, ipt=c.ipt, ms=c.ms)
 
+    def sweep(self, stream=None):
+        """Every SpMV candidate with its best time (list of dicts)."""
+        cap = 64
+        arr = (Choice * cap)()
+        cnt = C.c_int32()
+        _check(lib().xb_tune_sweep(self._h, arr, cap, C.byref(cnt), _stream(stream)))
+        return [dict(variant=arr[i].variant, block=arr[i].block, ipt=arr[i].ipt, ms=arr[i].ms)
+                for i in range(min(cnt.value, cap))]
+
+    def tune_mlp(self, model, stream=None):
+        """Learned tuning: returns (choice dict, predicted restart length m)."""
+        c = Choice()
+        m = C.c_int32()
+        _check(lib().xb_tune_mlp(self._h, C.byref(self._csr), model._h, C.byref(c), C.byref(m),
+                                 _stream(stream)))
+        return dict(variant=c.variant, block=c.block, ipt=c.ipt), m.value
+
     # ---- vector ops ----
     def dot(self, x, y, stream=None):
         import torch
@@ -295,3 +327,111 @@ def mm_ratio(r, s, t):
 def dafrt(samp, theta):
     arr = (C.c_double * len(samp))(*samp)
     return lib().xb_dafrt(len(samp), arr, theta)
+
+
+TUNER_HEADS = (5, 4, 5, 6)          # variant, CTA size, items per thread, restart m
+TUNER_BLOCKS = (64, 128, 256, 512)
+TUNER_IPTS = (1, 4, 8, 16, 32)
+TUNER_RESTARTS = (10, 20, 30, 50, 80, 120)
+
+
+class Mlp:
+    """The learned tuner's MLP; every forward/backward/update step runs in the
+    library's CUDA kernels."""
+
+    def __init__(self, d_in=8, h1=64, h2=64, heads=TUNER_HEADS, seed=0, _handle=None):
+        if _handle is not None:
+            self._h = _handle
+        else:
+            hs = (C.c_int32 * len(heads))(*heads)
+            h = C.c_void_p()
+            _check(lib().xb_mlp_create(d_in, h1, h2, len(heads), hs, seed, C.byref(h)))
+            self._h = h
+        self.dims = (d_in, h1, h2, tuple(heads))
+
+    @classmethod
+    def load(cls, path):
+        h = C.c_void_p()
+        _check(lib().xb_mlp_load(path.encode(), C.byref(h)))
+        import struct
+        with open(path, "rb") as f:
+            f.read(8)
+            d_in, h1, h2, nh = struct.unpack("4i", f.read(16))
+            heads = struct.unpack("8i", f.read(32))[:nh]
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.dims = (d_in, h1, h2, tuple(heads))
+        return obj
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xb_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def param_count(self):
+        return int(lib().xb_mlp_param_count(self._h))
+
+    def get_params(self):
+        import numpy as np
+        P = np.zeros(self.param_count(), np.float32)
+        _check(lib().xb_mlp_get_params(self._h, P.ctypes.data_as(C.POINTER(C.c_float))))
+        return P
+
+    def set_params(self, P):
+        import numpy as np
+        P = np.ascontiguousarray(P, np.float32)
+        _check(lib().xb_mlp_set_params(self._h, P.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def set_norm(self, mu, sd):
+        import numpy as np
+        mu = np.ascontiguousarray(mu, np.float32)
+        sd = np.ascontiguousarray(sd, np.float32)
+        _check(lib().xb_mlp_set_norm(self._h, mu.ctypes.data_as(C.POINTER(C.c_float)),
+                                     sd.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def forward(self, X, stream=None):
+        import torch
+        _need(X, torch.float32, "X")
+        out = torch.empty((X.shape[0], sum(self.dims[3])), dtype=torch.float32, device=X.device)
+        _check(lib().xb_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def loss_grad(self, X, labels, stream=None):
+        import torch
+        _need(X, torch.float32, "X")
+        _need(labels, torch.int32, "labels")
+        g = torch.empty(self.param_count(), dtype=torch.float32, device=X.device)
+        loss = C.c_float()
+        _check(lib().xb_mlp_loss_grad(self._h, _ptr(X), _ptr(labels), X.shape[0], C.byref(loss),
+                                      _ptr(g), _stream(stream)))
+        return loss.value, g
+
+    def adam(self, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        _check(lib().xb_mlp_adam(self._h, t, lr, b1, b2, eps, _stream(stream)))
+
+    def train(self, X, labels, epochs=200, batch=256, lr=3e-3, seed=0, stream=None):
+        import torch
+        _need(X, torch.float32, "X")
+        _need(labels, torch.int32, "labels")
+        loss = C.c_float()
+        _check(lib().xb_mlp_train(self._h, _ptr(X), _ptr(labels), X.shape[0], epochs, batch, lr,
+                                  seed, C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def predict(self, X, stream=None):
+        import numpy as np
+        import torch
+        _need(X, torch.float32, "X")
+        out = np.zeros((X.shape[0], len(self.dims[3])), np.int32)
+        _check(lib().xb_mlp_predict(self._h, _ptr(X), X.shape[0],
+                                    out.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream)))
+        return out
+
+    def save(self, path):
+        _check(lib().xb_mlp_save(self._h, path.encode()))

@@ -1,0 +1,43 @@
+"""What the learned tuner gains over the method without it (GPU, live).
+
+Held-out matrices (a seed the training data never used) are swept by the
+exhaustive tuner; the committed model (trained by the library's own kernels
+on 20k sweep timings) picks a configuration from the features alone.  It must
+beat the untuned default (the STABLE policy: fixed variant, 256 x 8, m = 30)
+and stay close to the exhaustive optimum."""
+import os
+
+import numpy as np
+import pytest
+
+from tests._gpu import lib_and_device
+
+pytestmark = pytest.mark.gpu
+
+
+def test_learned_tuner_beats_default_on_held_out():
+    xb, dev = lib_and_device()
+    from paper_2405_01599_gb300 import tuner
+    model = xb.Mlp.load(tuner.MODEL_PATH)
+    D = tuner.make_data(24, seed=901, log_every=0)
+    summ, per = tuner.evaluate(model, D)
+    print(summ)
+    assert summ["variant_acc"] >= 0.8
+    assert summ["spmv_regret"] <= 1.15          # close to the exhaustive optimum
+    assert summ["spmv_gain_vs_default"] >= 1.05  # faster than no tuning
+    assert summ["m_regret"] <= 1.6
+
+
+def test_tune_mlp_entry_point_matches_python_prediction():
+    xb, dev = lib_and_device()
+    import torch
+    from paper_2405_01599_gb300 import gen, tuner
+    model = xb.Mlp.load(tuner.MODEL_PATH)
+    A = gen.powerlaw(n=150000, seed=77)
+    plan = xb.Plan.from_host(A, dev)
+    ch, m = plan.tune_mlp(model)
+    t = [torch.as_tensor(A[k], device=dev) for k in ("rowptr", "col", "val")]
+    _, feat = xb.features(t[0], t[1], t[2], False)
+    pred = model.predict(torch.tensor(feat[None, :], device=dev))[0]
+    assert ch["variant"] == pred[0] == xb.VAR_SEGSCAN
+    assert m == xb.TUNER_RESTARTS[pred[3]]
