@@ -319,6 +319,46 @@ int xb_mlp_load(const char *path, xb_mlp **out);
 int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, int32_t *m_out,
                 void *stream);
 
+/* ---- batched solve: many uneven systems in one persistent launch ----------
+ * Each system is an independent A x = b in general CRS (device pointers, the
+ * xb_csr rules with sym_upper = 0) solved by restarted GMRES(m) with MGS,
+ * the same algorithm as gmres_solve.  One persistent kernel (captured once in
+ * a CUDA graph, replayed by xb_batch_run) holds as many CTAs as fit on the
+ * GPU; each CTA takes the next system from an atomic work queue (largest
+ * systems first) and solves it alone with block-level reductions, so CTAs
+ * never wait on each other.  opt: tol, maxiter (per system), maxtime_s (whole
+ * launch; the kernel checks %globaltimer at every restart).  Per system:
+ * m in [1, XB_BATCH_MAX_M] and the SpMV mode inside the CTA (0: thread per
+ * row, 1: warp per row), as chosen by a tuner; zero_x = 1 makes the kernel
+ * start from x = 0 (so a replay repeats the same solve). */
+#define XB_BATCH_MAX_M 128
+typedef struct xb_batch_sys {
+    int32_t n, nnz;
+    const int32_t *rowptr, *col;
+    const double *val, *b;
+    double *x;
+    int32_t m, mode, zero_x;
+} xb_batch_sys;
+typedef struct xb_batch_info {
+    int32_t status, iters, restarts, m, mode;
+    double res_true;         /* ||b - A x|| / ||b|| at exit                   */
+    double ms;               /* device time spent on this system              */
+} xb_batch_info;
+typedef struct xb_batch xb_batch;
+/* Validate, allocate the per-system workspace ((m+1)(n+31) doubles each) and
+ * capture the graph.  Does not run it. */
+int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *opt, void *stream,
+                    xb_batch **out);
+/* Replay the captured launch on `stream` (asynchronous). */
+int xb_batch_run(xb_batch *b, void *stream);
+/* Wait for `stream` and copy the per-system results to the HOST array infos;
+ * returns the first non-OK system status, else XB_OK. */
+int xb_batch_results(xb_batch *b, xb_batch_info *infos, void *stream);
+int xb_batch_destroy(xb_batch *b);
+/* create + run + results + destroy. */
+int xb_batch_solve(int32_t count, const xb_batch_sys *sys, const xb_options *opt,
+                   xb_batch_info *infos, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

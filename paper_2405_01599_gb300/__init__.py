@@ -57,6 +57,17 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchSys(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p), ("m", C.c_int32),
+                ("mode", C.c_int32), ("zero_x", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("restarts", C.c_int32),
+                ("m", C.c_int32), ("mode", C.c_int32), ("res_true", C.c_double), ("ms", C.c_double)]
+
+
 class Choice(C.Structure):
     _fields_ = [("variant", C.c_int32), ("block", C.c_int32), ("ipt", C.c_int32),
                 ("ms", C.c_float)]
@@ -117,6 +128,11 @@ def lib():
         "xb_mlp_predict": (i32, [vp, vp, i32, P(i32), vp]),
         "xb_mlp_save": (i32, [vp, C.c_char_p]),
         "xb_mlp_load": (i32, [C.c_char_p, P(vp)]),
+        "xb_batch_create": (i32, [i32, P(BatchSys), P(Options), vp, P(vp)]),
+        "xb_batch_run": (i32, [vp, vp]),
+        "xb_batch_results": (i32, [vp, P(BatchInfo), vp]),
+        "xb_batch_destroy": (i32, [vp]),
+        "xb_batch_solve": (i32, [i32, P(BatchSys), P(Options), P(BatchInfo), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -435,3 +451,48 @@ class Mlp:
 
     def save(self, path):
         _check(lib().xb_mlp_save(self._h, path.encode()))
+
+
+class Batch:
+    """Many independent systems solved by GMRES(m) in one persistent,
+    graph-captured launch (xb_batch_*).  systems: list of dicts with device
+    tensors rowptr, col, val, b, x and ints m, mode (0 thread/row, 1 warp/row).
+    """
+
+    def __init__(self, systems, stream=None, zero_x=True, **opts):
+        import torch
+        self._keep = []
+        arr = (BatchSys * max(1, len(systems)))()
+        for i, q in enumerate(systems):
+            for k in ("rowptr", "col"):
+                _need(q[k], torch.int32, k)
+            for k in ("val", "b", "x"):
+                _need(q[k], torch.float64, k)
+            arr[i] = BatchSys(q["rowptr"].numel() - 1, q["col"].numel(), _ptr(q["rowptr"]),
+                              _ptr(q["col"]), _ptr(q["val"]), _ptr(q["b"]), _ptr(q["x"]),
+                              int(q.get("m", 30)), int(q.get("mode", 0)), int(zero_x))
+            self._keep.append(q)
+        self.count = len(systems)
+        o = default_options(**opts)
+        h = C.c_void_p()
+        _check(lib().xb_batch_create(self.count, arr, C.byref(o), _stream(stream), C.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().xb_batch_run(self._h, _stream(stream)))
+
+    def results(self, stream=None):
+        infos = (BatchInfo * max(1, self.count))()
+        lib().xb_batch_results(self._h, infos, _stream(stream))
+        return [{k: getattr(infos[i], k) for k, _ in BatchInfo._fields_} for i in range(self.count)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().xb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

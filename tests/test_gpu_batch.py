@@ -1,0 +1,76 @@
+"""Batched persistent GMRES(m) (one graph-captured launch for many uneven
+systems) against the CPU oracle: every system reaches the true residual
+tolerance, iteration counts agree with the oracle's GMRES(m), replays are
+bit-identical, and the time budget ends the launch with a status, not a hang."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_01599_gb300 import gen
+from tests._gpu import lib_and_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _systems(dev, specs):
+    import torch
+    out, mats = [], []
+    for A, m, mode in specs:
+        b = oracle.spmv(A, np.ones(A["n"]))
+        out.append(dict(rowptr=torch.as_tensor(A["rowptr"], device=dev),
+                        col=torch.as_tensor(A["col"], device=dev),
+                        val=torch.as_tensor(A["val"], device=dev),
+                        b=torch.tensor(b, device=dev),
+                        x=torch.zeros(A["n"], dtype=torch.float64, device=dev), m=m, mode=mode))
+        mats.append((A, b))
+    return out, mats
+
+
+SPECS = [
+    (lambda: gen.poisson2d(40), 30, 0), (lambda: gen.poisson2d(33), 20, 1),
+    (lambda: gen.laplace3d(12), 30, 0), (lambda: gen.convdiff3d(N=14), 10, 0),
+    (lambda: gen.powerlaw(n=6000, seed=4), 30, 1), (lambda: gen.powerlaw(n=3000, seed=5), 50, 0),
+    (lambda: gen.random200(), 30, 0), (lambda: gen.poisson2d(8), 5, 1),
+] * 3
+
+
+def test_batch_matches_oracle_and_replays(env=None):
+    xb, dev = lib_and_device()
+    specs = [(f(), m, mode) for f, m, mode in SPECS]
+    systems, mats = _systems(dev, specs)
+    bt = xb.Batch(systems, tol=1e-8, maxiter=20000, maxtime_s=60.0)
+    bt.run()
+    res = bt.results()
+    xs = [q["x"].cpu().numpy().copy() for q in systems]
+    for (A, b), r, x, (_, m, mode) in zip(mats, res, xs, specs):
+        assert r["status"] == 0, r
+        rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+        assert rel <= 1e-8 and abs(r["res_true"] - rel) <= 1e-9
+        _, io = oracle.gmres(A, b, m=m, tol=1e-8)
+        assert abs(r["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (r, io["iters"])
+        assert r["m"] == m and r["mode"] == mode
+    # a replay of the captured graph (x restarts from 0) gives identical results
+    bt.run()
+    res2 = bt.results()
+    for q, x, r, r2 in zip(systems, xs, res, res2):
+        np.testing.assert_array_equal(q["x"].cpu().numpy(), x)
+        assert r["iters"] == r2["iters"]
+
+
+def test_batch_time_budget_returns_status():
+    xb, dev = lib_and_device()
+    systems, _ = _systems(dev, [(gen.poisson2d(150), 5, 0)] * 4)
+    bt = xb.Batch(systems, tol=1e-14, maxiter=10 ** 7, maxtime_s=0.05)
+    bt.run()
+    res = bt.results()
+    assert all(r["status"] == xb.XB_ENOCONV for r in res)
+
+
+def test_batch_empty_and_bad_args():
+    xb, dev = lib_and_device()
+    bt = xb.Batch([])
+    bt.run()
+    assert bt.results() == []
+    systems, _ = _systems(dev, [(gen.poisson2d(5), 0, 0)])
+    with pytest.raises(xb.XbError):
+        xb.Batch(systems)
