@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=4_000_000)
     ap.add_argument("--no-extras", action="store_true", help="skip per-variant/sym/solver lines")
-    ap.add_argument("--solvers", action="store_true", help="also time the large solver cases")
+    ap.add_argument("--no-solvers", action="store_true",
+                    help="skip the GMRES time-to-1e-8 comparison (256^3 convection-diffusion)")
+    ap.add_argument("--batch", action="store_true",
+                    help="also run the 512-system batched solve (default / learned / exhaustive)")
     ap.add_argument("--variant", default=None, choices=["row", "nnz", "segscan"],
                     help="fixed SpMV variant instead of the exhaustive tuner")
     ap.add_argument("--block", type=int, default=256)
@@ -369,14 +372,142 @@ def extras(xb, torch, dev, plan, A, x, y, args):
     # config 1: 64x64 Poisson GMRES(30) to 1e-8, b = A*ones, x0 = 0
     P = gen.poisson2d(64)
     pp = xb.Plan.from_host(P, dev)
-    bp = torch.tensor(oracle.spmv(P, np.ones(P["n"])), device=dev)
+    bp_h = oracle.spmv(P, np.ones(P["n"]))
+    bp = torch.tensor(bp_h, device=dev)
+    xo, io = oracle.gmres(P, bp_h, m=30, tol=1e-8)
     for ce in (1, 8):
         xs = torch.zeros(P["n"], dtype=torch.float64, device=dev)
         t0 = time.perf_counter()
         info = pp.gmres(bp, xs, m=30, tol=1e-8, check_every=ce)
         res[f"c1_gmres30_check{ce}"] = {"s": time.perf_counter() - t0, "iters": info["iters"],
+                                        "oracle_iters": io["iters"],
                                         "res_true": info["res_true"], "status": info["status"]}
+    xs = torch.zeros(P["n"], dtype=torch.float64, device=dev)
+    info = pp.gmres(bp, xs, m=30, tol=1e-8, precision=xb.PREC_MIXED, check_every=8)
+    res["c1_gmres30_mixed"] = {"iters_inner": info["inner_iters"], "outer": info["outer"],
+                               "res_true": info["res_true"],
+                               "err_vs_fp64_oracle": float(np.max(np.abs(xs.cpu().numpy() - xo)) /
+                                                           np.max(np.abs(xo)))}
+    if not args.no_solvers:
+        res.update(solvers(xb, torch, dev, plan, A, args))
+    if args.batch:
+        res["c5_batch"] = batch(xb, torch, dev, args)
     return res
+
+
+def solvers(xb, torch, dev, plan3, A3, args):
+    """Time to true ||b - A x|| / ||b|| <= 1e-8 (b = A*ones, x0 = 0)."""
+    from paper_2405_01599_gb300 import gen, tuner
+    out = {}
+    # config 3: BiCGStab on the power-law matrix (tuned SpMV)
+    n3 = A3["n"]
+    b3 = torch.empty(n3, dtype=torch.float64, device=dev)
+    plan3.spmv(torch.ones(n3, dtype=torch.float64, device=dev), b3)
+    x3 = torch.zeros(n3, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    info = plan3.bicgstab(b3, x3, tol=1e-8, maxtime_s=120.0, check_every=4)
+    out["c3_bicgstab"] = {"s": time.perf_counter() - t0, "iters": info["iters"],
+                          "res_true": info["res_true"], "status": info["status"],
+                          "spmv_calls": info["spmv_calls"]}
+    # config 4: 256^3 convection-diffusion, Peclet 10, upwind
+    A = gen.convdiff3d(N=256, pe=10.0)
+    n = A["n"]
+    model = xb.Mlp.load(tuner.MODEL_PATH)
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+
+    def run(label, plan, **kw):
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        plan.spmv(ones, b)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = plan.gmres(b, x, tol=1e-8, maxtime_s=300.0, check_every=10, timing=1, **kw)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        err = float((x - ones).abs().max().item())
+        out[label] = {"s": el, "status": info["status"], "iters": info["iters"] or info["inner_iters"],
+                      "outer": info["outer"], "res_true": info["res_true"],
+                      "err_vs_exact_solution": err, "spmv_calls": info["spmv_calls"],
+                      "GBs_solve": info["bytes_alg"] / el / 1e9,
+                      "spmv_ms_avg": info["spmv_ms"] / max(1, info["spmv_calls"]),
+                      "variant": xb.VARIANT_NAMES.get(info["variant_used"], "?"),
+                      "block": info["block_used"], "ipt": info["ipt_used"], **kw}
+
+    p_plain = xb.Plan.from_host(A, dev)           # no tuning: the plan's default variant
+    run("c4_plain_fp64_m30", p_plain, m=30)
+    p_ex = xb.Plan.from_host(A, dev)
+    t0 = time.perf_counter()
+    p_ex.tune()
+    t_ex = time.perf_counter() - t0
+    run("c4_exhaustive_fp64_m30", p_ex, m=30)
+    out["c4_exhaustive_fp64_m30"]["tune_s"] = t_ex
+    p_ml = xb.Plan.from_host(A, dev)
+    t0 = time.perf_counter()
+    ch, m = p_ml.tune_mlp(model)
+    t_ml = time.perf_counter() - t0
+    run("c4_mlp_fp64", p_ml, m=m)
+    run("c4_mlp_mixed", p_ml, m=m, precision=xb.PREC_MIXED, tol_inner=1e-4, maxiter_inner=2000)
+    out["c4_mlp_mixed"]["tune_s"] = t_ml
+    out["c4_mlp_fp64"]["tune_s"] = t_ml
+    base = out["c4_plain_fp64_m30"]["s"]
+    out["c4_speedup_vs_plain_fp64"] = {k: base / out[k]["s"] for k in
+                                       ("c4_exhaustive_fp64_m30", "c4_mlp_fp64", "c4_mlp_mixed")}
+    return out
+
+
+def batch(xb, torch, dev, args):
+    """512 uneven systems in one persistent graph-captured launch: untuned
+    default vs the exhaustive run-time tuner (each system's SpMV candidates
+    timed, Sec. 3.1; m fixed at 30) vs the learned tuner (SpMV choice and m)."""
+    from paper_2405_01599_gb300 import gen, tuner
+    specs = gen.batch_specs(512, seed=5)
+    model = xb.Mlp.load(tuner.MODEL_PATH)
+    systems, plans = [], []
+    t_ml = t_ex = 0.0
+    mode_of = lambda v: 1 if v == xb.VAR_SEGSCAN else 0
+    for sp in specs:
+        A = gen.from_spec(sp)
+        pl = xb.Plan.from_host(A, dev)
+        n = A["n"]
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        pl.spmv(torch.ones(n, dtype=torch.float64, device=dev), b)
+        t0 = time.perf_counter()
+        ch, m = pl.tune_mlp(model)
+        t_ml += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ce = pl.tune()
+        t_ex += time.perf_counter() - t0
+        systems.append(dict(rowptr=pl._keep[0], col=pl._keep[1], val=pl._keep[2], b=b,
+                            x=torch.zeros(n, dtype=torch.float64, device=dev),
+                            m_ml=m, mode_ml=mode_of(ch["variant"]), mode_ex=mode_of(ce["variant"])))
+        plans.append(pl)
+    opts = dict(tol=1e-8, maxiter=20000, maxtime_s=30.0)
+
+    def run(ms, modes):
+        for q, m, md in zip(systems, ms, modes):
+            q["m"], q["mode"] = int(m), int(md)
+        bt = xb.Batch(systems, **opts)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bt.run()
+        e1.record()
+        r = bt.results()
+        bt.close()
+        return e0.elapsed_time(e1), r
+
+    N = len(systems)
+    t_def, r_def = run([30] * N, [0] * N)
+    t_exh, r_exh = run([30] * N, [q["mode_ex"] for q in systems])
+    t_mlp, r_mlp = run([q["m_ml"] for q in systems], [q["mode_ml"] for q in systems])
+    ok = lambda r: int(sum(1 for q in r if q["status"] == 0))
+    return {"systems": N, "sum_n": int(sum(q["b"].numel() for q in systems)),
+            "default_ms": t_def, "exhaustive_ms": t_exh, "learned_ms": t_mlp,
+            "learned_tune_s": t_ml, "exhaustive_tune_s": t_ex,
+            "converged": {"default": ok(r_def), "exhaustive": ok(r_exh), "learned": ok(r_mlp)},
+            "learned_speedup_vs_default": t_def / t_mlp,
+            "learned_speedup_vs_exhaustive": t_exh / t_mlp,
+            "max_system_ms": {"default": max(q["ms"] for q in r_def),
+                              "learned": max(q["ms"] for q in r_mlp)}}
 
 
 if __name__ == "__main__":

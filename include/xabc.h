@@ -293,7 +293,8 @@ int xb_mlp_set_norm(xb_mlp *m, const float *mu, const float *sd);
 int xb_mlp_forward(xb_mlp *m, const float *X, int32_t B, float *logits, void *stream);
 /* Mean over the batch of the summed per-head softmax cross-entropy, and its
  * gradient (kept in the model for xb_mlp_adam; copied to the DEVICE array
- * grad_out when it is not NULL).  labels: device [B][nheads].  *loss: host. */
+ * grad_out when it is not NULL).  labels: device [B][nheads]; a negative
+ * label leaves that head of that sample out of the loss.  *loss: host. */
 int xb_mlp_loss_grad(xb_mlp *m, const float *X, const int32_t *labels, int32_t B, float *loss,
                      float *grad_out, void *stream);
 /* One Adam step (Kingma & Ba; t counts from 1) with the stored gradient. */

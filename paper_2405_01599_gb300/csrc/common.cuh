@@ -34,7 +34,7 @@ int cuda_error(cudaError_t e, const char *where);
     } while (0)
 
 // ---- device constants ------------------------------------------------------
-constexpr int kRedSlots = 1024;     // max CTAs of a reduction grid
+constexpr int kRedSlots = 2048;     // max CTAs of a reduction grid
 constexpr int kScalars = 4096;      // device scalar scratch per plan (doubles)
 
 int num_sms();                      // cached cudaDevAttrMultiProcessorCount

@@ -48,9 +48,22 @@ __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * block
 
 __global__ void k_dot(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                       double *__restrict__ part, unsigned *__restrict__ ticket,
-                      double *__restrict__ out, int sq) {
-    double v[1] = {0.0};
-    for (int64_t i = gtid(); i < n; i += gstride()) v[0] = fma(x[i], y[i], v[0]);
+                      double *__restrict__ out, int sq, int vec) {
+    double a0 = 0.0, a1 = 0.0;
+    int64_t done = 0;
+    if (vec) {
+        const double2 *x2 = reinterpret_cast<const double2 *>(x);
+        const double2 *y2 = reinterpret_cast<const double2 *>(y);
+        const int64_t nv = n / 2;
+        for (int64_t e = gtid(); e < nv; e += gstride()) {
+            const double2 a = x2[e], b = y2[e];
+            a0 = fma(a.x, b.x, a0);
+            a1 = fma(a.y, b.y, a1);
+        }
+        done = nv * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) a0 = fma(x[i], y[i], a0);
+    double v[1] = {a0 + a1};
     double t[1];
     if (grid_reduce<1>(v, part, ticket, t) && threadIdx.x == 0) *out = sq ? sqrt(t[0]) : t[0];
 }
@@ -142,40 +155,107 @@ __device__ void gm_givens(xb::GmDev st, int j, double hn) {
     if (res <= st.misc[xb::GM_TAU]) st.misc[xb::GM_STOP] = 1.0;
 }
 
+template <typename VB>
+struct V16;
+template <>
+struct V16<double> {
+    using T = double2;
+    static constexpr int N = 2;
+    __device__ static double get(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
+    __device__ static void set(double2 &v, int k, double a) {
+        if (k == 0) v.x = a;
+        else v.y = a;
+    }
+};
+template <>
+struct V16<float> {
+    using T = float4;
+    static constexpr int N = 4;
+    __device__ static float get(const float4 &v, int k) {
+        return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+    }
+    __device__ static void set(float4 &v, int k, float a) {
+        if (k == 0) v.x = a;
+        else if (k == 1) v.y = a;
+        else if (k == 2) v.z = a;
+        else v.w = a;
+    }
+};
+
+// One element of the MGS launch: OP 0 dot(w, vn); OP 1 w -= c vp, dot(w, vn);
+// OP 2 w -= c vp, dot(w, w).
+template <int OP, typename VB>
+__device__ __forceinline__ VB mgs_elem(VB &w, VB vp, VB vn, VB c, VB acc) {
+    if (OP != 0) w = fma(-c, vp, w);
+    return OP == 2 ? fma(w, w, acc) : fma(w, vn, acc);
+}
+
 // One launch of the MGS sweep of Arnoldi step j:
 //   i == 0      : h_0j = (w, v_0)
 //   0 < i <= j  : w -= h_{i-1,j} v_{i-1};  h_ij = (w, v_i)
 //   i == j+1    : w -= h_jj v_j;  h_{j+1,j} = ||w||, then Givens.
 // Basis vectors are stored unnormalised with scales sc (v_i = sc[i]*V_i).
-template <typename VB>
+// Operands move as 16-byte vectors (two per thread per iteration) when the
+// three arrays are 16-byte aligned.
+template <int OP, typename VB>
 __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
                                              const VB *__restrict__ vprev,
                                              const VB *__restrict__ vnext, xb::GmDev st, int j,
                                              int i, double *__restrict__ part,
-                                             unsigned *__restrict__ ticket) {
+                                             unsigned *__restrict__ ticket, int vec) {
     if (st.misc[xb::GM_STOP] != 0.0) return;
-    const double cd = vprev ? st.misc[xb::GM_COEF] : 0.0;
-    const VB c = (VB)cd;
-    VB acc = VB(0);
-    if (vprev && vnext) {
-        for (int64_t e = gtid(); e < n; e += gstride()) {
-            const VB a = fma(-c, vprev[e], w[e]);
-            w[e] = a;
-            acc = fma(a, vnext[e], acc);
+    const VB c = (VB)(OP != 0 ? st.misc[xb::GM_COEF] : 0.0);
+    VB acc0 = VB(0), acc1 = VB(0);
+    int64_t done = 0;
+    if (vec) {
+        using T = typename V16<VB>::T;
+        constexpr int N = V16<VB>::N;
+        const int64_t nv = n / N;
+        T *w2 = reinterpret_cast<T *>(w);
+        const T *p2 = reinterpret_cast<const T *>(OP != 0 ? vprev : w);
+        const T *q2 = reinterpret_cast<const T *>(OP != 2 ? vnext : w);
+        const int64_t st2 = 2 * gstride();
+        int64_t e = gtid();
+        for (; e + gstride() < nv; e += st2) {
+            const int64_t f = e + gstride();
+            T a = w2[e], b = w2[f];
+            const T pa = OP != 0 ? p2[e] : a, pb = OP != 0 ? p2[f] : b;
+            const T qa = OP != 2 ? q2[e] : a, qb = OP != 2 ? q2[f] : b;
+#pragma unroll
+            for (int k = 0; k < N; k++) {
+                VB x = V16<VB>::get(a, k), y = V16<VB>::get(b, k);
+                acc0 = mgs_elem<OP>(x, V16<VB>::get(pa, k), V16<VB>::get(qa, k), c, acc0);
+                acc1 = mgs_elem<OP>(y, V16<VB>::get(pb, k), V16<VB>::get(qb, k), c, acc1);
+                V16<VB>::set(a, k, x);
+                V16<VB>::set(b, k, y);
+            }
+            if (OP != 0) {
+                w2[e] = a;
+                w2[f] = b;
+            }
         }
-    } else if (vprev) {
-        for (int64_t e = gtid(); e < n; e += gstride()) {
-            const VB a = fma(-c, vprev[e], w[e]);
-            w[e] = a;
-            acc = fma(a, a, acc);
+        for (; e < nv; e += gstride()) {
+            T a = w2[e];
+            const T pa = OP != 0 ? p2[e] : a, qa = OP != 2 ? q2[e] : a;
+#pragma unroll
+            for (int k = 0; k < N; k++) {
+                VB x = V16<VB>::get(a, k);
+                acc0 = mgs_elem<OP>(x, V16<VB>::get(pa, k), V16<VB>::get(qa, k), c, acc0);
+                V16<VB>::set(a, k, x);
+            }
+            if (OP != 0) w2[e] = a;
         }
-    } else {
-        for (int64_t e = gtid(); e < n; e += gstride()) acc = fma(w[e], vnext[e], acc);
+        done = nv * N;
     }
-    double v[1] = {(double)acc};
+    for (int64_t e = done + gtid(); e < n; e += gstride()) {
+        VB x = w[e];
+        acc0 = mgs_elem<OP>(x, OP != 0 ? vprev[e] : x, OP != 2 ? vnext[e] : x, c, acc0);
+        if (OP != 0) w[e] = x;
+    }
+    double v[1] = {(double)acc0 + (double)acc1};
     double t[1];
     if (grid_reduce<1>(v, part, ticket, t) && threadIdx.x == 0) {
-        if (vnext) {
+        if (OP != 2) {
             const double h = st.sc[i] * t[0];
             st.H[(size_t)j * (st.M + 1) + i] = h;
             st.misc[xb::GM_COEF] = st.sc[i] * h;
@@ -200,15 +280,40 @@ __global__ void k_gm_solve(xb::GmDev st) {
     for (int i = 0; i < k; i++) st.y[i] *= st.sc[i];
 }
 
-// x += sum_i y_i V_i (each basis vector read once).
+// x += sum_i y_i V_i (each basis vector read once; 16-byte vectors when the
+// basis and x are aligned).
 template <typename VB, typename VX>
 __global__ void __launch_bounds__(kVB) k_gm_xupd(int64_t n, const VB *__restrict__ V, int64_t ld,
-                                                 xb::GmDev st, VX *__restrict__ x) {
+                                                 xb::GmDev st, VX *__restrict__ x, int vec) {
     __shared__ double ys[512];
     const int k = (int)st.misc[xb::GM_K];
     for (int i = threadIdx.x; i < k && i < 512; i += blockDim.x) ys[i] = st.y[i];
     __syncthreads();
-    for (int64_t e = gtid(); e < n; e += gstride()) {
+    int64_t done = 0;
+    if (vec) {
+        using T = typename V16<VB>::T;
+        using TX = typename V16<VX>::T;
+        constexpr int N = V16<VB>::N;
+        static_assert(V16<VB>::N == V16<VX>::N, "same width");
+        const int64_t nv = n / N;
+        for (int64_t e = gtid(); e < nv; e += gstride()) {
+            VX s[N];
+#pragma unroll
+            for (int q = 0; q < N; q++) s[q] = VX(0);
+            for (int i = 0; i < k; i++) {
+                const T v = reinterpret_cast<const T *>(V + (size_t)i * ld)[e];
+                const VX yi = (VX)ys[i];
+#pragma unroll
+                for (int q = 0; q < N; q++) s[q] = fma(yi, (VX)V16<VB>::get(v, q), s[q]);
+            }
+            TX a = reinterpret_cast<TX *>(x)[e];
+#pragma unroll
+            for (int q = 0; q < N; q++) V16<VX>::set(a, q, V16<VX>::get(a, q) + s[q]);
+            reinterpret_cast<TX *>(x)[e] = a;
+        }
+        done = nv * N;
+    }
+    for (int64_t e = done + gtid(); e < n; e += gstride()) {
         VX s = VX(0);
         for (int i = 0; i < k; i++) s = fma((VX)ys[i], (VX)V[(size_t)i * ld + e], s);
         x[e] += s;
@@ -367,13 +472,15 @@ GmDev gm_layout(double *base, int M) {
 
 int vdot(xb_plan *p, int64_t n, const double *x, const double *y, double *out, cudaStream_t s) {
     const int g = reduce_grid(n, kVB);
-    k_dot<<<g, kVB, 0, s>>>(n, x, y, p->d_part, p->d_ticket, out, 0);
+    const int vec = (((uintptr_t)x | (uintptr_t)y) % 16) == 0 ? 1 : 0;
+    k_dot<<<g, kVB, 0, s>>>(n, x, y, p->d_part, p->d_ticket, out, 0, vec);
     XB_LAUNCHED("k_dot");
     return XB_OK;
 }
 int vnrm2(xb_plan *p, int64_t n, const double *x, double *out, cudaStream_t s) {
     const int g = reduce_grid(n, kVB);
-    k_dot<<<g, kVB, 0, s>>>(n, x, x, p->d_part, p->d_ticket, out, 1);
+    const int vec = ((uintptr_t)x % 16) == 0 ? 1 : 0;
+    k_dot<<<g, kVB, 0, s>>>(n, x, x, p->d_part, p->d_ticket, out, 1, vec);
     XB_LAUNCHED("k_nrm2");
     return XB_OK;
 }
@@ -418,11 +525,14 @@ template <typename VB>
 int gm_mgs_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
                 cudaStream_t s) {
     const int g = reduce_grid(n, kVB);
-    for (int i = 0; i <= j + 1; i++) {
-        const VB *vprev = i > 0 ? V + (size_t)(i - 1) * ld : nullptr;
-        const VB *vnext = i <= j ? V + (size_t)i * ld : nullptr;
-        k_mgs<VB><<<g, kVB, 0, s>>>(n, w, vprev, vnext, st, j, i, p->d_part, p->d_ticket);
-    }
+    const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)w % 16) == 0 &&
+                     ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
+    k_mgs<0, VB><<<g, kVB, 0, s>>>(n, w, nullptr, V, st, j, 0, p->d_part, p->d_ticket, vec);
+    for (int i = 1; i <= j; i++)
+        k_mgs<1, VB><<<g, kVB, 0, s>>>(n, w, V + (size_t)(i - 1) * ld, V + (size_t)i * ld, st, j, i,
+                                       p->d_part, p->d_ticket, vec);
+    k_mgs<2, VB><<<g, kVB, 0, s>>>(n, w, V + (size_t)j * ld, nullptr, st, j, j + 1, p->d_part,
+                                   p->d_ticket, vec);
     XB_LAUNCHED("k_mgs");
     return XB_OK;
 }
@@ -438,7 +548,9 @@ int gm_update(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, int k, V
     (void)k;
     k_gm_solve<<<1, 32, 0, s>>>(st);
     XB_LAUNCHED("k_gm_solve");
-    k_gm_xupd<VB, VX><<<stream_grid(n), kVB, 0, s>>>(n, V, ld, st, x);
+    const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)x % 16) == 0 &&
+                     ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
+    k_gm_xupd<VB, VX><<<stream_grid(n), kVB, 0, s>>>(n, V, ld, st, x, vec);
     XB_LAUNCHED("k_gm_xupd");
     return XB_OK;
 }

@@ -86,6 +86,11 @@ __global__ void k_xent(int B, Dims d, const int *__restrict__ heads, const float
         float se = 0.f;
         for (int c = 0; c < K; c++) se += expf(lg[off + c] - mx);
         const int y = lab[(size_t)s * d.nh + h];
+        if (y < 0) {  // no label for this head: no loss, no gradient
+            for (int c = 0; c < K; c++) g[off + c] = 0.f;
+            off += K;
+            continue;
+        }
         ls += -(lg[off + y] - mx - logf(se));
         for (int c = 0; c < K; c++)
             g[off + c] = (expf(lg[off + c] - mx) / se - (c == y ? 1.f : 0.f)) / (float)B;

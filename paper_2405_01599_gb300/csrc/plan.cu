@@ -40,7 +40,7 @@ int num_sms() {
 
 int reduce_grid(int64_t n, int block) {
     int64_t want = (n + block * 4 - 1) / (block * 4);
-    int64_t cap = std::min<int64_t>(kRedSlots, (int64_t)num_sms() * 4);
+    int64_t cap = std::min<int64_t>(kRedSlots, (int64_t)num_sms() * 8);
     return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 

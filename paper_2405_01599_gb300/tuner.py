@@ -41,9 +41,13 @@ DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 MODEL_PATH = os.path.join(DATA_DIR, "mlp_tuner.bin")
 
 
-def random_spec(rng):
-    """One matrix recipe, n log-uniform on [1e3, 2e5]."""
-    n = int(math.exp(rng.uniform(math.log(1e3), math.log(2e5))))
+def random_spec(rng, large=False):
+    """One matrix recipe, n log-uniform on [1e3, 2e5] (large: [2e5, 5e6] for
+    the random kinds, up to 256^3 for the stencils)."""
+    if large:
+        n = int(math.exp(rng.uniform(math.log(2e5), math.log(5e6))))
+    else:
+        n = int(math.exp(rng.uniform(math.log(1e3), math.log(2e5))))
     kind = rng.choice(["poisson2d", "laplace3d", "convdiff3d", "powerlaw", "fixedrows",
                        "poisson2d_sym", "laplace3d_sym", "randsym"],
                       p=[0.14, 0.12, 0.12, 0.26, 0.12, 0.08, 0.08, 0.08])
@@ -51,7 +55,10 @@ def random_spec(rng):
     if kind in ("poisson2d", "poisson2d_sym"):
         return (kind, max(4, int(round(math.sqrt(n)))))
     if kind in ("laplace3d", "laplace3d_sym", "convdiff3d"):
-        return (kind, max(3, int(round(n ** (1 / 3)))))
+        side = max(3, int(round(n ** (1 / 3))))
+        if large:
+            side = int(rng.integers(60, 257))
+        return (kind, side)
     if kind == "powerlaw":
         return (kind, n, float(rng.uniform(4, 40)), float(rng.uniform(0.3, 2.0)), seed)
     if kind == "fixedrows":
@@ -135,7 +142,7 @@ def record(xb, torch, dev, A, gmres_cap_s=0.1, gmres_maxiter=1500):
     return dict(raw=raw, feat=feat, times=times, mtimes=mt, t_sweep=t_sweep, best=best)
 
 
-def make_data(count, seed, dev="cuda", log_every=50):
+def make_data(count, seed, dev="cuda", log_every=50, large=False):
     import torch
 
     import paper_2405_01599_gb300 as xb
@@ -144,9 +151,12 @@ def make_data(count, seed, dev="cuda", log_every=50):
     recs, specs = [], []
     t0 = time.perf_counter()
     for i in range(count):
-        spec = random_spec(rng)
+        spec = random_spec(rng, large)
         A = make(spec)
-        recs.append(record(xb, torch, torch.device(dev), A))
+        if large:  # cap each GMRES(m) timing; unconverged runs are extrapolated
+            recs.append(record(xb, torch, torch.device(dev), A, gmres_cap_s=0.6, gmres_maxiter=600))
+        else:
+            recs.append(record(xb, torch, torch.device(dev), A))
         specs.append(repr(spec))
         if log_every and (i + 1) % log_every == 0:
             print(f"[tuner data] {i + 1}/{count} matrices, {time.perf_counter() - t0:.0f}s", flush=True)
@@ -158,13 +168,20 @@ def make_data(count, seed, dev="cuda", log_every=50):
                 specs=np.array(specs))
 
 
+M_LABEL_MAX_N = 200_000  # above this the m timings are capped extrapolations
+
+
 def labels_of(D):
-    """Head labels: (variant, CTA-size class, ipt class, m class)."""
+    """Head labels: (variant, CTA-size class, ipt class, m class).  The m label
+    is -1 (left out of the loss) for matrices larger than M_LABEL_MAX_N: their
+    GMRES(m) timings were cut short, and extrapolating a capped run favours
+    small m, whose restarted iteration stalls later."""
     N = D["feat"].shape[0]
     lab = np.zeros((N, 4), np.int32)
     for s in range(N):
         v, b, i = ALL_CANDS[int(np.nanargmin(D["times"][s]))]
-        lab[s] = (v, BLOCKS.index(b), IPTS.index(i), int(np.argmin(D["mtimes"][s])))
+        mlab = int(np.argmin(D["mtimes"][s])) if D["raw"][s][0] <= M_LABEL_MAX_N else -1
+        lab[s] = (v, BLOCKS.index(b), IPTS.index(i), mlab)
     return lab
 
 
@@ -215,7 +232,7 @@ def evaluate(model, D, dev="cuda"):
         out["spmv_regret"].append(float(t_ml / t_best))
         out["spmv_gain_vs_default"].append(float(t_def / t_ml))
         mt = D["mtimes"][s]
-        if np.isfinite(mt).any():
+        if np.isfinite(mt).any() and D["raw"][s][0] <= M_LABEL_MAX_N:
             m_ml = mt[pred[s, 3]]
             out["m_regret"].append(float(m_ml / np.min(mt)))
             out["m_gain_vs_default"].append(float(mt[RESTARTS.index(30)] / m_ml))
@@ -227,6 +244,7 @@ def evaluate(model, D, dev="cuda"):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--make-data", type=int, default=0)
+    ap.add_argument("--large", action="store_true", help="matrices with n in [2e5, 5e6]")
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--out", default=None)
     ap.add_argument("--train", nargs="*", default=None, help="dataset(s) to concatenate")
@@ -236,7 +254,7 @@ def main():
     a = ap.parse_args()
     D = None
     if a.make_data:
-        D = make_data(a.make_data, a.seed)
+        D = make_data(a.make_data, a.seed, large=a.large)
         print(f"[tuner data] {n_records(D)} timing records from {len(D['feat'])} matrices")
         if a.out:
             np.savez_compressed(a.out, **D)
