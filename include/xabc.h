@@ -325,10 +325,13 @@ int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, i
  * xb_csr rules with sym_upper = 0) solved by restarted GMRES(m) with MGS,
  * the same algorithm as gmres_solve.  One persistent kernel (captured once in
  * a CUDA graph, replayed by xb_batch_run) holds as many CTAs as fit on the
- * GPU; each CTA takes the next system from an atomic work queue (largest
- * systems first) and solves it alone with block-level reductions, so CTAs
- * never wait on each other.  opt: tol, maxiter (per system), maxtime_s (whole
- * launch; the kernel checks %globaltimer at every restart).  Per system:
+ * GPU, in 8-CTA clusters; work comes from an atomic queue (largest systems
+ * first).  A system with n >= 100000 (XB_BATCH_COOP_MIN_N in the environment
+ * overrides the threshold) is solved by a whole cluster, its dot products
+ * combined through distributed shared memory; smaller systems take one CTA
+ * each and need no inter-CTA synchronisation.  opt: tol, maxiter (per
+ * system), maxtime_s (whole launch; checked at every restart), dafrt /
+ * dafrt_theta / m_max (the restart-length rule, per system).  Per system:
  * m in [1, XB_BATCH_MAX_M] and the SpMV mode inside the CTA (0: thread per
  * row, 1: warp per row), as chosen by a tuner; zero_x = 1 makes the kernel
  * start from x = 0 (so a replay repeats the same solve). */

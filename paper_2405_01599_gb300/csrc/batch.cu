@@ -1,27 +1,52 @@
 // Batched solve of many independent systems in ONE persistent kernel launch,
-// captured in a CUDA graph and replayed.  Each CTA pulls the next system from
-// an atomic work queue (systems ordered largest first, so the long solves
-// start early) and runs the whole restarted GMRES(m) for it with block-level
-// reductions: the CTAs never wait on one another, so there is no inter-CTA
-// spin.  A %globaltimer deadline bounds the launch's run time.
+// captured in a CUDA graph and replayed.
 //
-// Per system the tuner's choices apply: the restart length m and the SpMV
-// mode inside the CTA (0: one thread per row; 1: one warp per row, for rows
-// long or uneven enough that a thread per row would serialise).
+// The launch is a grid of 8-CTA thread-block clusters.  Each cluster pulls
+// work from an atomic queue (systems ordered largest first):
+//   - a system with n >= kLargeN is solved by the whole cluster: every CTA
+//     owns a slice of the rows, dot products are combined across the cluster
+//     through distributed shared memory (every CTA sums the 8 partials in rank
+//     order, so all CTAs hold identical values), and hardware cluster
+//     barriers order the shared vectors;
+//   - smaller systems are taken one per CTA and solved with block-level
+//     reductions only.
+// Every cluster barrier sits on a path whose branch conditions are
+// cluster-uniform (iteration counts, reduced values, and a time-budget flag
+// that rank 0 decides and broadcasts through a reduction), so all CTAs of a
+// cluster reach the same barriers in the same order.
+//
+// The solver is restarted GMRES(m) with modified Gram-Schmidt (fused: each
+// pass applies the previous projection and takes the next inner product),
+// Givens least squares, the true-residual check at every restart (fault
+// convergence narrows the implicit threshold), and, when enabled, the
+// MM-ratio restart rule of Eq. (1) / Fig. 2 / Sec. 4.3 (m grows by 5, up to
+// m_max, when 5 consecutive restart residuals change by less than theta).
 #include "common.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
+namespace cg = cooperative_groups;
+
+namespace {
+constexpr int kCl = 8;          // CTAs per cluster
+constexpr int kBT = 512;        // threads per CTA
+constexpr int kLargeN = 100000; // systems this large are solved by a whole cluster
+}  // namespace
+
 struct xb_batch_dev {
-    int n, nnz, m, mode, zero_x;
+    int n, nnz, m, m_max, mode, zero_x, coop;
     int64_t ld;
     const int *rowptr, *col;
     const double *val, *b;
     double *x;
-    double *ws;  // (m+1)*ld basis, then (m+1)*m Hessenberg
+    double *V;  // (m_max+1) * ld basis
+    double *H;  // per cooperating CTA: (m_max+1) * m_max Hessenberg (column-major)
 };
 
 struct xb_batch {
@@ -37,211 +62,303 @@ struct xb_batch {
 
 namespace {
 
-constexpr int kBT = 512;  // threads per CTA of the batched kernel
-
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
+struct Smem {
+    double sh[40];
+    double slot[2];  // this CTA's partial of the current cluster reduction
+    double g[XB_BATCH_MAX_M + 1], cs[XB_BATCH_MAX_M], sn[XB_BATCH_MAX_M], yv[XB_BATCH_MAX_M];
+    unsigned long long t_start;
+    int q, q2, big;
+    int flag;
+};
+
 // Sum over the CTA, result returned to every thread.
-__device__ double cta_sum(double v, double *sh) {
+__device__ double cta_sum(double v, Smem &S) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
-    if (lane == 0) sh[w] = v;
+    if (lane == 0) S.sh[w] = v;
     __syncthreads();
     if (w == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        v = lane < (int)(blockDim.x >> 5) ? S.sh[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[32] = v;
+        if (lane == 0) S.sh[32] = v;
     }
     __syncthreads();
-    return sh[32];
+    return S.sh[32];
 }
 
-// y = alpha*A*x (+ beta*y when beta != 0), CTA-wide.
-__device__ void cta_spmv(const xb_batch_dev &S, double alpha, const double *__restrict__ x,
-                         double beta, double *__restrict__ y) {
-    if (S.mode == 0) {
-        for (int r = threadIdx.x; r < S.n; r += blockDim.x) {
+// The solve's view of the work: rows [r0, r1) of this CTA, and whether the
+// CTAs of the cluster cooperate on this system.
+struct Part {
+    int r0, r1, coop, phase;
+};
+
+// Sum over all cooperating CTAs (one cluster barrier), identical everywhere.
+// The two partial slots alternate, so a slot is rewritten only after every
+// CTA has passed the barrier of the reduction that follows its last read.
+__device__ double coop_sum(double v, Smem &S, Part &P) {
+    const double t = cta_sum(v, S);
+    if (!P.coop) return t;
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x == 0) S.slot[P.phase] = t;
+    cl.sync();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int r = 0; r < kCl; r++) tot += cl.map_shared_rank(S.slot, r)[P.phase];
+        S.sh[34] = tot;
+    }
+    __syncthreads();
+    const double tot = S.sh[34];
+    __syncthreads();
+    P.phase ^= 1;
+    return tot;
+}
+
+// Make every cooperating CTA's writes to the shared vectors visible to all.
+__device__ __forceinline__ void coop_barrier(const Part &P) {
+    if (P.coop) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// y[r0:r1] = alpha*A[r0:r1,:]*x (+ beta*y).  x is written by the other CTAs
+// of the cluster during the launch, so it is read at L2 (ld.global.cg), the
+// coherence point, never through the SM-local read-only path.
+__device__ void part_spmv(const xb_batch_dev &D, const Part &P, double alpha, const double *x,
+                          double beta, double *y) {
+    if (D.mode == 0) {
+        for (int r = P.r0 + threadIdx.x; r < P.r1; r += blockDim.x) {
             double s = 0.0;
-            for (int k = S.rowptr[r]; k < S.rowptr[r + 1]; k++) s = fma(S.val[k], x[S.col[k]], s);
+            for (int k = __ldg(D.rowptr + r); k < __ldg(D.rowptr + r + 1); k++)
+                s = fma(__ldg(D.val + k), __ldcg(x + __ldg(D.col + k)), s);
             y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
         }
     } else {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int r = w; r < S.n; r += nw) {
+        for (int r = P.r0 + w; r < P.r1; r += nw) {
             double s = 0.0;
-            for (int k = S.rowptr[r] + lane; k < S.rowptr[r + 1]; k += 32)
-                s = fma(S.val[k], x[S.col[k]], s);
+            for (int k = __ldg(D.rowptr + r) + lane; k < __ldg(D.rowptr + r + 1); k += 32)
+                s = fma(__ldg(D.val + k), __ldcg(x + __ldg(D.col + k)), s);
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
         }
     }
+    // rows were stored by other threads than the ones that read them next
+    // (mode 1: lane 0 of a warp), so the CTA meets before anyone reads y
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBT) k_batch_gmres(const xb_batch_dev *__restrict__ sys,
-                                                     xb_batch_info *__restrict__ out,
-                                                     const int *__restrict__ order, int count,
-                                                     int *__restrict__ queue, double tol,
-                                                     int maxiter, unsigned long long budget_ns) {
-    __shared__ double sh[40];
-    __shared__ double g[XB_BATCH_MAX_M + 1], cs[XB_BATCH_MAX_M], sn[XB_BATCH_MAX_M], yv[XB_BATCH_MAX_M];
-    __shared__ int s_id, s_flag;
-    __shared__ unsigned long long s_t0;
-    if (threadIdx.x == 0) s_t0 = gtimer();
-    __syncthreads();
-    const unsigned long long t_start = s_t0;
-    for (;;) {
-        if (threadIdx.x == 0) s_id = atomicAdd(queue, 1);
-        __syncthreads();
-        const int q = s_id;
-        __syncthreads();
-        if (q >= count) return;
-        const int id = order[q];
-        const xb_batch_dev S = sys[id];
-        const int n = S.n, m = S.m;
-        const int64_t ld = S.ld;
-        double *V = S.ws;
-        double *H = S.ws + (size_t)(m + 1) * ld;  // column-major (m+1) x m
-        unsigned long long ts = gtimer();
-        if (S.zero_x)
-            for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = 0.0;
-        __syncthreads();
-        // ||b||
-        double a = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(S.b[i], S.b[i], a);
-        const double bnorm = sqrt(cta_sum(a, sh));
-        int iters = 0, restarts = 0, status = XB_OK, claimed = 0;
-        double tau = tol, res_true = 0.0;
-        if (bnorm == 0.0) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = 0.0;
+__device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, int maxiter,
+                          unsigned long long deadline, int rank, double theta,
+                          xb_batch_info *out) {
+    const unsigned long long ts = gtimer();
+    const int m_max = D.m_max;
+    const int64_t ld = D.ld;
+    double *V = D.V;
+    double *H = D.H + (P.coop ? (size_t)rank * (m_max + 1) * m_max : 0);
+    const int r0 = P.r0, r1 = P.r1;
+    if (D.zero_x)
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) D.x[i] = 0.0;
+    double a = 0.0;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) a = fma(D.b[i], D.b[i], a);
+    const double bnorm = sqrt(coop_sum(a, S, P));
+    int iters = 0, restarts = 0, status = XB_OK, claimed = 0, m = D.m, K = 0;
+    double tau = tol, res_true = 0.0;
+    double samp[5];  // restart residuals for the MM-ratio rule (same in every thread)
+    if (bnorm == 0.0) {
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) D.x[i] = 0.0;
+    } else {
+        for (;;) {
+            coop_barrier(P);  // x complete before A x
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) V[i] = D.b[i];
+            __syncthreads();  // the SpMV reads V_0 rows through other threads
+            part_spmv(D, P, -1.0, D.x, 1.0, V);
+            a = 0.0;
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) a = fma(V[i], V[i], a);
+            const double beta = sqrt(coop_sum(a, S, P));
+            // the time budget is rank 0's decision, broadcast by a reduction
+            const double late =
+                coop_sum((rank == 0 && threadIdx.x == 0 && gtimer() > deadline) ? 1.0 : 0.0, S, P);
+            res_true = beta / bnorm;
+            if (res_true <= tol) {
+                status = XB_OK;
+                break;
+            }
+            if (iters >= maxiter || late > 0.0) {
+                status = XB_ENOCONV;
+                break;
+            }
+            if (claimed) tau *= tol / res_true;  // fault convergence: narrow the threshold
+            claimed = 0;
+            if (restarts > 0) {  // restart-frequency rule (Eq. 1): judge every 5 samples
+                samp[K++] = res_true;
+                if (K == 5) {
+                    double mx = samp[0], mn = samp[0];
+                    for (int z = 1; z < 5; z++) {
+                        mx = fmax(mx, samp[z]);
+                        mn = fmin(mn, samp[z]);
+                    }
+                    if (mn > 0.0 && mx / mn < theta) m = min(m + 5, m_max);
+                    K = 0;
+                }
+            }
+            const double ib = 1.0 / beta;
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) V[i] *= ib;
+            for (int i = threadIdx.x; i <= m; i += blockDim.x) S.g[i] = 0.0;
             __syncthreads();
-        } else {
-            for (;;) {
-                // r = b - A x into V_0
-                for (int i = threadIdx.x; i < n; i += blockDim.x) V[i] = S.b[i];
-                __syncthreads();
-                cta_spmv(S, -1.0, S.x, 1.0, V);
-                a = 0.0;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(V[i], V[i], a);
-                const double beta = sqrt(cta_sum(a, sh));
-                res_true = beta / bnorm;
-                if (res_true <= tol) {
-                    status = XB_OK;
-                    break;
-                }
-                if (iters >= maxiter || gtimer() - t_start > budget_ns) {
-                    status = XB_ENOCONV;
-                    break;
-                }
-                if (claimed) tau *= tol / res_true;  // fault convergence: narrow the threshold
-                claimed = 0;
-                const double ib = 1.0 / beta;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) V[i] *= ib;
-                for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = 0.0;
-                __syncthreads();
-                if (threadIdx.x == 0) g[0] = beta;
-                int k = 0;
-                for (int j = 0; j < m; j++) {
-                    iters++;
-                    double *w = V + (size_t)(j + 1) * ld;
-                    cta_spmv(S, 1.0, V + (size_t)j * ld, 0.0, w);
-                    // modified Gram-Schmidt
-                    double len2 = 0.0;
-                    for (int i = 0; i <= j; i++) {
-                        const double *vi = V + (size_t)i * ld;
-                        a = 0.0;
-                        for (int e = threadIdx.x; e < n; e += blockDim.x) a = fma(w[e], vi[e], a);
-                        const double h = cta_sum(a, sh);
-                        for (int e = threadIdx.x; e < n; e += blockDim.x) w[e] = fma(-h, vi[e], w[e]);
-                        if (threadIdx.x == 0) H[(size_t)j * (m + 1) + i] = h;
-                        len2 += h * h;
-                        __syncthreads();
-                    }
+            if (threadIdx.x == 0) S.g[0] = beta;
+            int k = 0;
+            for (int j = 0; j < m; j++) {
+                iters++;
+                double *w = V + (size_t)(j + 1) * ld;
+                coop_barrier(P);  // v_j complete
+                part_spmv(D, P, 1.0, V + (size_t)j * ld, 0.0, w);
+                // fused MGS: pass i applies the projection on v_{i-1}, takes (w, v_i)
+                double len2 = 0.0, hprev = 0.0;
+                for (int i = 0; i <= j; i++) {
+                    const double *vi = V + (size_t)i * ld;
+                    const double *vp = i > 0 ? V + (size_t)(i - 1) * ld : vi;
                     a = 0.0;
-                    for (int e = threadIdx.x; e < n; e += blockDim.x) a = fma(w[e], w[e], a);
-                    const double hn = sqrt(cta_sum(a, sh));
-                    if (threadIdx.x == 0) {
-                        double *col = H + (size_t)j * (m + 1);
-                        col[j + 1] = hn;
-                        for (int i = 0; i < j; i++) {
-                            const double c0 = col[i], c1 = col[i + 1];
-                            col[i] = cs[i] * c0 + sn[i] * c1;
-                            col[i + 1] = -sn[i] * c0 + cs[i] * c1;
-                        }
-                        const double c0 = col[j];
-                        const double rr = hypot(c0, hn);
-                        int flag = 0;
-                        if (rr == 0.0) {
-                            flag = 2;
-                        } else {
-                            cs[j] = c0 / rr;
-                            sn[j] = hn / rr;
-                            col[j] = rr;
-                            col[j + 1] = 0.0;
-                            g[j + 1] = -sn[j] * g[j];
-                            g[j] = cs[j] * g[j];
-                            if (hn <= 1e-14 * sqrt(len2 + hn * hn)) flag = 1;
-                            else if (fabs(g[j + 1]) / bnorm <= tau) flag = 3;
-                        }
-                        s_flag = flag;
+                    for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
+                        double we = w[e];
+                        if (i > 0) we = fma(-hprev, vp[e], we);
+                        w[e] = we;
+                        a = fma(we, vi[e], a);
                     }
-                    __syncthreads();
-                    const int flag = s_flag;
-                    if (flag == 2) {
-                        k = j;
-                        status = XB_EBREAKDOWN;
-                        break;
-                    }
-                    k = j + 1;
-                    if (flag == 1) {
-                        claimed = 1;
-                        break;
-                    }
-                    const double ih = 1.0 / hn;
-                    for (int e = threadIdx.x; e < n; e += blockDim.x) w[e] *= ih;
-                    __syncthreads();
-                    if (flag == 3) {
-                        claimed = 1;
-                        break;
-                    }
-                    if (iters >= maxiter) break;
+                    const double h = coop_sum(a, S, P);
+                    if (threadIdx.x == 0) H[(size_t)j * (m_max + 1) + i] = h;
+                    len2 += h * h;
+                    hprev = h;
                 }
-                if (status == XB_EBREAKDOWN) break;
-                // R y = g, x += V y
+                a = 0.0;
+                const double *vj = V + (size_t)j * ld;
+                for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
+                    const double we = fma(-hprev, vj[e], w[e]);
+                    w[e] = we;
+                    a = fma(we, we, a);
+                }
+                const double hn = sqrt(coop_sum(a, S, P));
                 if (threadIdx.x == 0) {
-                    for (int i = k - 1; i >= 0; i--) {
-                        double s = g[i];
-                        for (int c = i + 1; c < k; c++) s -= H[(size_t)c * (m + 1) + i] * yv[c];
-                        yv[i] = s / H[(size_t)i * (m + 1) + i];
+                    double *col = H + (size_t)j * (m_max + 1);
+                    col[j + 1] = hn;
+                    for (int i = 0; i < j; i++) {
+                        const double c0 = col[i], c1 = col[i + 1];
+                        col[i] = S.cs[i] * c0 + S.sn[i] * c1;
+                        col[i + 1] = -S.sn[i] * c0 + S.cs[i] * c1;
                     }
+                    const double c0 = col[j];
+                    const double rr = hypot(c0, hn);
+                    int flag = 0;
+                    if (rr == 0.0) {
+                        flag = 2;
+                    } else {
+                        S.cs[j] = c0 / rr;
+                        S.sn[j] = hn / rr;
+                        col[j] = rr;
+                        col[j + 1] = 0.0;
+                        S.g[j + 1] = -S.sn[j] * S.g[j];
+                        S.g[j] = S.cs[j] * S.g[j];
+                        if (hn <= 1e-14 * sqrt(len2 + hn * hn)) flag = 1;
+                        else if (fabs(S.g[j + 1]) / bnorm <= tau) flag = 3;
+                    }
+                    S.flag = flag;
                 }
                 __syncthreads();
-                for (int e = threadIdx.x; e < n; e += blockDim.x) {
-                    double s = 0.0;
-                    for (int i = 0; i < k; i++) s = fma(yv[i], V[(size_t)i * ld + e], s);
-                    S.x[e] += s;
-                }
+                const int flag = S.flag;
                 __syncthreads();
-                restarts++;
+                if (flag == 2) {
+                    k = j;
+                    status = XB_EBREAKDOWN;
+                    break;
+                }
+                k = j + 1;
+                if (flag == 1) {
+                    claimed = 1;
+                    break;
+                }
+                const double ih = 1.0 / hn;
+                for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) w[e] *= ih;
+                if (flag == 3) {
+                    claimed = 1;
+                    break;
+                }
+                if (iters >= maxiter) break;
+            }
+            if (status == XB_EBREAKDOWN) break;
+            // R y = g (every cooperating CTA holds the same R and g), x += V y
+            if (threadIdx.x == 0) {
+                for (int i = k - 1; i >= 0; i--) {
+                    double s = S.g[i];
+                    for (int c = i + 1; c < k; c++) s -= H[(size_t)c * (m_max + 1) + i] * S.yv[c];
+                    S.yv[i] = s / H[(size_t)i * (m_max + 1) + i];
+                }
+            }
+            __syncthreads();
+            for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
+                double s = 0.0;
+                for (int i = 0; i < k; i++) s = fma(S.yv[i], V[(size_t)i * ld + e], s);
+                D.x[e] += s;
+            }
+            restarts++;
+        }
+    }
+    if (threadIdx.x == 0 && rank == 0) {
+        xb_batch_info inf;
+        inf.status = status;
+        inf.iters = iters;
+        inf.restarts = restarts;
+        inf.m = m;
+        inf.mode = D.mode;
+        inf.res_true = res_true;
+        inf.ms = (double)(gtimer() - ts) * 1e-6;
+        *out = inf;
+    }
+    __syncthreads();
+}
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT)
+    k_batch_gmres(const xb_batch_dev *__restrict__ sys, xb_batch_info *__restrict__ out,
+                  const int *__restrict__ order, int count, int *__restrict__ queue, double tol,
+                  int maxiter, unsigned long long budget_ns, double theta) {
+    __shared__ Smem S;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    if (threadIdx.x == 0) S.t_start = gtimer();
+    // one deadline for the whole cluster: rank 0's start plus the budget
+    cl.sync();
+    const unsigned long long deadline = cl.map_shared_rank(&S, 0)->t_start + budget_ns;
+    cl.sync();
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int q = atomicAdd(queue, 1);
+            S.q = q;
+            S.big = (q < count && sys[order[q]].coop) ? 1 : 0;
+            S.q2 = (q < count && !S.big) ? atomicAdd(queue, kCl - 1) : count;
+        }
+        cl.sync();
+        const Smem *L = cl.map_shared_rank(&S, 0);
+        const int q = L->q, q2 = L->q2, big = L->big;
+        cl.sync();  // the leader may overwrite q only after every CTA has read it
+        if (q >= count) return;  // cluster-uniform
+        if (big) {
+            const xb_batch_dev D = sys[order[q]];
+            const int per = (D.n + kCl - 1) / kCl;
+            Part P{min(D.n, rank * per), min(D.n, (rank + 1) * per), 1, 0};
+            solve_one(D, P, S, tol, maxiter, deadline, rank, theta, out + order[q]);
+        } else {
+            const int mine = rank == 0 ? q : q2 + rank - 1;
+            if (mine < count) {
+                const xb_batch_dev D = sys[order[mine]];
+                Part P{0, D.n, 0, 0};
+                solve_one(D, P, S, tol, maxiter, deadline, 0, theta, out + order[mine]);
             }
         }
-        if (threadIdx.x == 0) {
-            xb_batch_info inf;
-            inf.status = status;
-            inf.iters = iters;
-            inf.restarts = restarts;
-            inf.m = m;
-            inf.mode = S.mode;
-            inf.res_true = res_true;
-            inf.ms = (double)(gtimer() - ts) * 1e-6;
-            out[id] = inf;
-        }
-        __syncthreads();
+        cl.sync();  // regroup before the next pull
     }
 }
 
@@ -267,13 +384,17 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
                     xb_batch **out) {
     if (count < 0 || (count > 0 && !sys) || !out) return xb::set_error(XB_EINVAL, "batch_create: bad argument");
     *out = nullptr;
+    (void)stream;
     xb_options o;
     if (opt) o = *opt;
     else xb_options_default(&o);
     if (!(o.tol > 0.0)) return xb::set_error(XB_EINVAL, "batch_create: tol must be > 0");
-    cudaStream_t s = (cudaStream_t)stream;
     std::vector<xb_batch_dev> h(count);
     size_t ws = 0;
+    // systems with n >= coop_min are solved by a whole cluster (environment
+    // variable XB_BATCH_COOP_MIN_N overrides the default)
+    long coop_min = kLargeN;
+    if (const char *env = std::getenv("XB_BATCH_COOP_MIN_N")) coop_min = std::max(1L, std::atol(env));
     for (int i = 0; i < count; i++) {
         const xb_batch_sys &q = sys[i];
         if (q.n < 0 || q.nnz < 0 || q.m < 1 || q.m > XB_BATCH_MAX_M || (q.mode != 0 && q.mode != 1) ||
@@ -284,15 +405,17 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
         d.n = q.n;
         d.nnz = q.nnz;
         d.m = q.m;
+        d.m_max = o.dafrt ? std::max(q.m, std::min(o.m_max, XB_BATCH_MAX_M)) : q.m;
         d.mode = q.mode;
         d.zero_x = q.zero_x;
+        d.coop = q.n >= coop_min ? 1 : 0;
         d.ld = ((int64_t)q.n + 31) / 32 * 32;
         d.rowptr = q.rowptr;
         d.col = q.col;
         d.val = q.val;
         d.b = q.b;
         d.x = q.x;
-        ws += (size_t)(q.m + 1) * d.ld + (size_t)(q.m + 1) * q.m + 32;
+        ws += (size_t)(d.m_max + 1) * d.ld + (size_t)(d.coop ? kCl : 1) * (d.m_max + 1) * d.m_max + 32;
     }
     xb_batch *bt = new xb_batch();
     bt->count = count;
@@ -307,8 +430,10 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     }
     size_t off = 0;
     for (int i = 0; i < count; i++) {
-        h[i].ws = bt->d_ws + off;
-        off += (size_t)(h[i].m + 1) * h[i].ld + (size_t)(h[i].m + 1) * h[i].m + 32;
+        h[i].V = bt->d_ws + off;
+        off += (size_t)(h[i].m_max + 1) * h[i].ld;
+        h[i].H = bt->d_ws + off;
+        off += (size_t)(h[i].coop ? kCl : 1) * (h[i].m_max + 1) * h[i].m_max + 32;
     }
     // largest first: the long solves start in the first wave
     std::vector<int> order(count);
@@ -325,16 +450,22 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     if (e == cudaSuccess && count > 0)
         e = cudaMemcpy(bt->d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(xb::cuda_error(e, "batch_create"));
-    // grid: as many CTAs as fit co-resident (persistent), at most one per system
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_gmres, kBT, 0);
-    if (e != cudaSuccess) return fail(xb::cuda_error(e, "batch_create: occupancy"));
-    bt->grid = std::max(1, std::min(count, std::max(1, per_sm) * xb::num_sms()));
-    const unsigned long long budget =
-        (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
-    // capture (on a private stream: the caller's may be the legacy default
+    // persistent grid: as many whole clusters as can be co-resident
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof lc);
+    lc.gridDim = dim3(kCl, 1, 1);
+    lc.blockDim = dim3(kBT, 1, 1);
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, (void *)k_batch_gmres, &lc);
+    if (e != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        clusters = std::max(1, xb::num_sms() / kCl);
+    }
+    bt->grid = kCl * std::max(1, clusters);
+    const unsigned long long budget = (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
+    const double theta = o.dafrt ? o.dafrt_theta : 0.0;  // theta 0: the rule never fires
+    // capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured): reset the queue, one persistent launch
-    (void)s;
     cudaStream_t cs = nullptr;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(xb::cuda_error(e, "batch_create: capture stream"));
@@ -345,7 +476,7 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     }
     cudaMemsetAsync(bt->d_queue, 0, sizeof(int), cs);
     k_batch_gmres<<<bt->grid, kBT, 0, cs>>>(bt->d_sys, bt->d_info, bt->d_order, count, bt->d_queue,
-                                             o.tol, o.maxiter, budget);
+                                             o.tol, o.maxiter, budget, theta);
     cudaError_t el = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &bt->graph);
     cudaStreamDestroy(cs);

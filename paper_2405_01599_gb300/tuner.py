@@ -39,6 +39,7 @@ BLOCKS = (64, 128, 256, 512)
 IPTS = (1, 4, 8, 16, 32)
 DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 MODEL_PATH = os.path.join(DATA_DIR, "mlp_tuner.bin")
+SMALL_CAP_S = 0.1        # per-solve time cap of the GMRES(m) timings
 
 
 def random_spec(rng, large=False):
@@ -110,7 +111,7 @@ def _randsym_fast(n, per, seed):
     return gen._mat(n, rowptr, Cc[o], V[o], True, kind="randsym")
 
 
-def record(xb, torch, dev, A, gmres_cap_s=0.1, gmres_maxiter=1500):
+def record(xb, torch, dev, A, gmres_cap_s=SMALL_CAP_S, gmres_maxiter=1500):
     """Sweep one matrix: features, every SpMV candidate's time, GMRES(m) times."""
     plan = xb.Plan.from_host(A, dev)
     t = [torch.as_tensor(A[k], device=dev) for k in ("rowptr", "col", "val")]
@@ -129,6 +130,7 @@ def record(xb, torch, dev, A, gmres_cap_s=0.1, gmres_maxiter=1500):
     b = torch.empty(n, dtype=torch.float64, device=dev)
     plan.spmv(torch.ones(n, dtype=torch.float64, device=dev), b)
     mt = np.full(len(RESTARTS), np.inf)
+    conv = np.zeros(len(RESTARTS), bool)
     for k, m in enumerate(RESTARTS):
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         info = plan.gmres(b, x, m=m, tol=1e-8, maxiter=gmres_maxiter, maxtime_s=gmres_cap_s,
@@ -137,9 +139,10 @@ def record(xb, torch, dev, A, gmres_cap_s=0.1, gmres_maxiter=1500):
         res = info["res_true"]
         if info["status"] == 0:
             mt[k] = ts
+            conv[k] = True
         elif 0.0 < res < 1.0:
             mt[k] = ts * math.log(1e-8) / math.log(res)
-    return dict(raw=raw, feat=feat, times=times, mtimes=mt, t_sweep=t_sweep, best=best)
+    return dict(raw=raw, feat=feat, times=times, mtimes=mt, mconv=conv, t_sweep=t_sweep, best=best)
 
 
 def make_data(count, seed, dev="cuda", log_every=50, large=False):
@@ -164,6 +167,7 @@ def make_data(count, seed, dev="cuda", log_every=50, large=False):
                 raw=np.stack([r["raw"] for r in recs]),
                 times=np.stack([r["times"] for r in recs]),
                 mtimes=np.stack([r["mtimes"] for r in recs]),
+                mconv=np.stack([r["mconv"] for r in recs]),
                 t_sweep=np.array([r["t_sweep"] for r in recs]),
                 specs=np.array(specs))
 
@@ -180,9 +184,21 @@ def labels_of(D):
     lab = np.zeros((N, 4), np.int32)
     for s in range(N):
         v, b, i = ALL_CANDS[int(np.nanargmin(D["times"][s]))]
-        mlab = int(np.argmin(D["mtimes"][s])) if D["raw"][s][0] <= M_LABEL_MAX_N else -1
-        lab[s] = (v, BLOCKS.index(b), IPTS.index(i), mlab)
+        lab[s] = (v, BLOCKS.index(b), IPTS.index(i), m_label(D, s))
     return lab
+
+
+def m_label(D, s):
+    """Fastest restart length among the runs that converged within the cap
+    (capped runs are extrapolations, which favour small m); -1 when none did
+    or the matrix is above M_LABEL_MAX_N."""
+    if D["raw"][s][0] > M_LABEL_MAX_N:
+        return -1
+    mt = D["mtimes"][s]
+    conv = D["mconv"][s] if "mconv" in D else (mt < SMALL_CAP_S)
+    if not conv.any():
+        return -1
+    return int(np.argmin(np.where(conv, mt, np.inf)))
 
 
 def n_records(D):
@@ -231,10 +247,10 @@ def evaluate(model, D, dev="cuda"):
         t_def = t[ALL_CANDS.index(dflt)]
         out["spmv_regret"].append(float(t_ml / t_best))
         out["spmv_gain_vs_default"].append(float(t_def / t_ml))
-        mt = D["mtimes"][s]
-        if np.isfinite(mt).any() and D["raw"][s][0] <= M_LABEL_MAX_N:
+        if m_label(D, s) >= 0:
+            mt = D["mtimes"][s]
             m_ml = mt[pred[s, 3]]
-            out["m_regret"].append(float(m_ml / np.min(mt)))
+            out["m_regret"].append(float(m_ml / mt[m_label(D, s)]))
             out["m_gain_vs_default"].append(float(mt[RESTARTS.index(30)] / m_ml))
     summ = {k: (float(np.exp(np.mean(np.log(v)))) if isinstance(v, list) and v else v)
             for k, v in out.items()}
@@ -260,6 +276,10 @@ def main():
             np.savez_compressed(a.out, **D)
     if a.train:
         parts = [dict(np.load(f)) for f in a.train]
+        for p_ in parts:
+            if "mconv" not in p_:
+                p_["mconv"] = p_["mtimes"] < (SMALL_CAP_S if p_["raw"][:, 0].max() <= M_LABEL_MAX_N
+                                              else 0.6)
         Dt = {k: np.concatenate([p_[k] for p_ in parts]) for k in parts[0]}
         print(f"[tuner train] {n_records(Dt)} timing records from {len(Dt['feat'])} matrices")
         model, loss = train_model(Dt, epochs=a.epochs)

@@ -27,14 +27,22 @@ def _systems(dev, specs):
 
 
 SPECS = [
+    (lambda: gen.poisson2d(130), 30, 0), (lambda: gen.powerlaw(n=20000, mean=20, sigma=0.6, seed=3), 30, 1),
+    (lambda: gen.powerlaw(n=20000, mean=12, sigma=0.5, seed=8), 30, 0),
+    (lambda: gen.laplace3d(28), 40, 0),
     (lambda: gen.poisson2d(40), 30, 0), (lambda: gen.poisson2d(33), 20, 1),
     (lambda: gen.laplace3d(12), 30, 0), (lambda: gen.convdiff3d(N=14), 10, 0),
-    (lambda: gen.powerlaw(n=6000, seed=4), 30, 1), (lambda: gen.powerlaw(n=3000, seed=5), 50, 0),
+    (lambda: gen.powerlaw(n=6000, mean=12, sigma=0.6, seed=4), 30, 1), (lambda: gen.powerlaw(n=3000, seed=5), 50, 0),
     (lambda: gen.random200(), 30, 0), (lambda: gen.poisson2d(8), 5, 1),
 ] * 3
 
 
-def test_batch_matches_oracle_and_replays(env=None):
+@pytest.mark.parametrize("coop_min", ["16384", "1000000000"])
+def test_batch_matches_oracle_and_replays(coop_min, monkeypatch):
+    """coop_min 16384: the systems with n >= 16384 go to whole clusters
+    (distributed-shared-memory reductions, cluster barriers); 1e9: every
+    system to a single CTA."""
+    monkeypatch.setenv("XB_BATCH_COOP_MIN_N", coop_min)
     xb, dev = lib_and_device()
     specs = [(f(), m, mode) for f, m, mode in SPECS]
     systems, mats = _systems(dev, specs)
@@ -55,6 +63,24 @@ def test_batch_matches_oracle_and_replays(env=None):
     for q, x, r, r2 in zip(systems, xs, res, res2):
         np.testing.assert_array_equal(q["x"].cpu().numpy(), x)
         assert r["iters"] == r2["iters"]
+
+
+def test_batch_restart_rule_grows_m(monkeypatch):
+    """With the MM-ratio rule on, a stagnating GMRES(5) grows its restart
+    length at run time (Eq. 1, Sec. 4.3) and still converges; the same
+    system from the cluster path and the single-CTA path agrees."""
+    monkeypatch.setenv("XB_BATCH_COOP_MIN_N", "16384")
+    xb, dev = lib_and_device()
+    specs = [(gen.poisson2d(140), 5, 0), (gen.poisson2d(60), 5, 0)]
+    systems, mats = _systems(dev, specs)
+    bt = xb.Batch(systems, tol=1e-8, maxiter=200000, maxtime_s=60.0, dafrt=1, m_max=60,
+                  dafrt_theta=10.0)
+    bt.run()
+    res = bt.results()
+    for (A, b), r, q in zip(mats, res, systems):
+        assert r["status"] == 0 and r["m"] > 5, r
+        x = q["x"].cpu().numpy()
+        assert np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b) <= 1e-8
 
 
 def test_batch_time_budget_returns_status():
