@@ -44,12 +44,18 @@ def parse():
                     help="skip the GMRES time-to-1e-8 comparison (256^3 convection-diffusion)")
     ap.add_argument("--batch", action="store_true",
                     help="also run the 512-system batched solve (default / learned / exhaustive)")
-    ap.add_argument("--variant", default=None, choices=["row", "nnz", "segscan"],
+    ap.add_argument("--variant", default=None,
+                    choices=["row", "nnz", "segscan", "sym-atomic", "sym-tile"],
                     help="fixed SpMV variant instead of the exhaustive tuner")
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--ipt", type=int, default=8)
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu captures); prints a short line")
+    ap.add_argument("--matrix", default="c3", choices=["c3", "c2-upper", "c2-full", "c4"],
+                    help="profile-only: power-law n (c3), 128^3 Laplacian upper/full (c2), "
+                         "256^3 convection-diffusion (c4)")
+    ap.add_argument("--gmres-steps", type=int, default=0,
+                    help="profile-only: run this many GMRES(30) Arnoldi steps instead of SpMVs")
     return ap.parse_args()
 
 
@@ -211,15 +217,33 @@ def main():
         pg = dist
     stream = torch.cuda.current_stream()
 
-    A = make_c3(args.n)
+    if args.profile_only and args.matrix != "c3":
+        from paper_2405_01599_gb300 import gen
+        A = {"c2-upper": lambda: gen.laplace3d(128, upper=True), "c2-full": lambda: gen.laplace3d(128),
+             "c4": lambda: gen.convdiff3d(N=256)}[args.matrix]()
+    else:
+        A = make_c3(args.n)
     n, nnz = A["n"], A["nnz"]
     plan = xb.Plan.from_host(A, dev)
     if args.variant:
-        v = {"row": xb.VAR_ROW, "nnz": xb.VAR_NNZ, "segscan": xb.VAR_SEGSCAN}[args.variant]
+        v = {"row": xb.VAR_ROW, "nnz": xb.VAR_NNZ, "segscan": xb.VAR_SEGSCAN,
+             "sym-atomic": xb.VAR_SYM_ATOMIC, "sym-tile": xb.VAR_SYM_TILE}[args.variant]
         plan.set_choice(v, args.block, args.ipt)
         choice = plan.choice()
     else:
         choice = plan.tune()
+    if args.profile_only and args.gmres_steps:
+        bvec = torch.empty(n, dtype=torch.float64, device=dev)
+        plan.spmv(torch.ones(n, dtype=torch.float64, device=dev), bvec)
+        xg = torch.zeros(n, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = plan.gmres(bvec, xg, m=30, tol=1e-30, maxiter=args.gmres_steps, check_every=10)
+        el = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "matrix": args.matrix, "gmres_steps": info["iters"],
+                              "s": el, "GBs_solve": info["bytes_alg"] / el / 1e9, "choice": choice}))
+        return
     x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, n), device=dev)
     y = torch.empty(n, dtype=torch.float64, device=dev)
     bytes_step = alg_bytes(A)
