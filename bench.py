@@ -72,7 +72,8 @@ class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+         "utilization.gpu")
 
     def __init__(self, index):
         self.index = index
@@ -106,7 +107,7 @@ class Clocks:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+        sm, mx, busy, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in self.rows:
             try:
@@ -115,11 +116,15 @@ class Clocks:
                 for k, nm in enumerate(names):
                     if r[4 + k].lower().startswith("active"):
                         reasons.add(nm)
+                if float(r[8]) >= 50:
+                    busy.append(float(r[0]))
             except Exception:
                 continue
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
+        use = busy if busy else sm
+        return {"sm_mhz": float(np.median(use)) if use else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "samples_under_load": len(busy),
+                "reasons": sorted(reasons)}
 
 
 def dist_init():
@@ -137,6 +142,24 @@ def make_c3(n):
 def alg_bytes(A, vb=8, beta=False):
     n, nnz = A["n"], A["nnz"]
     return (vb + 4) * nnz + 4 * (n + 1) + 2 * vb * n + (vb * n if beta else 0)
+
+
+# DRAM bytes (read + write) of one headline SpMV launch from an ncu capture, keyed by
+# (variant, block, ipt, n, nnz) and valid only while the kernel source is unchanged
+# (sha256 of csrc/spmv.cu at capture time); the capture and its command are summarised
+# in profiles/.
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(choice_name, block, ipt, n, nnz):
+    import hashlib
+    ent = NCU_TRAFFIC.get((choice_name, block, ipt, n, nnz))
+    if ent is None:
+        return None
+    with open(os.path.join(ROOT, "paper_2405_01599_gb300", "csrc", "spmv.cu"), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != ent[1]:
+            return None
+    return ent[0]
 
 
 def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None):
@@ -163,9 +186,7 @@ def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None):
         if time.perf_counter() > t_end or len(times) >= 50:
             break
     t = float(np.median(times))
-    b = 12 * sub["nnz"] + 4 * (r1 + 1) + 8 * r1 + 8 * r1 + 0  # x gathered, y written
-    b += 8 * r1  # x once (rows of the sample)
-    return b / t / 1e9, t, sub, len(times)
+    return alg_bytes(sub) / t / 1e9, t, sub, len(times)
 
 
 def run_reference(args, ws, rank):
@@ -185,8 +206,7 @@ def run_reference(args, ws, rank):
     for _ in range(args.steps):
         L.orc_spmv(sub["n"], sub["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
     el = time.perf_counter() - t0
-    b = 12 * sub["nnz"] + 4 * (sub["n"] + 1) + 16 * sub["n"] + 8 * sub["n"]
-    val = b * args.steps / el / 1e9
+    val = alg_bytes(sub) * args.steps / el / 1e9
     sample = f"rows 0..{sub['n']} of the n=4M power-law matrix ({sub['nnz']} non-zeros) per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": ws,
@@ -255,7 +275,13 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     clocks = Clocks(local)
     clocks.start()
-    time.sleep(0.3)
+    # untimed load phase (~1 s of the same SpMV) so the clock samples see the GPU busy
+    # right before and during the timed steps
+    t_load = time.perf_counter() + (0.0 if args.profile_only else 1.0)
+    while time.perf_counter() < t_load:
+        for _ in range(50):
+            plan.spmv(x, y)
+        torch.cuda.synchronize()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -324,9 +350,12 @@ def main():
                                    "block": choice["block"], "ipt": choice["ipt"]},
                    "alg_bytes_per_step": bytes_step,
                    "l2": "inputs larger than L2 (0.70 GB streamed per step > 129 MB)",
+                   "clocks_window": "1 s untimed load phase of the same SpMV, then the timed steps",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": ncu_traffic(xb.VARIANT_NAMES[choice["variant"]], choice["block"],
+                                            choice["ipt"], n, nnz),
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "kernel": "spmv (" + xb.VARIANT_NAMES[choice["variant"]] + ")"},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 8 * n,

@@ -190,19 +190,42 @@ __device__ __forceinline__ VB mgs_elem(VB &w, VB vp, VB vn, VB c, VB acc) {
     return OP == 2 ? fma(w, w, acc) : fma(w, vn, acc);
 }
 
+// 16-byte load with an L2 evict-first policy: v_{i-1} is read for the last time
+// in the sweep, so its lines should make way for w and v_i.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double2 ld_last_use(const double2 *a, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_last_use(const float4 *a, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+
 // One launch of the MGS sweep of Arnoldi step j:
 //   i == 0      : h_0j = (w, v_0)
 //   0 < i <= j  : w -= h_{i-1,j} v_{i-1};  h_ij = (w, v_i)
 //   i == j+1    : w -= h_jj v_j;  h_{j+1,j} = ||w||, then Givens.
 // Basis vectors are stored unnormalised with scales sc (v_i = sc[i]*V_i).
-// Operands move as 16-byte vectors (two per thread per iteration) when the
-// three arrays are 16-byte aligned.
+// Operands move as 16-byte vectors (two grid-wide chunks per thread per
+// iteration) when the three arrays are 16-byte aligned.  With rev set the
+// chunks are walked from the end of the vectors: consecutive launches of a
+// sweep alternate direction, so each starts on the w and v_i lines that the
+// previous one touched last and still finds them in L2.
 template <int OP, typename VB>
 __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
                                              const VB *__restrict__ vprev,
                                              const VB *__restrict__ vnext, xb::GmDev st, int j,
                                              int i, double *__restrict__ part,
-                                             unsigned *__restrict__ ticket, int vec) {
+                                             unsigned *__restrict__ ticket, int vec, int rev) {
     if (st.misc[xb::GM_STOP] != 0.0) return;
     const VB c = (VB)(OP != 0 ? st.misc[xb::GM_COEF] : 0.0);
     VB acc0 = VB(0), acc1 = VB(0);
@@ -214,29 +237,14 @@ __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
         T *w2 = reinterpret_cast<T *>(w);
         const T *p2 = reinterpret_cast<const T *>(OP != 0 ? vprev : w);
         const T *q2 = reinterpret_cast<const T *>(OP != 2 ? vnext : w);
-        const int64_t st2 = 2 * gstride();
-        int64_t e = gtid();
-        for (; e + gstride() < nv; e += st2) {
-            const int64_t f = e + gstride();
-            T a = w2[e], b = w2[f];
-            const T pa = OP != 0 ? p2[e] : a, pb = OP != 0 ? p2[f] : b;
-            const T qa = OP != 2 ? q2[e] : a, qb = OP != 2 ? q2[f] : b;
-#pragma unroll
-            for (int k = 0; k < N; k++) {
-                VB x = V16<VB>::get(a, k), y = V16<VB>::get(b, k);
-                acc0 = mgs_elem<OP>(x, V16<VB>::get(pa, k), V16<VB>::get(qa, k), c, acc0);
-                acc1 = mgs_elem<OP>(y, V16<VB>::get(pb, k), V16<VB>::get(qb, k), c, acc1);
-                V16<VB>::set(a, k, x);
-                V16<VB>::set(b, k, y);
-            }
-            if (OP != 0) {
-                w2[e] = a;
-                w2[f] = b;
-            }
-        }
-        for (; e < nv; e += gstride()) {
+        const uint64_t pol = l2_evict_first();
+        const int64_t gs = gstride();
+        const int64_t full = nv / gs;            // grid-wide chunks every thread owns
+        const int64_t et = full * gs + gtid();   // this thread's slot in the partial chunk
+        auto one = [&](int64_t e) {
             T a = w2[e];
-            const T pa = OP != 0 ? p2[e] : a, qa = OP != 2 ? q2[e] : a;
+            const T pa = OP != 0 ? ld_last_use(p2 + e, pol) : a;
+            const T qa = OP != 2 ? q2[e] : a;
 #pragma unroll
             for (int k = 0; k < N; k++) {
                 VB x = V16<VB>::get(a, k);
@@ -244,7 +252,32 @@ __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
                 V16<VB>::set(a, k, x);
             }
             if (OP != 0) w2[e] = a;
+        };
+        if (rev && et < nv) one(et);
+        int64_t k = 0;
+        for (; k + 1 < full; k += 2) {
+            const int64_t ka = rev ? full - 1 - k : k;
+            const int64_t e = ka * gs + gtid();
+            const int64_t f = rev ? e - gs : e + gs;
+            T a = w2[e], b = w2[f];
+            const T pa = OP != 0 ? ld_last_use(p2 + e, pol) : a;
+            const T pb = OP != 0 ? ld_last_use(p2 + f, pol) : b;
+            const T qa = OP != 2 ? q2[e] : a, qb = OP != 2 ? q2[f] : b;
+#pragma unroll
+            for (int q = 0; q < N; q++) {
+                VB x = V16<VB>::get(a, q), y = V16<VB>::get(b, q);
+                acc0 = mgs_elem<OP>(x, V16<VB>::get(pa, q), V16<VB>::get(qa, q), c, acc0);
+                acc1 = mgs_elem<OP>(y, V16<VB>::get(pb, q), V16<VB>::get(qb, q), c, acc1);
+                V16<VB>::set(a, q, x);
+                V16<VB>::set(b, q, y);
+            }
+            if (OP != 0) {
+                w2[e] = a;
+                w2[f] = b;
+            }
         }
+        if (k < full) one((rev ? full - 1 - k : k) * gs + gtid());
+        if (!rev && et < nv) one(et);
         done = nv * N;
     }
     for (int64_t e = done + gtid(); e < n; e += gstride()) {
@@ -527,12 +560,14 @@ int gm_mgs_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w,
     const int g = reduce_grid(n, kVB);
     const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)w % 16) == 0 &&
                      ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
-    k_mgs<0, VB><<<g, kVB, 0, s>>>(n, w, nullptr, V, st, j, 0, p->d_part, p->d_ticket, vec);
+    // pass i walks backwards when i is even: pass 0 then starts on the tail of w
+    // that the SpMV wrote last
+    k_mgs<0, VB><<<g, kVB, 0, s>>>(n, w, nullptr, V, st, j, 0, p->d_part, p->d_ticket, vec, 1);
     for (int i = 1; i <= j; i++)
         k_mgs<1, VB><<<g, kVB, 0, s>>>(n, w, V + (size_t)(i - 1) * ld, V + (size_t)i * ld, st, j, i,
-                                       p->d_part, p->d_ticket, vec);
+                                       p->d_part, p->d_ticket, vec, (i & 1) ? 0 : 1);
     k_mgs<2, VB><<<g, kVB, 0, s>>>(n, w, V + (size_t)j * ld, nullptr, st, j, j + 1, p->d_part,
-                                   p->d_ticket, vec);
+                                   p->d_ticket, vec, ((j + 1) & 1) ? 0 : 1);
     XB_LAUNCHED("k_mgs");
     return XB_OK;
 }

@@ -459,7 +459,7 @@ __global__ void k_yscale(int n, V beta, V *__restrict__ y) {
 // every transpose term u*x_i goes to y[j] through a device FP64 atomic (an
 // L2 reduction, no FP64 work on the SM).  y must hold beta*y beforehand.
 // ---------------------------------------------------------------------------
-template <typename V>
+template <typename V, bool A1>
 __global__ void __launch_bounds__(512) k_sym_atomic(int n, const int *__restrict__ rowptr,
                                                     const int *__restrict__ col,
                                                     const V *__restrict__ val,
@@ -467,9 +467,9 @@ __global__ void __launch_bounds__(512) k_sym_atomic(int n, const int *__restrict
                                                     V *__restrict__ y, const V *__restrict__ adev) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    if (adev) alpha = *adev;
+    if (!A1 && adev) alpha = *adev;
     const int a = rowptr[r], b = rowptr[r + 1];
-    const V axi = alpha * x[r];
+    const V axi = A1 ? x[r] : alpha * x[r];
     V s = V(0);
     for (int k = a; k < b; k++) {
         const int j = col[k];
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(512) k_sym_atomic(int n, const int *__restrict
         s = fma(u, x[j], s);
         if (j != r) atomicAdd(&y[j], u * axi);
     }
-    atomicAdd(&y[r], alpha * s);
+    atomicAdd(&y[r], A1 ? s : alpha * s);
 }
 
 // ---------------------------------------------------------------------------
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(512) k_sym_atomic(int n, const int *__restrict
 // non-zero region beyond the tile) reach device memory, as FP64 atomics.
 // Each tile row is then added to y once.  y must hold beta*y beforehand.
 // ---------------------------------------------------------------------------
-template <typename V, int IPT>
+template <typename V, int IPT, bool A1>
 __global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr,
                                                   const int *__restrict__ col,
                                                   const V *__restrict__ val,
@@ -498,13 +498,13 @@ __global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr
     extern __shared__ __align__(16) unsigned char sm_[];
     const int B = blockDim.x, tid = threadIdx.x;
     const int T = B * IPT;
-    if (adev) alpha = *adev;
+    if (!A1 && adev) alpha = *adev;
     const int r0 = trow[blockIdx.x], r1 = trow[blockIdx.x + 1];
     const int k0 = rowptr[r0], k1 = rowptr[r1];
     const int cnt = k1 - k0;
     V *red = reinterpret_cast<V *>(sm_);  // 32
     if (cnt > T) {  // one long row r0: whole CTA
-        const V axi = alpha * x[r0];
+        const V axi = A1 ? x[r0] : alpha * x[r0];
         V s = V(0);
         for (int e = k0 + tid; e < k1; e += B) {
             const int j = col[e];
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr
             if (j != r0) atomicAdd(&y[j], u * axi);
         }
         s = xbd::block_sum(s, red);
-        if (tid == 0) atomicAdd(&y[r0], alpha * s);
+        if (tid == 0) atomicAdd(&y[r0], A1 ? s : alpha * s);
         return;
     }
     V *acc = red + 32;     // B
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr
     V s = V(0);
     if (tid < nr) {
         const int r = r0 + tid;
-        const V axi = alpha * x[r];
+        const V axi = A1 ? x[r] : alpha * x[r];
         const int a = srp[tid], b = srp[tid + 1];
         for (int e = a; e < b; e++) {
             const int j = sc[e];
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr
         }
     }
     __syncthreads();
-    if (tid < nr) atomicAdd(&y[r0 + tid], fma(alpha, s, acc[tid]));
+    if (tid < nr) atomicAdd(&y[r0 + tid], A1 ? s + acc[tid] : fma(alpha, s, acc[tid]));
 }
 
 // Opt every kernel instantiation into the device's full shared-memory
@@ -658,8 +658,12 @@ int launch_sym(xb_plan *p, int variant, const int *rp, const int *ci, const V *v
     if (n == 0) return XB_OK;
     k_yscale<V><<<(n + 255) / 256, 256, 0, s>>>(n, beta, y);
     XB_LAUNCHED("k_yscale");
+    const bool a1 = (adev == nullptr && alpha == V(1));
     if (variant == XB_VAR_SYM_ATOMIC) {
-        k_sym_atomic<V><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
+        if (a1)
+            k_sym_atomic<V, true><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
+        else
+            k_sym_atomic<V, false><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
         XB_LAUNCHED("k_sym_atomic");
         return XB_OK;
     }
@@ -671,8 +675,15 @@ int launch_sym(xb_plan *p, int variant, const int *rp, const int *ci, const V *v
                       (size_t)block * ipt * 4 + (block + 1) * 4;
 #define XB_SYM(I)                                                                         \
     case I:                                                                               \
-        XB_TRY(smem_optin((const void *)k_sym_tile<V, I>, sm));                           \
-        k_sym_tile<V, I><<<tp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, y, tp->d_row, adev); \
+        if (a1) {                                                                         \
+            XB_TRY(smem_optin((const void *)k_sym_tile<V, I, true>, sm));                  \
+            k_sym_tile<V, I, true><<<tp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, y,   \
+                                                                tp->d_row, adev);         \
+        } else {                                                                          \
+            XB_TRY(smem_optin((const void *)k_sym_tile<V, I, false>, sm));                 \
+            k_sym_tile<V, I, false><<<tp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, y,  \
+                                                                 tp->d_row, adev);        \
+        }                                                                                 \
         break;
     switch (ipt) {
         XB_SYM(1) XB_SYM(2) XB_SYM(4) XB_SYM(8) XB_SYM(16)

@@ -266,6 +266,8 @@ def main():
     ap.add_argument("--train", nargs="*", default=None, help="dataset(s) to concatenate")
     ap.add_argument("--model", default=None)
     ap.add_argument("--evaluate", default=None)
+    ap.add_argument("--evaluate-data", default=None,
+                    help="saved held-out sweep (.npz) for --evaluate instead of --make-data")
     ap.add_argument("--epochs", type=int, default=400)
     a = ap.parse_args()
     D = None
@@ -291,6 +293,8 @@ def main():
     if a.evaluate:
         import paper_2405_01599_gb300 as xb
         model = xb.Mlp.load(a.evaluate)
+        if D is None and a.evaluate_data:
+            D = dict(np.load(a.evaluate_data))
         if D is None:
             raise SystemExit("--evaluate needs --make-data (held-out matrices)")
         summ, _ = evaluate(model, D)
