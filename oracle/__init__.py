@@ -54,8 +54,13 @@ def lib():
         L.orc_dafrt.restype = vi
         L.orc_arnoldi.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, vi, _f64p, _f64p]
         L.orc_arnoldi.restype = vi
+        L.orc_arnoldi_ortho.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, vi, vi, vi, _f64p,
+                                        _f64p]
+        L.orc_arnoldi_ortho.restype = vi
+        L.orc_gs_qr.argtypes = [vi, vi, _f64p, vi, vi, _f64p, _f64p]
+        L.orc_gs_qr.restype = vi
         L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
-                                vi, vd, vi, vi, _i32p, _f64p, vp, vp, vi]
+                                vi, vd, vi, vi, vi, _i32p, _f64p, vp, vp, vi]
         L.orc_gmres.restype = vi
         L.orc_bicgstab.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vd, vi,
                                    _i32p, _f64p]
@@ -124,32 +129,51 @@ def dafrt(samp, theta):
     return lib().orc_dafrt(samp.size, samp, float(theta))
 
 
-def arnoldi(A, v0, m):
+# orthogonalisations (Sec. 3.2.2) and the accuracy policy (Sec. 3.3.2)
+MGS, CGS, DGKS, BCGS, AUTO = 0, 1, 2, 3, 4
+
+
+def arnoldi(A, v0, m, ortho=MGS, bl=4):
     n, rp, ci, va = _csr(A)
     V = np.zeros((m + 1) * n)
     H = np.zeros((m + 1) * m)
-    k = lib().orc_arnoldi(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
-                          np.ascontiguousarray(v0, np.float64), m, V, H)
+    k = lib().orc_arnoldi_ortho(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
+                                np.ascontiguousarray(v0, np.float64), m, int(ortho), int(bl),
+                                V, H)
     return k, V.reshape(m + 1, n), H.reshape(m + 1, m)
 
 
+def gs_qr(X, ortho=MGS, bl=4):
+    """Gram-Schmidt QR of the columns of X (n x k) with the given
+    orthogonalisation; returns (Q, R, columns done)."""
+    X = np.asarray(X, np.float64)
+    n, k = X.shape
+    Xc = np.ascontiguousarray(X.T)  # column j contiguous
+    Q = np.zeros(n * k)
+    R = np.zeros(k * k)
+    d = lib().orc_gs_qr(n, k, Xc, int(ortho), int(bl), Q, R)
+    return Q.reshape(k, n).T, R.reshape(k, k).T, d
+
+
 def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
-          dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0):
+          dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0, ortho=MGS):
     """Restarted GMRES(m); returns (x, info dict)."""
     n, rp, ci, va = _csr(A)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
-    ii = np.zeros(4, np.int32)
+    ii = np.zeros(5, np.int32)
     dd = np.zeros(2)
     hist = np.zeros(max(hist_cap, 1))
     mh = np.zeros(max(hist_cap, 1), np.int32)
     st = lib().orc_gmres(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
                          np.ascontiguousarray(b, np.float64), x, int(m),
                          int(m_max if m_max is not None else m), float(tol), int(maxiter),
-                         1 if dafrt else 0, float(theta), int(window), int(dm), ii, dd,
+                         1 if dafrt else 0, float(theta), int(window), int(dm), int(ortho),
+                         ii, dd,
                          hist.ctypes.data if hist_cap else None,
                          mh.ctypes.data if hist_cap else None, int(hist_cap))
     info = dict(status=st, iters=int(ii[0]), restarts=int(ii[1]), m_final=int(ii[2]),
-                faults=int(ii[3]), res_implicit=float(dd[0]), res_true=float(dd[1]))
+                faults=int(ii[3]), ortho=int(ii[4]), res_implicit=float(dd[0]),
+                res_true=float(dd[1]))
     if hist_cap:
         k = min(info["restarts"] + 1, hist_cap)
         info["hist"] = hist[:k].copy()

@@ -2,8 +2,9 @@
  * oracle.c -- plain, slow, obviously-correct FP64 CPU reference for the hot
  * path of "Xabclib: A Fully Auto-tuned Sparse Iterative Solver" (Katagiri et
  * al.): CRS sparse matrix-vector multiply inside the restarted Krylov solvers
- * GMRES(m) and BiCGStab, the restart-frequency rule (Eq. 1, Fig. 2, Sec. 4.3),
- * and the pieces the GPU library adds around them (FP32-inside-FP64 iterative
+ * GMRES(m) and BiCGStab, the four re-orthogonalisations and the accuracy
+ * policy that picks one (Sec. 3.2.2, 3.3.2), the restart-frequency rule (Eq. 1,
+ * Fig. 2, Sec. 4.3), and the pieces the GPU library adds around them (FP32-inside-FP64 iterative
  * refinement, matrix features, and a small MLP with analytic gradients).
  *
  * THIS FILE IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and
@@ -188,12 +189,70 @@ int orc_dafrt(int I, const double *samp, double theta)
 /* Arnoldi with modified Gram-Schmidt (Sec. 3.2.2, "MGS: the default")       */
 /* ------------------------------------------------------------------------ */
 
-/* k steps of Arnoldi from v1 = v0/||v0||.  V is (m+1) x n (row j = v_{j+1}),
- * H is (m+1) x m row-major, both zero-filled here.  MGS per step j:
- * w = A v_j; for i = 1..j: h_ij = (w, v_i), w -= h_ij v_i; h_{j+1,j} = ||w||.
- * Stops early on breakdown (h_{j+1,j} == 0).  Returns the number of steps. */
-int orc_arnoldi(int n, int kind, const int *rp, const int *ci, const double *v,
-                const double *v0, int m, double *V, double *H)
+/* ------------------------------------------------------------------------ */
+/* Orthogonalisation of w against v_0..v_j (Sec. 3.2.2: the four             */
+/* re-orthogonalisation implementations OpenATLib offers)                    */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_MGS 0  /* modified Gram-Schmidt, the default                     */
+#define ORC_CGS 1  /* classical Gram-Schmidt                                 */
+#define ORC_DGKS 2 /* DGKS: classical Gram-Schmidt run two times             */
+#define ORC_BCGS 3 /* blocked CGS: CGS inside a block, MGS between blocks    */
+#define ORC_AUTO 4 /* accuracy policy (Sec. 3.3.2) chooses among the above   */
+
+/* V holds v_0..v_j as rows of length n; on return w is orthogonalised and
+ * h[0..j] holds the projection coefficients (h_ij of the Hessenberg column).
+ *   MGS : for i = 0..j: h_i = (w, v_i); w -= h_i v_i           (w updated each time)
+ *   CGS : h_i = (w, v_i) for all i with w fixed; then w -= sum_i h_i v_i
+ *   DGKS: CGS, then CGS again on the result; h = first + second coefficients
+ *   BCGS: the basis in consecutive blocks of bl vectors, taken in order; per
+ *         block CGS against the current w, then w updated before the next
+ *         block (bl = 4 in the solvers). */
+static void orth(int ortho, int bl, int n, int j, const double *V, double *w, double *h)
+{
+    if (ortho == ORC_MGS) {
+        for (int i = 0; i <= j; i++) {
+            h[i] = dot(n, w, V + (size_t)i * n);
+            for (int q = 0; q < n; q++)
+                w[q] -= h[i] * V[(size_t)i * n + q];
+        }
+        return;
+    }
+    if (ortho == ORC_CGS || ortho == ORC_DGKS) {
+        double *h2 = (double *)malloc(sizeof(double) * (size_t)(j + 1));
+        int passes = (ortho == ORC_DGKS) ? 2 : 1;
+        for (int i = 0; i <= j; i++) h[i] = 0.0;
+        for (int pass = 0; pass < passes; pass++) {
+            for (int i = 0; i <= j; i++)
+                h2[i] = dot(n, w, V + (size_t)i * n);
+            for (int i = 0; i <= j; i++) {
+                for (int q = 0; q < n; q++)
+                    w[q] -= h2[i] * V[(size_t)i * n + q];
+                h[i] += h2[i];
+            }
+        }
+        free(h2);
+        return;
+    }
+    /* ORC_BCGS */
+    for (int i0 = 0; i0 <= j; i0 += bl) {
+        int i1 = i0 + bl - 1;
+        if (i1 > j) i1 = j;
+        for (int i = i0; i <= i1; i++)
+            h[i] = dot(n, w, V + (size_t)i * n);
+        for (int i = i0; i <= i1; i++)
+            for (int q = 0; q < n; q++)
+                w[q] -= h[i] * V[(size_t)i * n + q];
+    }
+}
+
+/* k steps of Arnoldi from v1 = v0/||v0|| with the given orthogonalisation
+ * (block length bl for BCGS).  V is (m+1) x n (row j = v_{j+1}), H is
+ * (m+1) x m row-major, both zero-filled here.  Per step j: w = A v_j,
+ * orth(w) gives h_{0..j,j}, h_{j+1,j} = ||w||.  Stops early on breakdown
+ * (h_{j+1,j} == 0).  Returns the number of steps. */
+int orc_arnoldi_ortho(int n, int kind, const int *rp, const int *ci, const double *v,
+                      const double *v0, int m, int ortho, int bl, double *V, double *H)
 {
     memset(V, 0, sizeof(double) * (size_t)(m + 1) * n);
     memset(H, 0, sizeof(double) * (size_t)(m + 1) * m);
@@ -201,15 +260,13 @@ int orc_arnoldi(int n, int kind, const int *rp, const int *ci, const double *v,
     for (int i = 0; i < n; i++)
         V[i] = v0[i] / b;
     double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double *h = (double *)malloc(sizeof(double) * (size_t)(m + 1));
     int steps = 0;
     for (int j = 0; j < m; j++) {
         matvec(kind, n, rp, ci, v, V + (size_t)j * n, w);
-        for (int i = 0; i <= j; i++) {
-            double h = dot(n, w, V + (size_t)i * n);
-            H[(size_t)i * m + j] = h;
-            for (int q = 0; q < n; q++)
-                w[q] -= h * V[(size_t)i * n + q];
-        }
+        orth(ortho, bl, n, j, V, w, h);
+        for (int i = 0; i <= j; i++)
+            H[(size_t)i * m + j] = h[i];
         double hn = nrm2(n, w);
         H[(size_t)(j + 1) * m + j] = hn;
         steps = j + 1;
@@ -219,7 +276,50 @@ int orc_arnoldi(int n, int kind, const int *rp, const int *ci, const double *v,
             V[(size_t)(j + 1) * n + q] = w[q] / hn;
     }
     free(w);
+    free(h);
     return steps;
+}
+
+/* Gram-Schmidt QR of the k columns of X (column-major n x k) with the given
+ * orthogonalisation: column j is orthogonalised against q_0..q_{j-1} by
+ * orth(), then normalised.  Q is column-major n x k, R column-major k x k
+ * (upper triangular: R[i + j*k] = h_i for i < j, R[j + j*k] = norm).
+ * Returns the number of columns before a zero norm (k if none). */
+int orc_gs_qr(int n, int k, const double *X, int ortho, int bl, double *Q, double *R)
+{
+    memset(R, 0, sizeof(double) * (size_t)k * k);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double *h = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    int done = k;
+    for (int j = 0; j < k; j++) {
+        memcpy(w, X + (size_t)j * n, sizeof(double) * (size_t)n);
+        if (j > 0) {
+            orth(ortho, bl, n, j - 1, Q, w, h);
+            for (int i = 0; i < j; i++) R[i + (size_t)j * k] = h[i];
+        }
+        double nr = nrm2(n, w);
+        R[j + (size_t)j * k] = nr;
+        if (nr == 0.0) { done = j; break; }
+        for (int q = 0; q < n; q++) Q[(size_t)j * n + q] = w[q] / nr;
+    }
+    free(w);
+    free(h);
+    return done;
+}
+
+/* Arnoldi with MGS (the default orthogonalisation). */
+int orc_arnoldi(int n, int kind, const int *rp, const int *ci, const double *v,
+                const double *v0, int m, double *V, double *H)
+{
+    return orc_arnoldi_ortho(n, kind, rp, ci, v, v0, m, ORC_MGS, 4, V, H);
+}
+
+/* The accuracy policy's choice (Sec. 3.3.2): MGS when the requested accuracy
+ * is 1e-10 or tighter, else BCGS; DGKS once a fault convergence occurred. */
+static int policy_ortho(double tol, int faulted)
+{
+    if (faulted) return ORC_DGKS;
+    return tol <= 1e-10 ? ORC_MGS : ORC_BCGS;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -251,23 +351,29 @@ int orc_arnoldi(int n, int kind, const int *rp, const int *ci, const double *v,
  * restart still exceeds tol, the cycle's claim was false: the fault counter
  * is incremented and the implicit threshold is narrowed, tau *= tol/res_true.
  *
+ *   ortho:    ORC_MGS / ORC_CGS / ORC_DGKS / ORC_BCGS (block length 4), or
+ *             ORC_AUTO: the accuracy policy of Sec. 3.3.2 (MGS for tol <= 1e-10,
+ *             else BCGS; DGKS from the first fault convergence on).
+ *
  * iinfo: [0] iterations, [1] restarts (cycles completed), [2] final m,
- *        [3] fault-convergence events.
+ *        [3] fault-convergence events, [4] orthogonalisation in use at exit.
  * dinfo: [0] last implicit relative residual, [1] true relative residual.
  * hist/mhist (may be NULL): true relative residual at the start of each cycle
  *        and the restart length m that cycle runs with, up to hist_cap entries.
  */
 int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
               const double *b, double *x, int m, int m_max, double tol,
-              int maxiter, int dafrt, double theta, int window, int dm,
+              int maxiter, int dafrt, double theta, int window, int dm, int ortho,
               int *iinfo, double *dinfo, double *hist, int *mhist, int hist_cap)
 {
     if (m_max < m) m_max = m;
     int iters = 0, restarts = 0, faults = 0, K = 0, claimed = 0, status = ORC_OK;
+    int cur = (ortho == ORC_AUTO) ? policy_ortho(tol, 0) : ortho;
     double tau = tol, res_impl = 0.0, res_true = 0.0;
     double bnorm = nrm2(n, b);
     iinfo[0] = iinfo[1] = iinfo[3] = 0;
     iinfo[2] = m;
+    iinfo[4] = cur;
     if (bnorm == 0.0) {
         for (int i = 0; i < n; i++) x[i] = 0.0;
         dinfo[0] = dinfo[1] = 0.0;
@@ -282,6 +388,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
     double *g = (double *)malloc(sizeof(double) * (size_t)(m_max + 1));
     double *y = (double *)malloc(sizeof(double) * (size_t)m_max);
     double *samp = (double *)malloc(sizeof(double) * (size_t)(window > 0 ? window : 1));
+    double *hc = (double *)malloc(sizeof(double) * (size_t)(m_max + 1));
 
     for (;;) {
         /* r = b - A x, true residual */
@@ -292,7 +399,11 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
         if (hist && restarts < hist_cap) { hist[restarts] = res_true; mhist[restarts] = m; }
         if (res_true <= tol) { status = ORC_OK; break; }
         if (iters >= maxiter) { status = ORC_ENOCONV; break; }
-        if (claimed) { faults++; tau *= tol / res_true; }
+        if (claimed) {
+            faults++;
+            tau *= tol / res_true;
+            if (ortho == ORC_AUTO) cur = policy_ortho(tol, 1);
+        }
         claimed = 0;
         if (dafrt && restarts > 0 && window > 0) {
             samp[K++] = res_true;
@@ -313,13 +424,11 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
         for (int j = 0; j < m; j++) {
             iters++;
             matvec(kind, n, rp, ci, va, V + (size_t)j * n, w);
+            orth(cur, 4, n, j, V, w, hc);
             double len2 = 0.0;
             for (int i = 0; i <= j; i++) {
-                double h = dot(n, w, V + (size_t)i * n);
-                H[(size_t)i * m_max + j] = h;
-                len2 += h * h;
-                for (int q = 0; q < n; q++)
-                    w[q] -= h * V[(size_t)i * n + q];
+                H[(size_t)i * m_max + j] = hc[i];
+                len2 += hc[i] * hc[i];
             }
             double hn = nrm2(n, w);
             H[(size_t)(j + 1) * m_max + j] = hn;
@@ -366,9 +475,11 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
     iinfo[1] = restarts;
     iinfo[2] = m;
     iinfo[3] = faults;
+    iinfo[4] = cur;
     dinfo[0] = res_impl;
     dinfo[1] = res_true;
     free(r); free(w); free(V); free(H); free(cs); free(sn); free(g); free(y); free(samp);
+    free(hc);
     return status;
 }
 
@@ -601,9 +712,9 @@ int orc_gmres_ir(int n, const int *rp, const int *ci, const double *va,
         if (outer >= max_outer) { status = ORC_ENOCONV; break; }
         slow = (rn > 0.5 * prev) ? slow + 1 : 0;
         if (slow >= 2) {
-            int ii[4]; double dd[2];
+            int ii[5]; double dd[2];
             status = orc_gmres(n, 0, rp, ci, va, b, x, m, m, tol, 1 << 30, 0, 0.0, 0, 0,
-                               ii, dd, NULL, NULL, 0);
+                               ORC_MGS, ii, dd, NULL, NULL, 0);
             iinfo[4] = ii[0];
             iinfo[5] = 1;
             res = dd[1];
