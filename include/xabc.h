@@ -50,8 +50,15 @@ extern "C" {
                              /*   out-of-tile (non-zero region) ones global    */
 #define XB_NUM_VARIANTS 5
 
-#define XB_ORTHO_MGS 0       /* modified Gram-Schmidt (Sec. 3.2.2, default)    */
-#define XB_ORTHO_CGS2 1      /* DGKS: classical Gram-Schmidt twice            */
+/* Re-orthogonalisation in the Arnoldi step (Sec. 3.2.2) and the accuracy
+ * policy choosing it (Sec. 3.3.2). */
+#define XB_ORTHO_MGS 0       /* modified Gram-Schmidt (the default)            */
+#define XB_ORTHO_CGS 1       /* classical Gram-Schmidt                         */
+#define XB_ORTHO_DGKS 2      /* DGKS: classical Gram-Schmidt run two times     */
+#define XB_ORTHO_BCGS 3      /* blocked CGS, block length 4: CGS inside a      */
+                             /*   block, MGS between blocks                    */
+#define XB_ORTHO_AUTO 4      /* policy: MGS if tol <= 1e-10 else BCGS; DGKS    */
+                             /*   after a fault convergence                    */
 
 #define XB_PREC_FP64 0
 #define XB_PREC_MIXED 1      /* FP32 SpMV + Arnoldi basis inside FP64          */
@@ -106,6 +113,7 @@ typedef struct xb_info {
     int32_t block_used;
     int32_t ipt_used;
     int32_t spmv_calls;      /* SpMV launches in the solve                    */
+    int32_t ortho_used;      /* XB_ORTHO_* in use at exit (GMRES)             */
     double res_implicit;     /* last implicit (recursive) relative residual   */
     double res_true;         /* ||b - A x|| / ||b|| at exit, FP64             */
     double t_solve_s;        /* host wall time of the solve                   */
@@ -244,6 +252,13 @@ int xb_axpy(int32_t n, double a, const double *x, double *y, void *stream); /* y
  * h[k] = ||w||.  h: device, k+1 doubles. */
 int xb_mgs(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, double *w,
            double *h, void *stream);
+/* Orthogonalise w against the k rows of V (row-major k x ld, ld >= n, rows
+ * orthonormal) with ortho = XB_ORTHO_MGS / CGS / DGKS / BCGS (Sec. 3.2.2):
+ * on return w is the orthogonalised vector, h[0..k-1] the projection
+ * coefficients (for DGKS the sum of both passes) and h[k] = ||w||.
+ * h: device, k+1 doubles; 1 <= k <= 512; XB_ORTHO_AUTO is rejected. */
+int xb_orth(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, double *w,
+            double *h, int32_t ortho, void *stream);
 
 /* ---- run-time auto-tuning ------------------------------------------------ */
 
@@ -326,14 +341,15 @@ int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, i
  * the same algorithm as gmres_solve.  One persistent kernel (captured once in
  * a CUDA graph, replayed by xb_batch_run) holds as many CTAs as fit on the
  * GPU, in 8-CTA clusters; work comes from an atomic queue (largest systems
- * first).  A system with n >= 100000 (XB_BATCH_COOP_MIN_N in the environment
+ * first).  A system with n >= 30000 (XB_BATCH_COOP_MIN_N in the environment
  * overrides the threshold) is solved by a whole cluster, its dot products
  * combined through distributed shared memory; smaller systems take one CTA
  * each and need no inter-CTA synchronisation.  opt: tol, maxiter (per
  * system), maxtime_s (whole launch; checked at every restart), dafrt /
  * dafrt_theta / m_max (the restart-length rule, per system).  Per system:
  * m in [1, XB_BATCH_MAX_M] and the SpMV mode inside the CTA (0: thread per
- * row, 1: warp per row), as chosen by a tuner; zero_x = 1 makes the kernel
+ * row; 1: thread per row in warp-sized row blocks, rows longer than 32
+ * non-zeros taken by the whole warp), as chosen by a tuner; zero_x = 1 makes the kernel
  * start from x = 0 (so a replay repeats the same solve). */
 #define XB_BATCH_MAX_M 128
 typedef struct xb_batch_sys {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libxabc.so")
 XB_OK, XB_EINVAL, XB_ENOMEM, XB_ECUDA, XB_ENOCONV, XB_EBREAKDOWN, XB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE = -1, 0, 1, 2, 3, 4
 VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile"}
-ORTHO_MGS, ORTHO_CGS2 = 0, 1
+ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 TUNER_NONE, TUNER_EXHAUSTIVE, TUNER_MLP = 0, 1, 2
 
@@ -49,7 +49,8 @@ class Options(C.Structure):
 class Info(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("status", "iters", "restarts", "m_final", "faults",
                                          "outer", "inner_iters", "fallback", "variant_used",
-                                         "block_used", "ipt_used", "spmv_calls")] + \
+                                         "block_used", "ipt_used", "spmv_calls",
+                                         "ortho_used")] + \
                [(k, C.c_double) for k in ("res_implicit", "res_true", "t_solve_s", "spmv_ms",
                                           "bytes_alg")]
 
@@ -109,6 +110,7 @@ def lib():
         "xb_dot": (i32, [vp, i32, vp, vp, vp, vp]),
         "xb_axpy": (i32, [i32, f64, vp, vp, vp]),
         "xb_mgs": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, vp]),
+        "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
         "xb_tune_exhaustive": (i32, [vp, P(Choice), vp]),
         "xb_mm_ratio": (f64, [P(f64), i32, i32]),
         "xb_dafrt": (i32, [i32, P(f64), f64]),
@@ -318,6 +320,16 @@ class Plan:
         h = torch.empty(k + 1, dtype=torch.float64, device=V.device)
         _check(lib().xb_mgs(self._h, w.numel(), k, _ptr(V), ld, _ptr(w), _ptr(h),
                             _stream(stream)))
+        return h
+
+    def orth(self, V, w, ortho, stream=None):
+        """Orthogonalise w against the k rows of V with ORTHO_MGS / CGS / DGKS /
+        BCGS; returns h (k projection coefficients, then ||w||)."""
+        import torch
+        k, ld = V.shape
+        h = torch.empty(k + 1, dtype=torch.float64, device=V.device)
+        _check(lib().xb_orth(self._h, w.numel(), k, _ptr(V), ld, _ptr(w), _ptr(h), int(ortho),
+                             _stream(stream)))
         return h
 
 

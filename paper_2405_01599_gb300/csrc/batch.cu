@@ -36,7 +36,7 @@ namespace cg = cooperative_groups;
 namespace {
 constexpr int kCl = 8;          // CTAs per cluster
 constexpr int kBT = 512;        // threads per CTA
-constexpr int kLargeN = 100000; // systems this large are solved by a whole cluster
+constexpr int kLargeN = 30000;  // systems this large are solved by a whole cluster
 }  // namespace
 
 struct xb_batch_dev {
@@ -129,28 +129,103 @@ __device__ __forceinline__ void coop_barrier(const Part &P) {
 // y[r0:r1] = alpha*A[r0:r1,:]*x (+ beta*y).  x is written by the other CTAs
 // of the cluster during the launch, so it is read at L2 (ld.global.cg), the
 // coherence point, never through the SM-local read-only path.
+//   mode 0: one thread per row;
+//   mode 1: rows in warp-sized blocks, one thread per row, except that rows
+//           longer than 32 non-zeros are taken by the whole warp in turn
+//           (lanes stride over the row, shuffle reduction), so a power-law
+//           row of thousands of entries does not serialise one thread.
+__device__ __forceinline__ double row_dot(const int *__restrict__ col,
+                                          const double *__restrict__ val, const double *x,
+                                          int ka, int kb, int step) {
+    double s0 = 0.0, s1 = 0.0;
+    int k = ka;
+    for (; k + step < kb; k += 2 * step) {
+        const int c0 = __ldg(col + k), c1 = __ldg(col + k + step);
+        const double v0 = __ldg(val + k), v1 = __ldg(val + k + step);
+        s0 = fma(v0, __ldcg(x + c0), s0);
+        s1 = fma(v1, __ldcg(x + c1), s1);
+    }
+    if (k < kb) s0 = fma(__ldg(val + k), __ldcg(x + __ldg(col + k)), s0);
+    return s0 + s1;
+}
+
 __device__ void part_spmv(const xb_batch_dev &D, const Part &P, double alpha, const double *x,
                           double beta, double *y) {
+    const int *__restrict__ rp = D.rowptr;
     if (D.mode == 0) {
         for (int r = P.r0 + threadIdx.x; r < P.r1; r += blockDim.x) {
-            double s = 0.0;
-            for (int k = __ldg(D.rowptr + r); k < __ldg(D.rowptr + r + 1); k++)
-                s = fma(__ldg(D.val + k), __ldcg(x + __ldg(D.col + k)), s);
+            const double s = row_dot(D.col, D.val, x, __ldg(rp + r), __ldg(rp + r + 1), 1);
             y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
         }
     } else {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int r = P.r0 + w; r < P.r1; r += nw) {
-            double s = 0.0;
-            for (int k = __ldg(D.rowptr + r) + lane; k < __ldg(D.rowptr + r + 1); k += 32)
-                s = fma(__ldg(D.val + k), __ldcg(x + __ldg(D.col + k)), s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
+        for (int base = P.r0 + 32 * w; base < P.r1; base += 32 * nw) {  // warp-uniform
+            const int r = base + lane;
+            int ka = 0, kb = 0;
+            if (r < P.r1) {
+                ka = __ldg(rp + r);
+                kb = __ldg(rp + r + 1);
+            }
+            const bool lng = kb - ka > 32;
+            double s = lng ? 0.0 : row_dot(D.col, D.val, x, ka, kb, 1);
+            unsigned todo = __ballot_sync(0xffffffffu, lng);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int la = __shfl_sync(0xffffffffu, ka, src);
+                const int lb = __shfl_sync(0xffffffffu, kb, src);
+                double t = row_dot(D.col, D.val, x, la + lane, lb, 32);
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == src) s = t;
+            }
+            if (r < P.r1) y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
         }
     }
-    // rows were stored by other threads than the ones that read them next
-    // (mode 1: lane 0 of a warp), so the CTA meets before anyone reads y
+    // rows were stored by other threads than the ones that read them next,
+    // so the CTA meets before anyone reads y
     __syncthreads();
+}
+
+// One fused MGS pass over rows [r0, r1) of this CTA (four rows per thread in
+// flight): OP 0 returns (w, vn); OP 1 applies w -= c vp and returns (w, vn);
+// OP 2 applies w -= c vp and returns (w, w).
+template <int OP>
+__device__ __forceinline__ double mgs_rows(double *__restrict__ w, const double *__restrict__ vp,
+                                           const double *__restrict__ vn, double c, int r0,
+                                           int r1) {
+    const int S = blockDim.x;
+    double a0 = 0.0, a1 = 0.0;
+    int e = r0 + threadIdx.x;
+    for (; e + 3 * S < r1; e += 4 * S) {
+        double x[4], p[4], q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) x[u] = w[e + u * S];
+        if (OP != 0) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) p[u] = vp[e + u * S];
+        }
+        if (OP != 2) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) q[u] = vn[e + u * S];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (OP != 0) x[u] = fma(-c, p[u], x[u]);
+            const double o = OP == 2 ? x[u] : q[u];
+            if (u & 1) a1 = fma(x[u], o, a1);
+            else a0 = fma(x[u], o, a0);
+            if (OP != 0) w[e + u * S] = x[u];
+        }
+    }
+    for (; e < r1; e += S) {
+        double xe = w[e];
+        if (OP != 0) {
+            xe = fma(-c, vp[e], xe);
+            w[e] = xe;
+        }
+        a0 = fma(xe, OP == 2 ? xe : vn[e], a0);
+    }
+    return a0 + a1;
 }
 
 __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, int maxiter,
@@ -222,26 +297,14 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
                 double len2 = 0.0, hprev = 0.0;
                 for (int i = 0; i <= j; i++) {
                     const double *vi = V + (size_t)i * ld;
-                    const double *vp = i > 0 ? V + (size_t)(i - 1) * ld : vi;
-                    a = 0.0;
-                    for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
-                        double we = w[e];
-                        if (i > 0) we = fma(-hprev, vp[e], we);
-                        w[e] = we;
-                        a = fma(we, vi[e], a);
-                    }
+                    a = i == 0 ? mgs_rows<0>(w, nullptr, vi, 0.0, r0, r1)
+                               : mgs_rows<1>(w, vi - ld, vi, hprev, r0, r1);
                     const double h = coop_sum(a, S, P);
                     if (threadIdx.x == 0) H[(size_t)j * (m_max + 1) + i] = h;
                     len2 += h * h;
                     hprev = h;
                 }
-                a = 0.0;
-                const double *vj = V + (size_t)j * ld;
-                for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
-                    const double we = fma(-hprev, vj[e], w[e]);
-                    w[e] = we;
-                    a = fma(we, we, a);
-                }
+                a = mgs_rows<2>(w, V + (size_t)j * ld, nullptr, hprev, r0, r1);
                 const double hn = sqrt(coop_sum(a, S, P));
                 if (threadIdx.x == 0) {
                     double *col = H + (size_t)j * (m_max + 1);
@@ -299,10 +362,26 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
                 }
             }
             __syncthreads();
-            for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
-                double s = 0.0;
-                for (int i = 0; i < k; i++) s = fma(S.yv[i], V[(size_t)i * ld + e], s);
-                D.x[e] += s;
+            {
+                const double *__restrict__ Vc = V;
+                double *__restrict__ xo = D.x;
+                const int B = blockDim.x;
+                int e = r0 + threadIdx.x;
+                for (; e + B < r1; e += 2 * B) {  // two rows per thread in flight
+                    double s0 = 0.0, s1 = 0.0;
+                    for (int i = 0; i < k; i++) {
+                        const double yi = S.yv[i];
+                        s0 = fma(yi, Vc[(size_t)i * ld + e], s0);
+                        s1 = fma(yi, Vc[(size_t)i * ld + e + B], s1);
+                    }
+                    xo[e] += s0;
+                    xo[e + B] += s1;
+                }
+                for (; e < r1; e += B) {
+                    double s0 = 0.0;
+                    for (int i = 0; i < k; i++) s0 = fma(S.yv[i], Vc[(size_t)i * ld + e], s0);
+                    xo[e] += s0;
+                }
             }
             restarts++;
         }
@@ -321,7 +400,7 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
     __syncthreads();
 }
 
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 1)
     k_batch_gmres(const xb_batch_dev *__restrict__ sys, xb_batch_info *__restrict__ out,
                   const int *__restrict__ order, int count, int *__restrict__ queue, double tol,
                   int maxiter, unsigned long long budget_ns, double theta) {

@@ -102,4 +102,30 @@ int xb_mgs(xb_plan *p, int32_t n, int32_t k, const double *V, int64_t ld, double
     return XB_OK;
 }
 
+int xb_orth(xb_plan *p, int32_t n, int32_t k, const double *V, int64_t ld, double *w, double *h,
+            int32_t ortho, void *stream) {
+    if (!p || n < 0 || k < 1 || k > 512 || ld < n || !V || !w || !h || ortho < XB_ORTHO_MGS ||
+        ortho > XB_ORTHO_BCGS)
+        return xb::set_error(XB_EINVAL, "xb_orth: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int M = k;
+    XB_TRY(xb::ensure_work(p, xb::gm_doubles(M) * sizeof(double) + 256));
+    double *base = static_cast<double *>(p->d_work);
+    XB_CUDA(cudaMemsetAsync(base, 0, xb::gm_doubles(M) * sizeof(double), s));
+    xb::GmDev st = xb::gm_layout(base, M);
+    // unit scales, raw mode: the column is left unrotated
+    std::vector<double> ones(M + 1, 1.0);
+    XB_CUDA(cudaMemcpyAsync(st.sc, ones.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+    double misc[xb::GM_NMISC] = {0};
+    misc[xb::GM_BNORM] = 1.0;
+    misc[xb::GM_TAU] = -1.0;
+    misc[xb::GM_RAW] = 1.0;
+    XB_CUDA(cudaMemcpyAsync(st.misc, misc, sizeof misc, cudaMemcpyHostToDevice, s));
+    XB_TRY(xb::gm_ortho_step<double>(p, st, n, V, ld, w, k - 1, ortho, s));
+    XB_CUDA(cudaMemcpyAsync(h, st.H + (size_t)(k - 1) * (M + 1), (k + 1) * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+    XB_CUDA(cudaStreamSynchronize(s));
+    return XB_OK;
+}
+
 }  // extern "C"

@@ -35,6 +35,7 @@ int cuda_error(cudaError_t e, const char *where);
 
 // ---- device constants ------------------------------------------------------
 constexpr int kRedSlots = 2048;     // max CTAs of a reduction grid
+constexpr int kRedValues = 16;      // max values reduced together by one grid
 constexpr int kScalars = 4096;      // device scalar scratch per plan (doubles)
 
 int num_sms();                      // cached cudaDevAttrMultiProcessorCount

@@ -3,6 +3,7 @@
 // no run-to-run variation), the fused modified Gram-Schmidt step of Arnoldi
 // (Sec. 3.2.2, MGS) with the Givens update folded into its final CTA, and the
 // fused BiCGStab updates.  Scalars never leave the device inside a step.
+#include <cstdlib>
 #include "krylov.cuh"
 
 #include <cmath>
@@ -216,16 +217,17 @@ __device__ __forceinline__ float4 ld_last_use(const float4 *a, uint64_t pol) {
 //   i == j+1    : w -= h_jj v_j;  h_{j+1,j} = ||w||, then Givens.
 // Basis vectors are stored unnormalised with scales sc (v_i = sc[i]*V_i).
 // Operands move as 16-byte vectors (two grid-wide chunks per thread per
-// iteration) when the three arrays are 16-byte aligned.  With rev set the
-// chunks are walked from the end of the vectors: consecutive launches of a
-// sweep alternate direction, so each starts on the w and v_i lines that the
-// previous one touched last and still finds them in L2.
+// iteration) when the three arrays are 16-byte aligned.  flags bit 0: walk the
+// chunks from the end of the vectors (consecutive launches of a sweep alternate
+// direction, so each starts on the w and v_i lines that the previous one
+// touched last and still finds them in L2); bit 1: load v_{i-1} with an L2
+// evict-first policy.
 template <int OP, typename VB>
 __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
                                              const VB *__restrict__ vprev,
                                              const VB *__restrict__ vnext, xb::GmDev st, int j,
                                              int i, double *__restrict__ part,
-                                             unsigned *__restrict__ ticket, int vec, int rev) {
+                                             unsigned *__restrict__ ticket, int vec, int flags) {
     if (st.misc[xb::GM_STOP] != 0.0) return;
     const VB c = (VB)(OP != 0 ? st.misc[xb::GM_COEF] : 0.0);
     VB acc0 = VB(0), acc1 = VB(0);
@@ -237,13 +239,14 @@ __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
         T *w2 = reinterpret_cast<T *>(w);
         const T *p2 = reinterpret_cast<const T *>(OP != 0 ? vprev : w);
         const T *q2 = reinterpret_cast<const T *>(OP != 2 ? vnext : w);
+        const bool rev = flags & 1, hint = flags & 2;
         const uint64_t pol = l2_evict_first();
         const int64_t gs = gstride();
         const int64_t full = nv / gs;            // grid-wide chunks every thread owns
         const int64_t et = full * gs + gtid();   // this thread's slot in the partial chunk
         auto one = [&](int64_t e) {
             T a = w2[e];
-            const T pa = OP != 0 ? ld_last_use(p2 + e, pol) : a;
+            const T pa = OP != 0 ? (hint ? ld_last_use(p2 + e, pol) : p2[e]) : a;
             const T qa = OP != 2 ? q2[e] : a;
 #pragma unroll
             for (int k = 0; k < N; k++) {
@@ -260,8 +263,8 @@ __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
             const int64_t e = ka * gs + gtid();
             const int64_t f = rev ? e - gs : e + gs;
             T a = w2[e], b = w2[f];
-            const T pa = OP != 0 ? ld_last_use(p2 + e, pol) : a;
-            const T pb = OP != 0 ? ld_last_use(p2 + f, pol) : b;
+            const T pa = OP != 0 ? (hint ? ld_last_use(p2 + e, pol) : p2[e]) : a;
+            const T pb = OP != 0 ? (hint ? ld_last_use(p2 + f, pol) : p2[f]) : b;
             const T qa = OP != 2 ? q2[e] : a, qb = OP != 2 ? q2[f] : b;
 #pragma unroll
             for (int q = 0; q < N; q++) {
@@ -298,6 +301,198 @@ __global__ void __launch_bounds__(kVB) k_mgs(int64_t n, VB *__restrict__ w,
         } else {
             gm_givens(st, j, sqrt(t[0]));
         }
+    }
+}
+
+// ---- block Gram-Schmidt family: CGS, DGKS, BCGS (Sec. 3.2.2) ----------------------
+
+constexpr int kMaxCoef = 520;  // >= M + 1 for every basis capacity M <= 512
+constexpr int kBgsAcc = 1, kBgsFin = 2, kBgsRev = 4;
+
+// Sum cnt <= NV per-thread values over the grid.  Returns true in every thread
+// of the last CTA to finish, with the totals in tot[0..cnt) (shared memory),
+// summed in a fixed order (deterministic).
+template <int NV>
+__device__ bool grid_reduce_n(const double (&v)[NV], int cnt, double *__restrict__ part,
+                              unsigned *__restrict__ ticket, double *tot) {
+    __shared__ double sh[NV][kVB / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int G = gridDim.x;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        if (q < cnt) {
+            double a = v[q];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) sh[q][wp] = a;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+        double a = 0.0;
+        for (int k = 0; k < nw; k++) a += sh[threadIdx.x][k];
+        part[(size_t)threadIdx.x * G + blockIdx.x] = a;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == (unsigned)G - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int q = wp; q < cnt; q += nw) {
+        double a = 0.0;
+        for (int i = lane; i < G; i += 32) a += __ldcg(part + (size_t)q * G + i);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) tot[q] = a;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+// U elements (16-byte vectors at e[0..U)) of one block Gram-Schmidt pass:
+// update by the nu pending vectors (at most KU when KU > 0), store w, then the
+// nd dot products (or the squared norm when fin).  The U elements' loads are
+// issued together.
+template <typename VB, int KD, int KU, int U>
+__device__ __forceinline__ void bgs_elems(int64_t ea, int64_t eb, typename V16<VB>::T *w2,
+                                          const typename V16<VB>::T *V2, int64_t ldv, int u0,
+                                          int nu, int d0, int nd, bool fin, const VB *cf,
+                                          VB (&acc)[KD]) {
+    using T = typename V16<VB>::T;
+    constexpr int N = V16<VB>::N;
+    const int64_t e[2] = {ea, eb};
+    T x[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) x[u] = w2[e[u]];
+    if (nu > 0) {
+        const int cnt = KU > 0 ? KU : nu;
+#pragma unroll 4
+        for (int i = 0; i < cnt; i++) {
+            if (KU > 0 && i >= nu) break;
+            const T *vi = V2 + (size_t)(u0 + i) * ldv;
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) v[u] = vi[e[u]];
+            const VB c = cf[i];
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int q = 0; q < N; q++)
+                    V16<VB>::set(x[u], q, fma(-c, V16<VB>::get(v[u], q), V16<VB>::get(x[u], q)));
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) w2[e[u]] = x[u];
+    }
+    if (fin) {
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int q = 0; q < N; q++)
+                acc[0] = fma(V16<VB>::get(x[u], q), V16<VB>::get(x[u], q), acc[0]);
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < KD; d++) {
+        if (d < nd) {
+            const T *vd = V2 + (size_t)(d0 + d) * ldv;
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) v[u] = vd[e[u]];
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int q = 0; q < N; q++)
+                    acc[d] = fma(V16<VB>::get(x[u], q), V16<VB>::get(v[u], q), acc[d]);
+        }
+    }
+}
+
+// One pass of the block Gram-Schmidt family for Arnoldi step j:
+//   w -= sum_{u0 <= i < u1} coef_i V_i          (the pending update; none if u0 == u1;
+//                                               at most KU vectors when KU > 0)
+//   then either the dots (w, V_i) for d0 <= i < d0 + nd (nd <= KD), or, with
+//   kBgsFin (nd == 0), (w, w).
+// The last CTA turns dots into Hessenberg entries h_i = sc_i (w, V_i) (added to
+// the column with kBgsAcc: the second pass of DGKS) and the coefficients the
+// next pass subtracts, coef_i = sc_i h_i; with kBgsFin it stores
+// h_{j+1,j} = ||w|| and applies the Givens update (or only stores it in raw
+// mode).  kBgsRev walks the grid-wide chunks from the end (alternating passes
+// start on the lines the previous pass touched last).  Operands move as
+// 16-byte vectors, two grid-wide chunks per thread per iteration, when V, w
+// and the row stride allow it.
+template <typename VB, int KD, int KU, int MINB>
+__global__ void __launch_bounds__(kVB, MINB) k_bgs(int64_t n, VB *__restrict__ w,
+                                             const VB *__restrict__ V, int64_t ld, int u0, int u1,
+                                             int d0, int nd, int flags, xb::GmDev st, int j,
+                                             double *__restrict__ part,
+                                             unsigned *__restrict__ ticket, int vec) {
+    if (st.misc[xb::GM_STOP] != 0.0) return;
+    __shared__ VB cf[kMaxCoef];
+    __shared__ double tot[KD];
+    const int nu = u1 - u0;
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) cf[i] = (VB)st.coef[u0 + i];
+    __syncthreads();
+    const bool fin = flags & kBgsFin, rev = flags & kBgsRev;
+    VB acc[KD];
+#pragma unroll
+    for (int q = 0; q < KD; q++) acc[q] = VB(0);
+    int64_t done = 0;
+    if (vec) {
+        using T = typename V16<VB>::T;
+        constexpr int N = V16<VB>::N;
+        const int64_t nv = n / N, ldv = ld / N;
+        T *w2 = reinterpret_cast<T *>(w);
+        const T *V2 = reinterpret_cast<const T *>(V);
+        const int64_t gs = gstride();
+        const int64_t full = nv / gs;           // grid-wide chunks every thread owns
+        const int64_t et = full * gs + gtid();  // this thread's slot in the partial chunk
+        if (rev && et < nv) bgs_elems<VB, KD, KU, 1>(et, et, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
+        int64_t k = 0;
+        for (; k + 1 < full; k += 2) {
+            const int64_t e = (rev ? full - 1 - k : k) * gs + gtid();
+            bgs_elems<VB, KD, KU, 2>(e, rev ? e - gs : e + gs, w2, V2, ldv, u0, nu, d0, nd, fin, cf,
+                                     acc);
+        }
+        if (k < full) {
+            const int64_t e = (rev ? full - 1 - k : k) * gs + gtid();
+            bgs_elems<VB, KD, KU, 1>(e, e, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
+        }
+        if (!rev && et < nv) bgs_elems<VB, KD, KU, 1>(et, et, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
+        done = nv * N;
+    }
+    for (int64_t e = done + gtid(); e < n; e += gstride()) {
+        VB x = w[e];
+        if (nu > 0) {
+            for (int i = 0; i < nu; i++) x = fma(-cf[i], V[(size_t)(u0 + i) * ld + e], x);
+            w[e] = x;
+        }
+        if (fin) {
+            acc[0] = fma(x, x, acc[0]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < KD; q++)
+                if (q < nd) acc[q] = fma(x, V[(size_t)(d0 + q) * ld + e], acc[q]);
+        }
+    }
+    double v[KD];
+#pragma unroll
+    for (int q = 0; q < KD; q++) v[q] = (double)acc[q];
+    if (!grid_reduce_n<KD>(v, fin ? 1 : nd, part, ticket, tot)) return;
+    double *col = st.H + (size_t)j * (st.M + 1);
+    if (!fin) {
+        for (int q = threadIdx.x; q < nd; q += blockDim.x) {
+            const int i = d0 + q;
+            const double h = st.sc[i] * tot[q];
+            col[i] = (flags & kBgsAcc) ? col[i] + h : h;
+            st.coef[i] = st.sc[i] * h;
+        }
+    } else if (threadIdx.x == 0) {
+        double len2 = 0.0;
+        for (int i = 0; i <= j; i++) len2 += col[i] * col[i];
+        st.misc[xb::GM_LEN2] = len2;
+        if (st.misc[xb::GM_RAW] != 0.0) col[j + 1] = sqrt(tot[0]);
+        else gm_givens(st, j, sqrt(tot[0]));
     }
 }
 
@@ -354,12 +549,30 @@ __global__ void __launch_bounds__(kVB) k_gm_xupd(int64_t n, const VB *__restrict
 }
 
 // ---- BiCGStab ------------------------------------------------------------------
+// Every kernel walks its vectors as 16-byte pairs when all of them are 16-byte
+// aligned (vec != 0), then finishes the odd tail element by element.
+
+__device__ __forceinline__ double2 ld2(const double *a, int64_t i) {
+    return reinterpret_cast<const double2 *>(a)[i];
+}
+__device__ __forceinline__ void st2(double *a, int64_t i, double2 v) {
+    reinterpret_cast<double2 *>(a)[i] = v;
+}
 
 // rho = (rhat, r) with rhat = r at a (re)start; alpha = omega = rho_old = 1.
 __global__ void k_bi_init(int64_t n, const double *__restrict__ r, double *__restrict__ sc,
-                          double tau2, double *__restrict__ part, unsigned *__restrict__ ticket) {
+                          double tau2, double *__restrict__ part, unsigned *__restrict__ ticket,
+                          int vec) {
     double v[1] = {0.0};
-    for (int64_t i = gtid(); i < n; i += gstride()) v[0] = fma(r[i], r[i], v[0]);
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = gtid(); i < n / 2; i += gstride()) {
+            const double2 a = ld2(r, i);
+            v[0] = fma(a.y, a.y, fma(a.x, a.x, v[0]));
+        }
+        done = n / 2 * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) v[0] = fma(r[i], r[i], v[0]);
     double t[1];
     if (grid_reduce<1>(v, part, ticket, t) && threadIdx.x == 0) {
         sc[xb::BI_RHO] = t[0];
@@ -375,20 +588,40 @@ __global__ void k_bi_init(int64_t n, const double *__restrict__ r, double *__res
 
 // p = r + beta (p - omega v), beta = (rho/rho_old)(alpha/omega).
 __global__ void k_bi_p(int64_t n, const double *__restrict__ sc, const double *__restrict__ r,
-                       double *__restrict__ p, const double *__restrict__ v) {
+                       double *__restrict__ p, const double *__restrict__ v, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
     const double beta = (sc[xb::BI_RHO] / sc[xb::BI_RHO_OLD]) * (sc[xb::BI_ALPHA] / sc[xb::BI_OMEGA]);
     const double om = sc[xb::BI_OMEGA];
-    for (int64_t i = gtid(); i < n; i += gstride()) p[i] = fma(beta, fma(-om, v[i], p[i]), r[i]);
+    auto f = [=](double ri, double pi, double vi) { return fma(beta, fma(-om, vi, pi), ri); };
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = gtid(); i < n / 2; i += gstride()) {
+            const double2 a = ld2(r, i), c = ld2(v, i);
+            double2 q = ld2(p, i);
+            q.x = f(a.x, q.x, c.x);
+            q.y = f(a.y, q.y, c.y);
+            st2(p, i, q);
+        }
+        done = n / 2 * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) p[i] = f(r[i], p[i], v[i]);
 }
 
 // sigma = (rhat, v); alpha = rho / sigma.
 __global__ void k_bi_sigma(int64_t n, double *__restrict__ sc, const double *__restrict__ rh,
                            const double *__restrict__ v, double *__restrict__ part,
-                           unsigned *__restrict__ ticket) {
+                           unsigned *__restrict__ ticket, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
     double a[1] = {0.0};
-    for (int64_t i = gtid(); i < n; i += gstride()) a[0] = fma(rh[i], v[i], a[0]);
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = gtid(); i < n / 2; i += gstride()) {
+            const double2 h = ld2(rh, i), w = ld2(v, i);
+            a[0] = fma(h.y, w.y, fma(h.x, w.x, a[0]));
+        }
+        done = n / 2 * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) a[0] = fma(rh[i], v[i], a[0]);
     double t[1];
     if (grid_reduce<1>(a, part, ticket, t) && threadIdx.x == 0) {
         if (t[0] == 0.0) sc[xb::BI_FLAG] = 3.0;
@@ -399,11 +632,23 @@ __global__ void k_bi_sigma(int64_t n, double *__restrict__ sc, const double *__r
 // s = r - alpha v, ||s||^2.
 __global__ void k_bi_s(int64_t n, double *__restrict__ sc, const double *__restrict__ r,
                        const double *__restrict__ v, double *__restrict__ s,
-                       double *__restrict__ part, unsigned *__restrict__ ticket) {
+                       double *__restrict__ part, unsigned *__restrict__ ticket, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
     const double al = sc[xb::BI_ALPHA];
     double a[1] = {0.0};
-    for (int64_t i = gtid(); i < n; i += gstride()) {
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = gtid(); i < n / 2; i += gstride()) {
+            const double2 q = ld2(r, i), w = ld2(v, i);
+            double2 si;
+            si.x = fma(-al, w.x, q.x);
+            si.y = fma(-al, w.y, q.y);
+            st2(s, i, si);
+            a[0] = fma(si.y, si.y, fma(si.x, si.x, a[0]));
+        }
+        done = n / 2 * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) {
         const double si = fma(-al, v[i], r[i]);
         s[i] = si;
         a[0] = fma(si, si, a[0]);
@@ -415,10 +660,19 @@ __global__ void k_bi_s(int64_t n, double *__restrict__ sc, const double *__restr
 // omega = (t, s) / (t, t).
 __global__ void k_bi_omega(int64_t n, double *__restrict__ sc, const double *__restrict__ t,
                            const double *__restrict__ s, double *__restrict__ part,
-                           unsigned *__restrict__ ticket) {
+                           unsigned *__restrict__ ticket, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
     double a[2] = {0.0, 0.0};
-    for (int64_t i = gtid(); i < n; i += gstride()) {
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = gtid(); i < n / 2; i += gstride()) {
+            const double2 u = ld2(t, i), w = ld2(s, i);
+            a[0] = fma(u.y, w.y, fma(u.x, w.x, a[0]));
+            a[1] = fma(u.y, u.y, fma(u.x, u.x, a[1]));
+        }
+        done = n / 2 * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) {
         a[0] = fma(t[i], s[i], a[0]);
         a[1] = fma(t[i], t[i], a[1]);
     }
@@ -436,7 +690,7 @@ __global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__
                         const double *__restrict__ p, const double *__restrict__ s,
                         const double *__restrict__ t, double *__restrict__ r,
                         const double *__restrict__ rh, double *__restrict__ part,
-                        unsigned *__restrict__ ticket) {
+                        unsigned *__restrict__ ticket, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
     const double al = sc[xb::BI_ALPHA];
     if (sc[xb::BI_SNORM2] <= sc[xb::BI_TAU2]) {
@@ -450,13 +704,29 @@ __global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__
     }
     const double om = sc[xb::BI_OMEGA];
     double a[2] = {0.0, 0.0};
-    for (int64_t i = gtid(); i < n; i += gstride()) {
-        const double si = s[i];
-        x[i] = fma(om, si, fma(al, p[i], x[i]));
-        const double ri = fma(-om, t[i], si);
-        r[i] = ri;
+    auto f = [&](double &xi, double pi, double si, double ti, double hi) {
+        xi = fma(om, si, fma(al, pi, xi));
+        const double ri = fma(-om, ti, si);
         a[0] = fma(ri, ri, a[0]);
-        a[1] = fma(rh[i], ri, a[1]);
+        a[1] = fma(hi, ri, a[1]);
+        return ri;
+    };
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = gtid(); i < n / 2; i += gstride()) {
+            double2 xv = ld2(x, i), rv;
+            const double2 pv = ld2(p, i), sv = ld2(s, i), tv = ld2(t, i), hv = ld2(rh, i);
+            rv.x = f(xv.x, pv.x, sv.x, tv.x, hv.x);
+            rv.y = f(xv.y, pv.y, sv.y, tv.y, hv.y);
+            st2(x, i, xv);
+            st2(r, i, rv);
+        }
+        done = n / 2 * 2;
+    }
+    for (int64_t i = done + gtid(); i < n; i += gstride()) {
+        double xi = x[i];
+        r[i] = f(xi, p[i], s[i], t[i], rh[i]);
+        x[i] = xi;
     }
     double tt[2];
     if (grid_reduce<2>(a, part, ticket, tt) && threadIdx.x == 0) {
@@ -498,6 +768,7 @@ GmDev gm_layout(double *base, int M) {
     st.g = q; q += M + 1;
     st.sc = q; q += M + 1;
     st.y = q; q += M;
+    st.coef = q; q += M + 1;
     st.misc = q; q += GM_NMISC;
     st.scf = reinterpret_cast<float *>(q);
     return st;
@@ -554,20 +825,33 @@ int gm_cycle_init_f32(xb_plan *p, GmDev st, int64_t n, const float *r0, double t
     return XB_OK;
 }
 
+// MGS traversal mode (flags of k_mgs: bit 0 alternate direction, bit 1
+// evict-first loads of v_{i-1}); XB_MGS_MODE=0..3 overrides the default.
+int mgs_mode(size_t elem) {
+    static const int env = [] {
+        const char *e = std::getenv("XB_MGS_MODE");
+        return e ? std::atoi(e) & 3 : -1;
+    }();
+    (void)elem;
+    return env >= 0 ? env : 3;
+}
+
 template <typename VB>
 int gm_mgs_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
                 cudaStream_t s) {
     const int g = reduce_grid(n, kVB);
     const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)w % 16) == 0 &&
                      ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
-    // pass i walks backwards when i is even: pass 0 then starts on the tail of w
-    // that the SpMV wrote last
-    k_mgs<0, VB><<<g, kVB, 0, s>>>(n, w, nullptr, V, st, j, 0, p->d_part, p->d_ticket, vec, 1);
+    // With alternation on, pass i walks backwards when i is even (pass 0 then
+    // starts on the tail of w that the SpMV wrote last).
+    const int mode = mgs_mode(sizeof(VB));
+    auto fl = [mode](int i) { return ((mode & 1) && !(i & 1) ? 1 : 0) | (mode & 2); };
+    k_mgs<0, VB><<<g, kVB, 0, s>>>(n, w, nullptr, V, st, j, 0, p->d_part, p->d_ticket, vec, fl(0));
     for (int i = 1; i <= j; i++)
         k_mgs<1, VB><<<g, kVB, 0, s>>>(n, w, V + (size_t)(i - 1) * ld, V + (size_t)i * ld, st, j, i,
-                                       p->d_part, p->d_ticket, vec, (i & 1) ? 0 : 1);
+                                       p->d_part, p->d_ticket, vec, fl(i));
     k_mgs<2, VB><<<g, kVB, 0, s>>>(n, w, V + (size_t)j * ld, nullptr, st, j, j + 1, p->d_part,
-                                   p->d_ticket, vec, ((j + 1) & 1) ? 0 : 1);
+                                   p->d_ticket, vec, fl(j + 1));
     XB_LAUNCHED("k_mgs");
     return XB_OK;
 }
@@ -575,6 +859,64 @@ template int gm_mgs_step<double>(xb_plan *, GmDev, int64_t, const double *, int6
                                   int, cudaStream_t);
 template int gm_mgs_step<float>(xb_plan *, GmDev, int64_t, const float *, int64_t, float *, int,
                                  cudaStream_t);
+
+double ortho_passes(int ortho, int j) {
+    const int nb = (j + 1 + 3) / 4;
+    switch (ortho) {
+        case XB_ORTHO_CGS: return 2.0 * j + 5.0;
+        case XB_ORTHO_DGKS: return 3.0 * j + 8.0;
+        case XB_ORTHO_BCGS: return 2.0 * (j + 1) + 2.0 * nb + 1.0;
+        default: return 4.0 * j + 5.0;
+    }
+}
+
+int ortho_choice(int ortho, double tol, bool faulted) {
+    if (ortho != XB_ORTHO_AUTO) return ortho;
+    if (faulted) return XB_ORTHO_DGKS;
+    return tol <= 1e-10 ? XB_ORTHO_MGS : XB_ORTHO_BCGS;
+}
+
+template <typename VB>
+int gm_ortho_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
+                  int ortho, cudaStream_t s) {
+    if (ortho == XB_ORTHO_MGS) return gm_mgs_step<VB>(p, st, n, V, ld, w, j, s);
+    constexpr int KD = 8;
+    const int g = reduce_grid(n, kVB);
+    const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)w % 16) == 0 &&
+                     ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
+    const bool zig = mgs_mode(sizeof(VB)) & 1;
+    int pass = 0;
+    // the first pass walks backwards (it starts on the tail of w the SpMV wrote last)
+    auto L = [&](int u0, int u1, int d0, int nd, int flags) {
+        if (zig && !(pass & 1)) flags |= kBgsRev;
+        pass++;
+        // 4 resident CTAs per SM (64 registers) measured faster than 2 with no spills
+        if (nd <= 4 && u1 - u0 <= 4)  // BCGS passes, and short CGS/DGKS sweeps
+            k_bgs<VB, 4, 4, 4><<<g, kVB, 0, s>>>(n, w, V, ld, u0, u1, d0, nd, flags, st, j,
+                                                 p->d_part, p->d_ticket, vec);
+        else
+            k_bgs<VB, KD, 0, 4><<<g, kVB, 0, s>>>(n, w, V, ld, u0, u1, d0, nd, flags, st, j,
+                                                  p->d_part, p->d_ticket, vec);
+    };
+    const int k = j + 1;  // basis vectors v_0..v_j
+    if (ortho == XB_ORTHO_BCGS) {
+        const int nb = (k + 3) / 4;
+        L(0, 0, 0, std::min(4, k), 0);
+        for (int b = 1; b < nb; b++) L(4 * (b - 1), 4 * b, 4 * b, std::min(4, k - 4 * b), 0);
+        L(4 * (nb - 1), k, 0, 0, kBgsFin);
+    } else {
+        for (int c = 0; c < k; c += KD) L(0, 0, c, std::min(KD, k - c), 0);
+        if (ortho == XB_ORTHO_DGKS)  // second CGS: update by the first, dots added to H
+            for (int c = 0; c < k; c += KD) L(0, c == 0 ? k : 0, c, std::min(KD, k - c), kBgsAcc);
+        L(0, k, 0, 0, kBgsFin);
+    }
+    XB_LAUNCHED("k_bgs");
+    return XB_OK;
+}
+template int gm_ortho_step<double>(xb_plan *, GmDev, int64_t, const double *, int64_t, double *,
+                                   int, int, cudaStream_t);
+template int gm_ortho_step<float>(xb_plan *, GmDev, int64_t, const float *, int64_t, float *,
+                                  int, int, cudaStream_t);
 
 template <typename VB, typename VX>
 int gm_update(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, int k, VX *x,
@@ -594,39 +936,46 @@ template int gm_update<double, double>(xb_plan *, GmDev, int64_t, const double *
 template int gm_update<float, float>(xb_plan *, GmDev, int64_t, const float *, int64_t, int,
                                      float *, cudaStream_t);
 
+static int al16(const void *a) { return ((uintptr_t)a % 16) == 0; }
+
 int bi_init(xb_plan *p, double *scal, int64_t n, const double *r, double tau2, cudaStream_t s) {
-    k_bi_init<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r, scal, tau2, p->d_part, p->d_ticket);
+    k_bi_init<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r, scal, tau2, p->d_part, p->d_ticket,
+                                                  al16(r));
     XB_LAUNCHED("k_bi_init");
     return XB_OK;
 }
 int bi_p_update(double *scal, int64_t n, const double *r, double *pv, const double *v,
                 cudaStream_t s) {
-    k_bi_p<<<stream_grid(n), kVB, 0, s>>>(n, scal, r, pv, v);
+    k_bi_p<<<stream_grid(n), kVB, 0, s>>>(n, scal, r, pv, v, al16(r) & al16(pv) & al16(v));
     XB_LAUNCHED("k_bi_p");
     return XB_OK;
 }
 int bi_sigma(xb_plan *p, double *scal, int64_t n, const double *rh, const double *v,
              cudaStream_t s) {
-    k_bi_sigma<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, rh, v, p->d_part, p->d_ticket);
+    k_bi_sigma<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, rh, v, p->d_part, p->d_ticket,
+                                                   al16(rh) & al16(v));
     XB_LAUNCHED("k_bi_sigma");
     return XB_OK;
 }
 int bi_s_update(xb_plan *p, double *scal, int64_t n, const double *r, const double *v, double *sv,
                 cudaStream_t s) {
-    k_bi_s<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, r, v, sv, p->d_part, p->d_ticket);
+    k_bi_s<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, r, v, sv, p->d_part, p->d_ticket,
+                                               al16(r) & al16(v) & al16(sv));
     XB_LAUNCHED("k_bi_s");
     return XB_OK;
 }
 int bi_omega(xb_plan *p, double *scal, int64_t n, const double *t, const double *sv,
              cudaStream_t s) {
-    k_bi_omega<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, t, sv, p->d_part, p->d_ticket);
+    k_bi_omega<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, t, sv, p->d_part, p->d_ticket,
+                                                   al16(t) & al16(sv));
     XB_LAUNCHED("k_bi_omega");
     return XB_OK;
 }
 int bi_xr_update(xb_plan *p, double *scal, int64_t n, double *x, const double *pv,
                  const double *sv, const double *t, double *r, const double *rh, cudaStream_t s) {
+    const int vec = al16(x) & al16(pv) & al16(sv) & al16(t) & al16(r) & al16(rh);
     k_bi_xr<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, x, pv, sv, t, r, rh, p->d_part,
-                                                p->d_ticket);
+                                                p->d_ticket, vec);
     XB_LAUNCHED("k_bi_xr");
     return XB_OK;
 }

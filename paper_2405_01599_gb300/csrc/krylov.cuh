@@ -10,9 +10,10 @@ namespace xb {
 //   sc: 1/||w|| of each stored (unnormalised) basis vector (M+1)
 //   scf: the same scales in FP32 (for the FP32 basis)
 //   y: least-squares solution times the basis scales (M)
+//   coef: pending update coefficients of the block Gram-Schmidt passes (M+1)
 //   misc: named scalars (below)
 struct GmDev {
-    double *H, *cs, *sn, *g, *sc, *y, *misc;
+    double *H, *cs, *sn, *g, *sc, *y, *coef, *misc;
     float *scf;
     int M;
 };
@@ -28,7 +29,7 @@ enum GmMisc {
     GM_RAW = 8,     // 1: plain MGS sweep, keep column j unrotated (no Givens)
     GM_NMISC = 9
 };
-inline size_t gm_doubles(int M) { return (size_t)(M + 1) * M + 2 * (size_t)M + 2 * (size_t)(M + 1) + M + GM_NMISC + (M + 2) / 2 + 8; }
+inline size_t gm_doubles(int M) { return (size_t)(M + 1) * M + 2 * (size_t)M + 3 * (size_t)(M + 1) + M + GM_NMISC + (M + 2) / 2 + 8; }
 GmDev gm_layout(double *base, int M);
 
 // BiCGStab scalars (indices into a device double array).
@@ -43,6 +44,18 @@ int gm_cycle_init(xb_plan *p, GmDev st, int64_t n, const double *r0, double tau,
 template <typename VB>
 int gm_mgs_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
                 cudaStream_t s);
+// Orthogonalisation of Arnoldi step j with XB_ORTHO_MGS / CGS / DGKS / BCGS
+// (the policy value is resolved by the caller); ends with h_{j+1,j} and the
+// Givens update like gm_mgs_step.
+template <typename VB>
+int gm_ortho_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
+                  int ortho, cudaStream_t s);
+// Algorithmic vector passes (multiples of n elements read + written) of one
+// orthogonalisation of step j.
+double ortho_passes(int ortho, int j);
+// The accuracy policy of Sec. 3.3.2: MGS for tol <= 1e-10, else BCGS; DGKS
+// once a fault convergence was seen.  Non-AUTO values pass through.
+int ortho_choice(int ortho, double tol, bool faulted);
 template <typename VB, typename VX>
 int gm_update(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, int k, VX *x,
               cudaStream_t s);

@@ -376,7 +376,7 @@ int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan
             e = cudaMemcpy(p->d_empty, empty.data(), empty.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: empty rows"));
     }
-    cudaError_t e = cudaMalloc(&p->d_part, (size_t)kRedSlots * 8 * sizeof(double));
+    cudaError_t e = cudaMalloc(&p->d_part, (size_t)kRedSlots * kRedValues * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_ticket, 64 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_scal, (size_t)kScalars * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ticket, 0, 64 * sizeof(unsigned), s);

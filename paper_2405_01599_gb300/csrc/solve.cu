@@ -119,6 +119,7 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
     bool claimed = false;
     double tau = o.tol, res_true = 0.0, res_impl = 0.0;
     const int check = std::max(1, o.check_every);
+    int ortho = xb::ortho_choice(o.ortho, o.tol, false);
     for (;;) {
         // true residual r = b - A x into V_0, then start the cycle
         XB_TRY(xb::residual(p, b, x, V, s));
@@ -143,6 +144,7 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
         if (claimed) {  // fault convergence: the implicit residual lied
             faults++;
             tau *= o.tol / res_true;
+            ortho = xb::ortho_choice(o.ortho, o.tol, true);
             p->h_pin[32] = tau;
             XB_CUDA(cudaMemcpyAsync(st.misc + xb::GM_TAU, p->h_pin + 32, sizeof(double),
                                     cudaMemcpyHostToDevice, s));
@@ -164,8 +166,9 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
             tm.end();
             ac.bytes += spmv_b;
             ac.spmv++;
-            XB_TRY(xb::gm_mgs_step<double>(p, st, n, V, ld, V + (size_t)(j + 1) * ld, j, s));
-            ac.bytes += 16.0 * n + 32.0 * n * j + 24.0 * n;
+            XB_TRY(xb::gm_ortho_step<double>(p, st, n, V, ld, V + (size_t)(j + 1) * ld, j, ortho,
+                                             s));
+            ac.bytes += 8.0 * n * xb::ortho_passes(ortho, j);
             launched++;
             const bool last = (j == m - 1) || (iters + launched >= iter_budget);
             if ((j + 1) % check == 0 || last) {
@@ -196,6 +199,7 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
     inf.restarts += restarts;
     inf.m_final = m;
     inf.faults += faults;
+    inf.ortho_used = ortho;
     inf.res_true = res_true;
     inf.res_implicit = res_impl;
     return status;
@@ -204,8 +208,8 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
 // ---- FP32 inner GMRES(m) from d = 0 ---------------------------------------------------
 
 int gmres_f32_inner(xb_plan *p, const float *r32, float *d, float *V, int64_t ld, xb::GmDev st,
-                    int m, double tol_in, int maxit, const xb_options &o, Acct &ac, int *steps,
-                    cudaStream_t s) {
+                    int m, double tol_in, int maxit, int ortho, const xb_options &o, Acct &ac,
+                    int *steps, cudaStream_t s) {
     const int64_t n = p->n;
     const double spmv_b = xb::spmv_alg_bytes(p, false, 4);
     *steps = 0;
@@ -240,8 +244,9 @@ int gmres_f32_inner(xb_plan *p, const float *r32, float *d, float *V, int64_t ld
                                               V + (size_t)j * ld, V + (size_t)(j + 1) * ld, s));
             ac.bytes += spmv_b;
             ac.spmv++;
-            XB_TRY(xb::gm_mgs_step<float>(p, st, n, V, ld, V + (size_t)(j + 1) * ld, j, s));
-            ac.bytes += 8.0 * n + 16.0 * n * j + 12.0 * n;
+            XB_TRY(xb::gm_ortho_step<float>(p, st, n, V, ld, V + (size_t)(j + 1) * ld, j, ortho,
+                                            s));
+            ac.bytes += 4.0 * n * xb::ortho_passes(ortho, j);
             launched++;
             const bool last = (j == m - 1) || (*steps + launched >= maxit);
             if ((j + 1) % check == 0 || last) {
@@ -334,8 +339,11 @@ int gmres_mixed(xb_plan *p, const double *b, double *x, const xb_options &o, xb_
         XB_TRY(xb::cast_f64_to_f32_scaled(n, r, sc + 1, r32, s));
         ac.bytes += 12.0 * n;
         int steps = 0;
-        XB_TRY(gmres_f32_inner(p, r32, d, V, ld, st, m, o.tol_inner, o.maxiter_inner, o, ac,
-                               &steps, s));
+        // the inner solve's accuracy target is tol_inner: the policy decides on it
+        const int ortho_in = xb::ortho_choice(o.ortho, o.tol_inner, inf.faults > 0);
+        inf.ortho_used = ortho_in;
+        XB_TRY(gmres_f32_inner(p, r32, d, V, ld, st, m, o.tol_inner, o.maxiter_inner, ortho_in, o,
+                               ac, &steps, s));
         inner_total += steps;
         XB_TRY(xb::add_scaled_f32(n, x, sc + 1, d, s));
         ac.bytes += 20.0 * n;
@@ -457,7 +465,8 @@ int check_args(xb_plan *p, const double *b, double *x, const xb_options &o) {
     if (o.m < 1 || o.m > 512) return xb::set_error(XB_EINVAL, "solve: m=%d not in [1,512]", o.m);
     if (o.variant != XB_VAR_AUTO && !xb::variant_fits(p, o.variant))
         return xb::set_error(XB_EINVAL, "solve: SpMV variant %d does not fit the storage", o.variant);
-    if (o.ortho != XB_ORTHO_MGS) return xb::set_error(XB_EINVAL, "solve: only MGS orthogonalisation");
+    if (o.ortho < XB_ORTHO_MGS || o.ortho > XB_ORTHO_AUTO)
+        return xb::set_error(XB_EINVAL, "solve: unknown orthogonalisation %d", o.ortho);
     return XB_OK;
 }
 
