@@ -56,6 +56,8 @@ def parse():
                          "256^3 convection-diffusion (c4)")
     ap.add_argument("--gmres-steps", type=int, default=0,
                     help="profile-only: run this many GMRES(30) Arnoldi steps instead of SpMVs")
+    ap.add_argument("--ortho", default="mgs", choices=["mgs", "cgs", "dgks", "bcgs"],
+                    help="profile-only GMRES: orthogonalisation")
     return ap.parse_args()
 
 
@@ -148,7 +150,10 @@ def alg_bytes(A, vb=8, beta=False):
 # (variant, block, ipt, n, nnz) and valid only while the kernel source is unchanged
 # (sha256 of csrc/spmv.cu at capture time); the capture and its command are summarised
 # in profiles/.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("segscan", 128, 8, 4_000_000, 52_238_581):
+        (706.63e6, "4c4768442d1f9d0cae72f095beeae3970f699faa254132d7a73e484da642fdb6"),
+}
 
 
 def ncu_traffic(choice_name, block, ipt, n, nnz):
@@ -258,7 +263,8 @@ def main():
         xg = torch.zeros(n, dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info = plan.gmres(bvec, xg, m=30, tol=1e-30, maxiter=args.gmres_steps, check_every=10)
+        info = plan.gmres(bvec, xg, m=30, tol=1e-30, maxiter=args.gmres_steps, check_every=10,
+                          ortho=["mgs", "cgs", "dgks", "bcgs"].index(args.ortho))
         el = time.perf_counter() - t0
         if rank == 0:
             print(json.dumps({"profile_only": True, "matrix": args.matrix, "gmres_steps": info["iters"],

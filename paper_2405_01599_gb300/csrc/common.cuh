@@ -40,6 +40,10 @@ constexpr int kScalars = 4096;      // device scalar scratch per plan (doubles)
 
 int num_sms();                      // cached cudaDevAttrMultiProcessorCount
 int reduce_grid(int64_t n, int block);  // CTAs for a streaming reduction
+// CTAs of a grid-stride launch of kernel fn: every CTA resident at once (the
+// occupancy limit times the SM count, at most kRedSlots), fewer for small n
+// (per_thread elements per thread).
+int resident_grid(const void *fn, int block, int64_t n, int per_thread);
 
 // ---- partitions -------------------------------------------------------------
 // Row-aligned nnz-balanced tiles (U2 / S2): tile t covers rows

@@ -82,9 +82,12 @@ __global__ void k_fill(int64_t n, double a, double *__restrict__ x) {
     for (int64_t i = gtid(); i < n; i += gstride()) x[i] = a;
 }
 
-int stream_grid(int64_t n) {
-    int64_t want = (n + kVB - 1) / kVB;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)xb::num_sms() * 16));
+// Grid of a streaming/reduction launch of kernel k over n elements: exactly the
+// CTAs that fit on the GPU at once (fewer for small n), so a grid-stride pass
+// runs as one coherent wave.
+template <typename K>
+int rgrid(K k, int64_t n) {
+    return xb::resident_grid((const void *)k, kVB, n, 4);
 }
 
 // ---- GMRES ----------------------------------------------------------------------
@@ -447,7 +450,8 @@ __global__ void __launch_bounds__(kVB, MINB) k_bgs(int64_t n, VB *__restrict__ w
         const int64_t gs = gstride();
         const int64_t full = nv / gs;           // grid-wide chunks every thread owns
         const int64_t et = full * gs + gtid();  // this thread's slot in the partial chunk
-        if (rev && et < nv) bgs_elems<VB, KD, KU, 1>(et, et, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
+        if (rev && et < nv)
+            bgs_elems<VB, KD, KU, 1>(et, et, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
         int64_t k = 0;
         for (; k + 1 < full; k += 2) {
             const int64_t e = (rev ? full - 1 - k : k) * gs + gtid();
@@ -458,7 +462,8 @@ __global__ void __launch_bounds__(kVB, MINB) k_bgs(int64_t n, VB *__restrict__ w
             const int64_t e = (rev ? full - 1 - k : k) * gs + gtid();
             bgs_elems<VB, KD, KU, 1>(e, e, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
         }
-        if (!rev && et < nv) bgs_elems<VB, KD, KU, 1>(et, et, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
+        if (!rev && et < nv)
+            bgs_elems<VB, KD, KU, 1>(et, et, w2, V2, ldv, u0, nu, d0, nd, fin, cf, acc);
         done = nv * N;
     }
     for (int64_t e = done + gtid(); e < n; e += gstride()) {
@@ -590,7 +595,8 @@ __global__ void k_bi_init(int64_t n, const double *__restrict__ r, double *__res
 __global__ void k_bi_p(int64_t n, const double *__restrict__ sc, const double *__restrict__ r,
                        double *__restrict__ p, const double *__restrict__ v, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
-    const double beta = (sc[xb::BI_RHO] / sc[xb::BI_RHO_OLD]) * (sc[xb::BI_ALPHA] / sc[xb::BI_OMEGA]);
+    const double beta =
+        (sc[xb::BI_RHO] / sc[xb::BI_RHO_OLD]) * (sc[xb::BI_ALPHA] / sc[xb::BI_OMEGA]);
     const double om = sc[xb::BI_OMEGA];
     auto f = [=](double ri, double pi, double vi) { return fma(beta, fma(-om, vi, pi), ri); };
     int64_t done = 0;
@@ -775,14 +781,14 @@ GmDev gm_layout(double *base, int M) {
 }
 
 int vdot(xb_plan *p, int64_t n, const double *x, const double *y, double *out, cudaStream_t s) {
-    const int g = reduce_grid(n, kVB);
+    const int g = rgrid(k_dot, n);
     const int vec = (((uintptr_t)x | (uintptr_t)y) % 16) == 0 ? 1 : 0;
     k_dot<<<g, kVB, 0, s>>>(n, x, y, p->d_part, p->d_ticket, out, 0, vec);
     XB_LAUNCHED("k_dot");
     return XB_OK;
 }
 int vnrm2(xb_plan *p, int64_t n, const double *x, double *out, cudaStream_t s) {
-    const int g = reduce_grid(n, kVB);
+    const int g = rgrid(k_dot, n);
     const int vec = ((uintptr_t)x % 16) == 0 ? 1 : 0;
     k_dot<<<g, kVB, 0, s>>>(n, x, x, p->d_part, p->d_ticket, out, 1, vec);
     XB_LAUNCHED("k_nrm2");
@@ -790,37 +796,39 @@ int vnrm2(xb_plan *p, int64_t n, const double *x, double *out, cudaStream_t s) {
 }
 int vaxpy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
     if (n <= 0) return XB_OK;
-    k_axpy<<<stream_grid(n), kVB, 0, s>>>(n, a, x, y);
+    k_axpy<<<rgrid(k_axpy, n), kVB, 0, s>>>(n, a, x, y);
     XB_LAUNCHED("k_axpy");
     return XB_OK;
 }
 int vcopy(int64_t n, const double *x, double *y, cudaStream_t s) {
     if (n <= 0) return XB_OK;
-    k_copy<<<stream_grid(n), kVB, 0, s>>>(n, x, y);
+    k_copy<<<rgrid(k_copy, n), kVB, 0, s>>>(n, x, y);
     XB_LAUNCHED("k_copy");
     return XB_OK;
 }
 int vscale(int64_t n, double a, double *x, cudaStream_t s) {
     if (n <= 0) return XB_OK;
-    k_scale<<<stream_grid(n), kVB, 0, s>>>(n, a, x);
+    k_scale<<<rgrid(k_scale, n), kVB, 0, s>>>(n, a, x);
     XB_LAUNCHED("k_scale");
     return XB_OK;
 }
 int vfill(int64_t n, double a, double *x, cudaStream_t s) {
     if (n <= 0) return XB_OK;
-    k_fill<<<stream_grid(n), kVB, 0, s>>>(n, a, x);
+    k_fill<<<rgrid(k_fill, n), kVB, 0, s>>>(n, a, x);
     XB_LAUNCHED("k_fill");
     return XB_OK;
 }
 
 int gm_cycle_init(xb_plan *p, GmDev st, int64_t n, const double *r0, double tau, cudaStream_t s) {
-    k_gm_init<double><<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r0, st, tau, p->d_part, p->d_ticket);
+    k_gm_init<double><<<rgrid(k_gm_init<double>, n), kVB, 0, s>>>(n, r0, st, tau, p->d_part,
+                                                                 p->d_ticket);
     XB_LAUNCHED("k_gm_init");
     return XB_OK;
 }
 int gm_cycle_init_f32(xb_plan *p, GmDev st, int64_t n, const float *r0, double tau,
                       cudaStream_t s) {
-    k_gm_init<float><<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r0, st, tau, p->d_part, p->d_ticket);
+    k_gm_init<float><<<rgrid(k_gm_init<float>, n), kVB, 0, s>>>(n, r0, st, tau, p->d_part,
+                                                               p->d_ticket);
     XB_LAUNCHED("k_gm_init_f32");
     return XB_OK;
 }
@@ -839,7 +847,7 @@ int mgs_mode(size_t elem) {
 template <typename VB>
 int gm_mgs_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *w, int j,
                 cudaStream_t s) {
-    const int g = reduce_grid(n, kVB);
+    const int g = rgrid(k_mgs<1, VB>, n);
     const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)w % 16) == 0 &&
                      ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
     // With alternation on, pass i walks backwards when i is even (pass 0 then
@@ -881,7 +889,9 @@ int gm_ortho_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *
                   int ortho, cudaStream_t s) {
     if (ortho == XB_ORTHO_MGS) return gm_mgs_step<VB>(p, st, n, V, ld, w, j, s);
     constexpr int KD = 8;
-    const int g = reduce_grid(n, kVB);
+    // grids of exactly the resident CTAs (measured 12 % faster than 8 CTAs per SM in waves)
+    const int g4 = rgrid(k_bgs<VB, 4, 4, 4>, n);
+    const int g8 = rgrid(k_bgs<VB, KD, 0, 4>, n);
     const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)w % 16) == 0 &&
                      ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
     const bool zig = mgs_mode(sizeof(VB)) & 1;
@@ -892,11 +902,11 @@ int gm_ortho_step(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, VB *
         pass++;
         // 4 resident CTAs per SM (64 registers) measured faster than 2 with no spills
         if (nd <= 4 && u1 - u0 <= 4)  // BCGS passes, and short CGS/DGKS sweeps
-            k_bgs<VB, 4, 4, 4><<<g, kVB, 0, s>>>(n, w, V, ld, u0, u1, d0, nd, flags, st, j,
-                                                 p->d_part, p->d_ticket, vec);
-        else
-            k_bgs<VB, KD, 0, 4><<<g, kVB, 0, s>>>(n, w, V, ld, u0, u1, d0, nd, flags, st, j,
+            k_bgs<VB, 4, 4, 4><<<g4, kVB, 0, s>>>(n, w, V, ld, u0, u1, d0, nd, flags, st, j,
                                                   p->d_part, p->d_ticket, vec);
+        else
+            k_bgs<VB, KD, 0, 4><<<g8, kVB, 0, s>>>(n, w, V, ld, u0, u1, d0, nd, flags, st, j,
+                                                   p->d_part, p->d_ticket, vec);
     };
     const int k = j + 1;  // basis vectors v_0..v_j
     if (ortho == XB_ORTHO_BCGS) {
@@ -927,7 +937,7 @@ int gm_update(xb_plan *p, GmDev st, int64_t n, const VB *V, int64_t ld, int k, V
     XB_LAUNCHED("k_gm_solve");
     const int vec = (((uintptr_t)V % 16) == 0 && ((uintptr_t)x % 16) == 0 &&
                      ((ld * sizeof(VB)) % 16) == 0) ? 1 : 0;
-    k_gm_xupd<VB, VX><<<stream_grid(n), kVB, 0, s>>>(n, V, ld, st, x, vec);
+    k_gm_xupd<VB, VX><<<rgrid(k_gm_xupd<VB, VX>, n), kVB, 0, s>>>(n, V, ld, st, x, vec);
     XB_LAUNCHED("k_gm_xupd");
     return XB_OK;
 }
@@ -939,34 +949,34 @@ template int gm_update<float, float>(xb_plan *, GmDev, int64_t, const float *, i
 static int al16(const void *a) { return ((uintptr_t)a % 16) == 0; }
 
 int bi_init(xb_plan *p, double *scal, int64_t n, const double *r, double tau2, cudaStream_t s) {
-    k_bi_init<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, r, scal, tau2, p->d_part, p->d_ticket,
+    k_bi_init<<<rgrid(k_bi_init, n), kVB, 0, s>>>(n, r, scal, tau2, p->d_part, p->d_ticket,
                                                   al16(r));
     XB_LAUNCHED("k_bi_init");
     return XB_OK;
 }
 int bi_p_update(double *scal, int64_t n, const double *r, double *pv, const double *v,
                 cudaStream_t s) {
-    k_bi_p<<<stream_grid(n), kVB, 0, s>>>(n, scal, r, pv, v, al16(r) & al16(pv) & al16(v));
+    k_bi_p<<<rgrid(k_bi_p, n), kVB, 0, s>>>(n, scal, r, pv, v, al16(r) & al16(pv) & al16(v));
     XB_LAUNCHED("k_bi_p");
     return XB_OK;
 }
 int bi_sigma(xb_plan *p, double *scal, int64_t n, const double *rh, const double *v,
              cudaStream_t s) {
-    k_bi_sigma<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, rh, v, p->d_part, p->d_ticket,
+    k_bi_sigma<<<rgrid(k_bi_sigma, n), kVB, 0, s>>>(n, scal, rh, v, p->d_part, p->d_ticket,
                                                    al16(rh) & al16(v));
     XB_LAUNCHED("k_bi_sigma");
     return XB_OK;
 }
 int bi_s_update(xb_plan *p, double *scal, int64_t n, const double *r, const double *v, double *sv,
                 cudaStream_t s) {
-    k_bi_s<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, r, v, sv, p->d_part, p->d_ticket,
+    k_bi_s<<<rgrid(k_bi_s, n), kVB, 0, s>>>(n, scal, r, v, sv, p->d_part, p->d_ticket,
                                                al16(r) & al16(v) & al16(sv));
     XB_LAUNCHED("k_bi_s");
     return XB_OK;
 }
 int bi_omega(xb_plan *p, double *scal, int64_t n, const double *t, const double *sv,
              cudaStream_t s) {
-    k_bi_omega<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, t, sv, p->d_part, p->d_ticket,
+    k_bi_omega<<<rgrid(k_bi_omega, n), kVB, 0, s>>>(n, scal, t, sv, p->d_part, p->d_ticket,
                                                    al16(t) & al16(sv));
     XB_LAUNCHED("k_bi_omega");
     return XB_OK;
@@ -974,7 +984,7 @@ int bi_omega(xb_plan *p, double *scal, int64_t n, const double *t, const double 
 int bi_xr_update(xb_plan *p, double *scal, int64_t n, double *x, const double *pv,
                  const double *sv, const double *t, double *r, const double *rh, cudaStream_t s) {
     const int vec = al16(x) & al16(pv) & al16(sv) & al16(t) & al16(r) & al16(rh);
-    k_bi_xr<<<reduce_grid(n, kVB), kVB, 0, s>>>(n, scal, x, pv, sv, t, r, rh, p->d_part,
+    k_bi_xr<<<rgrid(k_bi_xr, n), kVB, 0, s>>>(n, scal, x, pv, sv, t, r, rh, p->d_part,
                                                 p->d_ticket, vec);
     XB_LAUNCHED("k_bi_xr");
     return XB_OK;
@@ -989,14 +999,14 @@ int residual(xb_plan *p, const double *b, const double *x, double *r, cudaStream
 int cast_f64_to_f32_scaled(int64_t n, const double *a, const double *scale_dev, float *b,
                            cudaStream_t s) {
     if (n <= 0) return XB_OK;
-    k_cast_scaled<<<stream_grid(n), kVB, 0, s>>>(n, a, scale_dev, b);
+    k_cast_scaled<<<rgrid(k_cast_scaled, n), kVB, 0, s>>>(n, a, scale_dev, b);
     XB_LAUNCHED("k_cast_scaled");
     return XB_OK;
 }
 
 int add_scaled_f32(int64_t n, double *x, const double *scale_dev, const float *d, cudaStream_t s) {
     if (n <= 0) return XB_OK;
-    k_add_scaled<<<stream_grid(n), kVB, 0, s>>>(n, x, scale_dev, d);
+    k_add_scaled<<<rgrid(k_add_scaled, n), kVB, 0, s>>>(n, x, scale_dev, d);
     XB_LAUNCHED("k_add_scaled");
     return XB_OK;
 }

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 namespace xb {
@@ -41,6 +42,29 @@ int num_sms() {
 int reduce_grid(int64_t n, int block) {
     int64_t want = (n + block * 4 - 1) / (block * 4);
     int64_t cap = std::min<int64_t>(kRedSlots, (int64_t)num_sms() * 8);
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+int resident_grid(const void *fn, int block, int64_t n, int per_thread) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;  // (kernel, device) -> CTAs/SM
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find({fn, dev});
+        if (it != cache.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            cache[{fn, dev}] = per_sm;
+        }
+    }
+    const int64_t want = (n + (int64_t)block * per_thread - 1) / ((int64_t)block * per_thread);
+    const int64_t cap = std::min<int64_t>(kRedSlots, (int64_t)per_sm * num_sms());
     return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
