@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--ipt", type=int, default=8)
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu captures); prints a short line")
-    ap.add_argument("--matrix", default="c3", choices=["c3", "c2-upper", "c2-full", "c4"],
+    ap.add_argument("--matrix", default="c3",
+                    choices=["c3", "c2-upper", "c2-full", "c4", "c4-160"],
                     help="profile-only: power-law n (c3), 128^3 Laplacian upper/full (c2), "
-                         "256^3 convection-diffusion (c4)")
+                         "256^3 (c4) or 160^3 (c4-160) convection-diffusion")
     ap.add_argument("--gmres-steps", type=int, default=0,
                     help="profile-only: run this many GMRES(30) Arnoldi steps instead of SpMVs")
     ap.add_argument("--ortho", default="mgs", choices=["mgs", "cgs", "dgks", "bcgs"],
@@ -245,7 +246,8 @@ def main():
     if args.profile_only and args.matrix != "c3":
         from paper_2405_01599_gb300 import gen
         A = {"c2-upper": lambda: gen.laplace3d(128, upper=True), "c2-full": lambda: gen.laplace3d(128),
-             "c4": lambda: gen.convdiff3d(N=256)}[args.matrix]()
+             "c4": lambda: gen.convdiff3d(N=256),
+             "c4-160": lambda: gen.convdiff3d(N=160)}[args.matrix]()
     else:
         A = make_c3(args.n)
     n, nnz = A["n"], A["nnz"]
