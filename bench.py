@@ -551,10 +551,10 @@ def batch(xb, torch, dev, args):
     # preconditioner; the cap bounds their share of the launch
     opts = dict(tol=1e-8, maxiter=3000, maxtime_s=60.0)
 
-    def run(ms, modes):
+    def run(ms, modes, **kw):
         for q, m, md in zip(systems, ms, modes):
             q["m"], q["mode"] = int(m), int(md)
-        bt = xb.Batch(systems, **opts)
+        bt = xb.Batch(systems, **opts, **kw)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         bt.run()
@@ -564,6 +564,8 @@ def batch(xb, torch, dev, args):
         return e0.elapsed_time(e1), r
 
     N = len(systems)
+    # MGS in every arm: inside the batched kernel (one SM per small system,
+    # latency-bound) BCGS measured no faster than MGS
     t_def, r_def = run([30] * N, [0] * N)
     t_exh, r_exh = run([30] * N, [q["mode_ex"] for q in systems])
     t_mlp, r_mlp = run([q["m_ml"] for q in systems], [q["mode_ml"] for q in systems])

@@ -346,7 +346,9 @@ int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, i
  * combined through distributed shared memory; smaller systems take one CTA
  * each and need no inter-CTA synchronisation.  opt: tol, maxiter (per
  * system), maxtime_s (whole launch; checked at every restart), dafrt /
- * dafrt_theta / m_max (the restart-length rule, per system).  Per system:
+ * dafrt_theta / m_max (the restart-length rule, per system), ortho
+ * (XB_ORTHO_MGS, XB_ORTHO_BCGS, or XB_ORTHO_AUTO: BCGS for tol > 1e-10,
+ * else MGS; others are rejected).  Per system:
  * m in [1, XB_BATCH_MAX_M] and the SpMV mode inside the CTA (0: thread per
  * row; 1: thread per row in warp-sized row blocks, rows longer than 32
  * non-zeros taken by the whole warp), as chosen by a tuner; zero_x = 1 makes the kernel

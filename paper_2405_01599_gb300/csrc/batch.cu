@@ -16,7 +16,9 @@
 // cluster reach the same barriers in the same order.
 //
 // The solver is restarted GMRES(m) with modified Gram-Schmidt (fused: each
-// pass applies the previous projection and takes the next inner product),
+// pass applies the previous projection and takes the next inner product) or
+// blocked classical Gram-Schmidt with block length 4 (one pass and one
+// four-value reduction per block),
 // Givens least squares, the true-residual check at every restart (fault
 // convergence narrows the implicit threshold), and, when enabled, the
 // MM-ratio restart rule of Eq. (1) / Fig. 2 / Sec. 4.3 (m grows by 5, up to
@@ -71,6 +73,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 struct Smem {
     double sh[40];
     double slot[2];  // this CTA's partial of the current cluster reduction
+    double sh4[4][kBT / 32], slot4[2][4], tot4[4];  // the same for 4 sums at once
     double g[XB_BATCH_MAX_M + 1], cs[XB_BATCH_MAX_M], sn[XB_BATCH_MAX_M], yv[XB_BATCH_MAX_M];
     unsigned long long t_start;
     int q, q2, big;
@@ -118,6 +121,40 @@ __device__ double coop_sum(double v, Smem &S, Part &P) {
     __syncthreads();
     P.phase ^= 1;
     return tot;
+}
+
+// Four sums at once over all cooperating CTAs (one CTA barrier pair and one
+// cluster barrier for the four), identical everywhere, in a fixed order.
+__device__ void coop_sum4(double (&v)[4], Smem &S, Part &P) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; q++) S.sh4[q][w] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double a = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) a += S.sh4[threadIdx.x][k];
+        if (P.coop) S.slot4[P.phase][threadIdx.x] = a;
+        else S.tot4[threadIdx.x] = a;
+    }
+    if (P.coop) {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        if (threadIdx.x < 4) {
+            double tot = 0.0;
+            for (int r = 0; r < kCl; r++) tot += cl.map_shared_rank(&S.slot4[0][0], r)[P.phase * 4 + threadIdx.x];
+            S.tot4[threadIdx.x] = tot;
+        }
+        P.phase ^= 1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = S.tot4[q];
+    __syncthreads();
 }
 
 // Make every cooperating CTA's writes to the shared vectors visible to all.
@@ -228,8 +265,54 @@ __device__ __forceinline__ double mgs_rows(double *__restrict__ w, const double 
     return a0 + a1;
 }
 
+// One block Gram-Schmidt pass over rows [r0, r1): w -= sum_{q < nu} c[q] V_{u0+q}
+// (nu <= 4), then the nd <= 4 dots (w, V_{d0+q}) into a[] (or (w, w) into a[0]
+// when nd == 0).  Two rows per thread, every load of both issued before their
+// arithmetic (the pass is latency-bound on one SM).
+template <int R>
+__device__ __forceinline__ void bgs_row(double *__restrict__ w, const double *__restrict__ V,
+                                        int64_t ld, int u0, int nu, const double (&c)[4], int d0,
+                                        int nd, int e0, int B, double (&a)[4]) {
+    double x[R], pu[R][4], pd[R][4];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int e = e0 + r * B;
+        x[r] = w[e];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            pu[r][q] = q < nu ? V[(size_t)(u0 + q) * ld + e] : 0.0;
+            pd[r][q] = q < nd ? V[(size_t)(d0 + q) * ld + e] : 0.0;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (q < nu) x[r] = fma(-c[q], pu[r][q], x[r]);
+        if (nu > 0) w[e0 + r * B] = x[r];
+        if (nd == 0) {
+            a[0] = fma(x[r], x[r], a[0]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q < nd) a[q] = fma(x[r], pd[r][q], a[q]);
+        }
+    }
+}
+
+__device__ __forceinline__ void bgs_rows(double *__restrict__ w, const double *__restrict__ V,
+                                         int64_t ld, int u0, int nu, const double (&c)[4], int d0,
+                                         int nd, int r0, int r1, double (&a)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) a[q] = 0.0;
+    const int B = blockDim.x;
+    int e = r0 + threadIdx.x;
+    for (; e + B < r1; e += 2 * B) bgs_row<2>(w, V, ld, u0, nu, c, d0, nd, e, B, a);
+    if (e < r1) bgs_row<1>(w, V, ld, u0, nu, c, d0, nd, e, B, a);
+}
+
 __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, int maxiter,
-                          unsigned long long deadline, int rank, double theta,
+                          unsigned long long deadline, int rank, double theta, int bcgs,
                           xb_batch_info *out) {
     const unsigned long long ts = gtimer();
     const int m_max = D.m_max;
@@ -293,19 +376,44 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
                 double *w = V + (size_t)(j + 1) * ld;
                 coop_barrier(P);  // v_j complete
                 part_spmv(D, P, 1.0, V + (size_t)j * ld, 0.0, w);
-                // fused MGS: pass i applies the projection on v_{i-1}, takes (w, v_i)
-                double len2 = 0.0, hprev = 0.0;
-                for (int i = 0; i <= j; i++) {
-                    const double *vi = V + (size_t)i * ld;
-                    a = i == 0 ? mgs_rows<0>(w, nullptr, vi, 0.0, r0, r1)
-                               : mgs_rows<1>(w, vi - ld, vi, hprev, r0, r1);
-                    const double h = coop_sum(a, S, P);
-                    if (threadIdx.x == 0) H[(size_t)j * (m_max + 1) + i] = h;
-                    len2 += h * h;
-                    hprev = h;
+                double len2 = 0.0, hn;
+                if (bcgs) {
+                    // BCGS, block length 4: one pass per block applies the previous
+                    // block's projection and takes the dots with this block
+                    double c[4] = {0.0, 0.0, 0.0, 0.0}, a4[4];
+                    int u0 = 0, nu = 0;
+                    for (int d0 = 0; d0 <= j; d0 += 4) {
+                        const int nd = min(4, j + 1 - d0);
+                        bgs_rows(w, V, ld, u0, nu, c, d0, nd, r0, r1, a4);
+                        coop_sum4(a4, S, P);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            if (q < nd) {
+                                if (threadIdx.x == 0) H[(size_t)j * (m_max + 1) + d0 + q] = a4[q];
+                                len2 += a4[q] * a4[q];
+                                c[q] = a4[q];
+                            }
+                        }
+                        u0 = d0;
+                        nu = nd;
+                    }
+                    bgs_rows(w, V, ld, u0, nu, c, 0, 0, r0, r1, a4);
+                    hn = sqrt(coop_sum(a4[0], S, P));
+                } else {
+                    // fused MGS: pass i applies the projection on v_{i-1}, takes (w, v_i)
+                    double hprev = 0.0;
+                    for (int i = 0; i <= j; i++) {
+                        const double *vi = V + (size_t)i * ld;
+                        a = i == 0 ? mgs_rows<0>(w, nullptr, vi, 0.0, r0, r1)
+                                   : mgs_rows<1>(w, vi - ld, vi, hprev, r0, r1);
+                        const double h = coop_sum(a, S, P);
+                        if (threadIdx.x == 0) H[(size_t)j * (m_max + 1) + i] = h;
+                        len2 += h * h;
+                        hprev = h;
+                    }
+                    a = mgs_rows<2>(w, V + (size_t)j * ld, nullptr, hprev, r0, r1);
+                    hn = sqrt(coop_sum(a, S, P));
                 }
-                a = mgs_rows<2>(w, V + (size_t)j * ld, nullptr, hprev, r0, r1);
-                const double hn = sqrt(coop_sum(a, S, P));
                 if (threadIdx.x == 0) {
                     double *col = H + (size_t)j * (m_max + 1);
                     col[j + 1] = hn;
@@ -403,7 +511,7 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 1)
     k_batch_gmres(const xb_batch_dev *__restrict__ sys, xb_batch_info *__restrict__ out,
                   const int *__restrict__ order, int count, int *__restrict__ queue, double tol,
-                  int maxiter, unsigned long long budget_ns, double theta) {
+                  int maxiter, unsigned long long budget_ns, double theta, int bcgs) {
     __shared__ Smem S;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -428,13 +536,13 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 1)
             const xb_batch_dev D = sys[order[q]];
             const int per = (D.n + kCl - 1) / kCl;
             Part P{min(D.n, rank * per), min(D.n, (rank + 1) * per), 1, 0};
-            solve_one(D, P, S, tol, maxiter, deadline, rank, theta, out + order[q]);
+            solve_one(D, P, S, tol, maxiter, deadline, rank, theta, bcgs, out + order[q]);
         } else {
             const int mine = rank == 0 ? q : q2 + rank - 1;
             if (mine < count) {
                 const xb_batch_dev D = sys[order[mine]];
                 Part P{0, D.n, 0, 0};
-                solve_one(D, P, S, tol, maxiter, deadline, 0, theta, out + order[mine]);
+                solve_one(D, P, S, tol, maxiter, deadline, 0, theta, bcgs, out + order[mine]);
             }
         }
         cl.sync();  // regroup before the next pull
@@ -468,6 +576,8 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     if (opt) o = *opt;
     else xb_options_default(&o);
     if (!(o.tol > 0.0)) return xb::set_error(XB_EINVAL, "batch_create: tol must be > 0");
+    if (o.ortho != XB_ORTHO_MGS && o.ortho != XB_ORTHO_BCGS && o.ortho != XB_ORTHO_AUTO)
+        return xb::set_error(XB_EINVAL, "batch_create: orthogonalisation must be MGS, BCGS or AUTO");
     std::vector<xb_batch_dev> h(count);
     size_t ws = 0;
     // systems with n >= coop_min are solved by a whole cluster (environment
@@ -543,6 +653,11 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     bt->grid = kCl * std::max(1, clusters);
     const unsigned long long budget = (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
     const double theta = o.dafrt ? o.dafrt_theta : 0.0;  // theta 0: the rule never fires
+    // orthogonalisation: MGS or BCGS (block length 4); the accuracy policy's
+    // choice for AUTO (no fault switch inside the launch)
+    const int ortho = o.ortho == XB_ORTHO_AUTO ? (o.tol <= 1e-10 ? XB_ORTHO_MGS : XB_ORTHO_BCGS)
+                                               : o.ortho;
+    const int bcgs = ortho == XB_ORTHO_BCGS ? 1 : 0;
     // capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured): reset the queue, one persistent launch
     cudaStream_t cs = nullptr;
@@ -555,7 +670,7 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     }
     cudaMemsetAsync(bt->d_queue, 0, sizeof(int), cs);
     k_batch_gmres<<<bt->grid, kBT, 0, cs>>>(bt->d_sys, bt->d_info, bt->d_order, count, bt->d_queue,
-                                             o.tol, o.maxiter, budget, theta);
+                                             o.tol, o.maxiter, budget, theta, bcgs);
     cudaError_t el = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &bt->graph);
     cudaStreamDestroy(cs);

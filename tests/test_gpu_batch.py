@@ -100,3 +100,33 @@ def test_batch_empty_and_bad_args():
     systems, _ = _systems(dev, [(gen.poisson2d(5), 0, 0)])
     with pytest.raises(xb.XbError):
         xb.Batch(systems)
+
+
+@pytest.mark.parametrize("coop_min", ["16384", "1000000000"])
+@pytest.mark.parametrize("ortho", [3, 4])
+def test_batch_bcgs_matches_oracle(coop_min, ortho, monkeypatch):
+    """BCGS with block length 4 inside the batched launch (explicitly, and as
+    the accuracy policy's choice at tol 1e-8): every system reaches the true
+    residual and the oracle's BCGS GMRES(m) iteration count within
+    max(3, 5 %), on the cluster and the single-CTA paths."""
+    monkeypatch.setenv("XB_BATCH_COOP_MIN_N", coop_min)
+    xb, dev = lib_and_device()
+    specs = [(f(), m, mode) for f, m, mode in SPECS[:12]]
+    systems, mats = _systems(dev, specs)
+    bt = xb.Batch(systems, tol=1e-8, maxiter=20000, maxtime_s=60.0, ortho=ortho)
+    bt.run()
+    res = bt.results()
+    for (A, b), r, q, (_, m, _) in zip(mats, res, systems, specs):
+        assert r["status"] == 0, r
+        x = q["x"].cpu().numpy()
+        assert np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b) <= 1e-8
+        _, io = oracle.gmres(A, b, m=m, tol=1e-8, ortho=oracle.BCGS)
+        assert abs(r["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (r, io["iters"])
+
+
+def test_batch_rejects_unsupported_orthogonalisation():
+    xb, dev = lib_and_device()
+    systems, _ = _systems(dev, [(gen.poisson2d(5), 5, 0)])
+    for o in (1, 2):
+        with pytest.raises(xb.XbError):
+            xb.Batch(systems, ortho=o)
