@@ -514,6 +514,28 @@ def solvers(xb, torch, dev, plan3, A3, args):
         ortho=xb.ORTHO_AUTO)
     out["c4_mlp_mixed"]["tune_s"] = t_ml
     out["c4_mlp_fp64"]["tune_s"] = t_ml
+    # numerical computation policies (Sec. 2.3.2, 3.3) on the 128^3 problem: time,
+    # memory and accuracy of each
+    A2 = gen.convdiff3d(N=128, pe=10.0)
+    n2 = A2["n"]
+    ones2 = torch.ones(n2, dtype=torch.float64, device=dev)
+    pol = {}
+    for name, code in (("time", xb.POLICY_TIME), ("accuracy", xb.POLICY_ACCURACY),
+                       ("memory", xb.POLICY_MEMORY), ("stable", xb.POLICY_STABLE)):
+        pp = xb.Plan.from_host(A2, dev)
+        b2 = torch.empty(n2, dtype=torch.float64, device=dev)
+        pp.spmv(ones2, b2)
+        x2 = torch.zeros(n2, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = pp.gmres(b2, x2, tol=1e-8, maxtime_s=120.0, check_every=10, policy=code)
+        torch.cuda.synchronize()
+        pol[name] = {"s": time.perf_counter() - t0, "status": info["status"],
+                     "iters": info["iters"], "m_final": info["m_final"],
+                     "res_true": info["res_true"], "mem_GB": info["mem_bytes"] / 1e9,
+                     "variant": xb.VARIANT_NAMES.get(info["variant_used"], "?"),
+                     "ortho_used": ["mgs", "cgs", "dgks", "bcgs"][info["ortho_used"]]}
+    out["c4_128_policies"] = pol
     base = out["c4_plain_fp64_m30"]["s"]
     out["c4_speedup_vs_plain_fp64"] = {k: base / out[k]["s"] for k in
                                        ("c4_exhaustive_fp64_m30", "c4_exhaustive_fp64_m30_policy",

@@ -38,6 +38,9 @@ extern "C" {
 #define XB_ENOCONV (-4)      /* iteration/time limit hit; x holds the iterate  */
 #define XB_EBREAKDOWN (-5)   /* Krylov breakdown (singular/indefinite pivot)   */
 #define XB_ETIMEOUT (-6)     /* a bounded device-side wait expired            */
+#define XB_EFAULT (-7)       /* fault convergence (Sec. 3.3.2): the implicit   */
+                             /*   residual met tol, the true one did not, and  */
+                             /*   fault_check was off; x holds the iterate     */
 
 /* ---- SpMV implementation variants (Sec. 3.2.2: U1-U3, S1-S3) ---------- */
 #define XB_VAR_AUTO (-1)     /* plan's tuned / default choice                  */
@@ -63,6 +66,23 @@ extern "C" {
 #define XB_PREC_FP64 0
 #define XB_PREC_MIXED 1      /* FP32 SpMV + Arnoldi basis inside FP64          */
                              /*   iterative refinement                         */
+
+/* Numerical computation policy (Sec. 2.3.2, 3.3).  Any value but NONE sets
+ * tuner, variant, m / m_max, dafrt, ortho and fault_check before the solve:
+ *   TIME     fastest: exhaustive SpMV tuning, the restart rule on (m up to
+ *            m_max >= 128), BCGS for tol > 1e-10 else MGS, fault_check 0;
+ *   ACCURACY as TIME, but fault_check 1 and the orthogonalisation policy
+ *            (DGKS after a fault convergence);
+ *   MEMORY   least memory: the SpMV without plan metadata (thread per row,
+ *            or atomic transposes for symmetric storage), m = 10 fixed, MGS,
+ *            FP64, fault_check 0;
+ *   STABLE   no auto-tuning: the plan's SpMV, m as given, MGS, no restart
+ *            rule, fault_check 0. */
+#define XB_POLICY_NONE 0     /* every option as given (default)               */
+#define XB_POLICY_TIME 1
+#define XB_POLICY_ACCURACY 2
+#define XB_POLICY_MEMORY 3
+#define XB_POLICY_STABLE 4
 
 #define XB_TUNER_NONE 0      /* fixed variant (options.variant or default)     */
 #define XB_TUNER_EXHAUSTIVE 1 /* time every candidate (Sec. 3.1)              */
@@ -98,6 +118,12 @@ typedef struct xb_options {
     int32_t tuner;           /* XB_TUNER_*                                     */
     int32_t check_every;     /* host reads the residual every k steps (>=1)   */
     int32_t timing;          /* 1: record per-SpMV CUDA-event times in info   */
+    int32_t policy;          /* XB_POLICY_* (numerical computation policy)     */
+    int32_t fault_check;     /* 1 (default): after an implicit convergence the */
+                             /*   true residual decides; a false claim narrows */
+                             /*   the implicit threshold and the solve goes on */
+                             /*   (Sec. 3.3.2); 0: stop at the first claim and */
+                             /*   return XB_EFAULT if the true residual misses */
 } xb_options;
 
 typedef struct xb_info {
@@ -119,6 +145,9 @@ typedef struct xb_info {
     double t_solve_s;        /* host wall time of the solve                   */
     double spmv_ms;          /* summed CUDA-event SpMV time (opt.timing)      */
     double bytes_alg;        /* algorithmic bytes of all launches (see docs)  */
+    double mem_bytes;        /* device memory the solve used: workspace it    */
+                             /*   requested, the SpMV variant's plan data and */
+                             /*   the FP32 matrix copy (mixed precision)      */
 } xb_info;
 
 typedef struct xb_plan xb_plan;

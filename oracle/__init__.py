@@ -60,7 +60,7 @@ def lib():
         L.orc_gs_qr.argtypes = [vi, vi, _f64p, vi, vi, _f64p, _f64p]
         L.orc_gs_qr.restype = vi
         L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
-                                vi, vd, vi, vi, vi, _i32p, _f64p, vp, vp, vi]
+                                vi, vd, vi, vi, vi, vi, _i32p, _f64p, vp, vp, vi]
         L.orc_gmres.restype = vi
         L.orc_bicgstab.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vd, vi,
                                    _i32p, _f64p]
@@ -156,7 +156,7 @@ def gs_qr(X, ortho=MGS, bl=4):
 
 
 def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
-          dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0, ortho=MGS):
+          dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0, ortho=MGS, fault_check=True):
     """Restarted GMRES(m); returns (x, info dict)."""
     n, rp, ci, va = _csr(A)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
@@ -168,7 +168,7 @@ def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
                          np.ascontiguousarray(b, np.float64), x, int(m),
                          int(m_max if m_max is not None else m), float(tol), int(maxiter),
                          1 if dafrt else 0, float(theta), int(window), int(dm), int(ortho),
-                         ii, dd,
+                         1 if fault_check else 0, ii, dd,
                          hist.ctypes.data if hist_cap else None,
                          mh.ctypes.data if hist_cap else None, int(hist_cap))
     info = dict(status=st, iters=int(ii[0]), restarts=int(ii[1]), m_final=int(ii[2]),

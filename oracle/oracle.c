@@ -31,6 +31,7 @@
 #define ORC_OK 0
 #define ORC_ENOCONV (-4)
 #define ORC_EBREAKDOWN (-5)
+#define ORC_EFAULT (-7)
 
 /* ------------------------------------------------------------------------ */
 /* Sparse matrix-vector products                                              */
@@ -354,6 +355,10 @@ static int policy_ortho(double tol, int faulted)
  *   ortho:    ORC_MGS / ORC_CGS / ORC_DGKS / ORC_BCGS (block length 4), or
  *             ORC_AUTO: the accuracy policy of Sec. 3.3.2 (MGS for tol <= 1e-10,
  *             else BCGS; DGKS from the first fault convergence on).
+ *   fault_check: 1 = the accuracy mechanism below; 0 = stop at the first
+ *             claimed convergence and return ORC_EFAULT (-7) when the true
+ *             residual misses tol (the time / memory / stable policies of
+ *             Sec. 2.3.2 do not recompute the error).
  *
  * iinfo: [0] iterations, [1] restarts (cycles completed), [2] final m,
  *        [3] fault-convergence events, [4] orthogonalisation in use at exit.
@@ -364,7 +369,8 @@ static int policy_ortho(double tol, int faulted)
 int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
               const double *b, double *x, int m, int m_max, double tol,
               int maxiter, int dafrt, double theta, int window, int dm, int ortho,
-              int *iinfo, double *dinfo, double *hist, int *mhist, int hist_cap)
+              int fault_check, int *iinfo, double *dinfo, double *hist, int *mhist,
+              int hist_cap)
 {
     if (m_max < m) m_max = m;
     int iters = 0, restarts = 0, faults = 0, K = 0, claimed = 0, status = ORC_OK;
@@ -399,6 +405,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
         if (hist && restarts < hist_cap) { hist[restarts] = res_true; mhist[restarts] = m; }
         if (res_true <= tol) { status = ORC_OK; break; }
         if (iters >= maxiter) { status = ORC_ENOCONV; break; }
+        if (claimed && !fault_check) { faults++; status = ORC_EFAULT; break; }
         if (claimed) {
             faults++;
             tau *= tol / res_true;
@@ -714,7 +721,7 @@ int orc_gmres_ir(int n, const int *rp, const int *ci, const double *va,
         if (slow >= 2) {
             int ii[5]; double dd[2];
             status = orc_gmres(n, 0, rp, ci, va, b, x, m, m, tol, 1 << 30, 0, 0.0, 0, 0,
-                               ORC_MGS, ii, dd, NULL, NULL, 0);
+                               ORC_MGS, 1, ii, dd, NULL, NULL, 0);
             iinfo[4] = ii[0];
             iinfo[5] = 1;
             res = dd[1];

@@ -16,10 +16,12 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libxabc.so")
 
-XB_OK, XB_EINVAL, XB_ENOMEM, XB_ECUDA, XB_ENOCONV, XB_EBREAKDOWN, XB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+XB_OK, XB_EINVAL, XB_ENOMEM, XB_ECUDA, XB_ENOCONV, XB_EBREAKDOWN, XB_ETIMEOUT, XB_EFAULT = \
+    0, -1, -2, -3, -4, -5, -6, -7
 VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE = -1, 0, 1, 2, 3, 4
 VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile"}
 ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
+POLICY_NONE, POLICY_TIME, POLICY_ACCURACY, POLICY_MEMORY, POLICY_STABLE = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 TUNER_NONE, TUNER_EXHAUSTIVE, TUNER_MLP = 0, 1, 2
 
@@ -43,7 +45,7 @@ class Options(C.Structure):
                 ("tol_inner", C.c_double), ("maxiter_inner", C.c_int32),
                 ("max_outer", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
                 ("ipt", C.c_int32), ("tuner", C.c_int32), ("check_every", C.c_int32),
-                ("timing", C.c_int32)]
+                ("timing", C.c_int32), ("policy", C.c_int32), ("fault_check", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -52,7 +54,7 @@ class Info(C.Structure):
                                          "block_used", "ipt_used", "spmv_calls",
                                          "ortho_used")] + \
                [(k, C.c_double) for k in ("res_implicit", "res_true", "t_solve_s", "spmv_ms",
-                                          "bytes_alg")]
+                                          "bytes_alg", "mem_bytes")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -339,6 +339,8 @@ void xb_options_default(xb_options *o) {
     o->tuner = XB_TUNER_NONE;
     o->check_every = 1;
     o->timing = 0;
+    o->policy = XB_POLICY_NONE;
+    o->fault_check = 1;
 }
 
 int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out) {

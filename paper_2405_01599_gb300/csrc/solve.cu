@@ -81,6 +81,7 @@ struct SpmvTimer {
 struct Acct {
     double bytes = 0.0;
     int spmv = 0;
+    double mem = 0.0;  // largest workspace the solve requested
 };
 
 struct Spmv {
@@ -99,6 +100,7 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
     const int64_t ld = ld_of(n);
     const size_t vbytes = (size_t)(M + 1) * ld * sizeof(double);
     XB_TRY(xb::ensure_work(p, vbytes + xb::gm_doubles(M) * sizeof(double) + 256));
+    ac.mem = std::max(ac.mem, (double)(vbytes + xb::gm_doubles(M) * sizeof(double) + 256));
     double *V = static_cast<double *>(p->d_work);
     xb::GmDev st = xb::gm_layout(V + (size_t)(M + 1) * ld, M);
     const double spmv_b = xb::spmv_alg_bytes(p, false, 8);
@@ -139,6 +141,11 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
         }
         if (secs_since(t0) > o.maxtime_s) {
             status = XB_ENOCONV;
+            break;
+        }
+        if (claimed && !o.fault_check) {  // stop at the claim: fault convergence
+            faults++;
+            status = XB_EFAULT;
             break;
         }
         if (claimed) {  // fault convergence: the implicit residual lied
@@ -280,6 +287,7 @@ int gmres_mixed(xb_plan *p, const double *b, double *x, const xb_options &o, xb_
     const size_t need = vbytes + xb::gm_doubles(M) * sizeof(double) + (size_t)ld * 8 +
                         2 * (size_t)ld * 4 + 64 * sizeof(double) + 1024;
     XB_TRY(xb::ensure_work(p, need));
+    ac.mem = std::max(ac.mem, (double)need);
     char *w = static_cast<char *>(p->d_work);
     float *V = reinterpret_cast<float *>(w);
     w += vbytes;
@@ -362,6 +370,7 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
     const int64_t n = p->n;
     const int64_t ld = ld_of(n);
     XB_TRY(xb::ensure_work(p, 6 * (size_t)ld * sizeof(double) + 64 * sizeof(double)));
+    ac.mem = std::max(ac.mem, (double)(6 * (size_t)ld * sizeof(double) + 64 * sizeof(double)));
     double *r = static_cast<double *>(p->d_work);
     double *rh = r + ld, *pv = rh + ld, *v = pv + ld, *sv = v + ld, *t = sv + ld;
     double *sc = t + ld;
@@ -394,6 +403,11 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
         }
         if (iters >= o.maxiter || secs_since(t0) > o.maxtime_s) {
             status = XB_ENOCONV;
+            break;
+        }
+        if (claimed && !o.fault_check) {  // stop at the claim: fault convergence
+            faults++;
+            status = XB_EFAULT;
             break;
         }
         if (claimed) {
@@ -470,12 +484,69 @@ int check_args(xb_plan *p, const double *b, double *x, const xb_options &o) {
     return XB_OK;
 }
 
+// The numerical computation policy (Sec. 2.3.2, 3.3): settings it fixes.
+void apply_policy(xb_options &o, const xb_plan *p) {
+    switch (o.policy) {
+        case XB_POLICY_TIME:
+        case XB_POLICY_ACCURACY:
+            o.tuner = XB_TUNER_EXHAUSTIVE;
+            o.variant = XB_VAR_AUTO;
+            o.dafrt = 1;
+            o.m_max = std::max(std::max(o.m_max, o.m), 128);
+            if (o.policy == XB_POLICY_TIME) {
+                o.ortho = xb::ortho_choice(XB_ORTHO_AUTO, o.tol, false);
+                o.fault_check = 0;
+            } else {
+                o.ortho = XB_ORTHO_AUTO;
+                o.fault_check = 1;
+            }
+            break;
+        case XB_POLICY_MEMORY:
+            o.tuner = XB_TUNER_NONE;
+            o.variant = p && p->sym ? XB_VAR_SYM_ATOMIC : XB_VAR_ROW;
+            o.block = 0;
+            o.m = 10;
+            o.dafrt = 0;
+            o.ortho = XB_ORTHO_MGS;
+            o.precision = XB_PREC_FP64;
+            o.fault_check = 0;
+            break;
+        case XB_POLICY_STABLE:
+            o.tuner = XB_TUNER_NONE;
+            o.variant = XB_VAR_AUTO;
+            o.dafrt = 0;
+            o.ortho = XB_ORTHO_MGS;
+            o.fault_check = 0;
+            break;
+        default:
+            break;
+    }
+}
+
+// Device bytes of the plan data the SpMV variant reads besides the matrix.
+double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
+    double b = 0.0;
+    if (variant == XB_VAR_NNZ || variant == XB_VAR_SYM_TILE) {
+        for (const auto &t : p->tiles)
+            if (t.block == block && t.ipt == ipt) b += 4.0 * (t.ntiles + 1);
+    } else if (variant == XB_VAR_SEGSCAN) {
+        b += 4.0 * ((p->nnz + 31) / 32 + 1);
+        if (p->bss.d_ne_rows) b += 4.0 * p->bss.n_ne + 4.0 * (p->bss.n_ne + 1);
+        for (const auto &g : p->segs)
+            if (g.block == block && g.ipt == ipt) b += 4.0 * (g.nblk + 1) + 12.0 * g.nblk;
+    }
+    return b;
+}
+
 template <typename F>
 int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb_info *info,
                void *stream, F body) {
     xb_options o;
     if (opt) o = *opt;
     else xb_options_default(&o);
+    if (o.policy < XB_POLICY_NONE || o.policy > XB_POLICY_STABLE)
+        return xb::set_error(XB_EINVAL, "solve: unknown policy %d", o.policy);
+    apply_policy(o, p);
     xb_info inf;
     std::memset(&inf, 0, sizeof inf);
     int st = check_args(p, b, x, o);
@@ -499,6 +570,11 @@ int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb
         inf.variant_used = o.variant == XB_VAR_AUTO ? p->variant : o.variant;
         inf.block_used = o.block > 0 ? o.block : p->block;
         inf.ipt_used = o.ipt > 0 ? o.ipt : p->ipt;
+        inf.mem_bytes = ac.mem + spmv_meta_bytes(p, inf.variant_used, inf.block_used, inf.ipt_used) +
+                        (o.precision == XB_PREC_MIXED ? 4.0 * p->nnz : 0.0);
+        if (st == XB_EFAULT)
+            xb::set_error(XB_EFAULT, "fault convergence: implicit residual met tol, "
+                                     "||b-Ax||/||b|| = %.3e", inf.res_true);
         if (st == XB_ENOCONV)
             xb::set_error(XB_ENOCONV, "not converged: ||b-Ax||/||b|| = %.3e > tol %.1e", inf.res_true,
                           o.tol);

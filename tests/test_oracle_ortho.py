@@ -105,3 +105,19 @@ def test_accuracy_policy_chooses_the_orthogonalisation():
     _, fault = oracle.gmres(A, b, m=30, tol=1e-14, ortho=oracle.AUTO, maxiter=20000)
     assert fault["faults"] >= 1 and fault["ortho"] == oracle.DGKS
     assert fault["status"] == 0 and fault["res_true"] <= 1e-14
+
+
+def test_fault_check_off_stops_at_the_false_claim():
+    """Without the accuracy mechanism (the time / memory / stable policies of
+    Sec. 2.3.2 do not recompute the error) the solve ends at the first claimed
+    convergence: the implicit residual meets tol, the true one does not
+    (fault convergence, status -7); with it the same solve reaches tol."""
+    A = gen.poisson2d(64)
+    b = oracle.spmv(A, np.ones(A["n"]))
+    x, off = oracle.gmres(A, b, m=30, tol=1e-14, maxiter=20000, fault_check=False)
+    assert off["status"] == -7 and off["faults"] == 1
+    assert off["res_implicit"] <= 1e-14 < off["res_true"]
+    r = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+    assert abs(r - off["res_true"]) <= 1e-3 * r
+    _, on = oracle.gmres(A, b, m=30, tol=1e-14, maxiter=20000, fault_check=True)
+    assert on["status"] == 0 and on["res_true"] <= 1e-14 and on["faults"] == 1
