@@ -59,6 +59,9 @@ def parse():
                     help="profile-only: run this many GMRES(30) Arnoldi steps instead of SpMVs")
     ap.add_argument("--ortho", default="mgs", choices=["mgs", "cgs", "dgks", "bcgs"],
                     help="profile-only GMRES: orthogonalisation")
+    ap.add_argument("--mixed", action="store_true",
+                    help="profile-only GMRES: FP32 inner solve in FP64 refinement (one outer "
+                         "step of --gmres-steps inner steps)")
     return ap.parse_args()
 
 
@@ -265,11 +268,14 @@ def main():
         xg = torch.zeros(n, dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        extra = dict(precision=xb.PREC_MIXED, tol_inner=1e-30, maxiter_inner=args.gmres_steps,
+                     max_outer=1) if args.mixed else {}
         info = plan.gmres(bvec, xg, m=30, tol=1e-30, maxiter=args.gmres_steps, check_every=10,
-                          ortho=["mgs", "cgs", "dgks", "bcgs"].index(args.ortho))
+                          ortho=["mgs", "cgs", "dgks", "bcgs"].index(args.ortho), **extra)
         el = time.perf_counter() - t0
         if rank == 0:
-            print(json.dumps({"profile_only": True, "matrix": args.matrix, "gmres_steps": info["iters"],
+            print(json.dumps({"profile_only": True, "matrix": args.matrix,
+                              "gmres_steps": info["iters"] or info["inner_iters"],
                               "s": el, "GBs_solve": info["bytes_alg"] / el / 1e9, "choice": choice}))
         return
     x = torch.tensor(np.random.default_rng(0).uniform(-1, 1, n), device=dev)
