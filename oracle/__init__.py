@@ -60,9 +60,12 @@ def lib():
         L.orc_gs_qr.argtypes = [vi, vi, _f64p, vi, vi, _f64p, _f64p]
         L.orc_gs_qr.restype = vi
         L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
-                                vi, vd, vi, vi, vi, vi, _i32p, _f64p, vp, vp, vi]
+                                vi, vd, vi, vi, vi, vi, vp, _i32p, _f64p, vp, vp, vi]
+        L.orc_ilu0.argtypes = [vi, _i32p, _i32p, _f64p, _f64p]
+        L.orc_ilu0.restype = vi
+        L.orc_ilu0_solve.argtypes = [vi, _i32p, _i32p, _f64p, _f64p, _f64p]
         L.orc_gmres.restype = vi
-        L.orc_bicgstab.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vd, vi,
+        L.orc_bicgstab.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vd, vi, vp,
                                    _i32p, _f64p]
         L.orc_bicgstab.restype = vi
         L.orc_gmres_f32_inner.argtypes = [vi, _i32p, _i32p, _f32p, _f32p, _f32p, vi, vd, vi]
@@ -155,9 +158,38 @@ def gs_qr(X, ortho=MGS, bl=4):
     return Q.reshape(k, n).T, R.reshape(k, k).T, d
 
 
+def ilu0(A):
+    """ILU(0) factors of a general CRS matrix in its own pattern (values
+    aligned with A's col array); returns (lu, status)."""
+    n, rp, ci, va = _csr(A)
+    lu = np.zeros(max(va.size, 1))
+    st = lib().orc_ilu0(n, rp, ci, va, lu)
+    return lu[:va.size], st
+
+
+def ilu0_solve(A, lu, r):
+    n, rp, ci, _ = _csr(A)
+    z = np.zeros(n)
+    lib().orc_ilu0_solve(n, rp, ci, np.ascontiguousarray(lu, np.float64),
+                         np.ascontiguousarray(r, np.float64), z)
+    return z
+
+
+def _prec(A, prec):
+    if not prec:
+        return None, None
+    lu, st = ilu0(A)
+    if st != 0:
+        raise ValueError("ILU(0) breakdown")
+    return lu, lu.ctypes.data
+
+
 def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
-          dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0, ortho=MGS, fault_check=True):
-    """Restarted GMRES(m); returns (x, info dict)."""
+          dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0, ortho=MGS, fault_check=True,
+          ilu=False):
+    """Restarted GMRES(m), right-preconditioned by ILU(0) when ilu; returns
+    (x, info dict)."""
+    keep, mptr = _prec(A, ilu)
     n, rp, ci, va = _csr(A)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     ii = np.zeros(5, np.int32)
@@ -168,7 +200,7 @@ def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
                          np.ascontiguousarray(b, np.float64), x, int(m),
                          int(m_max if m_max is not None else m), float(tol), int(maxiter),
                          1 if dafrt else 0, float(theta), int(window), int(dm), int(ortho),
-                         1 if fault_check else 0, ii, dd,
+                         1 if fault_check else 0, mptr, ii, dd,
                          hist.ctypes.data if hist_cap else None,
                          mh.ctypes.data if hist_cap else None, int(hist_cap))
     info = dict(status=st, iters=int(ii[0]), restarts=int(ii[1]), m_final=int(ii[2]),
@@ -181,14 +213,15 @@ def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
     return x, info
 
 
-def bicgstab(A, b, x0=None, tol=1e-8, maxiter=100000):
+def bicgstab(A, b, x0=None, tol=1e-8, maxiter=100000, ilu=False):
+    keep, mptr = _prec(A, ilu)
     n, rp, ci, va = _csr(A)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     ii = np.zeros(4, np.int32)
     dd = np.zeros(2)
     st = lib().orc_bicgstab(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
                             np.ascontiguousarray(b, np.float64), x, float(tol), int(maxiter),
-                            ii, dd)
+                            mptr, ii, dd)
     return x, dict(status=st, iters=int(ii[0]), restarts=int(ii[1]), faults=int(ii[3]),
                    res_implicit=float(dd[0]), res_true=float(dd[1]))
 

@@ -324,6 +324,69 @@ static int policy_ortho(double tol, int faulted)
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILU(0) preconditioner (the preconditioner of the paper's solver runs,     */
+/* Sec. 4.3): incomplete LU with the sparsity pattern of A, general CRS.     */
+/* ------------------------------------------------------------------------ */
+
+/* Position of column j in row i (binary search over the sorted columns), or -1. */
+static int find_col(const int *rp, const int *ci, int i, int j)
+{
+    int lo = rp[i], hi = rp[i + 1] - 1;
+    while (lo <= hi) {
+        int mid = lo + (hi - lo) / 2;
+        if (ci[mid] == j) return mid;
+        if (ci[mid] < j) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* lu = ILU(0) factors of A in A's pattern: the strictly lower part holds L
+ * (unit diagonal not stored), the rest U.  Row by row (IKJ): for each stored
+ * (i, k) with k < i, in ascending k: l_ik = a_ik / u_kk, then
+ * a_ij -= l_ik u_kj for every stored (i, j) with j > k whose (k, j) is stored.
+ * Returns ORC_EBREAKDOWN (-5) if a diagonal entry is missing or becomes 0. */
+int orc_ilu0(int n, const int *rp, const int *ci, const double *va, double *lu)
+{
+    for (int p = 0; p < rp[n]; p++) lu[p] = va[p];
+    for (int i = 0; i < n; i++) {
+        for (int p = rp[i]; p < rp[i + 1] && ci[p] < i; p++) {
+            int k = ci[p];
+            int dk = find_col(rp, ci, k, k);
+            if (dk < 0 || lu[dk] == 0.0) return ORC_EBREAKDOWN;
+            lu[p] /= lu[dk];
+            for (int q = p + 1; q < rp[i + 1]; q++) {
+                int kq = find_col(rp, ci, k, ci[q]);
+                if (kq >= 0) lu[q] -= lu[p] * lu[kq];
+            }
+        }
+        int di = find_col(rp, ci, i, i);
+        if (di < 0 || lu[di] == 0.0) return ORC_EBREAKDOWN;
+    }
+    return ORC_OK;
+}
+
+/* z = (LU)^{-1} r: forward substitution with the unit lower factor, then
+ * backward substitution with the upper factor. */
+void orc_ilu0_solve(int n, const int *rp, const int *ci, const double *lu, const double *r,
+                    double *z)
+{
+    for (int i = 0; i < n; i++) {
+        double s = r[i];
+        for (int p = rp[i]; p < rp[i + 1] && ci[p] < i; p++) s -= lu[p] * z[ci[p]];
+        z[i] = s;
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = z[i], d = 0.0;
+        for (int p = rp[i]; p < rp[i + 1]; p++) {
+            if (ci[p] > i) s -= lu[p] * z[ci[p]];
+            else if (ci[p] == i) d = lu[p];
+        }
+        z[i] = s / d;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Restarted GMRES(m) (Saad & Schultz; listed in Sec. 2.2, run in Sec. 4.3)  */
 /* ------------------------------------------------------------------------ */
 
@@ -355,6 +418,10 @@ static int policy_ortho(double tol, int faulted)
  *   ortho:    ORC_MGS / ORC_CGS / ORC_DGKS / ORC_BCGS (block length 4), or
  *             ORC_AUTO: the accuracy policy of Sec. 3.3.2 (MGS for tol <= 1e-10,
  *             else BCGS; DGKS from the first fault convergence on).
+ *   M:        ILU(0) factors from orc_ilu0 (general CRS only) for right
+ *             preconditioning, Arnoldi on A M^{-1}: w = A (M^{-1} v_j) and
+ *             x += M^{-1} (V y); NULL = no preconditioner.  Residuals stay
+ *             those of A x = b.
  *   fault_check: 1 = the accuracy mechanism below; 0 = stop at the first
  *             claimed convergence and return ORC_EFAULT (-7) when the true
  *             residual misses tol (the time / memory / stable policies of
@@ -369,8 +436,8 @@ static int policy_ortho(double tol, int faulted)
 int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
               const double *b, double *x, int m, int m_max, double tol,
               int maxiter, int dafrt, double theta, int window, int dm, int ortho,
-              int fault_check, int *iinfo, double *dinfo, double *hist, int *mhist,
-              int hist_cap)
+              int fault_check, const double *M, int *iinfo, double *dinfo, double *hist,
+              int *mhist, int hist_cap)
 {
     if (m_max < m) m_max = m;
     int iters = 0, restarts = 0, faults = 0, K = 0, claimed = 0, status = ORC_OK;
@@ -395,6 +462,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
     double *y = (double *)malloc(sizeof(double) * (size_t)m_max);
     double *samp = (double *)malloc(sizeof(double) * (size_t)(window > 0 ? window : 1));
     double *hc = (double *)malloc(sizeof(double) * (size_t)(m_max + 1));
+    double *tz = (double *)malloc(sizeof(double) * (size_t)n);
 
     for (;;) {
         /* r = b - A x, true residual */
@@ -430,7 +498,12 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
         int k = 0, broke = 0;
         for (int j = 0; j < m; j++) {
             iters++;
-            matvec(kind, n, rp, ci, va, V + (size_t)j * n, w);
+            if (M) {
+                orc_ilu0_solve(n, rp, ci, M, V + (size_t)j * n, tz);
+                matvec(kind, n, rp, ci, va, tz, w);
+            } else {
+                matvec(kind, n, rp, ci, va, V + (size_t)j * n, w);
+            }
             orth(cur, 4, n, j, V, w, hc);
             double len2 = 0.0;
             for (int i = 0; i <= j; i++) {
@@ -473,9 +546,18 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
                 s -= H[(size_t)i * m_max + q] * y[q];
             y[i] = s / H[(size_t)i * m_max + i];
         }
-        for (int i = 0; i < k; i++)
-            for (int q = 0; q < n; q++)
-                x[q] += y[i] * V[(size_t)i * n + q];
+        if (M) {
+            for (int q = 0; q < n; q++) w[q] = 0.0;
+            for (int i = 0; i < k; i++)
+                for (int q = 0; q < n; q++)
+                    w[q] += y[i] * V[(size_t)i * n + q];
+            orc_ilu0_solve(n, rp, ci, M, w, tz);
+            for (int q = 0; q < n; q++) x[q] += tz[q];
+        } else {
+            for (int i = 0; i < k; i++)
+                for (int q = 0; q < n; q++)
+                    x[q] += y[i] * V[(size_t)i * n + q];
+        }
         restarts++;
     }
     iinfo[0] = iters;
@@ -486,7 +568,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
     dinfo[0] = res_impl;
     dinfo[1] = res_true;
     free(r); free(w); free(V); free(H); free(cs); free(sn); free(g); free(y); free(samp);
-    free(hc);
+    free(hc); free(tz);
     return status;
 }
 
@@ -502,6 +584,9 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
  *   if ||s||/||b|| <= tau: x += alpha p, stop
  *   t = A s; omega = (t, s)/(t, t); x += alpha p + omega s; r = s - omega t
  *   rho = rho'; stop if ||r||/||b|| <= tau
+ * With M (ILU(0) factors, general CRS) the iteration is right-preconditioned:
+ * p^ = M^{-1} p and s^ = M^{-1} s replace p and s in the products with A and in
+ * the update of x (x += alpha p^ + omega s^); residuals stay those of A x = b.
  * Breakdown (status -5) when rho', (rhat, v) or (t, t) is exactly zero, or omega
  * is zero without convergence.  The true residual is checked after every
  * claimed convergence; a false claim (fault convergence, Sec. 3.3.2) restarts
@@ -510,7 +595,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
  * dinfo: [0] last recursive relative residual, [1] true relative residual.
  */
 int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va,
-                 const double *b, double *x, double tol, int maxiter,
+                 const double *b, double *x, double tol, int maxiter, const double *M,
                  int *iinfo, double *dinfo)
 {
     int iters = 0, restarts = 0, faults = 0, claimed = 0, status = ORC_OK;
@@ -526,6 +611,7 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
     double *r = (double *)malloc(bytes), *rh = (double *)malloc(bytes);
     double *p = (double *)malloc(bytes), *v = (double *)malloc(bytes);
     double *s = (double *)malloc(bytes), *t = (double *)malloc(bytes);
+    double *ph = (double *)malloc(bytes), *sh = (double *)malloc(bytes);
     for (;;) {
         matvec(kind, n, rp, ci, va, x, r);
         for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
@@ -544,23 +630,27 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
             if (rho1 == 0.0) { broke = 1; break; }
             double beta = (rho1 / rho) * (alpha / omega);
             for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-            matvec(kind, n, rp, ci, va, p, v);
+            if (M) orc_ilu0_solve(n, rp, ci, M, p, ph);
+            else for (int i = 0; i < n; i++) ph[i] = p[i];
+            matvec(kind, n, rp, ci, va, ph, v);
             double sigma = dot(n, rh, v);
             if (sigma == 0.0) { broke = 1; break; }
             alpha = rho1 / sigma;
             for (int i = 0; i < n; i++) s[i] = r[i] - alpha * v[i];
             double sn = nrm2(n, s) / bnorm;
             if (sn <= tau) {
-                for (int i = 0; i < n; i++) x[i] += alpha * p[i];
+                for (int i = 0; i < n; i++) x[i] += alpha * ph[i];
                 res_rec = sn;
                 claimed = 1;
                 break;
             }
-            matvec(kind, n, rp, ci, va, s, t);
+            if (M) orc_ilu0_solve(n, rp, ci, M, s, sh);
+            else for (int i = 0; i < n; i++) sh[i] = s[i];
+            matvec(kind, n, rp, ci, va, sh, t);
             double tt = dot(n, t, t);
             if (tt == 0.0) { broke = 1; break; }
             omega = dot(n, t, s) / tt;
-            for (int i = 0; i < n; i++) x[i] += alpha * p[i] + omega * s[i];
+            for (int i = 0; i < n; i++) x[i] += alpha * ph[i] + omega * sh[i];
             for (int i = 0; i < n; i++) r[i] = s[i] - omega * t[i];
             rho = rho1;
             res_rec = nrm2(n, r) / bnorm;
@@ -580,7 +670,7 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
     iinfo[3] = faults;
     dinfo[0] = res_rec;
     dinfo[1] = res_true;
-    free(r); free(rh); free(p); free(v); free(s); free(t);
+    free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
     return status;
 }
 
@@ -721,7 +811,7 @@ int orc_gmres_ir(int n, const int *rp, const int *ci, const double *va,
         if (slow >= 2) {
             int ii[5]; double dd[2];
             status = orc_gmres(n, 0, rp, ci, va, b, x, m, m, tol, 1 << 30, 0, 0.0, 0, 0,
-                               ORC_MGS, 1, ii, dd, NULL, NULL, 0);
+                               ORC_MGS, 1, NULL, ii, dd, NULL, NULL, 0);
             iinfo[4] = ii[0];
             iinfo[5] = 1;
             res = dd[1];
