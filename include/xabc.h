@@ -84,6 +84,12 @@ extern "C" {
 #define XB_POLICY_MEMORY 3
 #define XB_POLICY_STABLE 4
 
+/* Preconditioner (Sec. 4.3 runs the solvers with ILU(0)). */
+#define XB_PRECOND_NONE 0
+#define XB_PRECOND_ILU0 1    /* incomplete LU in A's pattern, right-applied:  */
+                             /*   the solvers iterate on A M^{-1} and report   */
+                             /*   residuals of A x = b                         */
+
 #define XB_TUNER_NONE 0      /* fixed variant (options.variant or default)     */
 #define XB_TUNER_EXHAUSTIVE 1 /* time every candidate (Sec. 3.1)              */
 #define XB_TUNER_MLP 2       /* learned tuner (xb_mlp_*)                       */
@@ -124,6 +130,8 @@ typedef struct xb_options {
                              /*   the implicit threshold and the solve goes on */
                              /*   (Sec. 3.3.2); 0: stop at the first claim and */
                              /*   return XB_EFAULT if the true residual misses */
+    int32_t precond;         /* XB_PRECOND_*: right preconditioner (FP64      */
+                             /*   GMRES and BiCGStab on general CRS)           */
 } xb_options;
 
 typedef struct xb_info {
@@ -288,6 +296,19 @@ int xb_mgs(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, dou
  * h: device, k+1 doubles; 1 <= k <= 512; XB_ORTHO_AUTO is rejected. */
 int xb_orth(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, double *w,
             double *h, int32_t ortho, void *stream);
+
+/* ---- ILU(0) preconditioner (Sec. 4.3) -------------------------------------
+ * Built once per plan on first use (dependency levels of the two triangles
+ * from the pattern on the host, numeric factorization on the device, level
+ * by level); general CRS only (XB_EINVAL for sym_upper plans).  A row without
+ * a stored diagonal or a zero pivot gives XB_EBREAKDOWN. */
+int xb_ilu0_setup(xb_plan *plan, void *stream);
+/* z = (L U)^{-1} r: forward then backward substitution, one launch per
+ * dependency level.  r and z: DEVICE, n doubles, distinct. */
+int xb_ilu0_apply(xb_plan *plan, const double *r, double *z, void *stream);
+/* Copy the factors (aligned with the plan's col array: strict lower part = L
+ * with unit diagonal not stored, the rest = U) to the DEVICE array lu (nnz). */
+int xb_ilu0_factors(xb_plan *plan, double *lu, void *stream);
 
 /* ---- run-time auto-tuning ------------------------------------------------ */
 

@@ -22,6 +22,7 @@ VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE = -1, 0, 1
 VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile"}
 ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
 POLICY_NONE, POLICY_TIME, POLICY_ACCURACY, POLICY_MEMORY, POLICY_STABLE = 0, 1, 2, 3, 4
+PRECOND_NONE, PRECOND_ILU0 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 TUNER_NONE, TUNER_EXHAUSTIVE, TUNER_MLP = 0, 1, 2
 
@@ -45,7 +46,8 @@ class Options(C.Structure):
                 ("tol_inner", C.c_double), ("maxiter_inner", C.c_int32),
                 ("max_outer", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
                 ("ipt", C.c_int32), ("tuner", C.c_int32), ("check_every", C.c_int32),
-                ("timing", C.c_int32), ("policy", C.c_int32), ("fault_check", C.c_int32)]
+                ("timing", C.c_int32), ("policy", C.c_int32), ("fault_check", C.c_int32),
+                ("precond", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -113,6 +115,9 @@ def lib():
         "xb_axpy": (i32, [i32, f64, vp, vp, vp]),
         "xb_mgs": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, vp]),
         "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
+        "xb_ilu0_setup": (i32, [vp, vp]),
+        "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
+        "xb_ilu0_factors": (i32, [vp, vp, vp]),
         "xb_tune_exhaustive": (i32, [vp, P(Choice), vp]),
         "xb_mm_ratio": (f64, [P(f64), i32, i32]),
         "xb_dafrt": (i32, [i32, P(f64), f64]),
@@ -323,6 +328,21 @@ class Plan:
         _check(lib().xb_mgs(self._h, w.numel(), k, _ptr(V), ld, _ptr(w), _ptr(h),
                             _stream(stream)))
         return h
+
+    def ilu0_setup(self, stream=None):
+        _check(lib().xb_ilu0_setup(self._h, _stream(stream)))
+
+    def ilu0_apply(self, r, z, stream=None):
+        """z = (L U)^{-1} r with the plan's ILU(0) factors."""
+        self._vec(r, z)
+        _check(lib().xb_ilu0_apply(self._h, _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
+    def ilu0_factors(self, stream=None):
+        import torch
+        lu = torch.empty(self.nnz, dtype=torch.float64, device=self._keep[2].device)
+        _check(lib().xb_ilu0_factors(self._h, _ptr(lu), _stream(stream)))
+        return lu
 
     def orth(self, V, w, ortho, stream=None):
         """Orthogonalise w against the k rows of V with ORTHO_MGS / CGS / DGKS /

@@ -76,6 +76,22 @@ struct BssData {
     bool built = false;
 };
 
+// ILU(0) preconditioner data (built on first use): factors in A's pattern
+// (strict lower part L with unit diagonal, the rest U), the diagonal
+// positions, and the rows grouped by dependency level for the forward (L)
+// and backward (U) substitutions: every row of a level depends only on rows
+// of earlier levels.
+struct IluData {
+    bool built = false;
+    int status = 0;                  // XB_OK or XB_EBREAKDOWN (zero pivot)
+    double *d_lu = nullptr;          // nnz
+    int *d_dpos = nullptr;           // n
+    int *d_lrows = nullptr, *d_urows = nullptr;  // n each, ordered by level
+    std::vector<int> loff, uoff;     // level offsets (levels + 1)
+    int *d_flag = nullptr;           // zero-pivot flag
+    double *d_tmp = nullptr;         // 2n scratch for the solvers
+};
+
 }  // namespace xb
 
 struct xb_plan {
@@ -90,6 +106,7 @@ struct xb_plan {
     std::vector<xb::TilePart> tiles;     // cache by (block, ipt)
     std::vector<xb::SegPart> segs;       // cache by (block, ipt)
     xb::BssData bss;
+    xb::IluData ilu;
     bool vec_ok = false;                 // val and col 16-byte aligned
     // reduction scratch
     double *d_part = nullptr;            // kRedSlots * 4 partials
@@ -112,6 +129,13 @@ const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err
 const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err);
 int ensure_val32(xb_plan *p, cudaStream_t s);
 int ensure_work(xb_plan *p, size_t bytes);
+// ILU(0): build (levels on the host from the pattern, factorization on the
+// device), apply z = (LU)^{-1} r on stream s, and the algorithmic bytes of one
+// application.
+int ensure_ilu(xb_plan *p, cudaStream_t s);
+int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s);
+double ilu_apply_bytes(const xb_plan *p);
+void ilu_free(xb_plan *p);
 bool variant_fits(const xb_plan *p, int variant);
 
 // SpMV dispatch: y = alpha*A*x + beta*y in value type double or float.

@@ -1,0 +1,250 @@
+// ILU(0) preconditioner (the preconditioner of the paper's solver runs,
+// Sec. 4.3): incomplete LU factorization in the sparsity pattern of A
+// (general CRS), applied as z = U^{-1} L^{-1} r.
+//
+// Setup: the host derives, from the pattern alone, the dependency level of
+// every row for the forward substitution (level(i) = 1 + max level(k) over the
+// stored k < i in row i) and for the backward one (over the stored j > i); rows
+// are grouped by level.  The numeric factorization then runs level by level on
+// the device, one warp per row: for each stored (i, k), k < i, in ascending k,
+// l_ik = a_ik / u_kk, and every stored (i, j), j > k, subtracts l_ik u_kj when
+// (k, j) is stored (binary search in row k, which an earlier level finished).
+// Each substitution is one launch per level; inside a level every row is
+// independent: a thread per row, with rows longer than 32 stored entries in
+// the triangle taken by the whole warp (lanes stride over the row, shuffle
+// reduction), so a power-law row does not serialise one thread.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace {
+
+__device__ __forceinline__ int find_in_row(const int *__restrict__ ci, int lo, int hi, int j) {
+    // search [lo, hi) of a sorted column list for j
+    hi -= 1;
+    while (lo <= hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        const int c = __ldg(ci + mid);
+        if (c == j) return mid;
+        if (c < j) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// Factor the rows listed in rows[0..cnt) (one dependency level), warp per row.
+__global__ void k_ilu_factor(int cnt, const int *__restrict__ rows, const int *__restrict__ rp,
+                             const int *__restrict__ ci, const int *__restrict__ dpos,
+                             double *__restrict__ lu, int *__restrict__ flag) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= cnt) return;  // warp-uniform
+    const int i = rows[w];
+    const int a = rp[i], e = rp[i + 1], d = dpos[i];
+    for (int p = a; p < d; p++) {
+        const int k = __ldg(ci + p);
+        const int dk = dpos[k];
+        const double piv = lu[dk];
+        if (piv == 0.0) {
+            if (lane == 0) atomicExch(flag, 1);
+            return;
+        }
+        const double lik = lu[p] / piv;
+        __syncwarp();
+        if (lane == 0) lu[p] = lik;
+        const int ke = rp[k + 1];
+        for (int q = p + 1 + lane; q < e; q += 32) {
+            const int pos = find_in_row(ci, dk + 1, ke, __ldg(ci + q));
+            if (pos >= 0) lu[q] = fma(-lik, lu[pos], lu[q]);
+        }
+        __syncwarp();  // row i's entries settled before the next l_ik is formed
+    }
+    if (lane == 0 && lu[d] == 0.0) atomicExch(flag, 1);
+}
+
+// One level of a substitution.  FWD: z_i = r_i - sum_{k<i} l_ik z_k over the
+// stored strictly lower entries.  Backward: z_i = (z_i - sum_{j>i} u_ij z_j) / u_ii.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_ilu_level(int cnt, const int *__restrict__ rows,
+                                                   const int *__restrict__ rp,
+                                                   const int *__restrict__ ci,
+                                                   const int *__restrict__ dpos,
+                                                   const double *__restrict__ lu,
+                                                   const double *__restrict__ r,
+                                                   double *__restrict__ z) {
+    const int lane = threadIdx.x & 31;
+    const int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31;  // warp's first slot
+    if (base >= cnt) return;  // warp-uniform
+    const int slot = base + lane;
+    int i = -1, ka = 0, kb = 0;
+    if (slot < cnt) {
+        i = rows[slot];
+        const int d = dpos[i];
+        ka = FWD ? rp[i] : d + 1;
+        kb = FWD ? d : rp[i + 1];
+    }
+    const bool lng = kb - ka > 32;
+    double s = 0.0;
+    if (!lng)
+        for (int k = ka; k < kb; k++) s = fma(__ldg(lu + k), z[__ldg(ci + k)], s);
+    unsigned todo = __ballot_sync(0xffffffffu, lng);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int la = __shfl_sync(0xffffffffu, ka, src);
+        const int lb = __shfl_sync(0xffffffffu, kb, src);
+        double t = 0.0;
+        for (int k = la + lane; k < lb; k += 32) t = fma(__ldg(lu + k), z[__ldg(ci + k)], t);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == src) s = t;
+    }
+    if (i >= 0) {
+        if (FWD) z[i] = r[i] - s;
+        else z[i] = (z[i] - s) / lu[dpos[i]];
+    }
+}
+
+// Rows grouped by level (counting sort), ascending row order inside a level.
+void group_levels(const std::vector<int> &lev, int nlev, std::vector<int> &rows,
+                  std::vector<int> &off) {
+    const int n = (int)lev.size();
+    off.assign(nlev + 1, 0);
+    for (int i = 0; i < n; i++) off[lev[i] + 1]++;
+    for (int l = 0; l < nlev; l++) off[l + 1] += off[l];
+    rows.resize(n);
+    std::vector<int> pos(off.begin(), off.end() - 1);
+    for (int i = 0; i < n; i++) rows[pos[lev[i]]++] = i;
+}
+
+}  // namespace
+
+namespace xb {
+
+void ilu_free(xb_plan *p) {
+    IluData &u = p->ilu;
+    cudaFree(u.d_lu);
+    cudaFree(u.d_dpos);
+    cudaFree(u.d_lrows);
+    cudaFree(u.d_urows);
+    cudaFree(u.d_flag);
+    cudaFree(u.d_tmp);
+    u = IluData();
+}
+
+int ensure_ilu(xb_plan *p, cudaStream_t s) {
+    IluData &u = p->ilu;
+    if (u.built) return u.status == XB_OK ? XB_OK : set_error(u.status, "ILU(0): zero pivot");
+    if (p->sym) return set_error(XB_EINVAL, "ILU(0) needs full (general) CRS storage");
+    const int n = p->n, nnz = p->nnz;
+    const std::vector<int> &rp = p->h_rowptr;
+    std::vector<int> ci(nnz);
+    if (nnz > 0) XB_CUDA(cudaMemcpy(ci.data(), p->col, (size_t)nnz * 4, cudaMemcpyDeviceToHost));
+    std::vector<int> dpos(n), lev(n, 0), ulev(n, 0);
+    int nl = n > 0 ? 1 : 0, nu = n > 0 ? 1 : 0;
+    for (int i = 0; i < n; i++) {
+        int d = -1, m = -1;
+        for (int q = rp[i]; q < rp[i + 1]; q++) {
+            const int k = ci[q];
+            if (k < i) m = std::max(m, lev[k]);
+            else if (k == i) d = q;
+        }
+        if (d < 0) return set_error(XB_EBREAKDOWN, "ILU(0): row %d has no diagonal entry", i);
+        dpos[i] = d;
+        lev[i] = m + 1;
+        nl = std::max(nl, lev[i] + 1);
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        int m = -1;
+        for (int q = dpos[i] + 1; q < rp[i + 1]; q++) m = std::max(m, ulev[ci[q]]);
+        ulev[i] = m + 1;
+        nu = std::max(nu, ulev[i] + 1);
+    }
+    std::vector<int> lrows, urows;
+    group_levels(lev, nl, lrows, u.loff);
+    group_levels(ulev, nu, urows, u.uoff);
+    auto up = [&](int **d, const std::vector<int> &h) -> int {
+        XB_CUDA(cudaMalloc(d, std::max<size_t>(1, h.size()) * 4));
+        if (!h.empty())
+            XB_CUDA(cudaMemcpyAsync(*d, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s));
+        return XB_OK;
+    };
+    XB_TRY(up(&u.d_dpos, dpos));
+    XB_TRY(up(&u.d_lrows, lrows));
+    XB_TRY(up(&u.d_urows, urows));
+    XB_CUDA(cudaMalloc(&u.d_lu, std::max<size_t>(1, (size_t)nnz) * sizeof(double)));
+    XB_CUDA(cudaMalloc(&u.d_flag, sizeof(int)));
+    XB_CUDA(cudaMalloc(&u.d_tmp, std::max<size_t>(1, 2 * (size_t)n) * sizeof(double)));
+    XB_CUDA(cudaMemsetAsync(u.d_flag, 0, sizeof(int), s));
+    if (nnz > 0)
+        XB_CUDA(cudaMemcpyAsync(u.d_lu, p->val, (size_t)nnz * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    for (int l = 0; l < nl; l++) {
+        const int cnt = u.loff[l + 1] - u.loff[l];
+        if (cnt == 0) continue;
+        const int wpb = 8;  // warps per CTA
+        k_ilu_factor<<<(cnt + wpb - 1) / wpb, 32 * wpb, 0, s>>>(
+            cnt, u.d_lrows + u.loff[l], p->rowptr, p->col, u.d_dpos, u.d_lu, u.d_flag);
+    }
+    XB_LAUNCHED("k_ilu_factor");
+    int flag = 0;
+    XB_CUDA(cudaMemcpyAsync(&flag, u.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    XB_CUDA(cudaStreamSynchronize(s));
+    u.built = true;
+    u.status = flag ? XB_EBREAKDOWN : XB_OK;
+    if (flag) return set_error(XB_EBREAKDOWN, "ILU(0): zero pivot");
+    return XB_OK;
+}
+
+int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s) {
+    IluData &u = p->ilu;
+    XB_TRY(ensure_ilu(p, s));
+    const int nl = (int)u.loff.size() - 1, nu = (int)u.uoff.size() - 1;
+    for (int l = 0; l < nl; l++) {
+        const int cnt = u.loff[l + 1] - u.loff[l];
+        k_ilu_level<true><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, u.d_lrows + u.loff[l], p->rowptr,
+                                                           p->col, u.d_dpos, u.d_lu, r, z);
+    }
+    for (int l = 0; l < nu; l++) {
+        const int cnt = u.uoff[l + 1] - u.uoff[l];
+        k_ilu_level<false><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, u.d_urows + u.uoff[l], p->rowptr,
+                                                            p->col, u.d_dpos, u.d_lu, z, z);
+    }
+    XB_LAUNCHED("k_ilu_level");
+    return XB_OK;
+}
+
+double ilu_apply_bytes(const xb_plan *p) {
+    // both triangles once (value + column), rowptr and diagonal positions
+    // twice, r read, z written by the forward pass, read and written by the
+    // backward pass, and each row's level slot twice
+    const double n = p->n, nnz = p->nnz;
+    return 12.0 * nnz + 2.0 * 4.0 * (n + 1) + 2.0 * 4.0 * n + 8.0 * n * 4.0 + 2.0 * 4.0 * n;
+}
+
+}  // namespace xb
+
+extern "C" {
+
+int xb_ilu0_setup(xb_plan *p, void *stream) {
+    if (!p) return xb::set_error(XB_EINVAL, "ilu0_setup: NULL plan");
+    return xb::ensure_ilu(p, (cudaStream_t)stream);
+}
+
+int xb_ilu0_apply(xb_plan *p, const double *r, double *z, void *stream) {
+    if (!p || (p->n > 0 && (!r || !z)) || r == z)
+        return xb::set_error(XB_EINVAL, "ilu0_apply: bad argument");
+    return xb::ilu_apply(p, r, z, (cudaStream_t)stream);
+}
+
+int xb_ilu0_factors(xb_plan *p, double *lu, void *stream) {
+    if (!p || (p->nnz > 0 && !lu)) return xb::set_error(XB_EINVAL, "ilu0_factors: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    XB_TRY(xb::ensure_ilu(p, s));
+    if (p->nnz > 0)
+        XB_CUDA(cudaMemcpyAsync(lu, p->ilu.d_lu, (size_t)p->nnz * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    return XB_OK;
+}
+
+}  // extern "C"

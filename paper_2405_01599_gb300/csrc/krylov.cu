@@ -690,13 +690,14 @@ __global__ void k_bi_omega(int64_t n, double *__restrict__ sc, const double *__r
     }
 }
 
-// x += alpha p + omega s;  r = s - omega t;  ||r||^2, rho_next = (rhat, r).
+// x += alpha p + omega sx;  r = s - omega t;  ||r||^2, rho_next = (rhat, r).
+// sx is s itself, or M^{-1} s (and p is M^{-1} p) under right preconditioning.
 // When ||s|| already met the threshold: x += alpha p only, flag = 1 (done).
 __global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__ x,
                         const double *__restrict__ p, const double *__restrict__ s,
-                        const double *__restrict__ t, double *__restrict__ r,
-                        const double *__restrict__ rh, double *__restrict__ part,
-                        unsigned *__restrict__ ticket, int vec) {
+                        const double *sx, const double *__restrict__ t,
+                        double *__restrict__ r, const double *__restrict__ rh,
+                        double *__restrict__ part, unsigned *__restrict__ ticket, int vec) {
     if (sc[xb::BI_FLAG] != 0.0) return;
     const double al = sc[xb::BI_ALPHA];
     if (sc[xb::BI_SNORM2] <= sc[xb::BI_TAU2]) {
@@ -710,8 +711,8 @@ __global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__
     }
     const double om = sc[xb::BI_OMEGA];
     double a[2] = {0.0, 0.0};
-    auto f = [&](double &xi, double pi, double si, double ti, double hi) {
-        xi = fma(om, si, fma(al, pi, xi));
+    auto f = [&](double &xi, double pi, double si, double sxi, double ti, double hi) {
+        xi = fma(om, sxi, fma(al, pi, xi));
         const double ri = fma(-om, ti, si);
         a[0] = fma(ri, ri, a[0]);
         a[1] = fma(hi, ri, a[1]);
@@ -722,8 +723,9 @@ __global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__
         for (int64_t i = gtid(); i < n / 2; i += gstride()) {
             double2 xv = ld2(x, i), rv;
             const double2 pv = ld2(p, i), sv = ld2(s, i), tv = ld2(t, i), hv = ld2(rh, i);
-            rv.x = f(xv.x, pv.x, sv.x, tv.x, hv.x);
-            rv.y = f(xv.y, pv.y, sv.y, tv.y, hv.y);
+            const double2 zv = ld2(sx, i);
+            rv.x = f(xv.x, pv.x, sv.x, zv.x, tv.x, hv.x);
+            rv.y = f(xv.y, pv.y, sv.y, zv.y, tv.y, hv.y);
             st2(x, i, xv);
             st2(r, i, rv);
         }
@@ -731,7 +733,7 @@ __global__ void k_bi_xr(int64_t n, double *__restrict__ sc, double *__restrict__
     }
     for (int64_t i = done + gtid(); i < n; i += gstride()) {
         double xi = x[i];
-        r[i] = f(xi, p[i], s[i], t[i], rh[i]);
+        r[i] = f(xi, p[i], s[i], sx[i], t[i], rh[i]);
         x[i] = xi;
     }
     double tt[2];
@@ -982,9 +984,10 @@ int bi_omega(xb_plan *p, double *scal, int64_t n, const double *t, const double 
     return XB_OK;
 }
 int bi_xr_update(xb_plan *p, double *scal, int64_t n, double *x, const double *pv,
-                 const double *sv, const double *t, double *r, const double *rh, cudaStream_t s) {
-    const int vec = al16(x) & al16(pv) & al16(sv) & al16(t) & al16(r) & al16(rh);
-    k_bi_xr<<<rgrid(k_bi_xr, n), kVB, 0, s>>>(n, scal, x, pv, sv, t, r, rh, p->d_part,
+                 const double *sv, const double *sx, const double *t, double *r, const double *rh,
+                 cudaStream_t s) {
+    const int vec = al16(x) & al16(pv) & al16(sv) & al16(sx) & al16(t) & al16(r) & al16(rh);
+    k_bi_xr<<<rgrid(k_bi_xr, n), kVB, 0, s>>>(n, scal, x, pv, sv, sx, t, r, rh, p->d_part,
                                                 p->d_ticket, vec);
     XB_LAUNCHED("k_bi_xr");
     return XB_OK;

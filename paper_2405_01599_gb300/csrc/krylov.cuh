@@ -72,7 +72,8 @@ int bi_s_update(xb_plan *p, double *scal, int64_t n, const double *r, const doub
 int bi_omega(xb_plan *p, double *scal, int64_t n, const double *t, const double *sv,
              cudaStream_t s);
 int bi_xr_update(xb_plan *p, double *scal, int64_t n, double *x, const double *pv,
-                 const double *sv, const double *t, double *r, const double *rh, cudaStream_t s);
+                 const double *sv, const double *sx, const double *t, double *r, const double *rh,
+                 cudaStream_t s);
 int residual(xb_plan *p, const double *b, const double *x, double *r, cudaStream_t s);
 int cast_f64_to_f32_scaled(int64_t n, const double *a, const double *scale_dev, float *b,
                            cudaStream_t s);

@@ -341,6 +341,7 @@ void xb_options_default(xb_options *o) {
     o->timing = 0;
     o->policy = XB_POLICY_NONE;
     o->fault_check = 1;
+    o->precond = XB_PRECOND_NONE;
 }
 
 int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out) {
@@ -446,6 +447,7 @@ int xb_plan_destroy(xb_plan *p) {
     cudaFree(p->d_ticket);
     cudaFree(p->d_scal);
     cudaFree(p->d_work);
+    xb::ilu_free(p);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);

@@ -98,11 +98,16 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
     const int M = o.dafrt ? std::max(o.m, std::min(std::max(o.m_max, o.m), 512)) : o.m;
     int m = std::min(o.m, M);
     const int64_t ld = ld_of(n);
-    const size_t vbytes = (size_t)(M + 1) * ld * sizeof(double);
+    const bool prec = o.precond == XB_PRECOND_ILU0;
+    const size_t vbytes = (size_t)(M + 1 + (prec ? 2 : 0)) * ld * sizeof(double);
     XB_TRY(xb::ensure_work(p, vbytes + xb::gm_doubles(M) * sizeof(double) + 256));
     ac.mem = std::max(ac.mem, (double)(vbytes + xb::gm_doubles(M) * sizeof(double) + 256));
     double *V = static_cast<double *>(p->d_work);
-    xb::GmDev st = xb::gm_layout(V + (size_t)(M + 1) * ld, M);
+    // right preconditioning: tz = M^{-1} v_j before the SpMV; tu = V y before x += M^{-1} tu
+    double *tz = V + (size_t)(M + 1) * ld, *tu = tz + ld;
+    xb::GmDev st = xb::gm_layout(V + (size_t)(M + 1 + (prec ? 2 : 0)) * ld, M);
+    if (prec) XB_TRY(xb::ensure_ilu(p, s));
+    const double prec_b = prec ? xb::ilu_apply_bytes(p) : 0.0;
     const double spmv_b = xb::spmv_alg_bytes(p, false, 8);
 
     XB_TRY(xb::vnrm2(p, n, b, st.misc + xb::GM_BNORM, s));
@@ -167,8 +172,14 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
         int launched = 0;
         double stop = 0.0;
         for (int j = 0; j < m; j++) {
+            const double *src = V + (size_t)j * ld;
+            if (prec) {
+                XB_TRY(xb::ilu_apply(p, src, tz, s));
+                ac.bytes += prec_b;
+                src = tz;
+            }
             tm.begin();
-            XB_TRY(xb::spmv_launch_dalpha(p, o.variant, o.block, o.ipt, st.sc + j, V + (size_t)j * ld,
+            XB_TRY(xb::spmv_launch_dalpha(p, o.variant, o.block, o.ipt, st.sc + j, src,
                                           V + (size_t)(j + 1) * ld, s));
             tm.end();
             ac.bytes += spmv_b;
@@ -196,7 +207,13 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
             break;
         }
         if (stop == 1.0) claimed = true;
-        if (k > 0) {
+        if (k > 0 && prec) {
+            XB_TRY(xb::vfill(n, 0.0, tu, s));
+            XB_TRY(xb::gm_update<double, double>(p, st, n, V, ld, k, tu, s));
+            XB_TRY(xb::ilu_apply(p, tu, tz, s));
+            XB_TRY(xb::vaxpy(n, 1.0, tz, x, s));
+            ac.bytes += 8.0 * n * k + 24.0 * n + prec_b + 24.0 * n;
+        } else if (k > 0) {
             XB_TRY(xb::gm_update<double, double>(p, st, n, V, ld, k, x, s));
             ac.bytes += 8.0 * n * k + 16.0 * n;
         }
@@ -369,11 +386,17 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
                  cudaStream_t s, Acct &ac, SpmvTimer &tm, clk::time_point t0) {
     const int64_t n = p->n;
     const int64_t ld = ld_of(n);
-    XB_TRY(xb::ensure_work(p, 6 * (size_t)ld * sizeof(double) + 64 * sizeof(double)));
-    ac.mem = std::max(ac.mem, (double)(6 * (size_t)ld * sizeof(double) + 64 * sizeof(double)));
+    const bool prec = o.precond == XB_PRECOND_ILU0;
+    const size_t nv = prec ? 8 : 6;
+    XB_TRY(xb::ensure_work(p, nv * (size_t)ld * sizeof(double) + 64 * sizeof(double)));
+    ac.mem = std::max(ac.mem, (double)(nv * (size_t)ld * sizeof(double) + 64 * sizeof(double)));
     double *r = static_cast<double *>(p->d_work);
     double *rh = r + ld, *pv = rh + ld, *v = pv + ld, *sv = v + ld, *t = sv + ld;
-    double *sc = t + ld;
+    // right preconditioning: ph = M^{-1} p and sh = M^{-1} s feed the SpMVs and x
+    double *ph = prec ? t + ld : pv, *sh = prec ? t + 2 * ld : sv;
+    double *sc = t + (prec ? 3 : 1) * ld;
+    if (prec) XB_TRY(xb::ensure_ilu(p, s));
+    const double prec_b = prec ? xb::ilu_apply_bytes(p) : 0.0;
     const double spmv_b = xb::spmv_alg_bytes(p, false, 8);
 
     XB_TRY(xb::vnrm2(p, n, b, sc + xb::BI_N, s));
@@ -429,17 +452,19 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
         while (iters < o.maxiter) {
             iters++;
             XB_TRY(xb::bi_p_update(sc, n, r, pv, v, s));
+            if (prec) XB_TRY(xb::ilu_apply(p, pv, ph, s));
             tm.begin();
-            XB_TRY(xb::spmv_launch(p, o.variant, o.block, o.ipt, 1.0, pv, 0.0, v, s));
+            XB_TRY(xb::spmv_launch(p, o.variant, o.block, o.ipt, 1.0, ph, 0.0, v, s));
             tm.end();
             XB_TRY(xb::bi_sigma(p, sc, n, rh, v, s));
             XB_TRY(xb::bi_s_update(p, sc, n, r, v, sv, s));
+            if (prec) XB_TRY(xb::ilu_apply(p, sv, sh, s));
             tm.begin();
-            XB_TRY(xb::spmv_launch(p, o.variant, o.block, o.ipt, 1.0, sv, 0.0, t, s));
+            XB_TRY(xb::spmv_launch(p, o.variant, o.block, o.ipt, 1.0, sh, 0.0, t, s));
             tm.end();
             XB_TRY(xb::bi_omega(p, sc, n, t, sv, s));
-            XB_TRY(xb::bi_xr_update(p, sc, n, x, pv, sv, t, r, rh, s));
-            ac.bytes += 2 * spmv_b + 144.0 * n;
+            XB_TRY(xb::bi_xr_update(p, sc, n, x, ph, sv, sh, t, r, rh, s));
+            ac.bytes += 2 * spmv_b + 144.0 * n + (prec ? 2.0 * prec_b : 0.0);
             ac.spmv += 2;
             if (iters % check == 0 || iters >= o.maxiter) {
                 XB_TRY(peek(p, sc, xb::BI_N, s));
@@ -481,6 +506,10 @@ int check_args(xb_plan *p, const double *b, double *x, const xb_options &o) {
         return xb::set_error(XB_EINVAL, "solve: SpMV variant %d does not fit the storage", o.variant);
     if (o.ortho < XB_ORTHO_MGS || o.ortho > XB_ORTHO_AUTO)
         return xb::set_error(XB_EINVAL, "solve: unknown orthogonalisation %d", o.ortho);
+    if (o.precond != XB_PRECOND_NONE && o.precond != XB_PRECOND_ILU0)
+        return xb::set_error(XB_EINVAL, "solve: unknown preconditioner %d", o.precond);
+    if (o.precond == XB_PRECOND_ILU0 && (p->sym || o.precision != XB_PREC_FP64))
+        return xb::set_error(XB_EINVAL, "solve: ILU(0) needs general CRS and FP64 precision");
     return XB_OK;
 }
 
@@ -571,7 +600,8 @@ int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb
         inf.block_used = o.block > 0 ? o.block : p->block;
         inf.ipt_used = o.ipt > 0 ? o.ipt : p->ipt;
         inf.mem_bytes = ac.mem + spmv_meta_bytes(p, inf.variant_used, inf.block_used, inf.ipt_used) +
-                        (o.precision == XB_PREC_MIXED ? 4.0 * p->nnz : 0.0);
+                        (o.precision == XB_PREC_MIXED ? 4.0 * p->nnz : 0.0) +
+                        (o.precond == XB_PRECOND_ILU0 ? 8.0 * p->nnz + 12.0 * p->n : 0.0);
         if (st == XB_EFAULT)
             xb::set_error(XB_EFAULT, "fault convergence: implicit residual met tol, "
                                      "||b-Ax||/||b|| = %.3e", inf.res_true);
