@@ -88,8 +88,13 @@ struct IluData {
     int *d_dpos = nullptr;           // n
     int *d_lrows = nullptr, *d_urows = nullptr;  // n each, ordered by level
     std::vector<int> loff, uoff;     // level offsets (levels + 1)
+    // per level, the rows whose triangle part is longer than a warp can take
+    // well (they get a whole CTA each), listed after the level's other rows
+    std::vector<int> lcnt_short, ucnt_short;
     int *d_flag = nullptr;           // zero-pivot flag
-    double *d_tmp = nullptr;         // 2n scratch for the solvers
+    double *d_in = nullptr, *d_out = nullptr;  // fixed operands of the captured solve
+    cudaGraph_t graph = nullptr;     // both substitutions, every level, captured once
+    cudaGraphExec_t exec = nullptr;
 };
 
 }  // namespace xb

@@ -12,13 +12,19 @@
 // Each substitution is one launch per level; inside a level every row is
 // independent: a thread per row, with rows longer than 32 stored entries in
 // the triangle taken by the whole warp (lanes stride over the row, shuffle
-// reduction), so a power-law row does not serialise one thread.
+// reduction), and rows longer than kLongRow by a whole CTA, so a power-law row
+// does not serialise one thread or one warp.  The launch sequence of both
+// substitutions is captured once into a CUDA graph on fixed operand buffers
+// (a 3D stencil has 3N - 2 levels per triangle, so per-launch overhead would
+// otherwise dominate).
 #include "common.cuh"
 
 #include <algorithm>
 #include <cmath>
 
 namespace {
+
+constexpr int kLongRow = 512;  // triangle entries above which a row gets a CTA
 
 __device__ __forceinline__ int find_in_row(const int *__restrict__ ci, int lo, int hi, int j) {
     // search [lo, hi) of a sorted column list for j
@@ -105,16 +111,66 @@ __global__ void __launch_bounds__(256) k_ilu_level(int cnt, const int *__restric
     }
 }
 
-// Rows grouped by level (counting sort), ascending row order inside a level.
-void group_levels(const std::vector<int> &lev, int nlev, std::vector<int> &rows,
-                  std::vector<int> &off) {
+// One level's long rows, a CTA per row (block reduction in a fixed order).
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_ilu_level_long(const int *__restrict__ rows,
+                                                        const int *__restrict__ rp,
+                                                        const int *__restrict__ ci,
+                                                        const int *__restrict__ dpos,
+                                                        const double *__restrict__ lu,
+                                                        const double *__restrict__ r,
+                                                        double *__restrict__ z) {
+    __shared__ double sh[8];
+    const int i = rows[blockIdx.x];
+    const int d = dpos[i];
+    const int ka = FWD ? rp[i] : d + 1, kb = FWD ? d : rp[i + 1];
+    double t = 0.0;
+    for (int k = ka + threadIdx.x; k < kb; k += blockDim.x)
+        t = fma(__ldg(lu + k), z[__ldg(ci + k)], t);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w];
+        if (FWD) z[i] = r[i] - s;
+        else z[i] = (z[i] - s) / lu[d];
+    }
+}
+
+// Rows grouped by level (counting sort), ascending row order inside a level,
+// the level's long rows (len[i] > kLongRow) moved to its end; nshort[l] = the
+// number of the others.
+void group_levels(const std::vector<int> &lev, const std::vector<int> &len, int nlev,
+                  std::vector<int> &rows, std::vector<int> &off, std::vector<int> &nshort) {
     const int n = (int)lev.size();
     off.assign(nlev + 1, 0);
     for (int i = 0; i < n; i++) off[lev[i] + 1]++;
     for (int l = 0; l < nlev; l++) off[l + 1] += off[l];
+    nshort.assign(nlev, 0);
+    for (int i = 0; i < n; i++)
+        if (len[i] <= kLongRow) nshort[lev[i]]++;
     rows.resize(n);
-    std::vector<int> pos(off.begin(), off.end() - 1);
-    for (int i = 0; i < n; i++) rows[pos[lev[i]]++] = i;
+    std::vector<int> ps(off.begin(), off.end() - 1), pl(nlev);
+    for (int l = 0; l < nlev; l++) pl[l] = off[l] + nshort[l];
+    for (int i = 0; i < n; i++) rows[len[i] <= kLongRow ? ps[lev[i]]++ : pl[lev[i]]++] = i;
+}
+
+// Launch one substitution's levels on stream s (also used inside the capture).
+template <bool FWD>
+void launch_levels(const xb_plan *p, const int *d_rows, const std::vector<int> &off,
+                   const std::vector<int> &nshort, const double *r, double *z, cudaStream_t s) {
+    const xb::IluData &u = p->ilu;
+    const int nl = (int)off.size() - 1;
+    for (int l = 0; l < nl; l++) {
+        const int cs = nshort[l], cl = off[l + 1] - off[l] - cs;
+        if (cs > 0)
+            k_ilu_level<FWD><<<(cs + 255) / 256, 256, 0, s>>>(cs, d_rows + off[l], p->rowptr,
+                                                             p->col, u.d_dpos, u.d_lu, r, z);
+        if (cl > 0)
+            k_ilu_level_long<FWD><<<cl, 256, 0, s>>>(d_rows + off[l] + cs, p->rowptr, p->col,
+                                                     u.d_dpos, u.d_lu, r, z);
+    }
 }
 
 }  // namespace
@@ -128,7 +184,10 @@ void ilu_free(xb_plan *p) {
     cudaFree(u.d_lrows);
     cudaFree(u.d_urows);
     cudaFree(u.d_flag);
-    cudaFree(u.d_tmp);
+    cudaFree(u.d_in);
+    cudaFree(u.d_out);
+    if (u.exec) cudaGraphExecDestroy(u.exec);
+    if (u.graph) cudaGraphDestroy(u.graph);
     u = IluData();
 }
 
@@ -160,9 +219,14 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
         ulev[i] = m + 1;
         nu = std::max(nu, ulev[i] + 1);
     }
+    std::vector<int> llen(n), ulen(n);
+    for (int i = 0; i < n; i++) {
+        llen[i] = dpos[i] - rp[i];
+        ulen[i] = rp[i + 1] - dpos[i] - 1;
+    }
     std::vector<int> lrows, urows;
-    group_levels(lev, nl, lrows, u.loff);
-    group_levels(ulev, nu, urows, u.uoff);
+    group_levels(lev, llen, nl, lrows, u.loff, u.lcnt_short);
+    group_levels(ulev, ulen, nu, urows, u.uoff, u.ucnt_short);
     auto up = [&](int **d, const std::vector<int> &h) -> int {
         XB_CUDA(cudaMalloc(d, std::max<size_t>(1, h.size()) * 4));
         if (!h.empty())
@@ -174,7 +238,8 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
     XB_TRY(up(&u.d_urows, urows));
     XB_CUDA(cudaMalloc(&u.d_lu, std::max<size_t>(1, (size_t)nnz) * sizeof(double)));
     XB_CUDA(cudaMalloc(&u.d_flag, sizeof(int)));
-    XB_CUDA(cudaMalloc(&u.d_tmp, std::max<size_t>(1, 2 * (size_t)n) * sizeof(double)));
+    XB_CUDA(cudaMalloc(&u.d_in, std::max<size_t>(1, (size_t)n) * sizeof(double)));
+    XB_CUDA(cudaMalloc(&u.d_out, std::max<size_t>(1, (size_t)n) * sizeof(double)));
     XB_CUDA(cudaMemsetAsync(u.d_flag, 0, sizeof(int), s));
     if (nnz > 0)
         XB_CUDA(cudaMemcpyAsync(u.d_lu, p->val, (size_t)nnz * sizeof(double),
@@ -193,24 +258,32 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
     u.built = true;
     u.status = flag ? XB_EBREAKDOWN : XB_OK;
     if (flag) return set_error(XB_EBREAKDOWN, "ILU(0): zero pivot");
+    // capture both substitutions (d_in -> d_out) on a private stream
+    cudaStream_t cs = nullptr;
+    XB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        launch_levels<true>(p, u.d_lrows, u.loff, u.lcnt_short, u.d_in, u.d_out, cs);
+        launch_levels<false>(p, u.d_urows, u.uoff, u.ucnt_short, u.d_out, u.d_out, cs);
+        e = cudaStreamEndCapture(cs, &u.graph);
+    }
+    cudaStreamDestroy(cs);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&u.exec, u.graph, 0);
+    if (e != cudaSuccess) {
+        u.built = false;
+        return cuda_error(e, "ILU(0): capture of the substitutions");
+    }
     return XB_OK;
 }
 
 int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s) {
     IluData &u = p->ilu;
     XB_TRY(ensure_ilu(p, s));
-    const int nl = (int)u.loff.size() - 1, nu = (int)u.uoff.size() - 1;
-    for (int l = 0; l < nl; l++) {
-        const int cnt = u.loff[l + 1] - u.loff[l];
-        k_ilu_level<true><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, u.d_lrows + u.loff[l], p->rowptr,
-                                                           p->col, u.d_dpos, u.d_lu, r, z);
-    }
-    for (int l = 0; l < nu; l++) {
-        const int cnt = u.uoff[l + 1] - u.uoff[l];
-        k_ilu_level<false><<<(cnt + 255) / 256, 256, 0, s>>>(cnt, u.d_urows + u.uoff[l], p->rowptr,
-                                                            p->col, u.d_dpos, u.d_lu, z, z);
-    }
-    XB_LAUNCHED("k_ilu_level");
+    if (p->n == 0) return XB_OK;
+    const size_t bytes = (size_t)p->n * sizeof(double);
+    XB_CUDA(cudaMemcpyAsync(u.d_in, r, bytes, cudaMemcpyDeviceToDevice, s));
+    XB_CUDA(cudaGraphLaunch(u.exec, s));
+    XB_CUDA(cudaMemcpyAsync(z, u.d_out, bytes, cudaMemcpyDeviceToDevice, s));
     return XB_OK;
 }
 
@@ -219,7 +292,8 @@ double ilu_apply_bytes(const xb_plan *p) {
     // twice, r read, z written by the forward pass, read and written by the
     // backward pass, and each row's level slot twice
     const double n = p->n, nnz = p->nnz;
-    return 12.0 * nnz + 2.0 * 4.0 * (n + 1) + 2.0 * 4.0 * n + 8.0 * n * 4.0 + 2.0 * 4.0 * n;
+    return 12.0 * nnz + 2.0 * 4.0 * (n + 1) + 2.0 * 4.0 * n + 8.0 * n * 4.0 + 2.0 * 4.0 * n +
+           32.0 * n;  // + copies into and out of the captured solve's buffers
 }
 
 }  // namespace xb
