@@ -88,9 +88,18 @@ struct IluData {
     int *d_dpos = nullptr;           // n
     int *d_lrows = nullptr, *d_urows = nullptr;  // n each, ordered by level
     std::vector<int> loff, uoff;     // level offsets (levels + 1)
-    // per level, the rows whose triangle part is longer than a warp can take
-    // well (they get a whole CTA each), listed after the level's other rows
-    std::vector<int> lcnt_short, ucnt_short;
+    // Inside a level rows are ordered by tier: short rows (<= 8 entries in the
+    // triangle) first, stored again level by level in ELL form (entry t of
+    // slot s at eoff[l] + t * count + s, padded with zero values) so a thread
+    // loads its row with no dependent index loads; then rows of up to 512
+    // entries (thread or warp per row, CSR); then longer rows (CTA per row).
+    std::vector<int> ln0, ln1, un0, un1;  // per level: ELL-tier and CSR-tier counts
+    std::vector<int> lw, uw;              // per level: ELL width
+    std::vector<long long> leoff, ueoff;  // per level: ELL base offset
+    int *d_lecol = nullptr, *d_uecol = nullptr;
+    double *d_leval = nullptr, *d_ueval = nullptr;
+    int *d_lesrc = nullptr, *d_uesrc = nullptr;  // factor position of each ELL entry (-1: pad)
+    double *d_udiag = nullptr;            // u_ii in backward level order
     int *d_flag = nullptr;           // zero-pivot flag
     double *d_in = nullptr, *d_out = nullptr;  // fixed operands of the captured solve
     cudaGraph_t graph = nullptr;     // both substitutions, every level, captured once

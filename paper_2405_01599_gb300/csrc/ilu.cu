@@ -25,6 +25,7 @@
 namespace {
 
 constexpr int kLongRow = 512;  // triangle entries above which a row gets a CTA
+constexpr int kEllMax = 8;     // triangle entries up to which a row is stored as ELL
 
 __device__ __forceinline__ int find_in_row(const int *__restrict__ ci, int lo, int hi, int j) {
     // search [lo, hi) of a sorted column list for j
@@ -138,37 +139,124 @@ __global__ void __launch_bounds__(256) k_ilu_level_long(const int *__restrict__ 
     }
 }
 
-// Rows grouped by level (counting sort), ascending row order inside a level,
-// the level's long rows (len[i] > kLongRow) moved to its end; nshort[l] = the
-// number of the others.
+// One level's short rows in ELL form, a thread per row: the row index, its
+// entries and (backward) its pivot are independent loads, then the gathers.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_ilu_ell(int cnt, int width, const int *__restrict__ rows,
+                                                 const int *__restrict__ ecol,
+                                                 const double *__restrict__ eval,
+                                                 const double *__restrict__ diag,
+                                                 const double *__restrict__ r,
+                                                 double *__restrict__ z) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= cnt) return;
+    const int i = __ldg(rows + slot);
+    double s = 0.0;
+    for (int t = 0; t < width; t++) {
+        const long long e = (long long)t * cnt + slot;
+        s = fma(__ldg(eval + e), z[__ldg(ecol + e)], s);
+    }
+    if (FWD) z[i] = r[i] - s;
+    else z[i] = (z[i] - s) / __ldg(diag + slot);
+}
+
+// ELL values from the factors (padding entries stay 0), and the pivots in
+// backward level order.
+__global__ void k_ell_fill(long long cnt, const int *__restrict__ src,
+                           const double *__restrict__ lu, double *__restrict__ val) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < cnt) val[e] = src[e] >= 0 ? lu[src[e]] : 0.0;
+}
+__global__ void k_diag_fill(int n, const int *__restrict__ rows, const int *__restrict__ dpos,
+                            const double *__restrict__ lu, double *__restrict__ diag) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) diag[s] = lu[dpos[rows[s]]];
+}
+
+// Rows grouped by level (counting sort), ascending row order inside each tier
+// of a level: ELL rows (len <= kEllMax), CSR rows (<= kLongRow), CTA rows;
+// n0[l], n1[l] = the first two tiers' counts.
+int tier_of(int len) { return len <= kEllMax ? 0 : (len <= kLongRow ? 1 : 2); }
 void group_levels(const std::vector<int> &lev, const std::vector<int> &len, int nlev,
-                  std::vector<int> &rows, std::vector<int> &off, std::vector<int> &nshort) {
+                  std::vector<int> &rows, std::vector<int> &off, std::vector<int> &n0,
+                  std::vector<int> &n1) {
     const int n = (int)lev.size();
     off.assign(nlev + 1, 0);
     for (int i = 0; i < n; i++) off[lev[i] + 1]++;
     for (int l = 0; l < nlev; l++) off[l + 1] += off[l];
-    nshort.assign(nlev, 0);
-    for (int i = 0; i < n; i++)
-        if (len[i] <= kLongRow) nshort[lev[i]]++;
+    n0.assign(nlev, 0);
+    n1.assign(nlev, 0);
+    for (int i = 0; i < n; i++) {
+        const int t = tier_of(len[i]);
+        if (t == 0) n0[lev[i]]++;
+        else if (t == 1) n1[lev[i]]++;
+    }
     rows.resize(n);
-    std::vector<int> ps(off.begin(), off.end() - 1), pl(nlev);
-    for (int l = 0; l < nlev; l++) pl[l] = off[l] + nshort[l];
-    for (int i = 0; i < n; i++) rows[len[i] <= kLongRow ? ps[lev[i]]++ : pl[lev[i]]++] = i;
+    std::vector<int> p0(nlev), p1(nlev), p2(nlev);
+    for (int l = 0; l < nlev; l++) {
+        p0[l] = off[l];
+        p1[l] = off[l] + n0[l];
+        p2[l] = off[l] + n0[l] + n1[l];
+    }
+    for (int i = 0; i < n; i++) {
+        const int t = tier_of(len[i]), l = lev[i];
+        rows[t == 0 ? p0[l]++ : (t == 1 ? p1[l]++ : p2[l]++)] = i;
+    }
+}
+
+// ELL layout of each level's first tier: width, base offsets, columns and the
+// factor position of every entry (padding: the row's first entry's column,
+// whose value is final before this level, with position -1 = value 0).
+// Entries of row i are positions [beg(i), end(i)) of the CRS arrays.
+template <typename Beg, typename End>
+void build_ell(const std::vector<int> &rows, const std::vector<int> &off,
+               const std::vector<int> &n0, const std::vector<int> &ci, Beg beg, End end,
+               std::vector<int> &w, std::vector<long long> &eoff, std::vector<int> &ecol,
+               std::vector<int> &esrc) {
+    const int nl = (int)n0.size();
+    w.assign(nl, 0);
+    eoff.assign(nl + 1, 0);
+    for (int l = 0; l < nl; l++) {
+        for (int q = 0; q < n0[l]; q++) {
+            const int i = rows[off[l] + q];
+            w[l] = std::max(w[l], end(i) - beg(i));
+        }
+        eoff[l + 1] = eoff[l] + (long long)w[l] * n0[l];
+    }
+    ecol.assign((size_t)eoff[nl], 0);
+    esrc.assign((size_t)eoff[nl], -1);
+    for (int l = 0; l < nl; l++)
+        for (int q = 0; q < n0[l]; q++) {
+            const int i = rows[off[l] + q];
+            const int b = beg(i), len = end(i) - b;
+            for (int t = 0; t < w[l]; t++) {
+                const long long e = eoff[l] + (long long)t * n0[l] + q;
+                ecol[e] = t < len ? ci[b + t] : ci[b];
+                esrc[e] = t < len ? b + t : -1;
+            }
+        }
 }
 
 // Launch one substitution's levels on stream s (also used inside the capture).
 template <bool FWD>
 void launch_levels(const xb_plan *p, const int *d_rows, const std::vector<int> &off,
-                   const std::vector<int> &nshort, const double *r, double *z, cudaStream_t s) {
+                   const std::vector<int> &n0, const std::vector<int> &n1,
+                   const std::vector<int> &w, const std::vector<long long> &eoff,
+                   const int *ecol, const double *eval, const double *diag, const double *r,
+                   double *z, cudaStream_t s) {
     const xb::IluData &u = p->ilu;
     const int nl = (int)off.size() - 1;
     for (int l = 0; l < nl; l++) {
-        const int cs = nshort[l], cl = off[l + 1] - off[l] - cs;
-        if (cs > 0)
-            k_ilu_level<FWD><<<(cs + 255) / 256, 256, 0, s>>>(cs, d_rows + off[l], p->rowptr,
+        const int c0 = n0[l], c1 = n1[l], c2 = off[l + 1] - off[l] - c0 - c1;
+        if (c0 > 0)
+            k_ilu_ell<FWD><<<(c0 + 255) / 256, 256, 0, s>>>(c0, w[l], d_rows + off[l],
+                                                           ecol + eoff[l], eval + eoff[l],
+                                                           diag + off[l], r, z);
+        if (c1 > 0)
+            k_ilu_level<FWD><<<(c1 + 255) / 256, 256, 0, s>>>(c1, d_rows + off[l] + c0, p->rowptr,
                                                              p->col, u.d_dpos, u.d_lu, r, z);
-        if (cl > 0)
-            k_ilu_level_long<FWD><<<cl, 256, 0, s>>>(d_rows + off[l] + cs, p->rowptr, p->col,
+        if (c2 > 0)
+            k_ilu_level_long<FWD><<<c2, 256, 0, s>>>(d_rows + off[l] + c0 + c1, p->rowptr, p->col,
                                                      u.d_dpos, u.d_lu, r, z);
     }
 }
@@ -186,6 +274,13 @@ void ilu_free(xb_plan *p) {
     cudaFree(u.d_flag);
     cudaFree(u.d_in);
     cudaFree(u.d_out);
+    cudaFree(u.d_lecol);
+    cudaFree(u.d_uecol);
+    cudaFree(u.d_leval);
+    cudaFree(u.d_ueval);
+    cudaFree(u.d_lesrc);
+    cudaFree(u.d_uesrc);
+    cudaFree(u.d_udiag);
     if (u.exec) cudaGraphExecDestroy(u.exec);
     if (u.graph) cudaGraphDestroy(u.graph);
     u = IluData();
@@ -225,8 +320,13 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
         ulen[i] = rp[i + 1] - dpos[i] - 1;
     }
     std::vector<int> lrows, urows;
-    group_levels(lev, llen, nl, lrows, u.loff, u.lcnt_short);
-    group_levels(ulev, ulen, nu, urows, u.uoff, u.ucnt_short);
+    group_levels(lev, llen, nl, lrows, u.loff, u.ln0, u.ln1);
+    group_levels(ulev, ulen, nu, urows, u.uoff, u.un0, u.un1);
+    std::vector<int> lecol, lesrc, uecol, uesrc;
+    build_ell(lrows, u.loff, u.ln0, ci, [&](int i) { return rp[i]; },
+              [&](int i) { return dpos[i]; }, u.lw, u.leoff, lecol, lesrc);
+    build_ell(urows, u.uoff, u.un0, ci, [&](int i) { return dpos[i] + 1; },
+              [&](int i) { return rp[i + 1]; }, u.uw, u.ueoff, uecol, uesrc);
     auto up = [&](int **d, const std::vector<int> &h) -> int {
         XB_CUDA(cudaMalloc(d, std::max<size_t>(1, h.size()) * 4));
         if (!h.empty())
@@ -236,6 +336,13 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
     XB_TRY(up(&u.d_dpos, dpos));
     XB_TRY(up(&u.d_lrows, lrows));
     XB_TRY(up(&u.d_urows, urows));
+    XB_TRY(up(&u.d_lecol, lecol));
+    XB_TRY(up(&u.d_lesrc, lesrc));
+    XB_TRY(up(&u.d_uecol, uecol));
+    XB_TRY(up(&u.d_uesrc, uesrc));
+    XB_CUDA(cudaMalloc(&u.d_leval, std::max<size_t>(1, lecol.size()) * sizeof(double)));
+    XB_CUDA(cudaMalloc(&u.d_ueval, std::max<size_t>(1, uecol.size()) * sizeof(double)));
+    XB_CUDA(cudaMalloc(&u.d_udiag, std::max<size_t>(1, (size_t)n) * sizeof(double)));
     XB_CUDA(cudaMalloc(&u.d_lu, std::max<size_t>(1, (size_t)nnz) * sizeof(double)));
     XB_CUDA(cudaMalloc(&u.d_flag, sizeof(int)));
     XB_CUDA(cudaMalloc(&u.d_in, std::max<size_t>(1, (size_t)n) * sizeof(double)));
@@ -252,6 +359,15 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
             cnt, u.d_lrows + u.loff[l], p->rowptr, p->col, u.d_dpos, u.d_lu, u.d_flag);
     }
     XB_LAUNCHED("k_ilu_factor");
+    if (!lecol.empty())
+        k_ell_fill<<<(unsigned)((lecol.size() + 255) / 256), 256, 0, s>>>(
+            (long long)lecol.size(), u.d_lesrc, u.d_lu, u.d_leval);
+    if (!uecol.empty())
+        k_ell_fill<<<(unsigned)((uecol.size() + 255) / 256), 256, 0, s>>>(
+            (long long)uecol.size(), u.d_uesrc, u.d_lu, u.d_ueval);
+    if (n > 0)
+        k_diag_fill<<<(n + 255) / 256, 256, 0, s>>>(n, u.d_urows, u.d_dpos, u.d_lu, u.d_udiag);
+    XB_LAUNCHED("k_ell_fill");
     int flag = 0;
     XB_CUDA(cudaMemcpyAsync(&flag, u.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     XB_CUDA(cudaStreamSynchronize(s));
@@ -263,8 +379,10 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
     XB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        launch_levels<true>(p, u.d_lrows, u.loff, u.lcnt_short, u.d_in, u.d_out, cs);
-        launch_levels<false>(p, u.d_urows, u.uoff, u.ucnt_short, u.d_out, u.d_out, cs);
+        launch_levels<true>(p, u.d_lrows, u.loff, u.ln0, u.ln1, u.lw, u.leoff, u.d_lecol,
+                            u.d_leval, u.d_udiag, u.d_in, u.d_out, cs);
+        launch_levels<false>(p, u.d_urows, u.uoff, u.un0, u.un1, u.uw, u.ueoff, u.d_uecol,
+                             u.d_ueval, u.d_udiag, u.d_out, u.d_out, cs);
         e = cudaStreamEndCapture(cs, &u.graph);
     }
     cudaStreamDestroy(cs);
