@@ -59,6 +59,8 @@ def parse():
                     help="profile-only: run this many GMRES(30) Arnoldi steps instead of SpMVs")
     ap.add_argument("--ortho", default="mgs", choices=["mgs", "cgs", "dgks", "bcgs"],
                     help="profile-only GMRES: orthogonalisation")
+    ap.add_argument("--ilu", action="store_true",
+                    help="profile-only GMRES: ILU(0) right preconditioning")
     ap.add_argument("--mixed", action="store_true",
                     help="profile-only GMRES: FP32 inner solve in FP64 refinement (one outer "
                          "step of --gmres-steps inner steps)")
@@ -270,6 +272,9 @@ def main():
         t0 = time.perf_counter()
         extra = dict(precision=xb.PREC_MIXED, tol_inner=1e-30, maxiter_inner=args.gmres_steps,
                      max_outer=1) if args.mixed else {}
+        if args.ilu:
+            plan.ilu0_setup()
+            extra["precond"] = xb.PRECOND_ILU0
         info = plan.gmres(bvec, xg, m=30, tol=1e-30, maxiter=args.gmres_steps, check_every=10,
                           ortho=["mgs", "cgs", "dgks", "bcgs"].index(args.ortho), **extra)
         el = time.perf_counter() - t0
