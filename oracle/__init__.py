@@ -61,6 +61,10 @@ def lib():
         L.orc_gs_qr.restype = vi
         L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
                                 vi, vd, vi, vi, vi, vi, vp, _i32p, _f64p, vp, vp, vi]
+        L.orc_sym_eig.argtypes = [vi, _f64p, _f64p, _f64p]
+        L.orc_lanczos.argtypes = [vi, vi, _i32p, _i32p, _f64p, vi, vi, vd, vi, _f64p, _f64p, vp,
+                                  _f64p, _i32p]
+        L.orc_lanczos.restype = vi
         L.orc_ilu0.argtypes = [vi, _i32p, _i32p, _f64p, _f64p]
         L.orc_ilu0.restype = vi
         L.orc_ilu0_solve.argtypes = [vi, _i32p, _i32p, _f64p, _f64p, _f64p]
@@ -156,6 +160,33 @@ def gs_qr(X, ortho=MGS, bl=4):
     R = np.zeros(k * k)
     d = lib().orc_gs_qr(n, k, Xc, int(ortho), int(bl), Q, R)
     return Q.reshape(k, n).T, R.reshape(k, k).T, d
+
+
+def sym_eig(M):
+    """Jacobi eigen-decomposition of a symmetric matrix: (eigenvalues largest
+    first, eigenvectors as columns)."""
+    M = np.array(M, dtype=np.float64, copy=True)
+    m = M.shape[0]
+    w = np.zeros(m)
+    S = np.zeros(m * m)
+    lib().orc_sym_eig(m, np.ascontiguousarray(M).reshape(-1), w, S)
+    return w, S.reshape(m, m)
+
+
+def lanczos(A, nev=10, m=40, tol=1e-10, maxrestart=1000, v0=None, vectors=True):
+    """The nev largest eigenvalues of a symmetric A by thick-restart Lanczos;
+    returns (evals, evecs (n x nev) or None, info)."""
+    n, rp, ci, va = _csr(A)
+    v0 = np.ones(n) if v0 is None else np.ascontiguousarray(v0, np.float64)
+    ev = np.zeros(nev)
+    res = np.zeros(nev)
+    vec = np.zeros(n * nev) if vectors else None
+    ii = np.zeros(2, np.int32)
+    st = lib().orc_lanczos(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va, int(nev),
+                           int(m), float(tol), int(maxrestart), v0, ev,
+                           vec.ctypes.data if vectors else None, res, ii)
+    return ev, (vec.reshape(nev, n).T if vectors else None), dict(
+        status=st, steps=int(ii[0]), restarts=int(ii[1]), resid=res)
 
 
 def ilu0(A):

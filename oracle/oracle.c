@@ -675,6 +675,158 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
 }
 
 /* ------------------------------------------------------------------------ */
+/* Restarted Lanczos eigensolver for symmetric matrices (Sec. 2.2, 4.3:      */
+/* OpenATI_EIGENSOLVE, restarted Lanczos), thick restart.                     */
+/* ------------------------------------------------------------------------ */
+
+/* Eigen-decomposition of the symmetric m x m matrix A (row-major, destroyed)
+ * by cyclic Jacobi rotations until the off-diagonal mass is below 1e-30 of
+ * the total: A = S diag(w) S^T, S row-major (column c = eigenvector c).
+ * Eigenpairs are returned sorted by eigenvalue, largest first. */
+void orc_sym_eig(int m, double *A, double *w, double *S)
+{
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++) S[i * m + j] = (i == j) ? 1.0 : 0.0;
+    double tot = 0.0;
+    for (int i = 0; i < m * m; i++) tot += A[i] * A[i];
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) off += 2.0 * A[p * m + q] * A[p * m + q];
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                /* rotation angle zeroing A[p][q]: tan(2t) = 2 apq / (aqq - app) */
+                double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                for (int k = 0; k < m; k++) { /* A = A G (columns p, q) */
+                    double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = c * akp - sn * akq;
+                    A[k * m + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < m; k++) { /* A = G^T A (rows p, q) */
+                    double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = c * apk - sn * aqk;
+                    A[q * m + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < m; k++) { /* S = S G */
+                    double skp = S[k * m + p], skq = S[k * m + q];
+                    S[k * m + p] = c * skp - sn * skq;
+                    S[k * m + q] = sn * skp + c * skq;
+                }
+            }
+    }
+    for (int i = 0; i < m; i++) w[i] = A[i * m + i];
+    /* sort descending (selection sort, columns of S follow) */
+    for (int i = 0; i < m; i++) {
+        int b = i;
+        for (int j = i + 1; j < m; j++) if (w[j] > w[b]) b = j;
+        if (b != i) {
+            double t = w[i]; w[i] = w[b]; w[b] = t;
+            for (int k = 0; k < m; k++) {
+                double u = S[k * m + i]; S[k * m + i] = S[k * m + b]; S[k * m + b] = u;
+            }
+        }
+    }
+}
+
+/*
+ * The nev largest eigenvalues of a symmetric A (general CRS holding both
+ * triangles, or upper storage with kind = 1) by restarted Lanczos with full
+ * re-orthogonalisation (DGKS) and thick restart (Krylov-Schur form):
+ *   - a cycle extends the orthonormal basis v_0..v_m by Lanczos steps
+ *     w = A v_j, orthogonalised against every basis vector (the coefficients
+ *     fill column j of the projected matrix T = V^T A V), v_{j+1} = w/||w||;
+ *   - T (m x m, symmetrised) = S diag(theta) S^T; the residual of Ritz pair i
+ *     is |beta_m S[m-1][i]| with beta_m = ||w|| of the last step;
+ *   - if the nev largest Ritz values have residual <= tol |theta_i| the
+ *     solve ends (the Ritz vectors V S[:, i] are the eigenvectors);
+ *   - else the k = nev + (m - nev)/2 leading Ritz vectors are kept as the new
+ *     v_0..v_{k-1}, v_m becomes v_k, and T restarts as diag(theta_0..k-1)
+ *     with row / column k holding beta_m S[m-1][i] (the thick restart).
+ * v0: starting vector (n).  evals: nev values (largest first); evecs (may be
+ * NULL): n x nev column-major; resid: nev Ritz residual norms.
+ * iinfo: [0] Lanczos steps (SpMVs), [1] restarts.  Returns 0, -4 (restart
+ * limit) or -5 (a zero vector: Krylov space exhausted before m steps).
+ */
+int orc_lanczos(int n, int kind, const int *rp, const int *ci, const double *va, int nev,
+                int m, double tol, int maxrestart, const double *v0, double *evals,
+                double *evecs, double *resid, int *iinfo)
+{
+    if (nev < 1 || m <= nev || m > n) return ORC_EBREAKDOWN;
+    double *V = (double *)calloc((size_t)(m + 1) * n, sizeof(double));
+    double *T = (double *)calloc((size_t)(m + 1) * (m + 1), sizeof(double)); /* T[i*(m+1)+j] */
+    double *A = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double *S = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double *th = (double *)malloc(sizeof(double) * (size_t)m);
+    double *h = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *Y = (double *)malloc(sizeof(double) * (size_t)m * n);
+    double nb = nrm2(n, v0);
+    for (int q = 0; q < n; q++) V[q] = v0[q] / nb;
+    int k = 0, steps = 0, status = ORC_ENOCONV, restarts = 0;
+    double beta = 0.0;
+    for (;;) {
+        for (int j = k; j < m; j++) {
+            double *w = V + (size_t)(j + 1) * n;
+            matvec(kind, n, rp, ci, va, V + (size_t)j * n, w);
+            steps++;
+            orth(ORC_DGKS, 4, n, j, V, w, h);
+            for (int i = 0; i <= j; i++) T[i * (m + 1) + j] = h[i];
+            beta = nrm2(n, w);
+            T[(j + 1) * (m + 1) + j] = beta;
+            if (beta == 0.0) { status = ORC_EBREAKDOWN; goto done; }
+            for (int q = 0; q < n; q++) w[q] /= beta;
+        }
+        /* symmetrised projected matrix and its eigenpairs */
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++)
+                A[i * m + j] = 0.5 * (T[i * (m + 1) + j] + T[j * (m + 1) + i]);
+        orc_sym_eig(m, A, th, S);
+        int conv = 1;
+        for (int i = 0; i < nev; i++) {
+            resid[i] = fabs(beta * S[(m - 1) * m + i]);
+            evals[i] = th[i];
+            if (resid[i] > tol * fabs(th[i])) conv = 0;
+        }
+        if (conv || restarts >= maxrestart) {
+            status = conv ? ORC_OK : ORC_ENOCONV;
+            if (evecs)
+                for (int i = 0; i < nev; i++)
+                    for (int q = 0; q < n; q++) {
+                        double sum = 0.0;
+                        for (int j = 0; j < m; j++) sum += V[(size_t)j * n + q] * S[j * m + i];
+                        evecs[(size_t)i * n + q] = sum;
+                    }
+            break;
+        }
+        /* thick restart with the k leading Ritz vectors */
+        k = nev + (m - nev) / 2;
+        for (int i = 0; i < k; i++)
+            for (int q = 0; q < n; q++) {
+                double sum = 0.0;
+                for (int j = 0; j < m; j++) sum += V[(size_t)j * n + q] * S[j * m + i];
+                Y[(size_t)i * n + q] = sum;
+            }
+        memcpy(V, Y, sizeof(double) * (size_t)k * n);
+        memcpy(V + (size_t)k * n, V + (size_t)m * n, sizeof(double) * (size_t)n);
+        for (int i = 0; i < (m + 1) * (m + 1); i++) T[i] = 0.0;
+        for (int i = 0; i < k; i++) {
+            T[i * (m + 1) + i] = th[i];
+            T[k * (m + 1) + i] = beta * S[(m - 1) * m + i];
+        }
+        restarts++;
+    }
+done:
+    iinfo[0] = steps;
+    iinfo[1] = restarts;
+    free(V); free(T); free(A); free(S); free(th); free(h); free(Y);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FP32-inside-FP64 iterative refinement with GMRES(m) as the inner solver.   */
 /* The paper's accuracy policy deliberately avoids refinement (Sec. 3.3.1);  */
 /* this is the library's precision extension, written as the textbook        */
