@@ -297,6 +297,23 @@ int xb_mgs(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, dou
 int xb_orth(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, double *w,
             double *h, int32_t ortho, void *stream);
 
+/* ---- restarted Lanczos eigensolver (OpenATI_EIGENSOLVE, Sec. 2.2 / 4.3) ---
+ * The nev largest eigenvalues of a symmetric A (general storage holding both
+ * triangles, or sym_upper) by thick-restart Lanczos with full DGKS
+ * re-orthogonalisation: cycles of m basis vectors (nev < m <= min(n, 512)),
+ * restarts keeping nev + (m - nev)/2 Ritz vectors, until every wanted Ritz
+ * pair has residual ||A y - theta y|| <= tol |theta| or maxrestart restarts.
+ * The plan's SpMV choice is used.  v0: DEVICE start vector (n), or NULL for a
+ * fixed pseudo-random one.  evals, resid: HOST arrays (nev), largest first;
+ * evecs: DEVICE n x nev column-major (unit Ritz vectors) or NULL; counts:
+ * HOST int[2] = {Lanczos steps (SpMVs), restarts} or NULL.  Returns XB_OK,
+ * XB_ENOCONV (restart limit; evals hold the current Ritz values) or
+ * XB_EBREAKDOWN (the start vector spans an invariant subspace of dimension
+ * < m).  Synchronises the stream. */
+int xb_lanczos(xb_plan *plan, int32_t nev, int32_t m, double tol, int32_t maxrestart,
+               const double *v0, double *evals, double *evecs, double *resid, int32_t *counts,
+               void *stream);
+
 /* ---- ILU(0) preconditioner (Sec. 4.3) -------------------------------------
  * Built once per plan on first use (dependency levels of the two triangles
  * from the pattern on the host, numeric factorization on the device, level

@@ -115,6 +115,7 @@ def lib():
         "xb_axpy": (i32, [i32, f64, vp, vp, vp]),
         "xb_mgs": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, vp]),
         "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
+        "xb_lanczos": (i32, [vp, i32, i32, f64, i32, vp, P(f64), vp, P(f64), P(i32), vp]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
         "xb_ilu0_factors": (i32, [vp, vp, vp]),
@@ -328,6 +329,27 @@ class Plan:
         _check(lib().xb_mgs(self._h, w.numel(), k, _ptr(V), ld, _ptr(w), _ptr(h),
                             _stream(stream)))
         return h
+
+    def lanczos(self, nev=10, m=40, tol=1e-8, maxrestart=1000, v0=None, vectors=True,
+                stream=None):
+        """The nev largest eigenvalues (thick-restart Lanczos); returns
+        (evals, evecs n x nev or None, info dict)."""
+        import numpy as np
+        import torch
+        dev = self._keep[2].device
+        if v0 is not None:
+            _need(v0, torch.float64, "v0")
+        ev = (C.c_double * nev)()
+        rs = (C.c_double * nev)()
+        cnt = (C.c_int32 * 2)()
+        vec = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
+        code = lib().xb_lanczos(self._h, nev, m, tol, maxrestart, _ptr(v0) if v0 is not None
+                                else None, ev, _ptr(vec) if vectors else None, rs, cnt,
+                                _stream(stream))
+        if code in (XB_EINVAL, XB_ENOMEM, XB_ECUDA):
+            raise XbError(code, last_error())
+        info = dict(status=code, steps=cnt[0], restarts=cnt[1], resid=np.array(rs[:]))
+        return np.array(ev[:]), (vec.T if vectors else None), info
 
     def ilu0_setup(self, stream=None):
         _check(lib().xb_ilu0_setup(self._h, _stream(stream)))

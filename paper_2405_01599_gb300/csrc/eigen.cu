@@ -1,0 +1,254 @@
+// Restarted Lanczos eigensolver for symmetric matrices (OpenATI_EIGENSOLVE,
+// restarted Lanczos, Sec. 2.2 / 4.3): the nev largest eigenvalues, thick
+// restart in Krylov-Schur form, full re-orthogonalisation.
+//
+// A cycle extends the orthonormal basis v_0..v_m: w = A v_j (the plan's SpMV,
+// general or symmetric storage), w orthogonalised against every basis vector
+// with DGKS on the device (the coefficients are column j of the projected
+// matrix T = V^T A V), v_{j+1} = w / ||w|| scaled on the device.  The m x m
+// projected matrix is symmetrised and diagonalised on the host (cyclic Jacobi;
+// m <= 512, so this is the small dense step, as in any Lanczos code); Ritz
+// pair i has residual |beta_m s_{m-1,i}|.  A restart keeps the
+// k = nev + (m - nev)/2 leading Ritz vectors (V S_k, one device pass over the
+// basis), moves v_m to v_k, and T restarts as diag(theta) with row k holding
+// beta_m s_{m-1,i}.
+#include "krylov.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+constexpr int kRotC = 8;  // outputs per thread in the basis rotation
+
+// x *= 1 / *h (h on the device: the norm just computed by the last GS pass)
+__global__ void k_scale_inv(int64_t n, double *__restrict__ x, const double *__restrict__ h) {
+    const double inv = 1.0 / *h;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= inv;
+}
+
+// Deterministic start vector: splitmix64 of the index, mapped to [-1, 1).
+__global__ void k_start_vector(int64_t n, double *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+// Y[c] = sum_{i < m} V[i] S[i][c] for the kRotC outputs c of this CTA's
+// column block (blockIdx.y); S is m x kc column-major (leading dimension m),
+// staged in shared memory.
+__global__ void __launch_bounds__(256) k_rotate(int64_t n, int m, int kc,
+                                                const double *__restrict__ V, int64_t ld,
+                                                const double *__restrict__ S,
+                                                double *__restrict__ Y, int64_t ldy) {
+    extern __shared__ double ss[];  // m x kRotC
+    const int c0 = blockIdx.y * kRotC;
+    const int nc = min(kRotC, kc - c0);
+    for (int t = threadIdx.x; t < m * kRotC; t += blockDim.x) {
+        const int i = t / kRotC, c = t % kRotC;
+        ss[t] = c < nc ? S[(size_t)(c0 + c) * m + i] : 0.0;
+    }
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc[kRotC];
+#pragma unroll
+        for (int c = 0; c < kRotC; c++) acc[c] = 0.0;
+        for (int i = 0; i < m; i++) {
+            const double v = V[(size_t)i * ld + e];
+#pragma unroll
+            for (int c = 0; c < kRotC; c++) acc[c] = fma(v, ss[i * kRotC + c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kRotC; c++)
+            if (c < nc) Y[(size_t)(c0 + c) * ldy + e] = acc[c];
+    }
+}
+
+// Cyclic Jacobi eigen-decomposition of the symmetric m x m matrix a
+// (row-major, destroyed): a = S diag(w) S^T with S column-major (column c
+// holds eigenvector c, s[c * m + r]); pairs sorted by eigenvalue, largest first.
+void jacobi_eig(int m, std::vector<double> &a, std::vector<double> &w, std::vector<double> &s) {
+    s.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; i++) s[(size_t)i * m + i] = 1.0;
+    double fro = 0.0;
+    for (double v : a) fro += v * v;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++)
+                off += 2.0 * a[(size_t)p * m + q] * a[(size_t)p * m + q];
+        if (off == 0.0 || off <= 1e-30 * fro) break;
+        for (int p = 0; p < m; p++)
+            for (int q = p + 1; q < m; q++) {
+                const double apq = a[(size_t)p * m + q];
+                if (apq == 0.0) continue;
+                const double theta = (a[(size_t)q * m + q] - a[(size_t)p * m + p]) / (2.0 * apq);
+                const double t = std::copysign(1.0, theta) / (std::fabs(theta) +
+                                                              std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int r = 0; r < m; r++) {  // columns p, q
+                    const double x = a[(size_t)r * m + p], y = a[(size_t)r * m + q];
+                    a[(size_t)r * m + p] = c * x - sn * y;
+                    a[(size_t)r * m + q] = sn * x + c * y;
+                }
+                for (int r = 0; r < m; r++) {  // rows p, q
+                    const double x = a[(size_t)p * m + r], y = a[(size_t)q * m + r];
+                    a[(size_t)p * m + r] = c * x - sn * y;
+                    a[(size_t)q * m + r] = sn * x + c * y;
+                }
+                for (int r = 0; r < m; r++) {  // eigenvector columns p, q
+                    const double x = s[(size_t)p * m + r], y = s[(size_t)q * m + r];
+                    s[(size_t)p * m + r] = c * x - sn * y;
+                    s[(size_t)q * m + r] = sn * x + c * y;
+                }
+            }
+    }
+    std::vector<int> ord(m);
+    for (int i = 0; i < m; i++) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+        return a[(size_t)x * m + x] > a[(size_t)y * m + y];
+    });
+    w.resize(m);
+    std::vector<double> s2((size_t)m * m);
+    for (int c = 0; c < m; c++) {
+        w[c] = a[(size_t)ord[c] * m + ord[c]];
+        std::memcpy(&s2[(size_t)c * m], &s[(size_t)ord[c] * m], sizeof(double) * m);
+    }
+    s.swap(s2);
+}
+
+int rotate(xb_plan *p, int64_t n, int m, int kc, const double *V, int64_t ld, const double *dS,
+           double *Y, int64_t ldy, cudaStream_t s) {
+    if (kc <= 0) return XB_OK;
+    const int gx = (int)std::min<int64_t>((n + 255) / 256, (int64_t)xb::num_sms() * 4);
+    dim3 grid(std::max(1, gx), (kc + kRotC - 1) / kRotC);
+    k_rotate<<<grid, 256, (size_t)m * kRotC * sizeof(double), s>>>(n, m, kc, V, ld, dS, Y, ldy);
+    XB_LAUNCHED("k_rotate");
+    (void)p;
+    return XB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, double tol, int32_t maxrestart,
+               const double *v0, double *evals, double *evecs, double *resid, int32_t *counts,
+               void *stream) {
+    if (!p || nev < 1 || m <= nev || m > 512 || m > p->n || !(tol > 0.0) || maxrestart < 0 ||
+        !evals || !resid)
+        return xb::set_error(XB_EINVAL, "lanczos: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = p->n;
+    const int64_t ld = (n + 63) / 64 * 64;
+    const int M = m;
+    const int kmax = nev + (m - nev) / 2;
+    const size_t vbytes = (size_t)(M + 1 + kmax) * ld * sizeof(double);
+    const size_t need = vbytes + xb::gm_doubles(M) * sizeof(double) + (size_t)M * M * 8 + 256;
+    XB_TRY(xb::ensure_work(p, need));
+    double *V = static_cast<double *>(p->d_work);
+    double *Y = V + (size_t)(M + 1) * ld;
+    double *gm = Y + (size_t)kmax * ld;
+    xb::GmDev st = xb::gm_layout(gm, M);
+    double *dS = gm + xb::gm_doubles(M);
+    // raw Gram-Schmidt state: unit scales, no Givens
+    XB_CUDA(cudaMemsetAsync(gm, 0, xb::gm_doubles(M) * sizeof(double), s));
+    std::vector<double> ones(M + 1, 1.0);
+    XB_CUDA(cudaMemcpyAsync(st.sc, ones.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                            s));
+    double misc[xb::GM_NMISC] = {0};
+    misc[xb::GM_BNORM] = 1.0;
+    misc[xb::GM_TAU] = -1.0;
+    misc[xb::GM_RAW] = 1.0;
+    XB_CUDA(cudaMemcpyAsync(st.misc, misc, sizeof misc, cudaMemcpyHostToDevice, s));
+    const int sg = std::max(1, (int)std::min<int64_t>((n + 255) / 256, xb::num_sms() * 8LL));
+    if (v0) XB_CUDA(cudaMemcpyAsync(V, v0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else k_start_vector<<<sg, 256, 0, s>>>(n, V);
+    XB_TRY(xb::vnrm2(p, n, V, st.y, s));  // y[0] holds ||v0|| (y is unused in raw mode)
+    k_scale_inv<<<sg, 256, 0, s>>>(n, V, st.y);
+    XB_LAUNCHED("k_scale_inv");
+
+    const int variant = p->variant;
+    std::vector<double> T((size_t)(M + 1) * (M + 1), 0.0), H((size_t)(M + 1) * M), a, w, S;
+    int k = 0, steps = 0, restarts = 0, status = XB_ENOCONV;
+    double beta = 0.0;
+    for (;;) {
+        for (int j = k; j < m; j++) {
+            double *vj = V + (size_t)j * ld, *wv = V + (size_t)(j + 1) * ld;
+            XB_TRY(xb::spmv_launch(p, variant, p->block, p->ipt, 1.0, vj, 0.0, wv, s));
+            XB_TRY(xb::gm_ortho_step<double>(p, st, n, V, ld, wv, j, XB_ORTHO_DGKS, s));
+            k_scale_inv<<<sg, 256, 0, s>>>(n, wv, st.H + (size_t)j * (M + 1) + j + 1);
+            steps++;
+        }
+        XB_CUDA(cudaMemcpyAsync(H.data(), st.H, H.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                s));
+        XB_CUDA(cudaStreamSynchronize(s));
+        for (int j = k; j < m; j++)
+            for (int i = 0; i <= j + 1; i++)
+                T[(size_t)i * (M + 1) + j] = H[(size_t)j * (M + 1) + i];
+        beta = T[(size_t)m * (M + 1) + m - 1];
+        bool broke = false;
+        for (int j = k; j < m; j++)
+            if (!(T[(size_t)(j + 1) * (M + 1) + j] > 0.0)) broke = true;
+        if (broke) {
+            status = XB_EBREAKDOWN;
+            xb::set_error(XB_EBREAKDOWN, "lanczos: invariant subspace before %d steps", m);
+            break;
+        }
+        a.assign((size_t)m * m, 0.0);
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++)
+                a[(size_t)i * m + j] =
+                    0.5 * (T[(size_t)i * (M + 1) + j] + T[(size_t)j * (M + 1) + i]);
+        jacobi_eig(m, a, w, S);
+        bool conv = true;
+        for (int i = 0; i < nev; i++) {
+            evals[i] = w[i];
+            resid[i] = std::fabs(beta * S[(size_t)i * m + m - 1]);
+            if (resid[i] > tol * std::fabs(w[i])) conv = false;
+        }
+        if (conv || restarts >= maxrestart) {
+            status = conv ? XB_OK : XB_ENOCONV;
+            if (evecs) {
+                XB_CUDA(cudaMemcpyAsync(dS, S.data(), (size_t)m * nev * sizeof(double),
+                                        cudaMemcpyHostToDevice, s));
+                XB_TRY(rotate(p, n, m, nev, V, ld, dS, evecs, n, s));
+            }
+            break;
+        }
+        // thick restart
+        k = kmax;
+        XB_CUDA(cudaMemcpyAsync(dS, S.data(), (size_t)m * k * sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+        XB_TRY(rotate(p, n, m, k, V, ld, dS, Y, ld, s));
+        XB_CUDA(cudaMemcpyAsync(V, Y, (size_t)k * ld * sizeof(double), cudaMemcpyDeviceToDevice,
+                                s));
+        XB_CUDA(cudaMemcpyAsync(V + (size_t)k * ld, V + (size_t)m * ld, ld * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        std::fill(T.begin(), T.end(), 0.0);
+        for (int i = 0; i < k; i++) {
+            T[(size_t)i * (M + 1) + i] = w[i];
+            T[(size_t)k * (M + 1) + i] = beta * S[(size_t)i * m + m - 1];
+        }
+        restarts++;
+    }
+    if (counts) {
+        counts[0] = steps;
+        counts[1] = restarts;
+    }
+    XB_CUDA(cudaStreamSynchronize(s));
+    return status;
+}
+
+}  // extern "C"
