@@ -303,16 +303,19 @@ int xb_orth(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, do
  * re-orthogonalisation: cycles of m basis vectors (nev < m <= min(n, 512)),
  * restarts keeping nev + (m - nev)/2 Ritz vectors, until every wanted Ritz
  * pair has residual ||A y - theta y|| <= tol |theta| or maxrestart restarts.
- * The plan's SpMV choice is used.  v0: DEVICE start vector (n), or NULL for a
+ * m_max > m turns on the restart rule (Eq. 1, Sec. 4.3): the worst relative
+ * wanted residual of each cycle is a sample, every 5 samples the MM ratio is
+ * compared with theta and m grows by 5 (up to m_max <= min(n, 512)) when the
+ * residuals stagnate.  The plan's SpMV choice is used.  v0: DEVICE start vector (n), or NULL for a
  * fixed pseudo-random one.  evals, resid: HOST arrays (nev), largest first;
  * evecs: DEVICE n x nev column-major (unit Ritz vectors) or NULL; counts:
- * HOST int[2] = {Lanczos steps (SpMVs), restarts} or NULL.  Returns XB_OK,
+ * HOST int[3] = {Lanczos steps (SpMVs), restarts, final m} or NULL.  Returns XB_OK,
  * XB_ENOCONV (restart limit; evals hold the current Ritz values) or
  * XB_EBREAKDOWN (the start vector spans an invariant subspace of dimension
  * < m).  Synchronises the stream. */
-int xb_lanczos(xb_plan *plan, int32_t nev, int32_t m, double tol, int32_t maxrestart,
-               const double *v0, double *evals, double *evecs, double *resid, int32_t *counts,
-               void *stream);
+int xb_lanczos(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
+               int32_t maxrestart, const double *v0, double *evals, double *evecs, double *resid,
+               int32_t *counts, void *stream);
 
 /* ---- ILU(0) preconditioner (Sec. 4.3) -------------------------------------
  * Built once per plan on first use (dependency levels of the two triangles

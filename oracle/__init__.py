@@ -62,8 +62,8 @@ def lib():
         L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
                                 vi, vd, vi, vi, vi, vi, vp, _i32p, _f64p, vp, vp, vi]
         L.orc_sym_eig.argtypes = [vi, _f64p, _f64p, _f64p]
-        L.orc_lanczos.argtypes = [vi, vi, _i32p, _i32p, _f64p, vi, vi, vd, vi, _f64p, _f64p, vp,
-                                  _f64p, _i32p]
+        L.orc_lanczos.argtypes = [vi, vi, _i32p, _i32p, _f64p, vi, vi, vi, vd, vd, vi, _f64p,
+                                  _f64p, vp, _f64p, _i32p]
         L.orc_lanczos.restype = vi
         L.orc_ilu0.argtypes = [vi, _i32p, _i32p, _f64p, _f64p]
         L.orc_ilu0.restype = vi
@@ -173,7 +173,8 @@ def sym_eig(M):
     return w, S.reshape(m, m)
 
 
-def lanczos(A, nev=10, m=40, tol=1e-10, maxrestart=1000, v0=None, vectors=True):
+def lanczos(A, nev=10, m=40, tol=1e-10, maxrestart=1000, v0=None, vectors=True, m_max=None,
+            theta=10.0):
     """The nev largest eigenvalues of a symmetric A by thick-restart Lanczos;
     returns (evals, evecs (n x nev) or None, info)."""
     n, rp, ci, va = _csr(A)
@@ -181,12 +182,13 @@ def lanczos(A, nev=10, m=40, tol=1e-10, maxrestart=1000, v0=None, vectors=True):
     ev = np.zeros(nev)
     res = np.zeros(nev)
     vec = np.zeros(n * nev) if vectors else None
-    ii = np.zeros(2, np.int32)
+    ii = np.zeros(3, np.int32)
     st = lib().orc_lanczos(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va, int(nev),
-                           int(m), float(tol), int(maxrestart), v0, ev,
+                           int(m), int(m_max if m_max is not None else m), float(theta),
+                           float(tol), int(maxrestart), v0, ev,
                            vec.ctypes.data if vectors else None, res, ii)
     return ev, (vec.reshape(nev, n).T if vectors else None), dict(
-        status=st, steps=int(ii[0]), restarts=int(ii[1]), resid=res)
+        status=st, steps=int(ii[0]), restarts=int(ii[1]), m_final=int(ii[2]), resid=res)
 
 
 def ilu0(A):

@@ -747,23 +747,32 @@ void orc_sym_eig(int m, double *A, double *w, double *S)
  *   - else the k = nev + (m - nev)/2 leading Ritz vectors are kept as the new
  *     v_0..v_{k-1}, v_m becomes v_k, and T restarts as diag(theta_0..k-1)
  *     with row / column k holding beta_m S[m-1][i] (the thick restart).
+ * Restart rule (Eq. 1, Fig. 2, Sec. 4.3) when m_max > m: after every cycle
+ * that does not converge, the largest relative residual of the wanted Ritz
+ * pairs is a sample; every 5 samples the MM ratio decides (orc_dafrt with
+ * theta) and m grows by 5 (capped at m_max) when the residuals stagnate.
  * v0: starting vector (n).  evals: nev values (largest first); evecs (may be
  * NULL): n x nev column-major; resid: nev Ritz residual norms.
- * iinfo: [0] Lanczos steps (SpMVs), [1] restarts.  Returns 0, -4 (restart
- * limit) or -5 (a zero vector: Krylov space exhausted before m steps).
+ * iinfo: [0] Lanczos steps (SpMVs), [1] restarts, [2] final m.  Returns 0,
+ * -4 (restart limit) or -5 (a zero vector: Krylov space exhausted before m
+ * steps).
  */
 int orc_lanczos(int n, int kind, const int *rp, const int *ci, const double *va, int nev,
-                int m, double tol, int maxrestart, const double *v0, double *evals,
-                double *evecs, double *resid, int *iinfo)
+                int m, int m_max, double theta, double tol, int maxrestart, const double *v0,
+                double *evals, double *evecs, double *resid, int *iinfo)
 {
-    if (nev < 1 || m <= nev || m > n) return ORC_EBREAKDOWN;
-    double *V = (double *)calloc((size_t)(m + 1) * n, sizeof(double));
-    double *T = (double *)calloc((size_t)(m + 1) * (m + 1), sizeof(double)); /* T[i*(m+1)+j] */
-    double *A = (double *)malloc(sizeof(double) * (size_t)m * m);
-    double *S = (double *)malloc(sizeof(double) * (size_t)m * m);
-    double *th = (double *)malloc(sizeof(double) * (size_t)m);
-    double *h = (double *)malloc(sizeof(double) * (size_t)(m + 1));
-    double *Y = (double *)malloc(sizeof(double) * (size_t)m * n);
+    if (m_max < m) m_max = m;
+    if (nev < 1 || m <= nev || m_max > n) return ORC_EBREAKDOWN;
+    int mm = m_max; /* capacity */
+    double *V = (double *)calloc((size_t)(mm + 1) * n, sizeof(double));
+    double *T = (double *)calloc((size_t)(mm + 1) * (mm + 1), sizeof(double)); /* T[i*(mm+1)+j] */
+    double *A = (double *)malloc(sizeof(double) * (size_t)mm * mm);
+    double *S = (double *)malloc(sizeof(double) * (size_t)mm * mm);
+    double *th = (double *)malloc(sizeof(double) * (size_t)mm);
+    double *h = (double *)malloc(sizeof(double) * (size_t)(mm + 1));
+    double *Y = (double *)malloc(sizeof(double) * (size_t)mm * n);
+    double samp[5];
+    int K = 0;
     double nb = nrm2(n, v0);
     for (int q = 0; q < n; q++) V[q] = v0[q] / nb;
     int k = 0, steps = 0, status = ORC_ENOCONV, restarts = 0;
@@ -774,16 +783,16 @@ int orc_lanczos(int n, int kind, const int *rp, const int *ci, const double *va,
             matvec(kind, n, rp, ci, va, V + (size_t)j * n, w);
             steps++;
             orth(ORC_DGKS, 4, n, j, V, w, h);
-            for (int i = 0; i <= j; i++) T[i * (m + 1) + j] = h[i];
+            for (int i = 0; i <= j; i++) T[i * (mm + 1) + j] = h[i];
             beta = nrm2(n, w);
-            T[(j + 1) * (m + 1) + j] = beta;
+            T[(j + 1) * (mm + 1) + j] = beta;
             if (beta == 0.0) { status = ORC_EBREAKDOWN; goto done; }
             for (int q = 0; q < n; q++) w[q] /= beta;
         }
         /* symmetrised projected matrix and its eigenpairs */
         for (int i = 0; i < m; i++)
             for (int j = 0; j < m; j++)
-                A[i * m + j] = 0.5 * (T[i * (m + 1) + j] + T[j * (m + 1) + i]);
+                A[i * m + j] = 0.5 * (T[i * (mm + 1) + j] + T[j * (mm + 1) + i]);
         orc_sym_eig(m, A, th, S);
         int conv = 1;
         for (int i = 0; i < nev; i++) {
@@ -802,6 +811,41 @@ int orc_lanczos(int n, int kind, const int *rp, const int *ci, const double *va,
                     }
             break;
         }
+        /* restart rule: the worst relative residual of the wanted pairs */
+        if (m_max > m || K > 0) {
+            double worst = 0.0;
+            for (int i = 0; i < nev; i++) {
+                double r = resid[i] / fabs(th[i]);
+                if (r > worst) worst = r;
+            }
+            samp[K++] = worst;
+            if (K == 5) {
+                int grow = orc_dafrt(5, samp, theta);
+                K = 0;
+                if (grow && m < m_max) {
+                    /* the thick restart below keeps k of the current m vectors;
+                       the next cycle runs to the larger m */
+                    int k2 = nev + (m - nev) / 2;
+                    for (int i = 0; i < k2; i++)
+                        for (int q = 0; q < n; q++) {
+                            double sum = 0.0;
+                            for (int j = 0; j < m; j++) sum += V[(size_t)j * n + q] * S[j * m + i];
+                            Y[(size_t)i * n + q] = sum;
+                        }
+                    memcpy(V, Y, sizeof(double) * (size_t)k2 * n);
+                    memcpy(V + (size_t)k2 * n, V + (size_t)m * n, sizeof(double) * (size_t)n);
+                    for (int i = 0; i < (mm + 1) * (mm + 1); i++) T[i] = 0.0;
+                    for (int i = 0; i < k2; i++) {
+                        T[i * (mm + 1) + i] = th[i];
+                        T[k2 * (mm + 1) + i] = beta * S[(m - 1) * m + i];
+                    }
+                    k = k2;
+                    m = m + 5 > m_max ? m_max : m + 5;
+                    restarts++;
+                    continue;
+                }
+            }
+        }
         /* thick restart with the k leading Ritz vectors */
         k = nev + (m - nev) / 2;
         for (int i = 0; i < k; i++)
@@ -812,16 +856,17 @@ int orc_lanczos(int n, int kind, const int *rp, const int *ci, const double *va,
             }
         memcpy(V, Y, sizeof(double) * (size_t)k * n);
         memcpy(V + (size_t)k * n, V + (size_t)m * n, sizeof(double) * (size_t)n);
-        for (int i = 0; i < (m + 1) * (m + 1); i++) T[i] = 0.0;
+        for (int i = 0; i < (mm + 1) * (mm + 1); i++) T[i] = 0.0;
         for (int i = 0; i < k; i++) {
-            T[i * (m + 1) + i] = th[i];
-            T[k * (m + 1) + i] = beta * S[(m - 1) * m + i];
+            T[i * (mm + 1) + i] = th[i];
+            T[k * (mm + 1) + i] = beta * S[(m - 1) * m + i];
         }
         restarts++;
     }
 done:
     iinfo[0] = steps;
     iinfo[1] = restarts;
+    iinfo[2] = m;
     free(V); free(T); free(A); free(S); free(th); free(h); free(Y);
     return status;
 }

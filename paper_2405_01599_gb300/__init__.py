@@ -115,7 +115,8 @@ def lib():
         "xb_axpy": (i32, [i32, f64, vp, vp, vp]),
         "xb_mgs": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, vp]),
         "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
-        "xb_lanczos": (i32, [vp, i32, i32, f64, i32, vp, P(f64), vp, P(f64), P(i32), vp]),
+        "xb_lanczos": (i32, [vp, i32, i32, i32, f64, f64, i32, vp, P(f64), vp, P(f64), P(i32),
+                             vp]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
         "xb_ilu0_factors": (i32, [vp, vp, vp]),
@@ -331,7 +332,7 @@ class Plan:
         return h
 
     def lanczos(self, nev=10, m=40, tol=1e-8, maxrestart=1000, v0=None, vectors=True,
-                stream=None):
+                m_max=None, theta=10.0, stream=None):
         """The nev largest eigenvalues (thick-restart Lanczos); returns
         (evals, evecs n x nev or None, info dict)."""
         import numpy as np
@@ -341,14 +342,16 @@ class Plan:
             _need(v0, torch.float64, "v0")
         ev = (C.c_double * nev)()
         rs = (C.c_double * nev)()
-        cnt = (C.c_int32 * 2)()
+        cnt = (C.c_int32 * 3)()
         vec = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
-        code = lib().xb_lanczos(self._h, nev, m, tol, maxrestart, _ptr(v0) if v0 is not None
+        code = lib().xb_lanczos(self._h, nev, m, m if m_max is None else m_max, theta, tol,
+                                maxrestart, _ptr(v0) if v0 is not None
                                 else None, ev, _ptr(vec) if vectors else None, rs, cnt,
                                 _stream(stream))
         if code in (XB_EINVAL, XB_ENOMEM, XB_ECUDA):
             raise XbError(code, last_error())
-        info = dict(status=code, steps=cnt[0], restarts=cnt[1], resid=np.array(rs[:]))
+        info = dict(status=code, steps=cnt[0], restarts=cnt[1], m_final=cnt[2],
+                    resid=np.array(rs[:]))
         return np.array(ev[:]), (vec.T if vectors else None), info
 
     def ilu0_setup(self, stream=None):

@@ -143,17 +143,18 @@ int rotate(xb_plan *p, int64_t n, int m, int kc, const double *V, int64_t ld, co
 
 extern "C" {
 
-int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, double tol, int32_t maxrestart,
-               const double *v0, double *evals, double *evecs, double *resid, int32_t *counts,
-               void *stream) {
-    if (!p || nev < 1 || m <= nev || m > 512 || m > p->n || !(tol > 0.0) || maxrestart < 0 ||
-        !evals || !resid)
+int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
+               int32_t maxrestart, const double *v0, double *evals, double *evecs, double *resid,
+               int32_t *counts, void *stream) {
+    if (m_max < m) m_max = m;
+    if (!p || nev < 1 || m <= nev || m_max > 512 || m_max > p->n || !(tol > 0.0) ||
+        maxrestart < 0 || !evals || !resid)
         return xb::set_error(XB_EINVAL, "lanczos: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = p->n;
     const int64_t ld = (n + 63) / 64 * 64;
-    const int M = m;
-    const int kmax = nev + (m - nev) / 2;
+    const int M = m_max;  // basis capacity
+    const int kmax = nev + (M - nev) / 2;
     const size_t vbytes = (size_t)(M + 1 + kmax) * ld * sizeof(double);
     const size_t need = vbytes + xb::gm_doubles(M) * sizeof(double) + (size_t)M * M * 8 + 256;
     XB_TRY(xb::ensure_work(p, need));
@@ -181,8 +182,8 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, double tol, int32_t maxrestar
 
     const int variant = p->variant;
     std::vector<double> T((size_t)(M + 1) * (M + 1), 0.0), H((size_t)(M + 1) * M), a, w, S;
-    int k = 0, steps = 0, restarts = 0, status = XB_ENOCONV;
-    double beta = 0.0;
+    int k = 0, steps = 0, restarts = 0, status = XB_ENOCONV, K = 0;
+    double beta = 0.0, samp[5];
     for (;;) {
         for (int j = k; j < m; j++) {
             double *vj = V + (size_t)j * ld, *wv = V + (size_t)(j + 1) * ld;
@@ -227,8 +228,20 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, double tol, int32_t maxrestar
             }
             break;
         }
-        // thick restart
-        k = kmax;
+        // restart rule (Eq. 1): worst relative residual of the wanted pairs,
+        // judged every 5 samples; m grows by 5 when the residuals stagnate
+        int m_next = m;
+        if (m_max > m || K > 0) {
+            double worst = 0.0;
+            for (int i = 0; i < nev; i++) worst = std::max(worst, resid[i] / std::fabs(w[i]));
+            samp[K++] = worst;
+            if (K == 5) {
+                if (xb_dafrt(5, samp, theta)) m_next = std::min(m + 5, m_max);
+                K = 0;
+            }
+        }
+        // thick restart with the leading Ritz vectors of this cycle
+        k = nev + (m - nev) / 2;
         XB_CUDA(cudaMemcpyAsync(dS, S.data(), (size_t)m * k * sizeof(double),
                                 cudaMemcpyHostToDevice, s));
         XB_TRY(rotate(p, n, m, k, V, ld, dS, Y, ld, s));
@@ -241,11 +254,13 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, double tol, int32_t maxrestar
             T[(size_t)i * (M + 1) + i] = w[i];
             T[(size_t)k * (M + 1) + i] = beta * S[(size_t)i * m + m - 1];
         }
+        m = m_next;
         restarts++;
     }
     if (counts) {
         counts[0] = steps;
         counts[1] = restarts;
+        counts[2] = m;
     }
     XB_CUDA(cudaStreamSynchronize(s));
     return status;

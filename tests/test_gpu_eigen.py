@@ -75,3 +75,25 @@ def test_lanczos_limits_and_arguments(env):
     v[3] = 1.0
     _, _, info = xb.Plan.from_host(D, dev).lanczos(nev=2, m=10, v0=v, vectors=False)
     assert info["status"] == xb.XB_EBREAKDOWN
+
+
+def test_lanczos_restart_rule(env):
+    """The restart rule grows a too-short cycle on the GPU as in the oracle:
+    same closed-form eigenvalues, m grown in steps of 5, far fewer SpMVs than
+    the fixed cycle."""
+    xb, dev = env
+    import torch
+    n = 400
+    A = gen.laplace1d(n)
+    v0 = torch.tensor(np.random.default_rng(1).standard_normal(n), device=dev)
+    ref = 2 + 2 * np.cos(np.arange(1, 7) * np.pi / (n + 1))
+    plan = xb.Plan.from_host(A, dev)
+    ev0, _, fixed = plan.lanczos(nev=6, m=10, tol=1e-10, v0=v0, maxrestart=5000, vectors=False)
+    ev1, _, grown = plan.lanczos(nev=6, m=10, tol=1e-10, v0=v0, maxrestart=5000, vectors=False,
+                                 m_max=60)
+    assert fixed["status"] == 0 and grown["status"] == 0
+    assert fixed["m_final"] == 10 and 10 < grown["m_final"] <= 60
+    assert (grown["m_final"] - 10) % 5 == 0
+    assert grown["steps"] < fixed["steps"] / 4
+    np.testing.assert_allclose(ev0, ref, atol=1e-10)
+    np.testing.assert_allclose(ev1, ref, atol=1e-10)

@@ -66,3 +66,23 @@ def test_lanczos_invariant_start_breaks_down():
     ev, _, info = oracle.lanczos(A, nev=3, m=20, tol=1e-12, v0=np.ones(n))
     assert info["status"] == 0
     np.testing.assert_allclose(ev, [50.0, 49.0, 48.0], atol=1e-9)
+
+
+def test_lanczos_restart_rule_grows_m():
+    """With m_max > m the restart rule (Eq. 1 over 5 samples of the worst
+    relative Ritz residual, m += 5 on stagnation) grows a too-short cycle and
+    converges in far fewer steps, to the same closed-form eigenvalues."""
+    n = 400
+    A = gen.laplace1d(n)
+    v0 = np.random.default_rng(1).standard_normal(n)
+    ref = 2 + 2 * np.cos(np.arange(1, 7) * np.pi / (n + 1))
+    ev0, _, fixed = oracle.lanczos(A, nev=6, m=10, tol=1e-10, v0=v0, vectors=False,
+                                   maxrestart=5000)
+    ev1, _, grown = oracle.lanczos(A, nev=6, m=10, tol=1e-10, v0=v0, vectors=False,
+                                   maxrestart=5000, m_max=60)
+    assert fixed["status"] == 0 and grown["status"] == 0
+    assert fixed["m_final"] == 10 and 10 < grown["m_final"] <= 60
+    assert (grown["m_final"] - 10) % 5 == 0
+    assert grown["steps"] < fixed["steps"] / 4
+    np.testing.assert_allclose(ev0, ref, atol=1e-10)
+    np.testing.assert_allclose(ev1, ref, atol=1e-10)
