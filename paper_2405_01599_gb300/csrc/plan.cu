@@ -3,6 +3,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -349,7 +350,9 @@ int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan
     if (!A || !out) return set_error(XB_EINVAL, "plan_create: NULL argument");
     *out = nullptr;
     const int n = A->n, nnz = A->nnz;
-    if (n < 0 || nnz < 0) return set_error(XB_EINVAL, "plan_create: n=%d nnz=%d", n, nnz);
+    if (n < 0 || nnz < 0 || n > INT_MAX - 64 || nnz > INT_MAX - 64)
+        return set_error(XB_EINVAL, "plan_create: n=%d nnz=%d (int32 indices, < 2^31 - 64)", n,
+                         nnz);
     if (n > 0 && (!A->rowptr || (nnz > 0 && (!A->col || !A->val))))
         return set_error(XB_EINVAL, "plan_create: NULL CRS array");
     cudaStream_t s = (cudaStream_t)stream;
