@@ -15,7 +15,6 @@
 #include "krylov.cuh"
 
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -128,14 +127,13 @@ void jacobi_eig(int m, std::vector<double> &a, std::vector<double> &w, std::vect
     s.swap(s2);
 }
 
-int rotate(xb_plan *p, int64_t n, int m, int kc, const double *V, int64_t ld, const double *dS,
-           double *Y, int64_t ldy, cudaStream_t s) {
+int rotate(int64_t n, int m, int kc, const double *V, int64_t ld, const double *dS, double *Y,
+           int64_t ldy, cudaStream_t s) {
     if (kc <= 0) return XB_OK;
     const int gx = (int)std::min<int64_t>((n + 255) / 256, (int64_t)xb::num_sms() * 4);
     dim3 grid(std::max(1, gx), (kc + kRotC - 1) / kRotC);
     k_rotate<<<grid, 256, (size_t)m * kRotC * sizeof(double), s>>>(n, m, kc, V, ld, dS, Y, ldy);
     XB_LAUNCHED("k_rotate");
-    (void)p;
     return XB_OK;
 }
 
@@ -224,7 +222,7 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
             if (evecs) {
                 XB_CUDA(cudaMemcpyAsync(dS, S.data(), (size_t)m * nev * sizeof(double),
                                         cudaMemcpyHostToDevice, s));
-                XB_TRY(rotate(p, n, m, nev, V, ld, dS, evecs, n, s));
+                XB_TRY(rotate(n, m, nev, V, ld, dS, evecs, n, s));
             }
             break;
         }
@@ -244,7 +242,7 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
         k = nev + (m - nev) / 2;
         XB_CUDA(cudaMemcpyAsync(dS, S.data(), (size_t)m * k * sizeof(double),
                                 cudaMemcpyHostToDevice, s));
-        XB_TRY(rotate(p, n, m, k, V, ld, dS, Y, ld, s));
+        XB_TRY(rotate(n, m, k, V, ld, dS, Y, ld, s));
         XB_CUDA(cudaMemcpyAsync(V, Y, (size_t)k * ld * sizeof(double), cudaMemcpyDeviceToDevice,
                                 s));
         XB_CUDA(cudaMemcpyAsync(V + (size_t)k * ld, V + (size_t)m * ld, ld * sizeof(double),

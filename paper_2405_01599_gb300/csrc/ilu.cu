@@ -290,6 +290,7 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
     IluData &u = p->ilu;
     if (u.built) return u.status == XB_OK ? XB_OK : set_error(u.status, "ILU(0): zero pivot");
     if (p->sym) return set_error(XB_EINVAL, "ILU(0) needs full (general) CRS storage");
+    ilu_free(p);  // a build that failed half-way left nothing usable
     const int n = p->n, nnz = p->nnz;
     const std::vector<int> &rp = p->h_rowptr;
     std::vector<int> ci(nnz);
