@@ -104,6 +104,13 @@ struct IluData {
     double *d_in = nullptr, *d_out = nullptr;  // fixed operands of the captured solve
     cudaGraph_t graph = nullptr;     // both substitutions, every level, captured once
     cudaGraphExec_t exec = nullptr;
+    // persistent substitution (one cooperative launch, a bounded grid barrier
+    // between levels): level tables on the device, barrier state, error flag
+    int *d_lmeta = nullptr, *d_umeta = nullptr;        // per level: off, n0, n1, w
+    long long *d_leo = nullptr, *d_ueo = nullptr;      // per level: ELL base offset
+    unsigned *d_bar = nullptr;                          // count, generation
+    int *d_err = nullptr;                               // 1: a barrier wait ran out
+    int pgrid = 0;                                      // CTAs of the persistent launch
 };
 
 }  // namespace xb
@@ -149,6 +156,7 @@ int ensure_work(xb_plan *p, size_t bytes);
 int ensure_ilu(xb_plan *p, cudaStream_t s);
 int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s);
 double ilu_apply_bytes(const xb_plan *p);
+int ilu_check(xb_plan *p);  // XB_ETIMEOUT if a substitution's barrier wait ran out
 void ilu_free(xb_plan *p);
 bool variant_fits(const xb_plan *p, int variant);
 

@@ -20,6 +20,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 
 namespace {
@@ -173,6 +174,136 @@ __global__ void k_diag_fill(int n, const int *__restrict__ rows, const int *__re
     if (s < n) diag[s] = lu[dpos[rows[s]]];
 }
 
+// ---- persistent substitution ---------------------------------------------------
+// Both substitutions in one cooperative launch (every CTA resident, one per
+// SM): each level is processed by the whole grid, then a grid barrier.  The
+// barrier is a counter and a generation word in global memory; a CTA that
+// waits longer than kBarSpins polls sets the error flag and leaves (every
+// wait is bounded).  Values of z written by other CTAs are read at L2.
+constexpr unsigned kBarSpins = 1u << 20;  // polls of ~0.5 us: a wait gives up after ~0.5 s
+
+struct TriDev {
+    int nlev;
+    const int *meta;        // per level: off, n0, n1, w (4 ints)
+    const long long *eoff;  // per level: ELL base offset
+    const int *rows, *ecol;
+    const double *eval, *diag;
+};
+
+__device__ __forceinline__ bool grid_bar(unsigned *bar, int *err) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+            ok = 1;
+        } else {
+            unsigned it = 0;
+            while (*gen == g && ++it < kBarSpins) {
+            }
+            ok = (it < kBarSpins);
+            if (!ok) atomicExch(err, 1);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok;
+}
+
+template <bool FWD>
+__device__ void persist_level(const TriDev &t, int l, const int *__restrict__ rp,
+                              const int *__restrict__ ci, const int *__restrict__ dpos,
+                              const double *__restrict__ lu, const double *__restrict__ r,
+                              double *z, double *sh) {
+    const int off = t.meta[4 * l], c0 = t.meta[4 * l + 1], c1 = t.meta[4 * l + 2];
+    const int w = t.meta[4 * l + 3];
+    const int c2 = t.meta[4 * (l + 1)] - off - c0 - c1;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    // ELL tier: a thread per row
+    const long long eo = t.eoff[l];
+    for (int slot = gt; slot < c0; slot += gs) {
+        const int i = t.rows[off + slot];
+        double s = 0.0;
+        for (int q = 0; q < w; q++) {
+            const long long e = eo + (long long)q * c0 + slot;
+            s = fma(__ldg(t.eval + e), __ldcg(z + __ldg(t.ecol + e)), s);
+        }
+        if (FWD) z[i] = __ldg(r + i) - s;
+        else z[i] = (__ldcg(z + i) - s) / __ldg(t.diag + off + slot);
+    }
+    // CSR tier: thread per row, warp for rows over 32 entries
+    const int lane = threadIdx.x & 31, wi = gt >> 5, nw = gs >> 5;
+    for (int base = wi * 32; base < c1; base += nw * 32) {  // warp-uniform
+        const int slot = base + lane;
+        int i = -1, ka = 0, kb = 0;
+        if (slot < c1) {
+            i = t.rows[off + c0 + slot];
+            const int d = dpos[i];
+            ka = FWD ? rp[i] : d + 1;
+            kb = FWD ? d : rp[i + 1];
+        }
+        const bool lng = kb - ka > 32;
+        double s = 0.0;
+        if (!lng)
+            for (int k = ka; k < kb; k++) s = fma(__ldg(lu + k), __ldcg(z + __ldg(ci + k)), s);
+        unsigned todo = __ballot_sync(0xffffffffu, lng);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int la = __shfl_sync(0xffffffffu, ka, src);
+            const int lb = __shfl_sync(0xffffffffu, kb, src);
+            double v = 0.0;
+            for (int k = la + lane; k < lb; k += 32)
+                v = fma(__ldg(lu + k), __ldcg(z + __ldg(ci + k)), v);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == src) s = v;
+        }
+        if (i >= 0) {
+            if (FWD) z[i] = __ldg(r + i) - s;
+            else z[i] = (__ldcg(z + i) - s) / lu[dpos[i]];
+        }
+    }
+    // long rows: a CTA per row (the loop bound is uniform over the CTA)
+    for (int q = blockIdx.x; q < c2; q += gridDim.x) {
+        const int i = t.rows[off + c0 + c1 + q];
+        const int d = dpos[i];
+        const int ka = FWD ? rp[i] : d + 1, kb = FWD ? d : rp[i + 1];
+        double v = 0.0;
+        for (int k = ka + threadIdx.x; k < kb; k += blockDim.x)
+            v = fma(__ldg(lu + k), __ldcg(z + __ldg(ci + k)), v);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) sum += sh[k];
+            if (FWD) z[i] = __ldg(r + i) - sum;
+            else z[i] = (__ldcg(z + i) - sum) / lu[d];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) k_ilu_persist(TriDev L, TriDev U, const int *rp,
+                                                     const int *ci, const int *dpos,
+                                                     const double *lu, const double *r,
+                                                     double *z, unsigned *bar, int *err) {
+    __shared__ double sh[16];
+    for (int l = 0; l < L.nlev; l++) {
+        persist_level<true>(L, l, rp, ci, dpos, lu, r, z, sh);
+        if (!grid_bar(bar, err)) return;
+    }
+    for (int l = 0; l < U.nlev; l++) {
+        persist_level<false>(U, l, rp, ci, dpos, lu, r, z, sh);
+        if (l + 1 < U.nlev && !grid_bar(bar, err)) return;
+    }
+}
+
 // Rows grouped by level (counting sort), ascending row order inside each tier
 // of a level: ELL rows (len <= kEllMax), CSR rows (<= kLongRow), CTA rows;
 // n0[l], n1[l] = the first two tiers' counts.
@@ -283,6 +414,12 @@ void ilu_free(xb_plan *p) {
     cudaFree(u.d_udiag);
     if (u.exec) cudaGraphExecDestroy(u.exec);
     if (u.graph) cudaGraphDestroy(u.graph);
+    cudaFree(u.d_lmeta);
+    cudaFree(u.d_umeta);
+    cudaFree(u.d_leo);
+    cudaFree(u.d_ueo);
+    cudaFree(u.d_bar);
+    cudaFree(u.d_err);
     u = IluData();
 }
 
@@ -392,6 +529,75 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
         u.built = false;
         return cuda_error(e, "ILU(0): capture of the substitutions");
     }
+    // level tables for the persistent substitution
+    auto meta = [](const std::vector<int> &off, const std::vector<int> &n0,
+                   const std::vector<int> &n1, const std::vector<int> &w) {
+        const int nl = (int)n0.size();
+        std::vector<int> m(4 * (nl + 1), 0);
+        for (int l = 0; l < nl; l++) {
+            m[4 * l] = off[l];
+            m[4 * l + 1] = n0[l];
+            m[4 * l + 2] = n1[l];
+            m[4 * l + 3] = w[l];
+        }
+        m[4 * nl] = off[nl];
+        return m;
+    };
+    XB_TRY(up(&u.d_lmeta, meta(u.loff, u.ln0, u.ln1, u.lw)));
+    XB_TRY(up(&u.d_umeta, meta(u.uoff, u.un0, u.un1, u.uw)));
+    XB_CUDA(cudaMalloc(&u.d_leo, u.leoff.size() * sizeof(long long)));
+    XB_CUDA(cudaMalloc(&u.d_ueo, u.ueoff.size() * sizeof(long long)));
+    XB_CUDA(cudaMemcpyAsync(u.d_leo, u.leoff.data(), u.leoff.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, s));
+    XB_CUDA(cudaMemcpyAsync(u.d_ueo, u.ueoff.data(), u.ueoff.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, s));
+    XB_CUDA(cudaMalloc(&u.d_bar, 2 * sizeof(unsigned)));
+    XB_CUDA(cudaMalloc(&u.d_err, sizeof(int)));
+    XB_CUDA(cudaMemsetAsync(u.d_err, 0, sizeof(int), s));
+    int dev = 0, coop = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ilu_persist, 512, 0) ==
+                    cudaSuccess &&
+        per >= 1)
+        u.pgrid = num_sms();
+    cudaGetLastError();
+    XB_CUDA(cudaStreamSynchronize(s));
+    return XB_OK;
+}
+
+// Which substitution to run: the persistent launch pays one grid barrier per
+// level, the captured graph one kernel per non-empty row tier of a level
+// (measured: ~6 us per barrier, ~4 us per graph kernel), so the persistent
+// launch wins when levels hold several tiers (power-law rows) and the graph
+// when every level is one ELL kernel (stencils).  XB_ILU_MODE=0/1 forces one.
+int ilu_mode(const IluData &u) {
+    static const int env = [] {
+        const char *e = std::getenv("XB_ILU_MODE");
+        return e ? std::atoi(e) : -1;
+    }();
+    if (env >= 0) return env;
+    long long levels = (long long)u.ln0.size() + (long long)u.un0.size(), kernels = 0;
+    auto tiers = [](const std::vector<int> &off, const std::vector<int> &n0,
+                    const std::vector<int> &n1) {
+        long long k = 0;
+        for (size_t l = 0; l < n0.size(); l++)
+            k += (n0[l] > 0) + (n1[l] > 0) + (off[l + 1] - off[l] > n0[l] + n1[l]);
+        return k;
+    };
+    kernels = tiers(u.loff, u.ln0, u.ln1) + tiers(u.uoff, u.un0, u.un1);
+    return 4 * kernels > 6 * levels ? 1 : 0;
+}
+
+int ilu_check(xb_plan *p) {
+    IluData &u = p->ilu;
+    if (!u.built || !u.d_err) return XB_OK;
+    int err = 0;
+    XB_CUDA(cudaMemcpy(&err, u.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        cudaMemset(u.d_err, 0, sizeof(int));
+        return set_error(XB_ETIMEOUT, "ILU(0): a level barrier wait ran out");
+    }
     return XB_OK;
 }
 
@@ -399,6 +605,19 @@ int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s) {
     IluData &u = p->ilu;
     XB_TRY(ensure_ilu(p, s));
     if (p->n == 0) return XB_OK;
+    if (u.pgrid > 0 && ilu_mode(u) == 1) {
+        TriDev L{(int)u.ln0.size(), u.d_lmeta, u.d_leo, u.d_lrows, u.d_lecol, u.d_leval, u.d_udiag};
+        TriDev U{(int)u.un0.size(), u.d_umeta, u.d_ueo, u.d_urows, u.d_uecol, u.d_ueval, u.d_udiag};
+        const int *rp = p->rowptr, *ci = p->col, *dp = u.d_dpos;
+        const double *lu = u.d_lu;
+        unsigned *bar = u.d_bar;
+        int *err = u.d_err;
+        void *args[] = {&L, &U, (void *)&rp, (void *)&ci, (void *)&dp, (void *)&lu, (void *)&r,
+                        (void *)&z, (void *)&bar, (void *)&err};
+        XB_CUDA(cudaMemsetAsync(u.d_bar, 0, 2 * sizeof(unsigned), s));
+        XB_CUDA(cudaLaunchCooperativeKernel((const void *)k_ilu_persist, u.pgrid, 512, args, 0, s));
+        return XB_OK;
+    }
     const size_t bytes = (size_t)p->n * sizeof(double);
     XB_CUDA(cudaMemcpyAsync(u.d_in, r, bytes, cudaMemcpyDeviceToDevice, s));
     XB_CUDA(cudaGraphLaunch(u.exec, s));
@@ -427,7 +646,10 @@ int xb_ilu0_setup(xb_plan *p, void *stream) {
 int xb_ilu0_apply(xb_plan *p, const double *r, double *z, void *stream) {
     if (!p || (p->n > 0 && (!r || !z)) || r == z)
         return xb::set_error(XB_EINVAL, "ilu0_apply: bad argument");
-    return xb::ilu_apply(p, r, z, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    XB_TRY(xb::ilu_apply(p, r, z, s));
+    XB_CUDA(cudaStreamSynchronize(s));
+    return xb::ilu_check(p);
 }
 
 int xb_ilu0_factors(xb_plan *p, double *lu, void *stream) {

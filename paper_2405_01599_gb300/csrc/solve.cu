@@ -590,6 +590,10 @@ int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb
             st = body(o, inf, s, ac, tm, t0);
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess && st == XB_OK) st = xb::cuda_error(e, "solve");
+            if (o.precond == XB_PRECOND_ILU0 && st != XB_ECUDA) {
+                const int ci = xb::ilu_check(p);
+                if (ci != XB_OK) st = ci;
+            }
         }
         tm.flush();
         inf.t_solve_s = secs_since(t0);
