@@ -10,7 +10,7 @@
  *   - Matrix and vector pointers are DEVICE pointers owned by the caller (for
  *     example torch tensors).  The library never frees caller memory.
  *   - CRS is 0-based: rowptr[n+1], col[nnz] ascending within each row, no
- *     duplicates, val[nnz] FP64.  n and nnz are < 2^31.
+ *     duplicates, val[nnz] FP64.  n and nnz are < 2^31 - 64 (int32 indices).
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *     default stream.  Work is enqueued on it in stream order; functions that
  *     must read a device result on the host (solvers, tuners) synchronise
