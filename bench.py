@@ -142,6 +142,22 @@ def dist_init():
     return ws, rank, local
 
 
+def max_over_ranks(ms, pg, dev=None):
+    """The slowest rank's time: replicas run concurrently, so the job takes as
+    long as its slowest rank (pg: torch.distributed or None)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, bytes_per_step, ms_per_step):
+    """Whole-job GB/s: every one of the ws ranks moved bytes_per_step per step."""
+    return ws * bytes_per_step / (ms_per_step * 1e-3) / 1e9
+
+
 def make_c3(n):
     from paper_2405_01599_gb300 import gen
     return gen.powerlaw(n=n, seed=3)
@@ -319,12 +335,9 @@ def main():
     total_ms = t0.elapsed_time(t1)
     per_launch = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
     avg_launch_ms = float(np.mean(per_launch))
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, pg, dev)
     ms_step = total_ms / args.steps
-    value = ws * bytes_step / (ms_step * 1e-3) / 1e9
+    value = job_rate(ws, bytes_step, ms_step)
     if args.profile_only:
         if rank == 0:
             print(json.dumps({"profile_only": True, "n": n, "nnz": nnz, "choice": choice,
@@ -379,8 +392,8 @@ def main():
         return e0.elapsed_time(e1)
 
     e2e_run(3)
-    e2e_ms = e2e_run(args.steps) / args.steps
-    e2e_val = ws * bytes_step / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(e2e_run(args.steps), pg, dev) / args.steps
+    e2e_val = job_rate(ws, bytes_step, e2e_ms)
     e2e_check = float((yd[(args.steps - 1) % 2] - y).abs().max().item())  # same x, same y
 
     if rank != 0:
