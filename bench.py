@@ -690,6 +690,9 @@ def batch(xb, torch, dev, args):
     # restart-frequency rule during it (m starts at 30, grows by 5 up to 128)
     t_exr, r_exr = run([30] * N, [q["mode_ex"] for q in systems], dafrt=1, m_max=128,
                        dafrt_theta=10.0)
+    # the learned choices as the starting point of the same rule
+    t_mlr, r_mlr = run([q["m_ml"] for q in systems], [q["mode_ml"] for q in systems], dafrt=1,
+                       m_max=128, dafrt_theta=10.0)
     ok = lambda r: int(sum(1 for q in r if q["status"] == 0))
     # systems every arm solved: their summed per-system device times compare the
     # tuners on work that finished (systems that hit the cap all ran 3000 steps)
@@ -710,7 +713,9 @@ def batch(xb, torch, dev, args):
                               "exhaustive": max(q["ms"] for q in r_exh),
                               "learned": max(q["ms"] for q in r_mlp)},
             "exhaustive_with_restart_rule": {"launch_ms": t_exr, "converged": ok(r_exr),
-                                             "solved_by_all_sum_ms": cs(r_exr)}}
+                                             "solved_by_all_sum_ms": cs(r_exr)},
+            "learned_with_restart_rule": {"launch_ms": t_mlr, "converged": ok(r_mlr),
+                                          "solved_by_all_sum_ms": cs(r_mlr)}}
 
 
 if __name__ == "__main__":
