@@ -130,8 +130,8 @@ struct xb_plan {
     xb::IluData ilu;
     bool vec_ok = false;                 // val and col 16-byte aligned
     // reduction scratch
-    double *d_part = nullptr;            // kRedSlots * 4 partials
-    unsigned *d_ticket = nullptr;        // 8 counters
+    double *d_part = nullptr;            // kRedSlots * kRedValues partials
+    unsigned *d_ticket = nullptr;        // 64 counters (one in use per reduction)
     double *d_scal = nullptr;            // kScalars
     // solver workspace (grown on demand)
     void *d_work = nullptr;
