@@ -1,6 +1,7 @@
 """CPU oracle for the CRS SpMV + restarted Krylov hot path (test infrastructure).
 
-Plain FP64 C (``oracle.c``) reached through ctypes.  Only the test suite,
+Plain FP64 C (``oracle.c``) reached through ctypes, and the restarted
+Arnoldi eigensolver in plain numpy / scipy (``eig.py``).  Only the test suite,
 ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline / reference arm
 may import this package; the CUDA library never does, and the two share no
 code.  ``build()`` compiles the C source with gcc (no architecture-specific
@@ -317,3 +318,6 @@ def adam(P, G, M, V, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     """In-place Adam step on float64 arrays P, M, V."""
     lib().orc_adam(P, np.ascontiguousarray(G, np.float64), M, V, P.size, int(t), float(lr),
                    float(b1), float(b2), float(eps))
+
+
+from .eig import LM as EIG_LM, LR as EIG_LR, arnoldi_eig, wanted_order  # noqa: E402,F401

@@ -91,12 +91,13 @@ def laplace3d(N, upper=False):
     return _mat(n, rp, c, v, upper, kind="laplace3d", side=N)
 
 
-def convdiff3d(N=256, pe=10.0):
+def convdiff3d(N=256, pe=10.0, dims=None):
     """3D convection-diffusion -Lap(u) + Pe*(u_x + u_y + u_z) on (0,1)^3.
 
     Zero Dirichlet boundary, h = 1/(N+1), first-order upwind for the positive
     velocity (Pe, Pe, Pe), scaled by h^2: diagonal 6 + 3*Pe*h, the -x/-y/-z
     neighbours -(1 + Pe*h), the +x/+y/+z neighbours -1.  Nonsymmetric.
+    dims = (Nx, Ny, Nz) gives a box grid with the same stencil (h from N).
     """
     h = 1.0 / (N + 1)
     ph = pe * h
@@ -107,8 +108,62 @@ def convdiff3d(N=256, pe=10.0):
         co[tuple(o)] = -(1.0 + ph)
         o[a] = 1
         co[tuple(o)] = -1.0
-    n, rp, c, v = _stencil((N, N, N), co)
+    n, rp, c, v = _stencil(tuple(dims) if dims is not None else (N, N, N), co)
     return _mat(n, rp, c, v, kind="convdiff3d", side=N, pe=pe)
+
+
+def quasi_triangular(n=400, per_row=4, seed=0, pair_frac=0.5, top=10.0, ratio=0.995,
+                     signed=False, off=1.0):
+    """Block upper-triangular n x n with a spectrum known by construction.
+
+    Diagonal blocks, top to bottom: 1 x 1 blocks [a] and 2 x 2 blocks
+    [[a, b], [-b, a]] (a block is 2 x 2 with probability pair_frac) with
+    eigenvalues a +- ib.  The a values are top * ratio**j, j = 0, 1, ...
+    (times a random sign if signed), assigned to the blocks in random order;
+    b is U[0.5, 2].  Right of each row's block: per_row distinct columns with
+    values off * U[-1, 1].  The blocks are kept in "blocks" as (a, b) pairs
+    (b = 0 for a 1 x 1 block).
+    """
+    rng = np.random.default_rng(seed)
+    sizes = []
+    i = 0
+    while i < n:
+        two = i + 1 < n and rng.random() < pair_frac
+        sizes.append(2 if two else 1)
+        i += sizes[-1]
+    nb = len(sizes)
+    a_vals = top * ratio ** np.arange(nb, dtype=np.float64)
+    if signed:
+        a_vals *= rng.choice([-1.0, 1.0], size=nb)
+    a_vals = rng.permutation(a_vals)
+    blocks = [(float(a), float(rng.uniform(0.5, 2.0)) if sz == 2 else 0.0)
+              for a, sz in zip(a_vals, sizes)]
+    rows_c, rows_v = [], []
+    i0 = 0
+    for (a, b), size in zip(blocks, sizes):
+        for r in range(size):
+            c = [i0, i0 + 1] if size == 2 else [i0]
+            v = ([a, b] if r == 0 else [-b, a]) if size == 2 else [a]
+            right = n - (i0 + size)
+            if right > 0:
+                cc = i0 + size + np.sort(rng.choice(right, size=min(per_row, right),
+                                                    replace=False))
+                c = c + cc.tolist()
+                v = v + (off * rng.uniform(-1.0, 1.0, size=len(cc))).tolist()
+            rows_c.append(np.array(c, np.int64))
+            rows_v.append(np.array(v, np.float64))
+        i0 += size
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in rows_c])
+    return _mat(n, rowptr, np.concatenate(rows_c), np.concatenate(rows_v),
+                kind="quasi_triangular", blocks=blocks)
+
+
+def toeplitz3(n, sub, diag, sup):
+    """Tridiagonal Toeplitz tridiag(sub, diag, sup), n x n (nonsymmetric for
+    sub != sup)."""
+    n_, rp, c, v = _stencil((n,), {(0,): float(diag), (-1,): float(sub), (1,): float(sup)})
+    return _mat(n_, rp, c, v, kind="toeplitz3", side=n)
 
 
 def random200(n=200, per_row=5, diag=10.0, seed=1):

@@ -1,0 +1,104 @@
+"""Pins of the oracle's restarted Arnoldi eigensolver (OpenATI_EIGENSOLVE,
+restarted Arnoldi for unsymmetric matrices, Sec. 2.2 / 4.3):
+  - block upper-triangular matrices whose spectrum is fixed by construction
+    (1 x 1 blocks a, 2 x 2 blocks [[a, b], [-b, a]] -> a +- ib): the wanted
+    eigenvalues, largest real part and largest modulus, complex pairs included;
+    every returned eigenvalue is one of the matrix's;
+  - the tridiagonal Toeplitz closed form d + 2 sqrt(l u) cos(j pi / (n + 1));
+  - the symmetric special case: the 1D Laplacian closed form;
+  - brute force: the dense spectrum of a random sparse nonsymmetric matrix;
+  - returned Ritz vectors satisfy A y = theta y to the requested tolerance
+    (so the restart keeps a valid Arnoldi relation), and the residual
+    estimate |beta e_m^T s| equals the true residual;
+  - the restart rule grows m on a stagnating problem; an invariant start
+    vector ends in a breakdown."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_01599_gb300 import gen
+
+
+def spectrum(A):
+    e = []
+    for a, b in A["blocks"]:
+        e += [complex(a, b), complex(a, -b)] if b else [complex(a, 0.0)]
+    return np.array(e)
+
+
+def true_resid(A, ev, X):
+    D = gen.to_dense(A)
+    return np.array([np.linalg.norm(D @ X[:, i] - ev[i] * X[:, i]) for i in range(len(ev))])
+
+
+@pytest.mark.parametrize("which", [oracle.EIG_LR, oracle.EIG_LM])
+def test_quasi_triangular_known_spectrum(which):
+    n, nev = 400, 8
+    A = gen.quasi_triangular(n, seed=2, signed=which == oracle.EIG_LM)
+    v0 = np.random.default_rng(3).standard_normal(n)
+    ev, X, info = oracle.arnoldi_eig(A, nev=nev, m=30, tol=1e-10, v0=v0, which=which)
+    assert info["status"] == 0 and info["restarts"] > 0
+    e = spectrum(A)
+    ref = e[oracle.wanted_order(e, which)[:nev]]
+    np.testing.assert_allclose(ev, ref, atol=1e-8)
+    assert np.any(np.abs(ev.imag) > 0.1)  # complex pairs among the wanted ones
+    assert np.all(np.min(np.abs(e[:, None] - ev[None, :]), axis=0) <= 1e-8)
+    r = true_resid(A, ev, X)
+    assert np.all(r <= 1e-9 * np.abs(ev))
+    # the estimate the stopping test uses is the true residual
+    np.testing.assert_allclose(r, info["resid"], rtol=1e-3, atol=1e-11)
+    np.testing.assert_allclose(np.linalg.norm(X, axis=0), 1.0, atol=1e-12)
+
+
+def test_toeplitz_closed_form():
+    n, l, d, u = 100, 1.0, 2.0, 1.2
+    A = gen.toeplitz3(n, l, d, u)
+    ev, X, info = oracle.arnoldi_eig(A, nev=5, m=30, tol=1e-10,
+                                     v0=np.random.default_rng(1).standard_normal(n))
+    assert info["status"] == 0
+    ref = d + 2 * np.sqrt(l * u) * np.cos(np.arange(1, 6) * np.pi / (n + 1))
+    np.testing.assert_allclose(ev.real, ref, atol=1e-8)
+    np.testing.assert_allclose(ev.imag, 0.0, atol=1e-8)
+
+
+def test_symmetric_special_case_laplacian():
+    n = 200
+    A = gen.laplace1d(n)
+    ev, X, info = oracle.arnoldi_eig(A, nev=4, m=30, tol=1e-10,
+                                     v0=np.random.default_rng(1).standard_normal(n))
+    assert info["status"] == 0
+    ref = 2 + 2 * np.cos(np.arange(1, 5) * np.pi / (n + 1))
+    np.testing.assert_allclose(ev, ref, atol=1e-9)
+
+
+def test_random_sparse_brute_force():
+    A = gen.random200(200, per_row=5, diag=0.0, seed=4)
+    e = np.linalg.eigvals(gen.to_dense(A))
+    ref = e[oracle.wanted_order(e, oracle.EIG_LR)[:6]]
+    ev, X, info = oracle.arnoldi_eig(A, nev=6, m=24, tol=1e-10,
+                                     v0=np.random.default_rng(5).standard_normal(200))
+    assert info["status"] == 0
+    np.testing.assert_allclose(ev, ref, atol=1e-8)
+    assert np.all(true_resid(A, ev, X) <= 1e-9 * np.abs(ev))
+
+
+def test_restart_rule_grows_m():
+    A = gen.quasi_triangular(3000, seed=7, ratio=0.999)  # top real parts 0.01 apart
+    v0 = np.random.default_rng(2).standard_normal(A["n"])
+    fixed = oracle.arnoldi_eig(A, nev=10, m=20, tol=1e-8, v0=v0, vectors=False,
+                               maxrestart=3000)[2]
+    rule = oracle.arnoldi_eig(A, nev=10, m=20, m_max=60, tol=1e-8, v0=v0, vectors=False,
+                              maxrestart=3000)[2]
+    assert fixed["status"] == 0 and rule["status"] == 0
+    assert fixed["m_final"] == 20 and rule["m_final"] > 20
+    assert rule["restarts"] < fixed["restarts"]
+
+
+def test_invariant_start_vector_breaks_down():
+    n = 50  # diag(1..50): A e_3 = 4 e_3 exactly, so the first step leaves w = 0
+    A = dict(n=n, nnz=n, rowptr=np.arange(n + 1, dtype=np.int32),
+             col=np.arange(n, dtype=np.int32), val=np.arange(1.0, n + 1), sym_upper=False)
+    v0 = np.zeros(50)
+    v0[3] = 1.0
+    ev, X, info = oracle.arnoldi_eig(A, nev=2, m=6, tol=1e-10, v0=v0)
+    assert info["status"] == -5
