@@ -90,6 +90,10 @@ extern "C" {
                              /*   the solvers iterate on A M^{-1} and report   */
                              /*   residuals of A x = b                         */
 
+/* Wanted end of the spectrum for the Arnoldi eigensolver. */
+#define XB_EIG_LR 0          /* largest real part first                        */
+#define XB_EIG_LM 1          /* largest modulus first                          */
+
 #define XB_TUNER_NONE 0      /* fixed variant (options.variant or default)     */
 #define XB_TUNER_EXHAUSTIVE 1 /* time every candidate (Sec. 3.1)              */
 #define XB_TUNER_MLP 2       /* learned tuner (xb_mlp_*)                       */
@@ -316,6 +320,38 @@ int xb_orth(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, do
 int xb_lanczos(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
                int32_t maxrestart, const double *v0, double *evals, double *evecs, double *resid,
                int32_t *counts, void *stream);
+
+/* ---- restarted Arnoldi eigensolver (OpenATI_EIGENSOLVE, Sec. 2.2 / 4.3) ---
+ * nev eigenvalues of a general A at the wanted end (which = XB_EIG_LR or
+ * XB_EIG_LM) by restarted Arnoldi in Krylov-Schur form: cycles of m basis
+ * vectors (nev + 2 <= m <= min(n, 512)) orthogonalised on the device with
+ * ortho = XB_ORTHO_MGS / CGS / DGKS / BCGS / AUTO (Sec. 3.2.2; AUTO = the
+ * accuracy rule of Sec. 3.3.2); the m x m projected matrix is put in complex
+ * Schur form on the host and reordered so that the wanted eigenvalues lead;
+ * a restart keeps the real invariant subspace of the k = nev + (m - nev)/2
+ * leading ones (k + 1 when k would split a conjugate pair).  Stops when every
+ * wanted Ritz pair has residual ||A y - theta y|| <= tol |theta| or after
+ * maxrestart restarts.  m_max > m turns on the restart rule (Eq. 1, Sec. 4.3)
+ * exactly as for xb_lanczos.  v0: DEVICE start vector (n) or NULL for a fixed
+ * pseudo-random one.  evals_re, evals_im, resid: HOST arrays (nev), wanted
+ * order; a conjugate pair is adjacent, positive imaginary part first.
+ * evecs_re / evecs_im: DEVICE n x nev column-major real and imaginary parts of
+ * the unit Ritz vectors (either may be NULL).  counts: HOST int[3] = {Arnoldi
+ * steps (SpMVs), restarts, final m} or NULL.  Returns XB_OK, XB_ENOCONV,
+ * XB_EBREAKDOWN (the start vector spans an invariant subspace of dimension
+ * < m) or XB_EINVAL.  Synchronises the stream. */
+int xb_arnoldi(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
+               int32_t maxrestart, int32_t which, int32_t ortho, const double *v0,
+               double *evals_re, double *evals_im, double *evecs_re, double *evecs_im,
+               double *resid, int32_t *counts, void *stream);
+
+/* Eigen-decomposition of a small general matrix, the dense step inside
+ * xb_arnoldi (host code, no device work): A is a HOST row-major n x n array
+ * (1 <= n <= 512); eigenvalues wr + i wi (HOST, n) in the order of `which`,
+ * conjugate pairs adjacent; vr / vi (HOST n x n column-major, both or
+ * neither NULL) the unit eigenvectors, largest entry real and positive. */
+int xb_dense_eig(int32_t n, const double *A, int32_t which, double *wr, double *wi, double *vr,
+                 double *vi);
 
 /* ---- ILU(0) preconditioner (Sec. 4.3) -------------------------------------
  * Built once per plan on first use (dependency levels of the two triangles

@@ -23,6 +23,7 @@ VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile
 ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
 POLICY_NONE, POLICY_TIME, POLICY_ACCURACY, POLICY_MEMORY, POLICY_STABLE = 0, 1, 2, 3, 4
 PRECOND_NONE, PRECOND_ILU0 = 0, 1
+EIG_LR, EIG_LM = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 TUNER_NONE, TUNER_EXHAUSTIVE, TUNER_MLP = 0, 1, 2
 
@@ -117,6 +118,9 @@ def lib():
         "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
         "xb_lanczos": (i32, [vp, i32, i32, i32, f64, f64, i32, vp, P(f64), vp, P(f64), P(i32),
                              vp]),
+        "xb_arnoldi": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, i32, vp, P(f64), P(f64), vp,
+                             vp, P(f64), P(i32), vp]),
+        "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
         "xb_ilu0_factors": (i32, [vp, vp, vp]),
@@ -354,6 +358,35 @@ class Plan:
                     resid=np.array(rs[:]))
         return np.array(ev[:]), (vec.T if vectors else None), info
 
+    def arnoldi(self, nev=10, m=20, tol=1e-8, maxrestart=1000, v0=None, vectors=True,
+                m_max=None, theta=10.0, which=EIG_LR, ortho=ORTHO_DGKS, stream=None):
+        """nev eigenvalues of a general A at the wanted end (EIG_LR: largest
+        real part, EIG_LM: largest modulus) by restarted Arnoldi; returns
+        (evals complex numpy (nev), evecs complex n x nev or None, info dict)."""
+        import numpy as np
+        import torch
+        dev = self._keep[2].device
+        if v0 is not None:
+            _need(v0, torch.float64, "v0")
+        er = (C.c_double * nev)()
+        ei = (C.c_double * nev)()
+        rs = (C.c_double * nev)()
+        cnt = (C.c_int32 * 3)()
+        vr = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
+        vi = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
+        code = lib().xb_arnoldi(self._h, nev, m, m if m_max is None else m_max, theta, tol,
+                                maxrestart, int(which), int(ortho),
+                                _ptr(v0) if v0 is not None else None, er, ei,
+                                _ptr(vr) if vectors else None, _ptr(vi) if vectors else None,
+                                rs, cnt, _stream(stream))
+        if code in (XB_EINVAL, XB_ENOMEM, XB_ECUDA):
+            raise XbError(code, last_error())
+        info = dict(status=code, steps=cnt[0], restarts=cnt[1], m_final=cnt[2],
+                    resid=np.array(rs[:]))
+        ev = np.array(er[:]) + 1j * np.array(ei[:])
+        vec = torch.complex(vr, vi).T if vectors else None
+        return ev, vec, info
+
     def ilu0_setup(self, stream=None):
         _check(lib().xb_ilu0_setup(self._h, _stream(stream)))
 
@@ -392,6 +425,22 @@ def features(rowptr, col, val, sym_upper=False, stream=None):
     feat = (C.c_float * 8)()
     _check(lib().xb_features(C.byref(csr), raw, feat, _stream(stream)))
     return np.array(raw[:]), np.array(feat[:], dtype=np.float32)
+
+
+def dense_eig(A, which=EIG_LR, vectors=True):
+    """Eigenvalues (wanted order, conjugate pairs adjacent) and unit
+    eigenvectors (columns) of a small dense general matrix: the host step of
+    the Arnoldi eigensolver."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    P = C.POINTER(C.c_double)
+    f = lambda a: a.ctypes.data_as(P)
+    wr, wi = np.zeros(n), np.zeros(n)
+    vr, vi = (np.zeros((n, n)), np.zeros((n, n))) if vectors else (None, None)
+    _check(lib().xb_dense_eig(n, f(A), int(which), f(wr), f(wi), f(vr) if vectors else None,
+                              f(vi) if vectors else None))
+    return wr + 1j * wi, ((vr + 1j * vi).T if vectors else None)
 
 
 def mm_ratio(r, s, t):

@@ -1,7 +1,8 @@
-// Restarted Lanczos eigensolver for symmetric matrices (OpenATI_EIGENSOLVE,
-// restarted Lanczos, Sec. 2.2 / 4.3): the nev largest eigenvalues, thick
-// restart in Krylov-Schur form, full re-orthogonalisation.
+// Restarted Lanczos (symmetric) and restarted Arnoldi (general) eigensolvers
+// (OpenATI_EIGENSOLVE, Sec. 2.2 / 4.3), both restarted in Krylov-Schur form
+// with full re-orthogonalisation on the device.
 //
+// Lanczos: the nev largest eigenvalues, thick restart.
 // A cycle extends the orthonormal basis v_0..v_m: w = A v_j (the plan's SpMV,
 // general or symmetric storage), w orthogonalised against every basis vector
 // with DGKS on the device (the coefficients are column j of the projected
@@ -12,6 +13,7 @@
 // k = nev + (m - nev)/2 leading Ritz vectors (V S_k, one device pass over the
 // basis), moves v_m to v_k, and T restarts as diag(theta) with row k holding
 // beta_m s_{m-1,i}.
+#include "deig.cuh"
 #include "krylov.cuh"
 
 #include <algorithm>
@@ -252,6 +254,174 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
             T[(size_t)i * (M + 1) + i] = w[i];
             T[(size_t)k * (M + 1) + i] = beta * S[(size_t)i * m + m - 1];
         }
+        m = m_next;
+        restarts++;
+    }
+    if (counts) {
+        counts[0] = steps;
+        counts[1] = restarts;
+        counts[2] = m;
+    }
+    XB_CUDA(cudaStreamSynchronize(s));
+    return status;
+}
+
+// Restarted Arnoldi.  A cycle extends v_0..v_m as Lanczos does, with the
+// caller's Gram-Schmidt variant; the coefficients fill the m x m projected
+// matrix H.  On the host H = Z T Z^H (complex Schur form), reordered so that
+// the wanted eigenvalues lead; Ritz pair i has residual |h_{m,m-1}| |e_m^T y_i|
+// with y_i the unit eigenvector of H.  A restart keeps the real invariant
+// subspace Q (m x k, orthonormal) of the k leading eigenvalues: V_k <- V_m Q
+// (one device pass), v_k <- v_m, and H restarts as Q^T H Q with row k holding
+// h_{m,m-1} e_m^T Q, so A V_k = V_k (Q^T H Q) + v_k (row k) holds again.
+int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
+               int32_t maxrestart, int32_t which, int32_t ortho, const double *v0,
+               double *evals_re, double *evals_im, double *evecs_re, double *evecs_im,
+               double *resid, int32_t *counts, void *stream) {
+    if (m_max < m) m_max = m;
+    if (!p || nev < 1 || m < nev + 2 || m_max > 512 || m_max > p->n || !(tol > 0.0) ||
+        maxrestart < 0 || !evals_re || !evals_im || !resid ||
+        (which != XB_EIG_LR && which != XB_EIG_LM) || ortho < XB_ORTHO_MGS ||
+        ortho > XB_ORTHO_AUTO)
+        return xb::set_error(XB_EINVAL, "arnoldi: bad argument");
+    ortho = xb::ortho_choice(ortho, tol, false);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = p->n;
+    const int64_t ld = (n + 63) / 64 * 64;
+    const int M = m_max;
+    const int kmax = std::min(M - 1, nev + (M - nev) / 2 + 1);
+    const size_t vbytes = (size_t)(M + 1 + kmax) * ld * sizeof(double);
+    // dS holds Q (m x k) or the real and imaginary Ritz coefficients (2 x m x nev)
+    const size_t need = vbytes + xb::gm_doubles(M) * sizeof(double) + (size_t)2 * M * M * 8 + 256;
+    XB_TRY(xb::ensure_work(p, need));
+    double *V = static_cast<double *>(p->d_work);
+    double *Y = V + (size_t)(M + 1) * ld;
+    double *gm = Y + (size_t)kmax * ld;
+    xb::GmDev st = xb::gm_layout(gm, M);
+    double *dS = gm + xb::gm_doubles(M);
+    XB_CUDA(cudaMemsetAsync(gm, 0, xb::gm_doubles(M) * sizeof(double), s));
+    std::vector<double> ones(M + 1, 1.0);
+    XB_CUDA(cudaMemcpyAsync(st.sc, ones.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                            s));
+    double misc[xb::GM_NMISC] = {0};
+    misc[xb::GM_BNORM] = 1.0;
+    misc[xb::GM_TAU] = -1.0;
+    misc[xb::GM_RAW] = 1.0;
+    XB_CUDA(cudaMemcpyAsync(st.misc, misc, sizeof misc, cudaMemcpyHostToDevice, s));
+    const int sg = std::max(1, (int)std::min<int64_t>((n + 255) / 256, xb::num_sms() * 8LL));
+    if (v0) XB_CUDA(cudaMemcpyAsync(V, v0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else k_start_vector<<<sg, 256, 0, s>>>(n, V);
+    XB_TRY(xb::vnrm2(p, n, V, st.y, s));
+    k_scale_inv<<<sg, 256, 0, s>>>(n, V, st.y);
+    XB_LAUNCHED("k_scale_inv");
+
+    const int variant = p->variant;
+    std::vector<double> T((size_t)(M + 1) * (M + 1), 0.0), H((size_t)(M + 1) * M), a, Q, AQ, S;
+    std::vector<xb::cplx> TS, Z, w, y;
+    std::vector<int> ord;
+    std::vector<signed char> kind;
+    int k = 0, steps = 0, restarts = 0, status = XB_ENOCONV, K = 0;
+    double beta = 0.0, samp[5];
+    for (;;) {
+        for (int j = k; j < m; j++) {
+            double *vj = V + (size_t)j * ld, *wv = V + (size_t)(j + 1) * ld;
+            XB_TRY(xb::spmv_launch(p, variant, p->block, p->ipt, 1.0, vj, 0.0, wv, s));
+            XB_TRY(xb::gm_ortho_step<double>(p, st, n, V, ld, wv, j, ortho, s));
+            k_scale_inv<<<sg, 256, 0, s>>>(n, wv, st.H + (size_t)j * (M + 1) + j + 1);
+            steps++;
+        }
+        XB_CUDA(cudaMemcpyAsync(H.data(), st.H, H.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                s));
+        XB_CUDA(cudaStreamSynchronize(s));
+        for (int j = k; j < m; j++)
+            for (int i = 0; i <= j + 1; i++)
+                T[(size_t)i * (M + 1) + j] = H[(size_t)j * (M + 1) + i];
+        beta = T[(size_t)m * (M + 1) + m - 1];
+        bool broke = false;
+        for (int j = k; j < m; j++)
+            if (!(T[(size_t)(j + 1) * (M + 1) + j] > 0.0)) broke = true;
+        if (broke) {
+            status = XB_EBREAKDOWN;
+            xb::set_error(XB_EBREAKDOWN, "arnoldi: invariant subspace before %d steps", m);
+            break;
+        }
+        a.assign((size_t)m * m, 0.0);
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++) a[(size_t)i * m + j] = T[(size_t)i * (M + 1) + j];
+        XB_TRY(xb::schur(m, a.data(), TS, Z));
+        xb::eig_order(m, TS, which, ord, kind, w);
+        // kept Ritz values: k = nev + (m - nev)/2, moved by one so that no
+        // conjugate pair is split
+        int kk = nev + (m - nev) / 2;
+        if (kind[kk - 1] == 1) kk = kk + 1 <= m - 1 ? kk + 1 : kk - 1;
+        xb::schur_reorder(m, TS, Z, ord, kk);
+        bool conv = true;
+        S.assign((size_t)2 * m * nev, 0.0);
+        for (int i = 0; i < nev; i++) {
+            xb::schur_eigvec(m, TS, Z, i, kind[i] == 0, y);
+            evals_re[i] = w[i].real();
+            evals_im[i] = w[i].imag();
+            resid[i] = std::fabs(beta) * std::abs(y[m - 1]);
+            if (!(resid[i] <= tol * std::abs(w[i]))) conv = false;
+            for (int r = 0; r < m; r++) {
+                S[(size_t)i * m + r] = y[r].real();
+                S[(size_t)(nev + i) * m + r] = y[r].imag();
+            }
+        }
+        if (conv || restarts >= maxrestart) {
+            status = conv ? XB_OK : XB_ENOCONV;
+            if (evecs_re || evecs_im) {
+                XB_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, s));
+                if (evecs_re) XB_TRY(rotate(n, m, nev, V, ld, dS, evecs_re, n, s));
+                if (evecs_im)
+                    XB_TRY(rotate(n, m, nev, V, ld, dS + (size_t)m * nev, evecs_im, n, s));
+            }
+            break;
+        }
+        // restart rule (Eq. 1), as for Lanczos
+        int m_next = m;
+        if (m_max > m || K > 0) {
+            double worst = 0.0;
+            for (int i = 0; i < nev; i++) worst = std::max(worst, resid[i] / std::abs(w[i]));
+            samp[K++] = worst;
+            if (K == 5) {
+                if (xb_dafrt(5, samp, theta)) m_next = std::min(m + 5, m_max);
+                K = 0;
+            }
+        }
+        const int got = xb::real_basis(m, Z, kk, Q);
+        if (got < nev) {
+            status = XB_EBREAKDOWN;
+            xb::set_error(XB_EBREAKDOWN, "arnoldi: kept Schur vectors lost rank (%d < %d)", got,
+                          nev);
+            break;
+        }
+        kk = got;
+        // T_k = Q^T H Q and the coupling row h_{m,m-1} e_m^T Q
+        AQ.assign((size_t)m * kk, 0.0);
+        for (int c = 0; c < kk; c++)
+            for (int r = 0; r < m; r++) {
+                double acc = 0.0;
+                for (int l = 0; l < m; l++) acc += a[(size_t)r * m + l] * Q[(size_t)c * m + l];
+                AQ[(size_t)c * m + r] = acc;
+            }
+        std::fill(T.begin(), T.end(), 0.0);
+        for (int i = 0; i < kk; i++)
+            for (int c = 0; c < kk; c++) {
+                double acc = 0.0;
+                for (int r = 0; r < m; r++) acc += Q[(size_t)i * m + r] * AQ[(size_t)c * m + r];
+                T[(size_t)i * (M + 1) + c] = acc;
+            }
+        for (int c = 0; c < kk; c++) T[(size_t)kk * (M + 1) + c] = beta * Q[(size_t)c * m + m - 1];
+        XB_CUDA(cudaMemcpyAsync(dS, Q.data(), (size_t)m * kk * sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+        XB_TRY(rotate(n, m, kk, V, ld, dS, Y, ld, s));
+        XB_CUDA(cudaMemcpyAsync(V, Y, (size_t)kk * ld * sizeof(double), cudaMemcpyDeviceToDevice,
+                                s));
+        XB_CUDA(cudaMemcpyAsync(V + (size_t)kk * ld, V + (size_t)m * ld, ld * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        k = kk;
         m = m_next;
         restarts++;
     }

@@ -1,5 +1,6 @@
 """Pins of the oracle's restarted Arnoldi eigensolver (OpenATI_EIGENSOLVE,
-restarted Arnoldi for unsymmetric matrices, Sec. 2.2 / 4.3):
+restarted Arnoldi for unsymmetric matrices, Sec. 2.2 / 4.3), and of the
+library's host-side dense eigen step against numpy:
   - block upper-triangular matrices whose spectrum is fixed by construction
     (1 x 1 blocks a, 2 x 2 blocks [[a, b], [-b, a]] -> a +- ib): the wanted
     eigenvalues, largest real part and largest modulus, complex pairs included;
@@ -102,3 +103,40 @@ def test_invariant_start_vector_breaks_down():
     v0[3] = 1.0
     ev, X, info = oracle.arnoldi_eig(A, nev=2, m=6, tol=1e-10, v0=v0)
     assert info["status"] == -5
+
+
+def test_dense_eig_host_step_matches_numpy():
+    """The library's host-side dense eigen step (Schur form, ordering,
+    eigenvectors) against numpy: host logic only, no device work."""
+    import paper_2405_01599_gb300 as xb
+    try:
+        xb.lib()
+    except ImportError:
+        pytest.skip("CUDA library not built")
+    rng = np.random.default_rng(11)
+    for trial in range(60):
+        n = int(rng.integers(1, 50))
+        kind = trial % 4
+        if kind == 0:
+            D = rng.standard_normal((n, n))
+        elif kind == 1:
+            D = np.triu(rng.standard_normal((n, n)), -1)
+        elif kind == 2:
+            B = rng.standard_normal((n, n))
+            D = B + B.T
+        else:
+            D = np.diag(rng.integers(-3, 3, n).astype(float))  # repeated eigenvalues
+        for which in (xb.EIG_LR, xb.EIG_LM):
+            w, V = xb.dense_eig(D, which)
+            e = np.linalg.eigvals(D)
+            ref = e[oracle.wanted_order(e, which)]
+            sc = max(1.0, np.max(np.abs(e)))
+            key = lambda z: sorted(z, key=lambda c: (round(c.real, 7), round(c.imag, 7)))
+            assert np.max(np.abs(np.array(key(w)) - np.array(key(ref)))) <= 1e-10 * sc
+            k = np.abs(w) if which == xb.EIG_LM else w.real
+            assert np.all(np.diff(k) <= 1e-9 * sc)
+            assert np.max(np.abs(D @ V - V * w)) <= 1e-10 * sc
+            np.testing.assert_allclose(np.linalg.norm(V, axis=0), 1.0, atol=1e-12)
+            for t in range(n):  # conjugate pairs adjacent, positive imaginary part first
+                if w[t].imag > 0:
+                    assert t + 1 < n and w[t + 1] == np.conj(w[t])
