@@ -52,13 +52,16 @@ def parse():
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed steps (for ncu captures); prints a short line")
     ap.add_argument("--matrix", default="c3",
-                    choices=["c3", "c2-upper", "c2-full", "c4", "c4-160"],
+                    choices=["c3", "c2-upper", "c2-full", "c4", "c4-160", "c2-box"],
                     help="profile-only: power-law n (c3), 128^3 Laplacian upper/full (c2), "
-                         "256^3 (c4) or 160^3 (c4-160) convection-diffusion")
+                         "256^3 (c4) or 160^3 (c4-160) convection-diffusion, 120 x 128 x 136 "
+                         "convection-diffusion box (c2-box)")
     ap.add_argument("--gmres-steps", type=int, default=0,
                     help="profile-only: run this many GMRES(30) Arnoldi steps instead of SpMVs")
+    ap.add_argument("--eig-restarts", type=int, default=0,
+                    help="profile-only: run this many restarts of Arnoldi (nev 10, m 40)")
     ap.add_argument("--ortho", default="mgs", choices=["mgs", "cgs", "dgks", "bcgs"],
-                    help="profile-only GMRES: orthogonalisation")
+                    help="profile-only GMRES / Arnoldi: orthogonalisation")
     ap.add_argument("--ilu", action="store_true",
                     help="profile-only GMRES: ILU(0) right preconditioning")
     ap.add_argument("--mixed", action="store_true",
@@ -268,7 +271,8 @@ def main():
         from paper_2405_01599_gb300 import gen
         A = {"c2-upper": lambda: gen.laplace3d(128, upper=True), "c2-full": lambda: gen.laplace3d(128),
              "c4": lambda: gen.convdiff3d(N=256),
-             "c4-160": lambda: gen.convdiff3d(N=160)}[args.matrix]()
+             "c4-160": lambda: gen.convdiff3d(N=160),
+             "c2-box": lambda: gen.convdiff3d(128, pe=10.0, dims=(120, 128, 136))}[args.matrix]()
     else:
         A = make_c3(args.n)
     n, nnz = A["n"], A["nnz"]
@@ -280,6 +284,18 @@ def main():
         choice = plan.choice()
     else:
         choice = plan.tune()
+    if args.profile_only and args.eig_restarts:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, _, ainfo = plan.arnoldi(nev=10, m=40, tol=1e-30, maxrestart=args.eig_restarts,
+                                    vectors=False,
+                                    ortho=["mgs", "cgs", "dgks", "bcgs"].index(args.ortho))
+        el = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "matrix": args.matrix,
+                              "arnoldi_steps": ainfo["steps"], "restarts": ainfo["restarts"],
+                              "s": el, "choice": choice}))
+        return
     if args.profile_only and args.gmres_steps:
         bvec = torch.empty(n, dtype=torch.float64, device=dev)
         plan.spmv(torch.ones(n, dtype=torch.float64, device=dev), bvec)

@@ -45,34 +45,35 @@ __global__ void k_start_vector(int64_t n, double *__restrict__ x) {
     }
 }
 
-// Y[c] = sum_{i < m} V[i] S[i][c] for the kRotC outputs c of this CTA's
-// column block (blockIdx.y); S is m x kc column-major (leading dimension m),
-// staged in shared memory.
-__global__ void __launch_bounds__(256) k_rotate(int64_t n, int m, int kc,
+// Y[c] = sum_{i < m} V[i] S[i][c] for the RC outputs c = c_base + RC * blockIdx.y + 0..RC-1
+// of this CTA; S is m x kc column-major (leading dimension m), the CTA's RC
+// columns staged in shared memory.  RC is exact (a tail of kc % kRotC columns
+// gets its own instantiation): the kernel is bound by the FP64 FMA pipe, so
+// no padded column is computed.
+template <int RC>
+__global__ void __launch_bounds__(256) k_rotate(int64_t n, int m, int c_base,
                                                 const double *__restrict__ V, int64_t ld,
                                                 const double *__restrict__ S,
                                                 double *__restrict__ Y, int64_t ldy) {
-    extern __shared__ double ss[];  // m x kRotC
-    const int c0 = blockIdx.y * kRotC;
-    const int nc = min(kRotC, kc - c0);
-    for (int t = threadIdx.x; t < m * kRotC; t += blockDim.x) {
-        const int i = t / kRotC, c = t % kRotC;
-        ss[t] = c < nc ? S[(size_t)(c0 + c) * m + i] : 0.0;
+    extern __shared__ double ss[];  // m x RC
+    const int c0 = c_base + blockIdx.y * RC;
+    for (int t = threadIdx.x; t < m * RC; t += blockDim.x) {
+        const int i = t / RC, c = t % RC;
+        ss[t] = S[(size_t)(c0 + c) * m + i];
     }
     __syncthreads();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        double acc[kRotC];
+        double acc[RC];
 #pragma unroll
-        for (int c = 0; c < kRotC; c++) acc[c] = 0.0;
+        for (int c = 0; c < RC; c++) acc[c] = 0.0;
         for (int i = 0; i < m; i++) {
             const double v = V[(size_t)i * ld + e];
 #pragma unroll
-            for (int c = 0; c < kRotC; c++) acc[c] = fma(v, ss[i * kRotC + c], acc[c]);
+            for (int c = 0; c < RC; c++) acc[c] = fma(v, ss[i * RC + c], acc[c]);
         }
 #pragma unroll
-        for (int c = 0; c < kRotC; c++)
-            if (c < nc) Y[(size_t)(c0 + c) * ldy + e] = acc[c];
+        for (int c = 0; c < RC; c++) Y[(size_t)(c0 + c) * ldy + e] = acc[c];
     }
 }
 
@@ -129,12 +130,30 @@ void jacobi_eig(int m, std::vector<double> &a, std::vector<double> &w, std::vect
     s.swap(s2);
 }
 
+template <int RC>
+void rotate_cols(int64_t n, int m, int c_base, int blocks, int gx, const double *V, int64_t ld,
+                 const double *dS, double *Y, int64_t ldy, cudaStream_t s) {
+    k_rotate<RC><<<dim3(gx, blocks), 256, (size_t)m * RC * sizeof(double), s>>>(n, m, c_base, V,
+                                                                               ld, dS, Y, ldy);
+}
+
+// Y (kc columns, stride ldy) = V (m rows, stride ld) times the m x kc matrix dS.
 int rotate(int64_t n, int m, int kc, const double *V, int64_t ld, const double *dS, double *Y,
            int64_t ldy, cudaStream_t s) {
     if (kc <= 0) return XB_OK;
-    const int gx = (int)std::min<int64_t>((n + 255) / 256, (int64_t)xb::num_sms() * 4);
-    dim3 grid(std::max(1, gx), (kc + kRotC - 1) / kRotC);
-    k_rotate<<<grid, 256, (size_t)m * kRotC * sizeof(double), s>>>(n, m, kc, V, ld, dS, Y, ldy);
+    const int gx = std::max(1, (int)std::min<int64_t>((n + 255) / 256, (int64_t)xb::num_sms() * 4));
+    const int full = kc / kRotC, c0 = full * kRotC;
+    if (full) rotate_cols<kRotC>(n, m, 0, full, gx, V, ld, dS, Y, ldy, s);
+    switch (kc - c0) {
+    case 1: rotate_cols<1>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    case 2: rotate_cols<2>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    case 3: rotate_cols<3>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    case 4: rotate_cols<4>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    case 5: rotate_cols<5>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    case 6: rotate_cols<6>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    case 7: rotate_cols<7>(n, m, c0, 1, gx, V, ld, dS, Y, ldy, s); break;
+    default: break;
+    }
     XB_LAUNCHED("k_rotate");
     return XB_OK;
 }
