@@ -541,6 +541,23 @@ def extras(xb, torch, dev, plan, A, x, y, args):
                       "lambda_max": float(ev[0].real),
                       "lambda_max_err_vs_closed_form": float(abs(ev[0] - lam_top)),
                       "max_abs_imag": float(np.max(np.abs(ev.imag)))}
+    # the numerical computation policies on the same eigenproblem (the paper's
+    # Fig. 9-11: time, memory and accuracy of Arnoldi under each policy)
+    pol = {}
+    for name, code in (("TIME", xb.POLICY_TIME), ("MEMORY", xb.POLICY_MEMORY),
+                       ("ACCURACY", xb.POLICY_ACCURACY), ("STABLE", xb.POLICY_STABLE)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, _, ainfo = pc.arnoldi(nev=10, m=40, tol=1e-8, vectors=False, policy=code,
+                                  maxrestart=3000)
+        torch.cuda.synchronize()
+        pol[name] = {"s": time.perf_counter() - t0, "status": ainfo["status"],
+                     "steps": ainfo["steps"], "restarts": ainfo["restarts"],
+                     "m_final": ainfo["m_final"], "ortho_used": ainfo["ortho_used"],
+                     "outer": ainfo["outer"], "mem_GB": ainfo["mem_bytes"] / 1e9,
+                     "true_resid_max": ainfo["true_resid"],
+                     "lambda_max_err_vs_closed_form": float(abs(ev[0] - lam_top))}
+    res["c2_arnoldi_convdiff_box_policies"] = pol
     del pc, CB
     # config 1: 64x64 Poisson GMRES(30) to 1e-8, b = A*ones, x0 = 0
     P = gen.poisson2d(64)

@@ -332,18 +332,30 @@ int xb_lanczos(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double thet
  * leading ones (k + 1 when k would split a conjugate pair).  Stops when every
  * wanted Ritz pair has residual ||A y - theta y|| <= tol |theta| or after
  * maxrestart restarts.  m_max > m turns on the restart rule (Eq. 1, Sec. 4.3)
- * exactly as for xb_lanczos.  v0: DEVICE start vector (n) or NULL for a fixed
- * pseudo-random one.  evals_re, evals_im, resid: HOST arrays (nev), wanted
- * order; a conjugate pair is adjacent, positive imaginary part first.
+ * exactly as for xb_lanczos.  policy (Sec. 2.3.2, 3.3): XB_POLICY_NONE runs
+ * the arguments as given; TIME tunes the SpMV (exhaustive), turns the restart
+ * rule on with m_max >= 128 and picks the Gram-Schmidt by the accuracy rule;
+ * MEMORY uses the SpMV without plan metadata (U1, S1 for sym_upper), a fixed
+ * m = max(nev + 2, min(m, 20)) and MGS; STABLE keeps the plan's SpMV and m,
+ * MGS, no rule; ACCURACY is TIME plus the outer loop of Sec. 3.3.2.  Under
+ * every policy but NONE, a claimed convergence is checked with the true
+ * residuals ||A y - theta y|| / |theta| (2 nev SpMVs): ACCURACY narrows the
+ * threshold by tol / (worst true residual), switches to DGKS and iterates
+ * on; the others return XB_EFAULT.  v0: DEVICE start vector (n) or NULL for
+ * a fixed pseudo-random one.  evals_re, evals_im, resid: HOST arrays (nev),
+ * wanted order; a conjugate pair is adjacent, positive imaginary part first.
  * evecs_re / evecs_im: DEVICE n x nev column-major real and imaginary parts of
- * the unit Ritz vectors (either may be NULL).  counts: HOST int[3] = {Arnoldi
- * steps (SpMVs), restarts, final m} or NULL.  Returns XB_OK, XB_ENOCONV,
+ * the unit Ritz vectors (either may be NULL).  counts: HOST int[5] = {Arnoldi
+ * steps (SpMVs), restarts, final m, Gram-Schmidt used at the end, outer
+ * passes} or NULL.  stats: HOST double[2] = {device bytes of the call's
+ * workspace and SpMV metadata, worst true relative residual of the last check
+ * (-1 if none)} or NULL.  Returns XB_OK, XB_ENOCONV, XB_EFAULT,
  * XB_EBREAKDOWN (the start vector spans an invariant subspace of dimension
  * < m) or XB_EINVAL.  Synchronises the stream. */
 int xb_arnoldi(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
-               int32_t maxrestart, int32_t which, int32_t ortho, const double *v0,
+               int32_t maxrestart, int32_t which, int32_t ortho, int32_t policy, const double *v0,
                double *evals_re, double *evals_im, double *evecs_re, double *evecs_im,
-               double *resid, int32_t *counts, void *stream);
+               double *resid, int32_t *counts, double *stats, void *stream);
 
 /* Eigen-decomposition of a small general matrix, the dense step inside
  * xb_arnoldi (host code, no device work): A is a HOST row-major n x n array

@@ -118,8 +118,8 @@ def lib():
         "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
         "xb_lanczos": (i32, [vp, i32, i32, i32, f64, f64, i32, vp, P(f64), vp, P(f64), P(i32),
                              vp]),
-        "xb_arnoldi": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, i32, vp, P(f64), P(f64), vp,
-                             vp, P(f64), P(i32), vp]),
+        "xb_arnoldi": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, i32, i32, vp, P(f64), P(f64),
+                             vp, vp, P(f64), P(i32), P(f64), vp]),
         "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
@@ -359,10 +359,12 @@ class Plan:
         return np.array(ev[:]), (vec.T if vectors else None), info
 
     def arnoldi(self, nev=10, m=20, tol=1e-8, maxrestart=1000, v0=None, vectors=True,
-                m_max=None, theta=10.0, which=EIG_LR, ortho=ORTHO_DGKS, stream=None):
+                m_max=None, theta=10.0, which=EIG_LR, ortho=ORTHO_DGKS, policy=POLICY_NONE,
+                stream=None):
         """nev eigenvalues of a general A at the wanted end (EIG_LR: largest
-        real part, EIG_LM: largest modulus) by restarted Arnoldi; returns
-        (evals complex numpy (nev), evecs complex n x nev or None, info dict)."""
+        real part, EIG_LM: largest modulus) by restarted Arnoldi, under an
+        optional numerical computation policy; returns (evals complex numpy
+        (nev), evecs complex n x nev or None, info dict)."""
         import numpy as np
         import torch
         dev = self._keep[2].device
@@ -371,17 +373,19 @@ class Plan:
         er = (C.c_double * nev)()
         ei = (C.c_double * nev)()
         rs = (C.c_double * nev)()
-        cnt = (C.c_int32 * 3)()
+        cnt = (C.c_int32 * 5)()
+        sts = (C.c_double * 2)()
         vr = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
         vi = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
         code = lib().xb_arnoldi(self._h, nev, m, m if m_max is None else m_max, theta, tol,
-                                maxrestart, int(which), int(ortho),
+                                maxrestart, int(which), int(ortho), int(policy),
                                 _ptr(v0) if v0 is not None else None, er, ei,
                                 _ptr(vr) if vectors else None, _ptr(vi) if vectors else None,
-                                rs, cnt, _stream(stream))
+                                rs, cnt, sts, _stream(stream))
         if code in (XB_EINVAL, XB_ENOMEM, XB_ECUDA):
             raise XbError(code, last_error())
         info = dict(status=code, steps=cnt[0], restarts=cnt[1], m_final=cnt[2],
+                    ortho_used=cnt[3], outer=cnt[4], mem_bytes=sts[0], true_resid=sts[1],
                     resid=np.array(rs[:]))
         ev = np.array(er[:]) + 1j * np.array(ei[:])
         vec = torch.complex(vr, vi).T if vectors else None

@@ -168,6 +168,9 @@ int spmv_launch_f32(xb_plan *p, int variant, int block, int ipt, float alpha, co
 // Algorithmic bytes of one SpMV (val+col once, rowptr once, x once, y once,
 // y read again when beta != 0).
 double spmv_alg_bytes(const xb_plan *p, bool beta_nonzero, int val_bytes);
+// Device bytes of the plan data a variant reads besides the matrix (tile
+// starts, BSS bitmask and warp rows, segment tables).
+double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt);
 
 // ---- vector kernels (vec.cu) ------------------------------------------------
 // Deterministic reductions write their result to a device double.

@@ -293,31 +293,76 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
 // subspace Q (m x k, orthonormal) of the k leading eigenvalues: V_k <- V_m Q
 // (one device pass), v_k <- v_m, and H restarts as Q^T H Q with row k holding
 // h_{m,m-1} e_m^T Q, so A V_k = V_k (Q^T H Q) + v_k (row k) holds again.
+//
+// Numerical computation policy (Sec. 2.3.2, 3.3; Fig. 9-11 run Arnoldi under
+// each): TIME tunes the SpMV, turns the restart rule on (m_max >= 128) and
+// takes the accuracy rule's Gram-Schmidt; MEMORY takes the SpMV without plan
+// metadata and a short fixed cycle (m <= 20) with MGS; STABLE keeps the
+// plan's SpMV and m, MGS; ACCURACY is TIME plus the outer loop of Sec. 3.3.2:
+// when the estimates claim convergence the true residuals ||A y - theta y||
+// are computed, and if one misses tol the iteration continues with the
+// threshold narrowed by tol / (true residual) and DGKS.  Under TIME, MEMORY
+// and STABLE the same check ends the run with XB_EFAULT instead.
 int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
-               int32_t maxrestart, int32_t which, int32_t ortho, const double *v0,
+               int32_t maxrestart, int32_t which, int32_t ortho, int32_t policy, const double *v0,
                double *evals_re, double *evals_im, double *evecs_re, double *evecs_im,
-               double *resid, int32_t *counts, void *stream) {
+               double *resid, int32_t *counts, double *stats, void *stream) {
     if (m_max < m) m_max = m;
     if (!p || nev < 1 || m < nev + 2 || m_max > 512 || m_max > p->n || !(tol > 0.0) ||
         maxrestart < 0 || !evals_re || !evals_im || !resid ||
         (which != XB_EIG_LR && which != XB_EIG_LM) || ortho < XB_ORTHO_MGS ||
-        ortho > XB_ORTHO_AUTO)
+        ortho > XB_ORTHO_AUTO || policy < XB_POLICY_NONE || policy > XB_POLICY_STABLE)
         return xb::set_error(XB_EINVAL, "arnoldi: bad argument");
-    ortho = xb::ortho_choice(ortho, tol, false);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = p->n;
+    int variant = p->variant, block = p->block, ipt = p->ipt;
+    bool check = policy != XB_POLICY_NONE;
+    const bool outer = policy == XB_POLICY_ACCURACY;
+    switch (policy) {
+        case XB_POLICY_TIME:
+        case XB_POLICY_ACCURACY:
+            XB_TRY(xb_tune_exhaustive(p, nullptr, stream));
+            variant = p->variant;
+            block = p->block;
+            ipt = p->ipt;
+            m_max = std::max<int>(m_max, (int)std::min<int64_t>(128, std::min<int64_t>(512, n)));
+            ortho = xb::ortho_choice(XB_ORTHO_AUTO, tol, false);
+            break;
+        case XB_POLICY_MEMORY:
+            variant = p->sym ? XB_VAR_SYM_ATOMIC : XB_VAR_ROW;
+            block = 256;
+            ipt = 1;
+            m = std::max(nev + 2, std::min(m, 20));
+            m_max = m;
+            ortho = XB_ORTHO_MGS;
+            break;
+        case XB_POLICY_STABLE:
+            m_max = m;
+            ortho = XB_ORTHO_MGS;
+            break;
+        default:
+            ortho = xb::ortho_choice(ortho, tol, false);
+            break;
+    }
     const int64_t ld = (n + 63) / 64 * 64;
     const int M = m_max;
     const int kmax = std::min(M - 1, nev + (M - nev) / 2 + 1);
     const size_t vbytes = (size_t)(M + 1 + kmax) * ld * sizeof(double);
-    // dS holds Q (m x k) or the real and imaginary Ritz coefficients (2 x m x nev)
-    const size_t need = vbytes + xb::gm_doubles(M) * sizeof(double) + (size_t)2 * M * M * 8 + 256;
+    // dS holds Q (m x k) or the real and imaginary Ritz coefficients (2 x m x nev);
+    // dres the true residual norms; XR, XI, TMP the Ritz vectors of the check
+    const size_t gbytes = xb::gm_doubles(M) * sizeof(double) + (size_t)2 * M * M * 8 +
+                          (size_t)2 * M * 8 + 256;
+    const size_t cbytes = check ? (size_t)(2 * nev + 1) * ld * sizeof(double) : 0;
+    const size_t need = vbytes + gbytes + cbytes;
     XB_TRY(xb::ensure_work(p, need));
     double *V = static_cast<double *>(p->d_work);
     double *Y = V + (size_t)(M + 1) * ld;
     double *gm = Y + (size_t)kmax * ld;
     xb::GmDev st = xb::gm_layout(gm, M);
     double *dS = gm + xb::gm_doubles(M);
+    double *dres = dS + (size_t)2 * M * M;
+    double *XR = reinterpret_cast<double *>(((uintptr_t)(dres + 2 * M) + 255) / 256 * 256);
+    double *XI = XR + (size_t)nev * ld, *TMP = XI + (size_t)nev * ld;
     XB_CUDA(cudaMemsetAsync(gm, 0, xb::gm_doubles(M) * sizeof(double), s));
     std::vector<double> ones(M + 1, 1.0);
     XB_CUDA(cudaMemcpyAsync(st.sc, ones.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice,
@@ -334,17 +379,26 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
     k_scale_inv<<<sg, 256, 0, s>>>(n, V, st.y);
     XB_LAUNCHED("k_scale_inv");
 
-    const int variant = p->variant;
     std::vector<double> T((size_t)(M + 1) * (M + 1), 0.0), H((size_t)(M + 1) * M), a, Q, AQ, S;
+    std::vector<double> hres(2 * (size_t)nev);
     std::vector<xb::cplx> TS, Z, w, y;
     std::vector<int> ord;
     std::vector<signed char> kind;
-    int k = 0, steps = 0, restarts = 0, status = XB_ENOCONV, K = 0;
-    double beta = 0.0, samp[5];
+    int k = 0, steps = 0, restarts = 0, status = XB_ENOCONV, K = 0, passes = 1;
+    double beta = 0.0, samp[5], tol_in = tol, true_max = -1.0;
+    // the wanted Ritz vectors of the current cycle (coefficients in dS) into
+    // (xr, xi) with column stride lx
+    auto ritz_vectors = [&](double *xr, double *xi, int64_t lx) -> int {
+        XB_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                s));
+        if (xr) XB_TRY(rotate(n, m, nev, V, ld, dS, xr, lx, s));
+        if (xi) XB_TRY(rotate(n, m, nev, V, ld, dS + (size_t)m * nev, xi, lx, s));
+        return XB_OK;
+    };
     for (;;) {
         for (int j = k; j < m; j++) {
             double *vj = V + (size_t)j * ld, *wv = V + (size_t)(j + 1) * ld;
-            XB_TRY(xb::spmv_launch(p, variant, p->block, p->ipt, 1.0, vj, 0.0, wv, s));
+            XB_TRY(xb::spmv_launch(p, variant, block, ipt, 1.0, vj, 0.0, wv, s));
             XB_TRY(xb::gm_ortho_step<double>(p, st, n, V, ld, wv, j, ortho, s));
             k_scale_inv<<<sg, 256, 0, s>>>(n, wv, st.H + (size_t)j * (M + 1) + j + 1);
             steps++;
@@ -381,21 +435,58 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
             evals_re[i] = w[i].real();
             evals_im[i] = w[i].imag();
             resid[i] = std::fabs(beta) * std::abs(y[m - 1]);
-            if (!(resid[i] <= tol * std::abs(w[i]))) conv = false;
+            if (!(resid[i] <= tol_in * std::abs(w[i]))) conv = false;
             for (int r = 0; r < m; r++) {
                 S[(size_t)i * m + r] = y[r].real();
                 S[(size_t)(nev + i) * m + r] = y[r].imag();
             }
         }
-        if (conv || restarts >= maxrestart) {
-            status = conv ? XB_OK : XB_ENOCONV;
-            if (evecs_re || evecs_im) {
-                XB_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double),
-                                        cudaMemcpyHostToDevice, s));
-                if (evecs_re) XB_TRY(rotate(n, m, nev, V, ld, dS, evecs_re, n, s));
-                if (evecs_im)
-                    XB_TRY(rotate(n, m, nev, V, ld, dS + (size_t)m * nev, evecs_im, n, s));
+        if (conv && check) {
+            // true residuals r = A x - theta x of the claimed pairs (Sec. 3.3.2)
+            XB_TRY(ritz_vectors(XR, XI, ld));
+            for (int i = 0; i < nev; i++) {
+                const double *xr = XR + (size_t)i * ld, *xi = XI + (size_t)i * ld;
+                const double tr = w[i].real(), ti = w[i].imag();
+                XB_TRY(xb::spmv_launch(p, variant, block, ipt, 1.0, xr, 0.0, TMP, s));
+                XB_TRY(xb::vaxpy(n, -tr, xr, TMP, s));
+                XB_TRY(xb::vaxpy(n, ti, xi, TMP, s));
+                XB_TRY(xb::vnrm2(p, n, TMP, dres + 2 * i, s));
+                XB_TRY(xb::spmv_launch(p, variant, block, ipt, 1.0, xi, 0.0, TMP, s));
+                XB_TRY(xb::vaxpy(n, -tr, xi, TMP, s));
+                XB_TRY(xb::vaxpy(n, -ti, xr, TMP, s));
+                XB_TRY(xb::vnrm2(p, n, TMP, dres + 2 * i + 1, s));
             }
+            XB_CUDA(cudaMemcpyAsync(hres.data(), dres, hres.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+            XB_CUDA(cudaStreamSynchronize(s));
+            true_max = 0.0;
+            for (int i = 0; i < nev; i++)
+                true_max = std::max(true_max,
+                                    std::hypot(hres[2 * i], hres[2 * i + 1]) / std::abs(w[i]));
+            if (true_max <= tol) {
+                status = XB_OK;
+            } else if (!outer) {
+                status = XB_EFAULT;
+                xb::set_error(XB_EFAULT, "fault convergence: Ritz residual estimates met tol, "
+                              "true relative residual %.3e", true_max);
+            } else {  // narrow the threshold, switch to DGKS, iterate on
+                tol_in *= tol / true_max;
+                ortho = xb::ortho_choice(XB_ORTHO_AUTO, tol, true);
+                passes++;
+                conv = false;
+            }
+            if (conv) {
+                if (evecs_re || evecs_im) XB_TRY(ritz_vectors(evecs_re, evecs_im, n));
+                break;
+            }
+        } else if (conv) {
+            status = XB_OK;
+            if (evecs_re || evecs_im) XB_TRY(ritz_vectors(evecs_re, evecs_im, n));
+            break;
+        }
+        if (restarts >= maxrestart) {
+            status = XB_ENOCONV;
+            if (evecs_re || evecs_im) XB_TRY(ritz_vectors(evecs_re, evecs_im, n));
             break;
         }
         // restart rule (Eq. 1), as for Lanczos
@@ -448,6 +539,12 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
         counts[0] = steps;
         counts[1] = restarts;
         counts[2] = m;
+        counts[3] = ortho;
+        counts[4] = passes;
+    }
+    if (stats) {
+        stats[0] = (double)need + xb::spmv_meta_bytes(p, variant, block, ipt);
+        stats[1] = true_max;
     }
     XB_CUDA(cudaStreamSynchronize(s));
     return status;

@@ -552,6 +552,10 @@ void apply_policy(xb_options &o, const xb_plan *p) {
     }
 }
 
+}  // namespace
+
+namespace xb {
+
 // Device bytes of the plan data the SpMV variant reads besides the matrix.
 double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
     double b = 0.0;
@@ -566,6 +570,10 @@ double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
     }
     return b;
 }
+
+}  // namespace xb
+
+namespace {
 
 template <typename F>
 int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb_info *info,
@@ -603,7 +611,7 @@ int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb
         inf.variant_used = o.variant == XB_VAR_AUTO ? p->variant : o.variant;
         inf.block_used = o.block > 0 ? o.block : p->block;
         inf.ipt_used = o.ipt > 0 ? o.ipt : p->ipt;
-        inf.mem_bytes = ac.mem + spmv_meta_bytes(p, inf.variant_used, inf.block_used, inf.ipt_used) +
+        inf.mem_bytes = ac.mem + xb::spmv_meta_bytes(p, inf.variant_used, inf.block_used, inf.ipt_used) +
                         (o.precision == XB_PREC_MIXED ? 4.0 * p->nnz : 0.0) +
                         (o.precond == XB_PRECOND_ILU0 ? 8.0 * p->nnz + 12.0 * p->n : 0.0);
         if (st == XB_EFAULT)

@@ -145,3 +145,48 @@ def test_arnoldi_breakdown_and_arguments(env):
     ev, Y, info = pb.arnoldi(nev=4, m=8, tol=1e-14, maxrestart=2, vectors=False)
     assert info["status"] == xb.XB_ENOCONV and info["restarts"] == 2
     assert np.all(np.isfinite(ev))
+
+
+def test_arnoldi_policies(env):
+    """Numerical computation policies (Sec. 2.3.2, 3.3) on the eigensolver:
+    every policy but NONE checks the true residuals of a claimed convergence;
+    TIME / STABLE give the oracle's eigenvalues for their settings; MEMORY
+    uses a short cycle and far less memory; ACCURACY ends within tol."""
+    import torch
+    xb, dev = env
+    A = gen.quasi_triangular(20000, seed=11)
+    n, nev, tol = A["n"], 10, 1e-8
+    v0h = np.random.default_rng(4).standard_normal(n)
+    v0 = torch.tensor(v0h, device=dev)
+    e = spectrum(A)
+    plan = xb.Plan.from_host(A, dev)
+    out = {}
+    for pol in (xb.POLICY_NONE, xb.POLICY_TIME, xb.POLICY_ACCURACY, xb.POLICY_MEMORY,
+                xb.POLICY_STABLE):
+        ev, Y, info = plan.arnoldi(nev=nev, m=40, tol=tol, v0=v0, policy=pol, maxrestart=3000,
+                                   ortho=xb.ORTHO_DGKS)
+        out[pol] = (ev, info)
+        assert info["status"] in (xb.XB_OK, xb.XB_EFAULT), (pol, info)
+        # every returned value is an eigenvalue of A (a short cycle may miss a wanted one)
+        assert np.all(np.min(np.abs(e[:, None] - ev[None, :]), axis=0) <= 1e-6), pol
+        if pol == xb.POLICY_NONE:
+            assert info["true_resid"] == -1.0 and info["outer"] == 1
+            continue
+        if info["status"] == xb.XB_OK:
+            assert 0.0 <= info["true_resid"] <= tol, (pol, info)
+        else:
+            assert info["true_resid"] > tol and pol != xb.POLICY_ACCURACY, (pol, info)
+    t, a, mem, stb = (out[p][1] for p in (xb.POLICY_TIME, xb.POLICY_ACCURACY,
+                                           xb.POLICY_MEMORY, xb.POLICY_STABLE))
+    assert t["ortho_used"] == xb.ORTHO_BCGS and stb["ortho_used"] == xb.ORTHO_MGS
+    assert mem["ortho_used"] == xb.ORTHO_MGS and mem["m_final"] == 20
+    assert stb["m_final"] == 40 and 40 <= t["m_final"] <= 128
+    assert a["status"] == xb.XB_OK
+    assert mem["mem_bytes"] < t["mem_bytes"] / 3
+    ref = e[oracle.wanted_order(e, 0)[:nev]]
+    np.testing.assert_allclose(out[xb.POLICY_TIME][0], ref, atol=1e-7)
+    np.testing.assert_allclose(out[xb.POLICY_STABLE][0], ref, atol=1e-7)
+    # STABLE = the arguments with MGS and no rule: the oracle's iteration
+    eo, _, io = oracle.arnoldi_eig(A, nev=nev, m=40, tol=tol, v0=v0h, vectors=False)
+    np.testing.assert_allclose(out[xb.POLICY_STABLE][0], eo, atol=1e-7)
+    assert abs(stb["restarts"] - io["restarts"]) <= 1, (stb, io)
