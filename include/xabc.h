@@ -310,16 +310,21 @@ int xb_orth(xb_plan *plan, int32_t n, int32_t k, const double *V, int64_t ld, do
  * m_max > m turns on the restart rule (Eq. 1, Sec. 4.3): the worst relative
  * wanted residual of each cycle is a sample, every 5 samples the MM ratio is
  * compared with theta and m grows by 5 (up to m_max <= min(n, 512)) when the
- * residuals stagnate.  The plan's SpMV choice is used.  v0: DEVICE start vector (n), or NULL for a
+ * residuals stagnate.  The plan's SpMV choice is used.  policy: as for
+ * xb_arnoldi (SpMV, cycle, restart rule, true-residual check, outer loop;
+ * MEMORY's cycle is m = max(nev + 1, min(m, 20))), but the Gram-Schmidt stays
+ * DGKS under every policy.  v0: DEVICE start vector (n), or NULL for a
  * fixed pseudo-random one.  evals, resid: HOST arrays (nev), largest first;
  * evecs: DEVICE n x nev column-major (unit Ritz vectors) or NULL; counts:
- * HOST int[3] = {Lanczos steps (SpMVs), restarts, final m} or NULL.  Returns XB_OK,
- * XB_ENOCONV (restart limit; evals hold the current Ritz values) or
+ * HOST int[5] = {Lanczos steps (SpMVs), restarts, final m, Gram-Schmidt used
+ * at the end, outer passes} or NULL; stats: HOST double[2] as for xb_arnoldi
+ * or NULL.  Returns XB_OK, XB_ENOCONV (restart limit; evals hold the current
+ * Ritz values), XB_EFAULT (a policy's true-residual check failed) or
  * XB_EBREAKDOWN (the start vector spans an invariant subspace of dimension
  * < m).  Synchronises the stream. */
 int xb_lanczos(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double theta, double tol,
-               int32_t maxrestart, const double *v0, double *evals, double *evecs, double *resid,
-               int32_t *counts, void *stream);
+               int32_t maxrestart, int32_t policy, const double *v0, double *evals,
+               double *evecs, double *resid, int32_t *counts, double *stats, void *stream);
 
 /* ---- restarted Arnoldi eigensolver (OpenATI_EIGENSOLVE, Sec. 2.2 / 4.3) ---
  * nev eigenvalues of a general A at the wanted end (which = XB_EIG_LR or

@@ -116,8 +116,8 @@ def lib():
         "xb_axpy": (i32, [i32, f64, vp, vp, vp]),
         "xb_mgs": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, vp]),
         "xb_orth": (i32, [vp, i32, i32, vp, C.c_int64, vp, vp, i32, vp]),
-        "xb_lanczos": (i32, [vp, i32, i32, i32, f64, f64, i32, vp, P(f64), vp, P(f64), P(i32),
-                             vp]),
+        "xb_lanczos": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, vp, P(f64), vp, P(f64),
+                             P(i32), P(f64), vp]),
         "xb_arnoldi": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, i32, i32, vp, P(f64), P(f64),
                              vp, vp, P(f64), P(i32), P(f64), vp]),
         "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
@@ -336,9 +336,10 @@ class Plan:
         return h
 
     def lanczos(self, nev=10, m=40, tol=1e-8, maxrestart=1000, v0=None, vectors=True,
-                m_max=None, theta=10.0, stream=None):
-        """The nev largest eigenvalues (thick-restart Lanczos); returns
-        (evals, evecs n x nev or None, info dict)."""
+                m_max=None, theta=10.0, policy=POLICY_NONE, stream=None):
+        """The nev largest eigenvalues (thick-restart Lanczos), under an optional
+        numerical computation policy; returns (evals, evecs n x nev or None,
+        info dict)."""
         import numpy as np
         import torch
         dev = self._keep[2].device
@@ -346,15 +347,17 @@ class Plan:
             _need(v0, torch.float64, "v0")
         ev = (C.c_double * nev)()
         rs = (C.c_double * nev)()
-        cnt = (C.c_int32 * 3)()
+        cnt = (C.c_int32 * 5)()
+        sts = (C.c_double * 2)()
         vec = torch.empty((nev, self.n), dtype=torch.float64, device=dev) if vectors else None
         code = lib().xb_lanczos(self._h, nev, m, m if m_max is None else m_max, theta, tol,
-                                maxrestart, _ptr(v0) if v0 is not None
-                                else None, ev, _ptr(vec) if vectors else None, rs, cnt,
+                                maxrestart, int(policy), _ptr(v0) if v0 is not None
+                                else None, ev, _ptr(vec) if vectors else None, rs, cnt, sts,
                                 _stream(stream))
         if code in (XB_EINVAL, XB_ENOMEM, XB_ECUDA):
             raise XbError(code, last_error())
         info = dict(status=code, steps=cnt[0], restarts=cnt[1], m_final=cnt[2],
+                    ortho_used=cnt[3], outer=cnt[4], mem_bytes=sts[0], true_resid=sts[1],
                     resid=np.array(rs[:]))
         return np.array(ev[:]), (vec.T if vectors else None), info
 

@@ -97,3 +97,40 @@ def test_lanczos_restart_rule(env):
     assert grown["steps"] < fixed["steps"] / 4
     np.testing.assert_allclose(ev0, ref, atol=1e-10)
     np.testing.assert_allclose(ev1, ref, atol=1e-10)
+
+
+def test_lanczos_policies(env):
+    """The numerical computation policies on the Lanczos eigensolver (the
+    paper's Table 4 counts Lanczos runs per policy): every policy but NONE
+    checks the true residuals of a claimed convergence; each policy's
+    settings (SpMV, cycle, memory) as defined, DGKS throughout; every policy
+    gives the oracle's eigenvalues."""
+    xb, dev = env
+    import torch
+    U = gen.random_sym_upper(3000, seed=7)
+    F = gen.full_from_upper(U)
+    nev, tol = 8, 1e-8
+    v0h = np.random.default_rng(5).standard_normal(U["n"])
+    eo, _, io = oracle.lanczos(F, nev=nev, m=40, tol=1e-12, v0=v0h, vectors=False)
+    scale = np.max(np.abs(eo))
+    plan = xb.Plan.from_host(U, dev)
+    out = {}
+    for pol in (xb.POLICY_NONE, xb.POLICY_TIME, xb.POLICY_ACCURACY, xb.POLICY_MEMORY,
+                xb.POLICY_STABLE):
+        ev, _, info = plan.lanczos(nev=nev, m=40, tol=tol, policy=pol, maxrestart=3000,
+                                   v0=torch.tensor(v0h, device=dev), vectors=False)
+        out[pol] = info
+        assert info["status"] in (xb.XB_OK, xb.XB_EFAULT), (pol, info)
+        np.testing.assert_allclose(ev, eo, atol=1e-6 * scale)
+        if pol == xb.POLICY_NONE:
+            assert info["true_resid"] == -1.0 and info["ortho_used"] == xb.ORTHO_DGKS
+        elif info["status"] == xb.XB_OK:
+            assert 0.0 <= info["true_resid"] <= tol, (pol, info)
+        else:
+            assert info["true_resid"] > tol and pol != xb.POLICY_ACCURACY, (pol, info)
+    t, mem, stb = out[xb.POLICY_TIME], out[xb.POLICY_MEMORY], out[xb.POLICY_STABLE]
+    # the thick restart needs an orthonormal basis: DGKS under every policy
+    assert all(out[p]["ortho_used"] == xb.ORTHO_DGKS for p in out)
+    assert 40 <= t["m_final"] <= 128 and mem["m_final"] == 20 and stb["m_final"] == 40
+    assert out[xb.POLICY_ACCURACY]["status"] == xb.XB_OK
+    assert mem["mem_bytes"] < t["mem_bytes"] / 3
