@@ -210,7 +210,7 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
     const size_t vbytes = (size_t)(M + 1 + kmax) * ld * sizeof(double);
     const size_t gbytes = xb::gm_doubles(M) * sizeof(double) + (size_t)M * M * 8 +
                           (size_t)M * 8 + 256;
-    const size_t cbytes = check ? (size_t)(nev + 1) * ld * sizeof(double) : 0;
+    const size_t cbytes = check ? (size_t)2 * ld * sizeof(double) : 0;  // one Ritz vector + A y
     const size_t need = vbytes + gbytes + cbytes;
     XB_TRY(xb::ensure_work(p, need));
     double *V = static_cast<double *>(p->d_work);
@@ -220,7 +220,7 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
     double *dS = gm + xb::gm_doubles(M);
     double *dres = dS + (size_t)M * M;
     double *XR = reinterpret_cast<double *>(((uintptr_t)(dres + M) + 255) / 256 * 256);
-    double *TMP = XR + (size_t)nev * ld;
+    double *TMP = XR + ld;
     // raw Gram-Schmidt state: unit scales, no Givens
     XB_CUDA(cudaMemsetAsync(gm, 0, xb::gm_doubles(M) * sizeof(double), s));
     std::vector<double> ones(M + 1, 1.0);
@@ -283,10 +283,13 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
             if (resid[i] > tol_in * std::fabs(w[i])) conv = false;
         }
         if (conv && check) {
-            // true residuals ||A y - theta y|| of the claimed pairs (Sec. 3.3.2)
-            XB_TRY(ritz_vectors(XR, ld));
+            // true residuals ||A y - theta y|| of the claimed pairs (Sec. 3.3.2),
+            // one Ritz vector at a time (two vectors of workspace)
+            XB_CUDA(cudaMemcpyAsync(dS, S.data(), (size_t)m * nev * sizeof(double),
+                                    cudaMemcpyHostToDevice, s));
             for (int i = 0; i < nev; i++) {
-                const double *y = XR + (size_t)i * ld;
+                const double *y = XR;
+                XB_TRY(rotate(n, m, 1, V, ld, dS + (size_t)i * m, XR, ld, s));
                 XB_TRY(xb::spmv_launch(p, variant, block, ipt, 1.0, y, 0.0, TMP, s));
                 XB_TRY(xb::vaxpy(n, -w[i], y, TMP, s));
                 XB_TRY(xb::vnrm2(p, n, TMP, dres + i, s));
@@ -429,10 +432,11 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
     const int kmax = std::min(M - 1, nev + (M - nev) / 2 + 1);
     const size_t vbytes = (size_t)(M + 1 + kmax) * ld * sizeof(double);
     // dS holds Q (m x k) or the real and imaginary Ritz coefficients (2 x m x nev);
-    // dres the true residual norms; XR, XI, TMP the Ritz vectors of the check
+    // dres the true residual norms; XR, XI, TMP one Ritz vector (real and
+    // imaginary part) and A times it
     const size_t gbytes = xb::gm_doubles(M) * sizeof(double) + (size_t)2 * M * M * 8 +
                           (size_t)2 * M * 8 + 256;
-    const size_t cbytes = check ? (size_t)(2 * nev + 1) * ld * sizeof(double) : 0;
+    const size_t cbytes = check ? (size_t)3 * ld * sizeof(double) : 0;  // Re y, Im y, A y
     const size_t need = vbytes + gbytes + cbytes;
     XB_TRY(xb::ensure_work(p, need));
     double *V = static_cast<double *>(p->d_work);
@@ -442,7 +446,7 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
     double *dS = gm + xb::gm_doubles(M);
     double *dres = dS + (size_t)2 * M * M;
     double *XR = reinterpret_cast<double *>(((uintptr_t)(dres + 2 * M) + 255) / 256 * 256);
-    double *XI = XR + (size_t)nev * ld, *TMP = XI + (size_t)nev * ld;
+    double *XI = XR + ld, *TMP = XI + ld;
     XB_CUDA(cudaMemsetAsync(gm, 0, xb::gm_doubles(M) * sizeof(double), s));
     std::vector<double> ones(M + 1, 1.0);
     XB_CUDA(cudaMemcpyAsync(st.sc, ones.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice,
@@ -522,10 +526,14 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
             }
         }
         if (conv && check) {
-            // true residuals r = A x - theta x of the claimed pairs (Sec. 3.3.2)
-            XB_TRY(ritz_vectors(XR, XI, ld));
+            // true residuals r = A x - theta x of the claimed pairs (Sec. 3.3.2),
+            // one Ritz vector at a time (three vectors of workspace)
+            XB_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, s));
             for (int i = 0; i < nev; i++) {
-                const double *xr = XR + (size_t)i * ld, *xi = XI + (size_t)i * ld;
+                const double *xr = XR, *xi = XI;
+                XB_TRY(rotate(n, m, 1, V, ld, dS + (size_t)i * m, XR, ld, s));
+                XB_TRY(rotate(n, m, 1, V, ld, dS + (size_t)(nev + i) * m, XI, ld, s));
                 const double tr = w[i].real(), ti = w[i].imag();
                 XB_TRY(xb::spmv_launch(p, variant, block, ipt, 1.0, xr, 0.0, TMP, s));
                 XB_TRY(xb::vaxpy(n, -tr, xr, TMP, s));
