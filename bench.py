@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="also run the 512-system batched solve (default / learned / exhaustive)")
     ap.add_argument("--variant", default=None,
-                    choices=["row", "nnz", "segscan", "sym-atomic", "sym-tile"],
+                    choices=["row", "nnz", "segscan", "sym-atomic", "sym-tile", "sell"],
                     help="fixed SpMV variant instead of the exhaustive tuner")
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--ipt", type=int, default=8)
@@ -278,7 +278,7 @@ def main():
     n, nnz = A["n"], A["nnz"]
     plan = xb.Plan.from_host(A, dev)
     if args.variant:
-        v = {"row": xb.VAR_ROW, "nnz": xb.VAR_NNZ, "segscan": xb.VAR_SEGSCAN,
+        v = {"row": xb.VAR_ROW, "nnz": xb.VAR_NNZ, "segscan": xb.VAR_SEGSCAN, "sell": xb.VAR_SELL,
              "sym-atomic": xb.VAR_SYM_ATOMIC, "sym-tile": xb.VAR_SYM_TILE}[args.variant]
         plan.set_choice(v, args.block, args.ipt)
         choice = plan.choice()

@@ -51,7 +51,12 @@ extern "C" {
 #define XB_VAR_SYM_TILE 4    /* S2/S3-like: nnz-balanced tiles, in-tile        */
                              /*   transpose terms in shared memory, only the   */
                              /*   out-of-tile (non-zero region) ones global    */
-#define XB_NUM_VARIANTS 5
+#define XB_VAR_SELL 5        /* format conversion (Sec. 5): SELL-C-sigma copy,  */
+                             /*   C = 32 rows per slice, rows sorted by length */
+                             /*   in windows of sigma = 32 * ipt rows; a thread */
+                             /*   per row, coalesced slice columns; built on   */
+                             /*   first use (general storage only)             */
+#define XB_NUM_VARIANTS 6
 
 /* Re-orthogonalisation in the Arnoldi step (Sec. 3.2.2) and the accuracy
  * policy choosing it (Sec. 3.3.2). */

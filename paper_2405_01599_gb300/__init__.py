@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libxabc.so")
 
 XB_OK, XB_EINVAL, XB_ENOMEM, XB_ECUDA, XB_ENOCONV, XB_EBREAKDOWN, XB_ETIMEOUT, XB_EFAULT = \
     0, -1, -2, -3, -4, -5, -6, -7
-VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE = -1, 0, 1, 2, 3, 4
-VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile"}
+VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE, VAR_SELL = -1, 0, 1, 2, 3, 4, 5
+VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile", 5: "sell"}
 ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
 POLICY_NONE, POLICY_TIME, POLICY_ACCURACY, POLICY_MEMORY, POLICY_STABLE = 0, 1, 2, 3, 4
 PRECOND_NONE, PRECOND_ILU0 = 0, 1

@@ -64,6 +64,22 @@ struct SegPart {
     int *d_carry_row = nullptr;
     double *d_carry_val = nullptr;   // raw partial sums (float in FP32 use)
 };
+// SELL-C-sigma copy (C = 32): rows sorted by length (longest first, stable)
+// inside windows of sigma rows; slice q holds sorted rows 32q..32q+31, its
+// entries stored column by column (entry j of its 32 rows at off[q] + 32 j +
+// lane), as wide as its longest row.  Padding is never read (a row stops at
+// its own length), so it is left unset.
+struct SellPart {
+    int sigma = 0;
+    int nslices = 0;
+    int64_t total = 0;               // entries including padding
+    int64_t *d_off = nullptr;        // nslices + 1
+    int *d_perm = nullptr;           // nslices * 32 row of each slot, -1 past n
+    int *d_len = nullptr;            // nslices * 32 length of each slot's row
+    int *d_col = nullptr;            // total
+    double *d_val = nullptr;         // total
+    float *d_val32 = nullptr;        // total, built on the first FP32 use
+};
 // The BSS "continuous location" data of the plan (independent of the launch
 // shape): bit e of d_endbits is set when non-zero e is the last one of its
 // row; with empty rows present, rows are renumbered over the non-empty ones
@@ -126,6 +142,7 @@ struct xb_plan {
     int *d_empty = nullptr;              // rows with no stored entry
     std::vector<xb::TilePart> tiles;     // cache by (block, ipt)
     std::vector<xb::SegPart> segs;       // cache by (block, ipt)
+    std::vector<xb::SellPart> sells;     // cache by sigma
     xb::BssData bss;
     xb::IluData ilu;
     bool vec_ok = false;                 // val and col 16-byte aligned
@@ -147,6 +164,9 @@ namespace xb {
 
 const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
 const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
+// SELL-32-sigma copy (FP32 values too when f32); XB_EINVAL when the padding
+// would exceed 3 nnz + 32 per slice.
+const SellPart *get_sell(xb_plan *p, int sigma, bool f32, cudaStream_t s, int *err);
 const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err);
 int ensure_val32(xb_plan *p, cudaStream_t s);
 int ensure_work(xb_plan *p, size_t bytes);

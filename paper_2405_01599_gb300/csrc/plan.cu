@@ -71,7 +71,7 @@ int resident_grid(const void *fn, int block, int64_t n, int per_thread) {
 
 bool variant_fits(const xb_plan *p, int v) {
     if (p->sym) return v == XB_VAR_SYM_ATOMIC || v == XB_VAR_SYM_TILE;
-    return v == XB_VAR_ROW || v == XB_VAR_NNZ || v == XB_VAR_SEGSCAN;
+    return v == XB_VAR_ROW || v == XB_VAR_NNZ || v == XB_VAR_SEGSCAN || v == XB_VAR_SELL;
 }
 
 // ---- partitions -------------------------------------------------------------
@@ -222,6 +222,122 @@ int ensure_val32(xb_plan *p, cudaStream_t s) {
     k_to_f32<<<num_sms() * 8, 256, 0, s>>>(p->nnz, p->val, p->val32);
     XB_LAUNCHED("k_to_f32");
     return XB_OK;
+}
+
+// Copy row perm[t]'s entries into slot t of the SELL layout (the slot's
+// lane of its slice, one column per entry); thread per slot.
+template <typename V>
+__global__ void k_sell_scatter(int64_t nslots, const int *__restrict__ perm,
+                               const int64_t *__restrict__ off, const int *__restrict__ rowptr,
+                               const int *__restrict__ col, const V *__restrict__ val,
+                               int *__restrict__ scol, V *__restrict__ sval) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nslots) return;
+    const int r = perm[t];
+    if (r < 0) return;
+    const int a = rowptr[r], len = rowptr[r + 1] - a;
+    const int64_t base = off[t >> 5] + (t & 31);
+    for (int j = 0; j < len; j++) {
+        if (scol) scol[base + 32LL * j] = col[a + j];
+        sval[base + 32LL * j] = val[a + j];
+    }
+}
+
+const SellPart *get_sell(xb_plan *p, int sigma, bool f32, cudaStream_t s, int *err) {
+    SellPart *sp = nullptr;
+    for (auto &t : p->sells)
+        if (t.sigma == sigma) sp = &t;
+    if (!sp) {
+        const int n = p->n;
+        const int *rp = p->h_rowptr.data();
+        SellPart t;
+        t.sigma = sigma;
+        t.nslices = (n + 31) / 32;
+        const size_t nslots = (size_t)t.nslices * 32;
+        std::vector<int> perm(nslots, -1);
+        for (int i = 0; i < n; i++) perm[i] = i;
+        auto len = [&](int r) { return rp[r + 1] - rp[r]; };
+        for (int w0 = 0; w0 < n; w0 += sigma) {
+            const int w1 = (int)std::min<int64_t>(n, (int64_t)w0 + sigma);
+            std::stable_sort(perm.begin() + w0, perm.begin() + w1,
+                             [&](int a, int b) { return len(a) > len(b); });
+        }
+        std::vector<int64_t> off((size_t)t.nslices + 1, 0);
+        for (int q = 0; q < t.nslices; q++) {
+            int wd = 0;
+            for (int l = 0; l < 32; l++) {
+                const int r = perm[(size_t)q * 32 + l];
+                if (r >= 0) wd = std::max(wd, len(r));
+            }
+            off[q + 1] = off[q] + 32LL * wd;
+        }
+        t.total = off[t.nslices];
+        if (t.total > 3LL * p->nnz + 32LL * t.nslices) {
+            *err = set_error(XB_EINVAL, "SELL-32-%d: padding to %lld entries for %d non-zeros",
+                             sigma, (long long)t.total, p->nnz);
+            return nullptr;
+        }
+        std::vector<int> slen(nslots, 0);
+        for (size_t q = 0; q < nslots; q++)
+            if (perm[q] >= 0) slen[q] = len(perm[q]);
+        const size_t tot = (size_t)std::max<int64_t>(t.total, 1);
+        cudaError_t e = cudaMalloc(&t.d_off, off.size() * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_perm, nslots * sizeof(int) + 4);
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_len, nslots * sizeof(int) + 4);
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_col, tot * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_val, tot * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t.d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nslots)
+            e = cudaMemcpy(t.d_perm, perm.data(), nslots * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && nslots)
+            e = cudaMemcpy(t.d_len, slen.data(), nslots * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(t.d_off);
+            cudaFree(t.d_perm);
+            cudaFree(t.d_len);
+            cudaFree(t.d_col);
+            cudaFree(t.d_val);
+            *err = cuda_error(e, "SELL copy");
+            return nullptr;
+        }
+        if (nslots) {
+            k_sell_scatter<double><<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(
+                (int64_t)nslots, t.d_perm, t.d_off, p->rowptr, p->col, p->val, t.d_col, t.d_val);
+            e = cudaGetLastError();
+        }
+        p->sells.push_back(t);  // owned by the plan from here (freed with it)
+        if (e != cudaSuccess) {
+            *err = cuda_error(e, "k_sell_scatter");
+            return nullptr;
+        }
+        sp = &p->sells.back();
+    }
+    if (f32 && !sp->d_val32) {
+        int r = ensure_val32(p, s);
+        if (r != XB_OK) {
+            *err = r;
+            return nullptr;
+        }
+        const size_t tot = (size_t)std::max<int64_t>(sp->total, 1);
+        cudaError_t e = cudaMalloc(&sp->d_val32, tot * sizeof(float));
+        if (e != cudaSuccess) {
+            *err = cuda_error(e, "SELL FP32 copy");
+            return nullptr;
+        }
+        const size_t nslots = (size_t)sp->nslices * 32;
+        if (nslots && p->nnz) {
+            k_sell_scatter<float><<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(
+                (int64_t)nslots, sp->d_perm, sp->d_off, p->rowptr, p->col, p->val32, nullptr,
+                sp->d_val32);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                *err = cuda_error(e, "k_sell_scatter");
+                return nullptr;
+            }
+        }
+    }
+    return sp;
 }
 
 int ensure_work(xb_plan *p, size_t bytes) {
@@ -440,6 +556,14 @@ int xb_plan_destroy(xb_plan *p) {
         cudaFree(t.d_row);
         cudaFree(t.d_carry_row);
         cudaFree(t.d_carry_val);
+    }
+    for (auto &t : p->sells) {
+        cudaFree(t.d_off);
+        cudaFree(t.d_perm);
+        cudaFree(t.d_len);
+        cudaFree(t.d_col);
+        cudaFree(t.d_val);
+        cudaFree(t.d_val32);
     }
     cudaFree(p->val32);
     cudaFree(p->bss.d_endbits);

@@ -562,6 +562,11 @@ double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
     if (variant == XB_VAR_NNZ || variant == XB_VAR_SYM_TILE) {
         for (const auto &t : p->tiles)
             if (t.block == block && t.ipt == ipt) b += 4.0 * (t.ntiles + 1);
+    } else if (variant == XB_VAR_SELL) {
+        for (const auto &t : p->sells)
+            if (t.sigma == 32 * ipt)
+                b += 8.0 * (t.nslices + 1) + 256.0 * t.nslices + 12.0 * t.total +
+                     (t.d_val32 ? 4.0 * t.total : 0.0);
     } else if (variant == XB_VAR_SEGSCAN) {
         b += 4.0 * ((p->nnz + 31) / 32 + 1);
         if (p->bss.d_ne_rows) b += 4.0 * p->bss.n_ne + 4.0 * (p->bss.n_ne + 1);

@@ -49,6 +49,58 @@ __global__ void __launch_bounds__(512) k_row(int n, const int *__restrict__ rowp
 }
 
 // ---------------------------------------------------------------------------
+// SELL-C-sigma (format conversion, C = 32): thread per row of a slice; the
+// warp's loads of entry j are 32 consecutive values and columns.  A row reads
+// its own length of entries (padding is never read) in CRS order, so the sum
+// is the one k_row forms.
+// ---------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(512) k_sell(int nslices, const int64_t *__restrict__ off,
+                                              const int *__restrict__ perm,
+                                              const int *__restrict__ slen,
+                                              const int *__restrict__ col,
+                                              const V *__restrict__ val, const V *__restrict__ x,
+                                              V alpha, V beta, int mode, V *__restrict__ y,
+                                              const V *__restrict__ adev) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if ((t >> 5) >= nslices) return;
+    const int r = perm[t];
+    if (r < 0) return;
+    if (adev) alpha = *adev;
+    const int len = slen[t];
+    const int64_t base = off[t >> 5] + (t & 31);
+    V s = V(0);
+#pragma unroll 4
+    for (int j = 0; j < len; j++) {
+        const int64_t k = base + 32LL * j;
+        s = fma(val[k], x[col[k]], s);
+    }
+    store_row(y, r, s, alpha, beta, mode);
+}
+
+template <typename V>
+const V *sell_values(const xb::SellPart *sp);
+template <>
+const double *sell_values<double>(const xb::SellPart *sp) { return sp->d_val; }
+template <>
+const float *sell_values<float>(const xb::SellPart *sp) { return sp->d_val32; }
+
+template <typename V>
+int launch_sell(xb_plan *p, int block, int ipt, V alpha, const V *x, V beta, int mode, V *y,
+                const V *adev, cudaStream_t s) {
+    if (ipt < 1 || ipt > 32) return xb::set_error(XB_EINVAL, "SELL: ipt %d not in 1..32", ipt);
+    int err = XB_OK;
+    const xb::SellPart *sp = xb::get_sell(p, 32 * ipt, sizeof(V) == sizeof(float), s, &err);
+    if (!sp) return err;
+    const int64_t threads = (int64_t)sp->nslices * 32;
+    k_sell<V><<<(unsigned)((threads + block - 1) / block), block, 0, s>>>(
+        sp->nslices, sp->d_off, sp->d_perm, sp->d_len, sp->d_col, sell_values<V>(sp), x, alpha,
+        beta, mode, y, adev);
+    XB_LAUNCHED("k_sell");
+    return XB_OK;
+}
+
+// ---------------------------------------------------------------------------
 // U2: row-aligned, nnz-balanced tiles.  A tile holds at most T = B*IPT
 // non-zeros and B rows; its val and x[col] are staged into shared memory with
 // coalesced loads (IPT independent loads and gathers in flight per thread),
@@ -725,6 +777,8 @@ int spmv_any(xb_plan *p, int variant, int block, int ipt, V alpha, const V *x, V
         case XB_VAR_SYM_TILE:
             return launch_sym<V>(p, variant, p->rowptr, p->col, va, block, ipt, alpha, x, beta, y,
                                  adev, s);
+        case XB_VAR_SELL:
+            return launch_sell<V>(p, block, ipt, alpha, x, beta, mode, y, adev, s);
     }
     return xb::set_error(XB_EINVAL, "unknown SpMV variant %d", variant);
 }

@@ -24,6 +24,10 @@ std::vector<Cand> candidates(const xb_plan *p) {
         for (int i : {4, 8, 16}) c.push_back({XB_VAR_NNZ, b, i});
     for (int b : {128, 256})
         for (int i : {4, 8, 16, 32}) c.push_back({XB_VAR_SEGSCAN, b, i});
+    // format conversion (Sec. 5): SELL-32-sigma, sigma = 32 (no reordering
+    // across slices) or 1024 rows; skipped when its padding is too large
+    for (int b : {128, 256, 512})
+        for (int i : {1, 32}) c.push_back({XB_VAR_SELL, b, i});
     return c;
 }
 

@@ -91,6 +91,18 @@ def laplace3d(N, upper=False):
     return _mat(n, rp, c, v, upper, kind="laplace3d", side=N)
 
 
+def stencil27(N):
+    """3D 27-point stencil on an N^3 grid (the FEM-like class of 10-30
+    non-zeros per row): diagonal 26, every neighbour in the 3 x 3 x 3 box -1."""
+    co = {}
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                co[(dx, dy, dz)] = 26.0 if (dx, dy, dz) == (0, 0, 0) else -1.0
+    n, rp, c, v = _stencil((N, N, N), co)
+    return _mat(n, rp, c, v, kind="stencil27", side=N)
+
+
 def convdiff3d(N=256, pe=10.0, dims=None):
     """3D convection-diffusion -Lap(u) + Pe*(u_x + u_y + u_z) on (0,1)^3.
 

@@ -18,7 +18,22 @@ GENERAL = {
     "row": (0, [(64, 1), (256, 1)]),
     "nnz": (1, [(64, 1), (128, 4), (256, 8), (512, 16), (256, 2)]),
     "segscan": (2, [(64, 4), (128, 4), (256, 8), (128, 16), (256, 16), (128, 32)]),
+    "sell": (5, [(64, 1), (256, 1), (128, 8), (512, 32)]),
 }
+
+
+def sell_accepts(A, sigma):
+    """The SELL-32-sigma copy is built unless its padding exceeds 3 nnz + 32
+    per slice (the format's definition: rows sorted by length inside windows
+    of sigma rows, slices of 32 as wide as their longest row)."""
+    L = np.diff(np.asarray(A["rowptr"], np.int64))
+    n = A["n"]
+    order = np.concatenate([w0 + np.argsort(-L[w0:w0 + sigma], kind="stable")
+                            for w0 in range(0, n, sigma)]) if n else np.zeros(0, np.int64)
+    Ls = np.zeros(((n + 31) // 32) * 32, np.int64)
+    Ls[:n] = L[order]
+    total = 32 * Ls.reshape(-1, 32).max(axis=1).sum() if n else 0
+    return total <= 3 * A["nnz"] + 32 * ((n + 31) // 32)
 
 
 def _adversarial():
@@ -79,6 +94,10 @@ def test_general_variants_match_oracle(env, mname):
         for vname, (v, shapes) in GENERAL.items():
             for block, ipt in shapes:
                 y = torch.tensor(y0, device=dev) if beta != 0 else torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+                if v == xb.VAR_SELL and not sell_accepts(A, 32 * ipt):
+                    with pytest.raises(xb.XbError):
+                        plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
+                    continue
                 plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
                 assert_rows_close(y.cpu().numpy(), yref, bound,
                                   what=f"{mname}/{vname}/b{block}i{ipt}/a{alpha}b{beta}")
@@ -178,8 +197,12 @@ def test_f32_path(env):
         Aabs["val"] = np.abs(A["val"])
         bound = oracle.spmv(Aabs, np.abs(x.astype(np.float64)))
         k = np.diff(A["rowptr"]).astype(np.float64)
-        for v in (0, 1, 2):
+        for v in (0, 1, 2, 5):
             y = torch.empty(A["n"], dtype=torch.float32, device=dev)
+            if v == xb.VAR_SELL:
+                plan.set_choice(xb.VAR_SELL, 256, 32)  # SELL-32-1024 (FP32 values)
+                if not sell_accepts(A, 1024):
+                    continue
             plan.spmv_f32(torch.tensor(x, device=dev), y, variant=v)
             err = np.abs(y.cpu().numpy().astype(np.float64) - yo.astype(np.float64))
             assert np.all(err <= 2 * (k + 2) * 6e-8 * bound + 1e-30), v
@@ -261,3 +284,46 @@ def test_bad_arguments_rejected(env):
     bad["rowptr"][-1] += 1
     with pytest.raises(xb.XbError):
         xb.Plan.from_host(bad, dev)
+
+
+def test_sell_layout_and_solvers(env):
+    """Format conversion (SELL-32-sigma): bit-identical to the thread-per-row
+    CRS kernel (same summation order, padding never read); a padding-heavy
+    matrix is rejected at sigma = 32 and accepted at sigma = 1024; GMRES in
+    FP64 and mixed precision run on the SELL copy and meet tol."""
+    xb, dev = env
+    import torch
+    A = gen.convdiff3d(N=24)
+    plan = xb.Plan.from_host(A, dev)
+    xt = torch.tensor(np.random.default_rng(9).uniform(-1, 1, A["n"]), device=dev)
+    y_row = torch.empty_like(xt)
+    plan.spmv(xt, y_row, variant=xb.VAR_ROW, block=256, ipt=1)
+    for ipt in (1, 8, 32):
+        y = torch.empty_like(xt)
+        plan.spmv(xt, y, variant=xb.VAR_SELL, block=256, ipt=ipt)
+        assert torch.equal(y, y_row), ipt
+    P = gen.powerlaw(n=3000, seed=1, cap=300)
+    pp = xb.Plan.from_host(P, dev)
+    assert not sell_accepts(P, 32) and sell_accepts(P, 1024)
+    xp = torch.tensor(np.random.default_rng(3).uniform(-1, 1, P["n"]), device=dev)
+    with pytest.raises(xb.XbError):
+        pp.spmv(xp, torch.empty_like(xp), variant=xb.VAR_SELL, block=256, ipt=1)
+    y = torch.empty_like(xp)
+    pp.spmv(xp, y, variant=xb.VAR_SELL, block=256, ipt=32)
+    y2 = torch.empty_like(xp)
+    pp.spmv(xp, y2, variant=xb.VAR_ROW, block=256, ipt=1)
+    assert torch.equal(y, y2)
+    # solvers on the converted copy
+    Q = gen.poisson2d(64)
+    pq = xb.Plan.from_host(Q, dev)
+    pq.set_choice(xb.VAR_SELL, 256, 32)
+    b_h = oracle.spmv(Q, np.ones(Q["n"]))
+    b = torch.tensor(b_h, device=dev)
+    _, oinfo = oracle.gmres(Q, b_h, m=30, tol=1e-8)
+    for prec in (xb.PREC_FP64, xb.PREC_MIXED):
+        x = torch.zeros_like(b)
+        info = pq.gmres(b, x, m=30, tol=1e-8, precision=prec)
+        assert info["status"] == 0 and info["res_true"] <= 1e-8, (prec, info)
+        assert info["variant_used"] == xb.VAR_SELL
+        if prec == xb.PREC_FP64:
+            assert abs(info["iters"] - oinfo["iters"]) <= max(3, 0.05 * oinfo["iters"])
