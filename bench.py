@@ -501,6 +501,28 @@ def extras(xb, torch, dev, plan, A, x, y, args):
         "full_tuned": {"choice": cf, "ms": ms_full, "GBs": bf / ms_full / 1e6, "GFLOPs": flops / ms_full / 1e6},
         "200_spmv_ms": {"sym": 200 * ms_sym, "full": 200 * ms_full},
     }
+    # format-conversion AT (Sec. 5): a 27-point stencil (128^3, 56M nnz), where
+    # the tuner converts to SELL-32-sigma; every general variant's throughput
+    try:
+        S27 = gen.stencil27(128)
+        p27 = xb.Plan.from_host(S27, dev)
+        c27 = p27.tune()
+        x27 = torch.ones(S27["n"], dtype=torch.float64, device=dev)
+        y27 = torch.empty_like(x27)
+        b27 = alg_bytes(S27)
+        t27 = {}
+        for lab, (v, b, i) in {"row": (xb.VAR_ROW, 256, 1), "nnz": (xb.VAR_NNZ, 256, 8),
+                               "segscan": (xb.VAR_SEGSCAN, 256, 8),
+                               "sell_s32": (xb.VAR_SELL, 128, 1),
+                               "sell_s1024": (xb.VAR_SELL, 128, 32)}.items():
+            ms = _time_spmv(torch, lambda: p27.spmv(x27, y27, variant=v, block=b, ipt=i), 50)
+            t27[lab] = {"ms": ms, "GBs": b27 / ms / 1e6}
+        res["stencil27_128_spmv"] = {"tuned": {"variant": xb.VARIANT_NAMES[c27["variant"]],
+                                               "block": c27["block"], "ipt": c27["ipt"]},
+                                     "variants": t27}
+        del p27, S27, x27, y27
+    except xb.XbError as e:
+        res["stencil27_128_spmv"] = {"error": str(e)}
     # restarted Lanczos (OpenATI_EIGENSOLVE): the 10 largest eigenvalues of the
     # 128^3 Laplacian (upper storage), as the paper asks for 10 eigenpairs
     torch.cuda.synchronize()
