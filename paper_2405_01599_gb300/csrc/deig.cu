@@ -168,8 +168,6 @@ int schur(int m, const double *A, std::vector<cplx> &T, std::vector<cplx> &Z) {
 
 void eig_order(int m, const std::vector<cplx> &T, int which, std::vector<int> &ord,
                std::vector<signed char> &kind, std::vector<cplx> &w) {
-    double scale = 0.0;
-    for (int i = 0; i < m; i++) scale = std::max(scale, std::abs(T[(size_t)i * m + i]));
     double fro = 0.0;
     for (const cplx &x : T) fro += std::norm(x);
     // imaginary parts below this are rounding of a real eigenvalue
@@ -221,7 +219,6 @@ void eig_order(int m, const std::vector<cplx> &T, int which, std::vector<int> &o
         kind.push_back(-1);
         w.push_back(cplx(re, -im));
     }
-    (void)scale;
 }
 
 void schur_reorder(int m, std::vector<cplx> &T, std::vector<cplx> &Z, const std::vector<int> &ord,
