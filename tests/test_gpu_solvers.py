@@ -185,7 +185,7 @@ def test_tuner_choice_is_valid_and_exact(env):
     A = gen.powerlaw(n=200000, seed=6)
     plan = xb.Plan.from_host(A, dev)
     ch = plan.tune()
-    assert ch["variant"] in (0, 1, 2) and ch["ms"] > 0
+    assert ch["variant"] in (0, 1, 2, 5) and ch["ms"] > 0  # a general-storage variant
     x = np.random.default_rng(1).uniform(-1, 1, A["n"])
     y = torch.empty(A["n"], dtype=torch.float64, device=dev)
     plan.spmv(torch.tensor(x, device=dev), y)
