@@ -158,6 +158,46 @@ int rotate(int64_t n, int m, int kc, const double *V, int64_t ld, const double *
     return XB_OK;
 }
 
+// Settings of one eigensolver run under a numerical computation policy
+// (Sec. 2.3.2, 3.3): TIME and ACCURACY tune the SpMV and turn the restart rule
+// on (m_max >= 128); MEMORY takes the SpMV without plan metadata and a fixed
+// cycle of at most 20 (at least m_min); STABLE keeps the plan's SpMV and m.
+// Every policy but NONE checks the true residuals of a claimed convergence;
+// ACCURACY iterates on after a miss (outer loop).  The Gram-Schmidt choice is
+// the solver's.
+struct EigRun {
+    int variant, block, ipt, m, m_max;
+    bool check, outer;
+};
+
+int eig_policy(xb_plan *p, int policy, int m_min, int m, int m_max, void *stream, EigRun &r) {
+    r = EigRun{p->variant, p->block, p->ipt, m, m_max, policy != XB_POLICY_NONE,
+               policy == XB_POLICY_ACCURACY};
+    switch (policy) {
+        case XB_POLICY_TIME:
+        case XB_POLICY_ACCURACY:
+            XB_TRY(xb_tune_exhaustive(p, nullptr, stream));
+            r.variant = p->variant;
+            r.block = p->block;
+            r.ipt = p->ipt;
+            r.m_max = std::max<int>(m_max, (int)std::min<int64_t>(128, std::min<int64_t>(512, p->n)));
+            break;
+        case XB_POLICY_MEMORY:
+            r.variant = p->sym ? XB_VAR_SYM_ATOMIC : XB_VAR_ROW;
+            r.block = 256;
+            r.ipt = 1;
+            r.m = std::max(m_min, std::min(m, 20));
+            r.m_max = r.m;
+            break;
+        case XB_POLICY_STABLE:
+            r.m_max = m;
+            break;
+        default:
+            break;
+    }
+    return XB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -179,31 +219,13 @@ int xb_lanczos(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
         return xb::set_error(XB_EINVAL, "lanczos: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = p->n;
-    int variant = p->variant, block = p->block, ipt = p->ipt;
+    EigRun run;
+    XB_TRY(eig_policy(p, policy, nev + 1, m, m_max, stream, run));
+    const int variant = run.variant, block = run.block, ipt = run.ipt;
+    const bool check = run.check, outer = run.outer;
+    m = run.m;
+    m_max = run.m_max;
     const int ortho = XB_ORTHO_DGKS;
-    const bool check = policy != XB_POLICY_NONE, outer = policy == XB_POLICY_ACCURACY;
-    switch (policy) {
-        case XB_POLICY_TIME:
-        case XB_POLICY_ACCURACY:
-            XB_TRY(xb_tune_exhaustive(p, nullptr, stream));
-            variant = p->variant;
-            block = p->block;
-            ipt = p->ipt;
-            m_max = std::max<int>(m_max, (int)std::min<int64_t>(128, std::min<int64_t>(512, n)));
-            break;
-        case XB_POLICY_MEMORY:
-            variant = p->sym ? XB_VAR_SYM_ATOMIC : XB_VAR_ROW;
-            block = 256;
-            ipt = 1;
-            m = std::max(nev + 1, std::min(m, 20));
-            m_max = m;
-            break;
-        case XB_POLICY_STABLE:
-            m_max = m;
-            break;
-        default:
-            break;
-    }
     const int64_t ld = (n + 63) / 64 * 64;
     const int M = m_max;  // basis capacity
     const int kmax = nev + (M - nev) / 2;
@@ -398,35 +420,20 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
         return xb::set_error(XB_EINVAL, "arnoldi: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = p->n;
-    int variant = p->variant, block = p->block, ipt = p->ipt;
-    bool check = policy != XB_POLICY_NONE;
-    const bool outer = policy == XB_POLICY_ACCURACY;
-    switch (policy) {
-        case XB_POLICY_TIME:
-        case XB_POLICY_ACCURACY:
-            XB_TRY(xb_tune_exhaustive(p, nullptr, stream));
-            variant = p->variant;
-            block = p->block;
-            ipt = p->ipt;
-            m_max = std::max<int>(m_max, (int)std::min<int64_t>(128, std::min<int64_t>(512, n)));
-            ortho = xb::ortho_choice(XB_ORTHO_AUTO, tol, false);
-            break;
-        case XB_POLICY_MEMORY:
-            variant = p->sym ? XB_VAR_SYM_ATOMIC : XB_VAR_ROW;
-            block = 256;
-            ipt = 1;
-            m = std::max(nev + 2, std::min(m, 20));
-            m_max = m;
-            ortho = XB_ORTHO_MGS;
-            break;
-        case XB_POLICY_STABLE:
-            m_max = m;
-            ortho = XB_ORTHO_MGS;
-            break;
-        default:
-            ortho = xb::ortho_choice(ortho, tol, false);
-            break;
-    }
+    EigRun run;
+    XB_TRY(eig_policy(p, policy, nev + 2, m, m_max, stream, run));
+    const int variant = run.variant, block = run.block, ipt = run.ipt;
+    const bool check = run.check, outer = run.outer;
+    m = run.m;
+    m_max = run.m_max;
+    // Gram-Schmidt: the accuracy rule under TIME / ACCURACY, MGS under MEMORY
+    // and STABLE, the argument (AUTO resolved) otherwise
+    if (policy == XB_POLICY_TIME || policy == XB_POLICY_ACCURACY)
+        ortho = xb::ortho_choice(XB_ORTHO_AUTO, tol, false);
+    else if (policy == XB_POLICY_MEMORY || policy == XB_POLICY_STABLE)
+        ortho = XB_ORTHO_MGS;
+    else
+        ortho = xb::ortho_choice(ortho, tol, false);
     const int64_t ld = (n + 63) / 64 * 64;
     const int M = m_max;
     const int kmax = std::min(M - 1, nev + (M - nev) / 2 + 1);
