@@ -37,6 +37,18 @@ def wanted_order(vals, which=LR):
     return sorted(range(len(vals)), key=lambda i: (-_key(vals[i], which), -vals[i].imag))
 
 
+def restart_basis(Hm, lam, order, kk, which=LR):
+    """The restart step: an orthonormal real basis Q (m x k) of the invariant
+    subspace of Hm belonging to its kk wanted eigenvalues (lam[order[:kk]],
+    conjugate pairs kept whole), from scipy's real Schur form ordered by a
+    threshold between the kk-th and (kk+1)-th keys, and T_k = Q^T Hm Q (the
+    leading quasi-triangular block).  k = kk unless keys tie at the threshold."""
+    thr = 0.5 * (_key(lam[order[kk - 1]], which) + _key(lam[order[kk]], which))
+    T, Z, sdim = scipy.linalg.schur(
+        Hm, output="real", sort=lambda re, im: _key(complex(re, im), which) > thr)
+    return Z[:, :sdim], T[:sdim, :sdim]
+
+
 def arnoldi_eig(A, nev=10, m=20, tol=1e-8, maxrestart=1000, v0=None, which=LR, m_max=None,
                 theta=10.0, vectors=True):
     """nev eigenvalues of the general CRS matrix A at the wanted end (LR:
@@ -95,14 +107,12 @@ def arnoldi_eig(A, nev=10, m=20, tol=1e-8, maxrestart=1000, v0=None, which=LR, m
         kk = nev + (m - nev) // 2
         if lam[order[kk - 1]].imag > 0:  # first of a conjugate pair: keep both
             kk = kk + 1 if kk + 1 <= m - 1 else kk - 1
-        thr = 0.5 * (_key(lam[order[kk - 1]], which) + _key(lam[order[kk]], which))
-        T, Z, sdim = scipy.linalg.schur(
-            Hm, output="real", sort=lambda re, im: _key(complex(re, im), which) > thr)
-        Q = Z[:, :sdim]
+        Q, Tk = restart_basis(Hm, lam, order, kk, which)
+        sdim = Q.shape[1]
         V[:sdim] = Q.T @ V[:m]
         V[sdim] = V[m]
         Hb[:] = 0.0
-        Hb[:sdim, :sdim] = T[:sdim, :sdim]
+        Hb[:sdim, :sdim] = Tk
         Hb[sdim, :sdim] = beta * Q[m - 1, :]
         k = sdim
         m = m_next

@@ -27,6 +27,19 @@ def spectrum(A):
     return np.array(e)
 
 
+def same_multiset(a, b, tol):
+    """Every value of a matched to a distinct value of b within tol (greedy,
+    nearest first): the two lists hold the same eigenvalues."""
+    b = list(np.asarray(b))
+    for x in np.asarray(a):
+        d = [abs(x - y) for y in b]
+        i = int(np.argmin(d))
+        if d[i] > tol:
+            return False
+        b.pop(i)
+    return not b
+
+
 def true_resid(A, ev, X):
     D = gen.to_dense(A)
     return np.array([np.linalg.norm(D @ X[:, i] - ev[i] * X[:, i]) for i in range(len(ev))])
@@ -49,6 +62,29 @@ def test_quasi_triangular_known_spectrum(which):
     # the estimate the stopping test uses is the true residual
     np.testing.assert_allclose(r, info["resid"], rtol=1e-3, atol=1e-11)
     np.testing.assert_allclose(np.linalg.norm(X, axis=0), 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("which", [oracle.EIG_LR, oracle.EIG_LM])
+def test_restart_basis_spans_the_wanted_invariant_subspace(which):
+    """The restart step on its own: Q is orthonormal, H Q = Q T_k (an
+    invariant subspace), and T_k carries exactly the kk wanted eigenvalues,
+    conjugate pairs whole."""
+    from oracle.eig import restart_basis
+    rng = np.random.default_rng(21 + which)
+    for m in (12, 30):
+        H = np.triu(rng.standard_normal((m, m)), -1)  # upper Hessenberg, like H_m
+        lam = np.linalg.eigvals(H)
+        order = oracle.wanted_order(lam, which)
+        kk = m // 2
+        if lam[order[kk - 1]].imag > 0:
+            kk += 1
+        Q, Tk = restart_basis(H, lam, order, kk, which)
+        assert Q.shape == (m, kk)
+        np.testing.assert_allclose(Q.T @ Q, np.eye(kk), atol=1e-13)
+        assert np.max(np.abs(H @ Q - Q @ Tk)) <= 1e-12 * np.max(np.abs(H))
+        got = np.sort_complex(np.linalg.eigvals(Tk))
+        want = np.sort_complex(lam[order[:kk]])
+        np.testing.assert_allclose(got, want, atol=1e-10)
 
 
 def test_toeplitz_closed_form():
@@ -103,6 +139,38 @@ def test_invariant_start_vector_breaks_down():
     v0[3] = 1.0
     ev, X, info = oracle.arnoldi_eig(A, nev=2, m=6, tol=1e-10, v0=v0)
     assert info["status"] == -5
+
+
+def test_dense_eig_special_matrices():
+    """Host dense step on matrices with a known spectrum: zero, 1 x 1, a
+    rotation (+-2i), a Jordan block (defective, all 2), the cyclic
+    permutation (roots of unity), extreme scalings."""
+    import paper_2405_01599_gb300 as xb
+    try:
+        xb.lib()
+    except ImportError:
+        pytest.skip("CUDA library not built")
+    w, V = xb.dense_eig(np.zeros((5, 5)))
+    assert np.all(w == 0)
+    w, V = xb.dense_eig(np.array([[3.0]]))
+    assert w[0] == 3.0 and V[0, 0] == 1.0
+    w, V = xb.dense_eig(np.array([[0.0, 2.0], [-2.0, 0.0]]))
+    np.testing.assert_allclose(w, [2j, -2j], atol=1e-15)
+    J = np.diag(np.full(6, 2.0)) + np.diag(np.ones(5), 1)
+    w, V = xb.dense_eig(J)
+    np.testing.assert_allclose(w, 2.0, atol=1e-14)
+    assert np.max(np.abs(J @ V - V * w)) <= 1e-14
+    n = 30
+    P = np.roll(np.eye(n), 1, axis=1)
+    w, V = xb.dense_eig(P, xb.EIG_LR)
+    roots = np.exp(2j * np.pi * np.arange(n) / n)
+    assert same_multiset(w, roots, 1e-13)
+    R = np.random.default_rng(0).standard_normal((40, 40))
+    ref = np.linalg.eigvals(R)
+    for scale in (1e150, 1e-150):
+        w, V = xb.dense_eig(R * scale)
+        assert same_multiset(w / scale, ref, 1e-12)
+        assert np.max(np.abs(R @ V - V * (w / scale))) <= 1e-12
 
 
 def test_dense_eig_host_step_matches_numpy():
