@@ -129,7 +129,8 @@ typedef struct xb_options {
     int32_t max_outer;       /* refinement steps cap (default 60)             */
     int32_t variant;         /* XB_VAR_* for the SpMV inside solvers          */
     int32_t block;           /* CTA size for SpMV (0 = plan default)          */
-    int32_t ipt;             /* items per thread (segscan / tile size)        */
+    int32_t ipt;             /* items per thread (segscan / tile size; SELL:  */
+                             /*   sorting window sigma = 32 * ipt rows)        */
     int32_t tuner;           /* XB_TUNER_*                                     */
     int32_t check_every;     /* host reads the residual every k steps (>=1)   */
     int32_t timing;          /* 1: record per-SpMV CUDA-event times in info   */
@@ -256,7 +257,11 @@ int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const in
                          double *y, void *stream);
 
 /* Any variant (XB_VAR_*; XB_VAR_AUTO = plan choice) with an explicit launch
- * shape (block/ipt 0 = plan choice). */
+ * shape (block/ipt 0 = plan choice).  XB_VAR_SELL builds the SELL-32-sigma
+ * copy of the matrix on its first use with that sigma (device memory held by
+ * the plan: 12 B per stored entry including padding plus 8 B per row) and
+ * returns XB_EINVAL when the padding would exceed 3 nnz + 32 per slice of 32
+ * rows; results equal XB_VAR_ROW's bit for bit. */
 int xb_spmv(xb_plan *plan, int32_t variant, int32_t block, int32_t ipt, double alpha,
             const double *x, double beta, double *y, void *stream);
 
