@@ -95,6 +95,12 @@ extern "C" {
                              /*   the solvers iterate on A M^{-1} and report   */
                              /*   residuals of A x = b                         */
 
+/* Solvers a policy file can name (SOLVER keyword, Sec. 2.3.2). */
+#define XB_SOLVER_GMRES 0
+#define XB_SOLVER_BICGSTAB 1
+#define XB_SOLVER_LANCZOS 2
+#define XB_SOLVER_ARNOLDI 3
+
 /* Wanted end of the spectrum for the Arnoldi eigensolver. */
 #define XB_EIG_LR 0          /* largest real part first                        */
 #define XB_EIG_LM 1          /* largest modulus first                          */
@@ -392,6 +398,29 @@ int xb_ilu0_apply(xb_plan *plan, const double *r, double *z, void *stream);
 /* Copy the factors (aligned with the plan's col array: strict lower part = L
  * with unit diagonal not stored, the rest = U) to the DEVICE array lu (nnz). */
 int xb_ilu0_factors(xb_plan *plan, double *lu, void *stream);
+
+/* ---- numerical policy file (Sec. 2.3.2) -----------------------------------
+ * The meta-solvers' user input: lines "<keyword> = <value>", keywords in any
+ * case, blank lines and lines starting with '#' or '!' skipped, keywords the
+ * file does not register ignored.  POLICY = TIME / ACCURACY / MEMORY / STABLE
+ * sets opt->policy (any other value: TIME, the default policy); RESIDUAL (a
+ * real, Fortran's D exponent accepted) sets opt->tol; MAXTIME (seconds) sets
+ * opt->maxtime_s; PRECONDITIONER = NONE / ILU0 / ILU(0) sets opt->precond;
+ * SOLVER = GMRES / BICGSTAB / LANCZOS / ARNOLDI goes to *solver
+ * (XB_SOLVER_*); MAXMEMORY (bytes, optional K / M / G / T suffix, powers of
+ * 1024) to *max_memory; CPU (the paper's thread count; the device is the
+ * caller's choice) to *cpu.  opt is updated in place (start from
+ * xb_options_default); solver, max_memory and cpu may be NULL and are left
+ * unchanged when their keyword is absent.  text: HOST, NUL-terminated.
+ * XB_EINVAL, with the line number in xb_last_error, for a line without '='
+ * or a value that does not parse.  Host only: no device work. */
+int xb_policy_parse(const char *text, xb_options *opt, int32_t *solver, double *max_memory,
+                    int32_t *cpu);
+/* Reads "OPENATI_POLICY_INPUT.<id>" (id: the caller's thread or device
+ * number) from directory dir (NULL or "" = the current directory) and parses
+ * it as xb_policy_parse does; XB_EINVAL if the file cannot be opened. */
+int xb_policy_read(const char *dir, int32_t id, xb_options *opt, int32_t *solver,
+                   double *max_memory, int32_t *cpu);
 
 /* ---- run-time auto-tuning ------------------------------------------------ */
 

@@ -24,6 +24,7 @@ ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
 POLICY_NONE, POLICY_TIME, POLICY_ACCURACY, POLICY_MEMORY, POLICY_STABLE = 0, 1, 2, 3, 4
 PRECOND_NONE, PRECOND_ILU0 = 0, 1
 EIG_LR, EIG_LM = 0, 1
+SOLVER_GMRES, SOLVER_BICGSTAB, SOLVER_LANCZOS, SOLVER_ARNOLDI = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 TUNER_NONE, TUNER_EXHAUSTIVE, TUNER_MLP = 0, 1, 2
 
@@ -121,6 +122,8 @@ def lib():
         "xb_arnoldi": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, i32, i32, vp, P(f64), P(f64),
                              vp, vp, P(f64), P(i32), P(f64), vp]),
         "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
+        "xb_policy_parse": (i32, [C.c_char_p, P(Options), P(i32), P(f64), P(i32)]),
+        "xb_policy_read": (i32, [C.c_char_p, i32, P(Options), P(i32), P(f64), P(i32)]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
         "xb_ilu0_factors": (i32, [vp, vp, vp]),
@@ -448,6 +451,34 @@ def dense_eig(A, which=EIG_LR, vectors=True):
     _check(lib().xb_dense_eig(n, f(A), int(which), f(wr), f(wi), f(vr) if vectors else None,
                               f(vi) if vectors else None))
     return wr + 1j * wi, ((vr + 1j * vi).T if vectors else None)
+
+
+def _policy_result(code, o, sv, mm, cpu):
+    _check(code)
+    extra = dict(solver=sv.value if sv.value >= 0 else None,
+                 max_memory=mm.value if mm.value >= 0 else None,
+                 cpu=cpu.value if cpu.value >= 0 else None)
+    return o, extra
+
+
+def policy_parse(text, opt=None):
+    """Numerical policy file contents (Sec. 2.3.2) -> (Options updated from
+    opt or the defaults, dict(solver, max_memory, cpu) with None for absent
+    keywords)."""
+    o = opt if opt is not None else default_options()
+    sv, mm, cpu = C.c_int32(-1), C.c_double(-1.0), C.c_int32(-1)
+    return _policy_result(lib().xb_policy_parse(text.encode(), C.byref(o), C.byref(sv),
+                                                C.byref(mm), C.byref(cpu)), o, sv, mm, cpu)
+
+
+def policy_read(thread_id=0, directory=None, opt=None):
+    """Read OPENATI_POLICY_INPUT.<thread_id> (from directory, default the
+    current one) as policy_parse does."""
+    o = opt if opt is not None else default_options()
+    sv, mm, cpu = C.c_int32(-1), C.c_double(-1.0), C.c_int32(-1)
+    d = directory.encode() if directory else None
+    return _policy_result(lib().xb_policy_read(d, int(thread_id), C.byref(o), C.byref(sv),
+                                               C.byref(mm), C.byref(cpu)), o, sv, mm, cpu)
 
 
 def mm_ratio(r, s, t):
