@@ -188,6 +188,19 @@ def _need(t, dtype, name):
         raise TypeError(f"{name} must be a contiguous {dtype} tensor (got {t.dtype})")
 
 
+def merge_options(options, kw):
+    """A copy of options (an Options) with the fields in kw replaced, or kw
+    itself when options is None (the solvers then start from the defaults)."""
+    if options is None:
+        return kw
+    o = Options.from_buffer_copy(options)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
 def default_options(**kw):
     o = Options()
     lib().xb_options_default(C.byref(o))
@@ -285,11 +298,12 @@ class Plan:
             raise XbError(code, d["error"])
         return d
 
-    def gmres(self, b, x, stream=None, **opts):
-        return self._solve(lib().gmres_solve, b, x, opts, stream)
+    def gmres(self, b, x, stream=None, options=None, **opts):
+        """GMRES(m); options: an Options (e.g. from policy_read), opts override fields."""
+        return self._solve(lib().gmres_solve, b, x, merge_options(options, opts), stream)
 
-    def bicgstab(self, b, x, stream=None, **opts):
-        return self._solve(lib().bicgstab_solve, b, x, opts, stream)
+    def bicgstab(self, b, x, stream=None, options=None, **opts):
+        return self._solve(lib().bicgstab_solve, b, x, merge_options(options, opts), stream)
 
     # ---- tuning ----
     def tune(self, stream=None):

@@ -66,3 +66,15 @@ def test_read_the_file_by_thread_number(lib):
     assert extra == dict(solver=xb.SOLVER_GMRES, max_memory=16 * 2.0 ** 30, cpu=16)
     with pytest.raises(xb.XbError):
         xb.policy_read(1, GOLDEN)  # no OPENATI_POLICY_INPUT.1
+
+
+def test_options_from_the_file_feed_the_solvers(lib):
+    """The solvers' binding takes the Options the reader filled; keyword
+    arguments override single fields of a copy (marshalling only)."""
+    o, _ = xb.policy_read(0, GOLDEN)
+    m = xb.merge_options(o, dict(m=50))
+    assert m.m == 50 and m.policy == xb.POLICY_ACCURACY and m.tol == 1e-8
+    assert o.m != 50 or xb.default_options().m == 50  # the original is not modified
+    assert xb.merge_options(None, dict(m=7)) == dict(m=7)
+    with pytest.raises(KeyError):
+        xb.merge_options(o, dict(not_a_field=1))
