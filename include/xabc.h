@@ -262,6 +262,17 @@ int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const in
                          const double *val, double alpha, const double *x, double beta,
                          double *y, void *stream);
 
+/* The SELL-32-sigma layout that XB_VAR_SELL builds (host logic, no device
+ * work; exposed for testing): rows sorted by length, longest first and
+ * stable, inside windows of sigma rows; slot q of slice q / 32 holds sorted
+ * row q.  HOST arrays: rowptr (n + 1); perm (32 ceil(n / 32): the row of each
+ * slot, -1 past n); slen (same length: the slot's row length); off
+ * (ceil(n / 32) + 1: entry offset of each slice, a slice being 32 times its
+ * longest row wide).  perm, slen, off may each be NULL; *total receives the
+ * padded entry count. */
+int xb_sell_layout(int32_t n, const int32_t *rowptr, int32_t sigma, int32_t *perm,
+                   int32_t *slen, int64_t *off, int64_t *total);
+
 /* Any variant (XB_VAR_*; XB_VAR_AUTO = plan choice) with an explicit launch
  * shape (block/ipt 0 = plan choice).  XB_VAR_SELL builds the SELL-32-sigma
  * copy of the matrix on its first use with that sigma (device memory held by

@@ -123,6 +123,8 @@ def lib():
                              vp, vp, P(f64), P(i32), P(f64), vp]),
         "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
         "xb_policy_parse": (i32, [C.c_char_p, P(Options), P(i32), P(f64), P(i32)]),
+        "xb_sell_layout": (i32, [i32, P(i32), i32, P(i32), P(i32), P(C.c_int64),
+                                 P(C.c_int64)]),
         "xb_policy_read": (i32, [C.c_char_p, i32, P(Options), P(i32), P(f64), P(i32)]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
@@ -186,6 +188,23 @@ def _need(t, dtype, name):
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous {dtype} tensor (got {t.dtype})")
+
+
+def sell_layout(rowptr, sigma):
+    """The SELL-32-sigma layout the SELL variant builds: (perm, slen, off,
+    total) as numpy arrays (host logic)."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    n = rp.size - 1
+    slots = 32 * ((n + 31) // 32)
+    perm = np.zeros(max(slots, 1), np.int32)
+    slen = np.zeros(max(slots, 1), np.int32)
+    off = np.zeros((n + 31) // 32 + 1, np.int64)
+    tot = C.c_int64()
+    f = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+    _check(lib().xb_sell_layout(n, f(rp, C.c_int32), int(sigma), f(perm, C.c_int32),
+                                f(slen, C.c_int32), f(off, C.c_int64), C.byref(tot)))
+    return perm[:slots], slen[:slots], off, tot.value
 
 
 def merge_options(options, kw):

@@ -167,6 +167,11 @@ const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err
 // SELL-32-sigma copy (FP32 values too when f32); XB_EINVAL when the padding
 // would exceed 3 nnz + 32 per slice.
 const SellPart *get_sell(xb_plan *p, int sigma, bool f32, cudaStream_t s, int *err);
+// The SELL-32-sigma layout on the host from the row pointer (n + 1 entries):
+// perm (slot -> row, -1 past n), slen (slot -> row length), off (slice entry
+// offsets, nslices + 1); returns the padded entry count.
+int64_t sell_layout(int n, const int *rp, int sigma, std::vector<int> &perm,
+                    std::vector<int> &slen, std::vector<int64_t> &off);
 const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err);
 int ensure_val32(xb_plan *p, cudaStream_t s);
 int ensure_work(xb_plan *p, size_t bytes);

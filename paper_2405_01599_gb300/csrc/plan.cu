@@ -243,43 +243,47 @@ __global__ void k_sell_scatter(int64_t nslots, const int *__restrict__ perm,
     }
 }
 
+int64_t sell_layout(int n, const int *rp, int sigma, std::vector<int> &perm,
+                    std::vector<int> &slen, std::vector<int64_t> &off) {
+    const int nslices = (n + 31) / 32;
+    const size_t nslots = (size_t)nslices * 32;
+    perm.assign(nslots, -1);
+    for (int i = 0; i < n; i++) perm[i] = i;
+    auto len = [&](int r) { return rp[r + 1] - rp[r]; };
+    for (int w0 = 0; w0 < n; w0 += sigma) {
+        const int w1 = (int)std::min<int64_t>(n, (int64_t)w0 + sigma);
+        std::stable_sort(perm.begin() + w0, perm.begin() + w1,
+                         [&](int a, int b) { return len(a) > len(b); });
+    }
+    slen.assign(nslots, 0);
+    for (size_t q = 0; q < nslots; q++)
+        if (perm[q] >= 0) slen[q] = len(perm[q]);
+    off.assign((size_t)nslices + 1, 0);
+    for (int q = 0; q < nslices; q++) {
+        int wd = 0;
+        for (int l = 0; l < 32; l++) wd = std::max(wd, slen[(size_t)q * 32 + l]);
+        off[q + 1] = off[q] + 32LL * wd;
+    }
+    return off[nslices];
+}
+
 const SellPart *get_sell(xb_plan *p, int sigma, bool f32, cudaStream_t s, int *err) {
     SellPart *sp = nullptr;
     for (auto &t : p->sells)
         if (t.sigma == sigma) sp = &t;
     if (!sp) {
-        const int n = p->n;
-        const int *rp = p->h_rowptr.data();
         SellPart t;
         t.sigma = sigma;
-        t.nslices = (n + 31) / 32;
+        t.nslices = (p->n + 31) / 32;
         const size_t nslots = (size_t)t.nslices * 32;
-        std::vector<int> perm(nslots, -1);
-        for (int i = 0; i < n; i++) perm[i] = i;
-        auto len = [&](int r) { return rp[r + 1] - rp[r]; };
-        for (int w0 = 0; w0 < n; w0 += sigma) {
-            const int w1 = (int)std::min<int64_t>(n, (int64_t)w0 + sigma);
-            std::stable_sort(perm.begin() + w0, perm.begin() + w1,
-                             [&](int a, int b) { return len(a) > len(b); });
-        }
-        std::vector<int64_t> off((size_t)t.nslices + 1, 0);
-        for (int q = 0; q < t.nslices; q++) {
-            int wd = 0;
-            for (int l = 0; l < 32; l++) {
-                const int r = perm[(size_t)q * 32 + l];
-                if (r >= 0) wd = std::max(wd, len(r));
-            }
-            off[q + 1] = off[q] + 32LL * wd;
-        }
-        t.total = off[t.nslices];
+        std::vector<int> perm, slen;
+        std::vector<int64_t> off;
+        t.total = sell_layout(p->n, p->h_rowptr.data(), sigma, perm, slen, off);
         if (t.total > 3LL * p->nnz + 32LL * t.nslices) {
             *err = set_error(XB_EINVAL, "SELL-32-%d: padding to %lld entries for %d non-zeros",
                              sigma, (long long)t.total, p->nnz);
             return nullptr;
         }
-        std::vector<int> slen(nslots, 0);
-        for (size_t q = 0; q < nslots; q++)
-            if (perm[q] >= 0) slen[q] = len(perm[q]);
         const size_t tot = (size_t)std::max<int64_t>(t.total, 1);
         cudaError_t e = cudaMalloc(&t.d_off, off.size() * sizeof(int64_t));
         if (e == cudaSuccess) e = cudaMalloc(&t.d_perm, nslots * sizeof(int) + 4);
@@ -644,3 +648,16 @@ int xb_features(const xb_csr *A, double *raw, float *feat, void *stream) {
 }
 
 }  // extern "C"
+
+extern "C" int xb_sell_layout(int32_t n, const int32_t *rowptr, int32_t sigma, int32_t *perm,
+                              int32_t *slen, int64_t *off, int64_t *total) {
+    if (n < 0 || !rowptr || sigma < 1 || !total)
+        return xb::set_error(XB_EINVAL, "sell_layout: bad argument");
+    std::vector<int> pv, lv;
+    std::vector<int64_t> ov;
+    *total = xb::sell_layout(n, rowptr, sigma, pv, lv, ov);
+    if (perm) std::copy(pv.begin(), pv.end(), perm);
+    if (slen) std::copy(lv.begin(), lv.end(), slen);
+    if (off) std::copy(ov.begin(), ov.end(), off);
+    return XB_OK;
+}
