@@ -409,6 +409,14 @@ int xb_ilu0_apply(xb_plan *plan, const double *r, double *z, void *stream);
 /* Copy the factors (aligned with the plan's col array: strict lower part = L
  * with unit diagonal not stored, the rest = U) to the DEVICE array lu (nnz). */
 int xb_ilu0_factors(xb_plan *plan, double *lu, void *stream);
+/* The dependency levels xb_ilu0_setup schedules by (host logic, no device
+ * work; exposed for testing): for the row pattern (HOST rowptr n + 1, col
+ * nnz, sorted rows), lev[i] = 1 + max lev over the row's strictly-lower
+ * columns (0 if none) and ulev[i] = 1 + max ulev over its strictly-upper
+ * columns; nlevels[0..1] = the level counts.  lev, ulev (n) and nlevels (2)
+ * are HOST arrays or NULL.  XB_EBREAKDOWN for a row without a diagonal. */
+int xb_ilu_levels(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t *lev,
+                  int32_t *ulev, int32_t *nlevels);
 
 /* ---- numerical policy file (Sec. 2.3.2) -----------------------------------
  * The meta-solvers' user input: lines "<keyword> = <value>", keywords in any

@@ -125,6 +125,7 @@ def lib():
         "xb_policy_parse": (i32, [C.c_char_p, P(Options), P(i32), P(f64), P(i32)]),
         "xb_sell_layout": (i32, [i32, P(i32), i32, P(i32), P(i32), P(C.c_int64),
                                  P(C.c_int64)]),
+        "xb_ilu_levels": (i32, [i32, P(i32), P(i32), P(i32), P(i32), P(i32)]),
         "xb_policy_read": (i32, [C.c_char_p, i32, P(Options), P(i32), P(f64), P(i32)]),
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
@@ -205,6 +206,21 @@ def sell_layout(rowptr, sigma):
     _check(lib().xb_sell_layout(n, f(rp, C.c_int32), int(sigma), f(perm, C.c_int32),
                                 f(slen, C.c_int32), f(off, C.c_int64), C.byref(tot)))
     return perm[:slots], slen[:slots], off, tot.value
+
+
+def ilu_levels(rowptr, col):
+    """Dependency levels of the ILU(0) triangles (host logic): (lev, ulev,
+    (number of lower levels, number of upper levels))."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    n = rp.size - 1
+    lev = np.zeros(max(n, 1), np.int32)
+    ulev = np.zeros(max(n, 1), np.int32)
+    nl = np.zeros(2, np.int32)
+    f = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(lib().xb_ilu_levels(n, f(rp), f(ci) if ci.size else None, f(lev), f(ulev), f(nl)))
+    return lev[:n], ulev[:n], (int(nl[0]), int(nl[1]))
 
 
 def merge_options(options, kw):

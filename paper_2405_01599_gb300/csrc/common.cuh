@@ -179,6 +179,12 @@ int ensure_work(xb_plan *p, size_t bytes);
 // device), apply z = (LU)^{-1} r on stream s, and the algorithmic bytes of one
 // application.
 int ensure_ilu(xb_plan *p, cudaStream_t s);
+// Dependency levels of the two triangles from the pattern (host): lev[i] = 1 +
+// the largest lev of the row's strictly-lower columns (0 if none), ulev[i]
+// likewise over its strictly-upper columns; dpos = each row's diagonal entry;
+// *nl, *nu = level counts.  XB_EBREAKDOWN for a row without a diagonal entry.
+int ilu_levels(int n, const int *rp, const int *ci, std::vector<int> &dpos, std::vector<int> &lev,
+               std::vector<int> &ulev, int *nl, int *nu);
 int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s);
 double ilu_apply_bytes(const xb_plan *p);
 int ilu_check(xb_plan *p);  // XB_ETIMEOUT if a substitution's barrier wait ran out

@@ -423,17 +423,13 @@ void ilu_free(xb_plan *p) {
     u = IluData();
 }
 
-int ensure_ilu(xb_plan *p, cudaStream_t s) {
-    IluData &u = p->ilu;
-    if (u.built) return u.status == XB_OK ? XB_OK : set_error(u.status, "ILU(0): zero pivot");
-    if (p->sym) return set_error(XB_EINVAL, "ILU(0) needs full (general) CRS storage");
-    ilu_free(p);  // a build that failed half-way left nothing usable
-    const int n = p->n, nnz = p->nnz;
-    const std::vector<int> &rp = p->h_rowptr;
-    std::vector<int> ci(nnz);
-    if (nnz > 0) XB_CUDA(cudaMemcpy(ci.data(), p->col, (size_t)nnz * 4, cudaMemcpyDeviceToHost));
-    std::vector<int> dpos(n), lev(n, 0), ulev(n, 0);
-    int nl = n > 0 ? 1 : 0, nu = n > 0 ? 1 : 0;
+int ilu_levels(int n, const int *rp, const int *ci, std::vector<int> &dpos, std::vector<int> &lev,
+               std::vector<int> &ulev, int *nl, int *nu) {
+    dpos.assign(n, 0);
+    lev.assign(n, 0);
+    ulev.assign(n, 0);
+    *nl = n > 0 ? 1 : 0;
+    *nu = n > 0 ? 1 : 0;
     for (int i = 0; i < n; i++) {
         int d = -1, m = -1;
         for (int q = rp[i]; q < rp[i + 1]; q++) {
@@ -444,14 +440,29 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
         if (d < 0) return set_error(XB_EBREAKDOWN, "ILU(0): row %d has no diagonal entry", i);
         dpos[i] = d;
         lev[i] = m + 1;
-        nl = std::max(nl, lev[i] + 1);
+        *nl = std::max(*nl, lev[i] + 1);
     }
     for (int i = n - 1; i >= 0; i--) {
         int m = -1;
         for (int q = dpos[i] + 1; q < rp[i + 1]; q++) m = std::max(m, ulev[ci[q]]);
         ulev[i] = m + 1;
-        nu = std::max(nu, ulev[i] + 1);
+        *nu = std::max(*nu, ulev[i] + 1);
     }
+    return XB_OK;
+}
+
+int ensure_ilu(xb_plan *p, cudaStream_t s) {
+    IluData &u = p->ilu;
+    if (u.built) return u.status == XB_OK ? XB_OK : set_error(u.status, "ILU(0): zero pivot");
+    if (p->sym) return set_error(XB_EINVAL, "ILU(0) needs full (general) CRS storage");
+    ilu_free(p);  // a build that failed half-way left nothing usable
+    const int n = p->n, nnz = p->nnz;
+    const std::vector<int> &rp = p->h_rowptr;
+    std::vector<int> ci(nnz);
+    if (nnz > 0) XB_CUDA(cudaMemcpy(ci.data(), p->col, (size_t)nnz * 4, cudaMemcpyDeviceToHost));
+    std::vector<int> dpos, lev, ulev;
+    int nl = 0, nu = 0;
+    XB_TRY(ilu_levels(n, rp.data(), ci.data(), dpos, lev, ulev, &nl, &nu));
     std::vector<int> llen(n), ulen(n);
     for (int i = 0; i < n; i++) {
         llen[i] = dpos[i] - rp[i];
@@ -663,3 +674,19 @@ int xb_ilu0_factors(xb_plan *p, double *lu, void *stream) {
 }
 
 }  // extern "C"
+
+extern "C" int xb_ilu_levels(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t *lev,
+                             int32_t *ulev, int32_t *nlevels) {
+    if (n < 0 || !rowptr || (n > 0 && !col))
+        return xb::set_error(XB_EINVAL, "ilu_levels: bad argument");
+    std::vector<int> d, l, u;
+    int nl = 0, nu = 0;
+    XB_TRY(xb::ilu_levels(n, rowptr, col, d, l, u, &nl, &nu));
+    if (lev) std::copy(l.begin(), l.end(), lev);
+    if (ulev) std::copy(u.begin(), u.end(), ulev);
+    if (nlevels) {
+        nlevels[0] = nl;
+        nlevels[1] = nu;
+    }
+    return XB_OK;
+}
