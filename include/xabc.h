@@ -396,6 +396,14 @@ int xb_arnoldi(xb_plan *plan, int32_t nev, int32_t m, int32_t m_max, double thet
  * neither NULL) the unit eigenvectors, largest entry real and positive. */
 int xb_dense_eig(int32_t n, const double *A, int32_t which, double *wr, double *wi, double *vr,
                  double *vi);
+/* The restart step of xb_arnoldi on a small dense matrix (host logic,
+ * exposed for testing): the k leading wanted eigenvalues of the HOST
+ * row-major n x n matrix A (2 <= n <= 512, 1 <= k < n; k moved by one when it
+ * would split a conjugate pair), their invariant subspace as an orthonormal
+ * real basis in Q (HOST, n x (k + 1) column-major room), *kout = its
+ * dimension. */
+int xb_dense_restart_basis(int32_t n, const double *A, int32_t which, int32_t k, double *Q,
+                           int32_t *kout);
 
 /* ---- ILU(0) preconditioner (Sec. 4.3) -------------------------------------
  * Built once per plan on first use (dependency levels of the two triangles

@@ -122,6 +122,7 @@ def lib():
         "xb_arnoldi": (i32, [vp, i32, i32, i32, f64, f64, i32, i32, i32, i32, vp, P(f64), P(f64),
                              vp, vp, P(f64), P(i32), P(f64), vp]),
         "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
+        "xb_dense_restart_basis": (i32, [i32, P(f64), i32, i32, P(f64), P(i32)]),
         "xb_policy_parse": (i32, [C.c_char_p, P(Options), P(i32), P(f64), P(i32)]),
         "xb_sell_layout": (i32, [i32, P(i32), i32, P(i32), P(i32), P(C.c_int64),
                                  P(C.c_int64)]),
@@ -189,6 +190,21 @@ def _need(t, dtype, name):
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous {dtype} tensor (got {t.dtype})")
+
+
+def dense_restart_basis(A, k, which=EIG_LR):
+    """The Arnoldi restart step on a small dense matrix (host logic): an
+    orthonormal real basis (n x k') of the invariant subspace of A's k leading
+    wanted eigenvalues (k' = k, or k +- 1 to keep a conjugate pair whole)."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    Q = np.zeros((k + 1) * n)
+    ko = C.c_int32()
+    P = C.POINTER(C.c_double)
+    _check(lib().xb_dense_restart_basis(n, A.ctypes.data_as(P), int(which), int(k),
+                                        Q.ctypes.data_as(P), C.byref(ko)))
+    return Q[:n * ko.value].reshape(ko.value, n).T
 
 
 def sell_layout(rowptr, sigma):

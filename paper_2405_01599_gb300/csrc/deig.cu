@@ -301,6 +301,11 @@ void schur_eigvec(int m, const std::vector<cplx> &T, const std::vector<cplx> &Z,
         for (int r = 0; r < m; r++) y[r] /= nrm;
 }
 
+int keep_count(const std::vector<signed char> &kind, int k0, int m) {
+    if (k0 >= 1 && k0 <= m && kind[k0 - 1] == 1) return k0 + 1 <= m - 1 ? k0 + 1 : k0 - 1;
+    return k0;
+}
+
 int real_basis(int m, const std::vector<cplx> &Z, int k, std::vector<double> &Q) {
     const int nc = 2 * k;
     std::vector<double> C((size_t)nc * m);  // candidate columns, column-major
@@ -354,6 +359,24 @@ int real_basis(int m, const std::vector<cplx> &Z, int k, std::vector<double> &Q)
 }  // namespace xb
 
 extern "C" {
+
+int xb_dense_restart_basis(int32_t n, const double *A, int32_t which, int32_t k, double *Q,
+                           int32_t *kout) {
+    if (n < 2 || n > 512 || !A || !Q || !kout || k < 1 || k >= n ||
+        (which != XB_EIG_LR && which != XB_EIG_LM))
+        return xb::set_error(XB_EINVAL, "dense_restart_basis: bad argument");
+    std::vector<xb::cplx> T, Z, w;
+    XB_TRY(xb::schur(n, A, T, Z));
+    std::vector<int> ord;
+    std::vector<signed char> kind;
+    xb::eig_order(n, T, which, ord, kind, w);
+    const int kk = xb::keep_count(kind, k, n);
+    xb::schur_reorder(n, T, Z, ord, kk);
+    std::vector<double> q;
+    *kout = xb::real_basis(n, Z, kk, q);
+    std::copy(q.begin(), q.begin() + (size_t)n * *kout, Q);
+    return XB_OK;
+}
 
 int xb_dense_eig(int32_t n, const double *A, int32_t which, double *wr, double *wi, double *vr,
                  double *vi) {

@@ -36,6 +36,10 @@ void schur_reorder(int m, std::vector<cplx> &T, std::vector<cplx> &Z, const std:
 void schur_eigvec(int m, const std::vector<cplx> &T, const std::vector<cplx> &Z, int i,
                   bool real_ev, std::vector<cplx> &y);
 
+// The number of leading wanted eigenvalues to keep, k0 moved by one (up if
+// room remains below m, else down) when it would split a conjugate pair.
+int keep_count(const std::vector<signed char> &kind, int k0, int m);
+
 // Orthonormal REAL basis (m x k column-major in Q) of the span of Z's first k
 // columns, which must be closed under conjugation: pivoted Gram-Schmidt
 // (two passes) over the 2k columns Re Z, Im Z.  Returns the number of

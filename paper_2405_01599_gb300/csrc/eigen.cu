@@ -516,8 +516,7 @@ int xb_arnoldi(xb_plan *p, int32_t nev, int32_t m, int32_t m_max, double theta, 
         xb::eig_order(m, TS, which, ord, kind, w);
         // kept Ritz values: k = nev + (m - nev)/2, moved by one so that no
         // conjugate pair is split
-        int kk = nev + (m - nev) / 2;
-        if (kind[kk - 1] == 1) kk = kk + 1 <= m - 1 ? kk + 1 : kk - 1;
+        int kk = xb::keep_count(kind, nev + (m - nev) / 2, m);
         xb::schur_reorder(m, TS, Z, ord, kk);
         bool conv = true;
         S.assign((size_t)2 * m * nev, 0.0);

@@ -141,6 +141,36 @@ def test_invariant_start_vector_breaks_down():
     assert info["status"] == -5
 
 
+@pytest.mark.parametrize("which", [0, 1])
+def test_library_restart_basis(which):
+    """The library's own restart step (host logic, the one xb_arnoldi runs):
+    an orthonormal real basis of the invariant subspace of the k wanted
+    eigenvalues, pairs whole; it spans the oracle's restart subspace."""
+    import paper_2405_01599_gb300 as xb
+    try:
+        xb.lib()
+    except ImportError:
+        pytest.skip("CUDA library not built")
+    from oracle.eig import restart_basis
+    rng = np.random.default_rng(31 + which)
+    for m in (10, 25, 40):
+        H = np.triu(rng.standard_normal((m, m)), -1)
+        lam = np.linalg.eigvals(H)
+        order = oracle.wanted_order(lam, which)
+        k0 = m // 2
+        Q = xb.dense_restart_basis(H, k0, which)
+        kk = Q.shape[1]
+        want_k = k0 + 1 if lam[order[k0 - 1]].imag > 0 else k0
+        assert kk == want_k
+        np.testing.assert_allclose(Q.T @ Q, np.eye(kk), atol=1e-12)
+        Tk = Q.T @ H @ Q
+        assert np.max(np.abs(H @ Q - Q @ Tk)) <= 1e-11 * np.max(np.abs(H))
+        assert same_multiset(np.linalg.eigvals(Tk), lam[order[:kk]], 1e-9)
+        Qo, _ = restart_basis(H, lam, order, kk, which)  # the oracle's subspace
+        s = np.linalg.svd(Qo.T @ Q, compute_uv=False)
+        np.testing.assert_allclose(s, 1.0, atol=1e-9)  # same subspace: all cosines 1
+
+
 def test_dense_eig_special_matrices():
     """Host dense step on matrices with a known spectrum: zero, 1 x 1, a
     rotation (+-2i), a Jordan block (defective, all 2), the cyclic
