@@ -172,23 +172,41 @@ def alg_bytes(A, vb=8, beta=False):
 
 
 # DRAM bytes (read + write) of one headline SpMV launch from an ncu capture, keyed by
-# (variant, block, ipt, n, nnz) and valid only while the kernel source is unchanged
-# (sha256 of csrc/spmv.cu at capture time); the capture and its command are summarised
-# in profiles/.
+# (variant, block, ipt, n, nnz) and valid only while the code that launch ran is
+# unchanged: the sha256 of the segmented-scan kernels, their launcher and the
+# row-store helper (csrc/spmv.cu) and of the plan builders of their row-end bitmask
+# and warp start rows (csrc/plan.cu), as cut out by HEADLINE_SRC below.  The
+# capture and its command are summarised in profiles/.
 NCU_TRAFFIC = {
     ("segscan", 128, 8, 4_000_000, 52_238_581):
-        (706.63e6, "4c4768442d1f9d0cae72f095beeae3970f699faa254132d7a73e484da642fdb6"),
+        (706.63e6, "e754fb61fd997d69e722bc8923891f434d2c502a07d577334435fb08ac5baff7"),
 }
+HEADLINE_SRC = [
+    ("spmv.cu", "__device__ __forceinline__ void store_row(", "// U1: one thread per row"),
+    ("spmv.cu", "// U3 (BSS) with the plan's row-end bitmask", "// S1-like baseline"),
+    ("spmv.cu", "int launch_seg(", "int launch_sym("),
+    ("plan.cu", "__global__ void k_seg_rows(", "__global__ void k_to_f32("),
+]
+
+
+def headline_src_hash():
+    import hashlib
+    parts = []
+    for fname, start, end in HEADLINE_SRC:
+        with open(os.path.join(ROOT, "paper_2405_01599_gb300", "csrc", fname)) as f:
+            src = f.read()
+        i = src.find(start)
+        j = src.find(end, i + 1) if i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        parts.append(src[i:j])
+    return hashlib.sha256("\0".join(parts).encode()).hexdigest()
 
 
 def ncu_traffic(choice_name, block, ipt, n, nnz):
-    import hashlib
     ent = NCU_TRAFFIC.get((choice_name, block, ipt, n, nnz))
-    if ent is None:
+    if ent is None or headline_src_hash() != ent[1]:
         return None
-    with open(os.path.join(ROOT, "paper_2405_01599_gb300", "csrc", "spmv.cu"), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != ent[1]:
-            return None
     return ent[0]
 
 
