@@ -276,8 +276,7 @@ def gmres_ir(A, b, x0=None, m=30, tol=1e-8, tol_in=1e-5, maxit_in=300, max_outer
     dd = np.zeros(2)
     st = lib().orc_gmres_ir(n, rp, ci, va, np.ascontiguousarray(b, np.float64), x, int(m),
                             float(tol), float(tol_in), int(maxit_in), int(max_outer), ii, dd)
-    return x, dict(status=st, inner_iters=int(ii[0]), outer=int(ii[1]),
-                   fallback_iters=int(ii[4]), fallback=int(ii[5]), res_true=float(dd[1]))
+    return x, dict(status=st, inner_iters=int(ii[0]), outer=int(ii[1]), res_true=float(dd[1]))
 
 
 def features(A):

@@ -159,6 +159,48 @@ def test_mixed_refinement_reaches_fp64_accuracy():
         assert info["outer"] >= 2  # FP32 inner alone cannot reach 1e-8
 
 
+def test_refinement_steps_contract_by_the_inner_tolerance():
+    """The plain refinement loop, step by step: the inner FP32 solve leaves
+    ||r/||r|| - A d|| <= tol_in (up to FP32 rounding), and x += ||r|| d makes
+    that the next FP64 residual, so each step shrinks ||b - A x|| by at most
+    about tol_in.  Residuals are recomputed densely here, independently of the
+    oracle; a dropped ||r|| scale, a wrong sign in the update or a residual
+    taken against float(A) breaks the bound."""
+    A = gen.poisson2d(32)
+    D = gen.to_dense(A)
+    b = _rhs_ones(A)
+    for tin in (0.3, 0.5):
+        res = []
+        for k in range(5):
+            x, info = oracle.gmres_ir(A, b, m=30, tol=1e-14, tol_in=tin, max_outer=k)
+            assert info["status"] == -4 and info["outer"] == k
+            res.append(np.linalg.norm(b - D @ x) / np.linalg.norm(b))
+            assert abs(res[-1] - info["res_true"]) <= 1e-12
+        assert res[0] == 1.0
+        for k in range(1, 5):
+            assert res[k] <= tin * (1 + 1e-3) * res[k - 1] + 1e-6, (tin, k, res)
+
+
+def test_stagnating_refinement_stays_plain():
+    """One inner Arnoldi step per refinement step contracts slowly (the
+    residual ratio climbs above 1/2); the plain loop keeps refining until
+    max_outer and never hands over to another solver: one inner step per
+    outer step, residual decreasing, ENOCONV at the cap."""
+    A = gen.poisson2d(32)
+    D = gen.to_dense(A)
+    b = _rhs_ones(A)
+    x, info = oracle.gmres_ir(A, b, m=30, tol=1e-8, tol_in=1e-4, maxit_in=1, max_outer=6)
+    assert info["status"] == -4 and info["outer"] == 6 and info["inner_iters"] == 6
+    prev = 1.0
+    for k in range(1, 7):
+        xk, _ = oracle.gmres_ir(A, b, m=30, tol=1e-8, tol_in=1e-4, maxit_in=1, max_outer=k)
+        rk = np.linalg.norm(b - D @ xk) / np.linalg.norm(b)
+        assert rk < prev
+        prev = rk
+    assert prev > 0.5 ** 6  # no FP64 solve took over
+    np.testing.assert_array_equal(x, xk)
+
+
 def test_inner_f32_solve_contracts_residual():
     A = gen.poisson2d(16)
     r = np.random.default_rng(0).standard_normal(A["n"]).astype(np.float32)
