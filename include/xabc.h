@@ -148,6 +148,15 @@ typedef struct xb_options {
                              /*   return XB_EFAULT if the true residual misses */
     int32_t precond;         /* XB_PRECOND_*: right preconditioner (FP64      */
                              /*   GMRES and BiCGStab on general CRS)           */
+    int32_t ir_fallback;     /* mixed precision only.  0: plain refinement    */
+                             /*   (FP64 residual, FP32 inner GMRES, x += ||r|| */
+                             /*   d) until tol or max_outer.  1 (default): a   */
+                             /*   library safeguard, not part of the method:   */
+                             /*   when the FP64 residual fails to halve in two */
+                             /*   consecutive refinement steps (FP32 cannot    */
+                             /*   resolve the system: kappa * 6e-8 near 1),    */
+                             /*   the solve continues as FP64 GMRES(m) from    */
+                             /*   the current x and xb_info.fallback = 1       */
 } xb_options;
 
 typedef struct xb_info {
@@ -244,20 +253,28 @@ int spmv_segscan(xb_plan *plan, double alpha, const double *x, double beta, doub
  * For callers that cannot allocate device memory -- their device memory is
  * owned by another allocator, or an allocation's implicit synchronisation is
  * not allowed where they call -- and therefore cannot create a plan either.
- * Takes the CRS arrays directly (device pointers, same rules as xb_csr with
- * sym_upper = 0) and computes y = alpha*A*x + beta*y with the U3 kernels at a
- * fixed shape of 256 threads x 8 non-zeros per thread.  Its scratch (16 bytes
+ * Takes the CRS arrays directly (device pointers, laid out as xb_csr with
+ * sym_upper = 0) and computes y = alpha*A*x + beta*y with a staged per-CTA
+ * segmented-scan kernel at a fixed shape of 256 threads x 8 non-zeros per
+ * thread.  The arrays are NOT validated (there is no plan to do it): the
+ * caller guarantees rowptr[0] = 0, rowptr non-decreasing, rowptr[n] = nnz and
+ * 0 <= col < n.  The kernel only keeps its own accesses inside x and y when
+ * they do not hold (an out-of-range column adds nothing, a row index past n
+ * is not stored); the result is then meaningless.  x and y must not overlap
+ * (XB_EINVAL).  Its scratch (16 bytes
  * per 2048 non-zeros) lives in one 4 MiB array compiled into the library,
  * which every GPU that loads the library holds until the process exits; it
  * calls no cudaMalloc/cudaFree.  Limit: nnz <= 262,142 * 2048 (about 5.4e8);
- * larger inputs return XB_EINVAL with that limit in the message.  The first
- * call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * larger inputs return XB_EINVAL with that limit in the message.  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress; after cudaDeviceReset the next call finds the
+ * reloaded array).  The first call on a device also loads the library's
+ * device code there, so make that first call before any stream capture.
  * All calls share the one array: calls that overlap on the GPU (for example
  * on two streams) race and must be serialised by the caller.  Each row is
- * summed in the same order as the other SpMV entry points up to the final
- * combination of partial sums, so results agree with spmv_segscan to within
- * rounding (the library's 1e-12 row tolerance). */
+ * summed in CRS order up to the final combination of partial sums, so
+ * results agree with spmv_segscan within rounding (the library's 1e-12 row
+ * tolerance), not bit for bit. */
 int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
                          const double *val, double alpha, const double *x, double beta,
                          double *y, void *stream);
@@ -272,6 +289,20 @@ int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowptr, const in
  * padded entry count. */
 int xb_sell_layout(int32_t n, const int32_t *rowptr, int32_t sigma, int32_t *perm,
                    int32_t *slen, int64_t *off, int64_t *total);
+
+/* The warp tiles that XB_VAR_NNZ (U2) builds for items per thread ipt (host
+ * logic, no device work; exposed for testing).  Rows are cut, in order, into
+ * tiles [r0, r1) whose non-zeros fit the 32*ipt-entry window starting at
+ * rowptr[r0] rounded down to a multiple of ipt; a tile takes rows while they
+ * fit, and stops at 32 rows while none of its rows is longer than ipt (kind 0,
+ * thread per row; otherwise kind 1, flat).  A row that overflows a window on
+ * its own is a long row (CTA per row).  HOST arrays: rowptr (n + 1); tiles
+ * (4 int32 per tile: r0, r1, number of non-empty rows before r0, kind + 4 if
+ * the tile has an empty row), filled up to cap_tiles tiles; longs, filled up
+ * to cap_long rows.  *ntiles and *nlong receive the full counts.  tiles and
+ * longs may be NULL (capacity 0) to query the counts. */
+int xb_u2_layout(int32_t n, const int32_t *rowptr, int32_t ipt, int32_t *tiles, int32_t cap_tiles,
+                 int32_t *ntiles, int32_t *longs, int32_t cap_long, int32_t *nlong);
 
 /* Any variant (XB_VAR_*; XB_VAR_AUTO = plan choice) with an explicit launch
  * shape (block/ipt 0 = plan choice).  XB_VAR_SELL builds the SELL-32-sigma

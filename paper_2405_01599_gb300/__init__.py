@@ -49,7 +49,7 @@ class Options(C.Structure):
                 ("max_outer", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
                 ("ipt", C.c_int32), ("tuner", C.c_int32), ("check_every", C.c_int32),
                 ("timing", C.c_int32), ("policy", C.c_int32), ("fault_check", C.c_int32),
-                ("precond", C.c_int32)]
+                ("precond", C.c_int32), ("ir_fallback", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -124,6 +124,7 @@ def lib():
         "xb_dense_eig": (i32, [i32, P(f64), i32, P(f64), P(f64), P(f64), P(f64)]),
         "xb_dense_restart_basis": (i32, [i32, P(f64), i32, i32, P(f64), P(i32)]),
         "xb_policy_parse": (i32, [C.c_char_p, P(Options), P(i32), P(f64), P(i32)]),
+        "xb_u2_layout": (i32, [i32, P(i32), i32, P(i32), i32, P(i32), P(i32), i32, P(i32)]),
         "xb_sell_layout": (i32, [i32, P(i32), i32, P(i32), P(i32), P(C.c_int64),
                                  P(C.c_int64)]),
         "xb_ilu_levels": (i32, [i32, P(i32), P(i32), P(i32), P(i32), P(i32)]),
@@ -222,6 +223,23 @@ def sell_layout(rowptr, sigma):
     _check(lib().xb_sell_layout(n, f(rp, C.c_int32), int(sigma), f(perm, C.c_int32),
                                 f(slen, C.c_int32), f(off, C.c_int64), C.byref(tot)))
     return perm[:slots], slen[:slots], off, tot.value
+
+
+def u2_layout(rowptr, ipt):
+    """The nnz-balanced warp tiles the NNZ (U2) variant builds: (tiles, longs)
+    with tiles an (ntiles, 4) int32 array {r0, r1, ne0, kind | 4*has_empty}
+    (host logic)."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    n = rp.size - 1
+    nt, nl = C.c_int32(), C.c_int32()
+    f = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(lib().xb_u2_layout(n, f(rp), int(ipt), None, 0, C.byref(nt), None, 0, C.byref(nl)))
+    tiles = np.zeros(4 * max(nt.value, 1), np.int32)
+    longs = np.zeros(max(nl.value, 1), np.int32)
+    _check(lib().xb_u2_layout(n, f(rp), int(ipt), f(tiles), nt.value, C.byref(nt), f(longs),
+                              nl.value, C.byref(nl)))
+    return tiles[:4 * nt.value].reshape(-1, 4), longs[:nl.value]
 
 
 def ilu_levels(rowptr, col):

@@ -54,6 +54,23 @@ struct TilePart {
     int ntiles = 0;
     int *d_row = nullptr;    // ntiles+1
 };
+// Row-aligned nnz-balanced warp tiles (U2).  Warp tile t covers rows
+// [r0, r1) whose non-zeros [k0, k1) fit the 32*ipt-entry window that starts
+// at k0 rounded down to a multiple of ipt; rows never cross tiles.  Kind:
+//   0  thread per row: at most 32 rows, none longer than ipt;
+//   1  flat: lane l sums window entries [l*ipt, (l+1)*ipt) inside [k0, k1),
+//      row ends from the BSS bitmask, rows joined by a segmented warp scan.
+// A row too long for a window is listed in d_long and gets a CTA.  When every
+// tile is 32 rows of kind 0 (uniform short rows) the tiles are implicit
+// (tile t = rows [32t, 32t + 32)) and no table is read.
+struct U2Part {
+    int ipt = 0;
+    int ntiles = 0, nlong = 0, nflat = 0;
+    bool implicit = false;
+    int4 *d_tile = nullptr;  // {r0, r1, ne0 (non-empty-row index of the first
+                             //  non-empty row >= r0), kind | 4 if it has empty rows}
+    int *d_long = nullptr;
+};
 // Flat nnz segments (U3, BSS): warp w owns non-zeros [w*W, (w+1)*W), W =
 // 32*ipt; d_row[w] is the (non-empty-row) index of the row holding non-zero
 // w*W; one carry slot per warp feeds the fix-up.
@@ -84,12 +101,29 @@ struct SellPart {
 // shape): bit e of d_endbits is set when non-zero e is the last one of its
 // row; with empty rows present, rows are renumbered over the non-empty ones
 // (d_ne_rows maps back, d_crp is the rowptr of the non-empty rows).
+// The BSS data format: A's values and columns copied in the order the
+// segmented-scan warps read them.  Warp chunk g holds non-zeros
+// [g*W, (g+1)*W), W = 32*ipt, and lane l of its warp owns the ipt consecutive
+// ones from g*W + l*ipt.  The copy stores the lane's values as vectors of VN
+// consecutive elements (VN = 2 for FP64, 4 for FP32): vector q of lane l sits
+// at g*W + (q*32 + l)*VN; columns likewise in vectors of 4.  The q-th vector
+// load of a warp therefore reads 32 consecutive 16-byte vectors (512 bytes,
+// four whole 128-byte lines) instead of 32 vectors 16*ipt/VN bytes apart.
+// Padded with zero values (column 0) to whole chunks.
+struct BssCopy {
+    int ipt = 0;
+    int64_t total = 0;               // entries including padding
+    int *d_col = nullptr;
+    double *d_val = nullptr;
+    float *d_val32 = nullptr;        // built on the first FP32 use
+};
 struct BssData {
     unsigned *d_endbits = nullptr;   // ceil(nnz/32) + 1 words
     int *d_ne_rows = nullptr;        // n_ne, or null when no row is empty
     int *d_crp = nullptr;            // n_ne + 1, or null (then rowptr)
     int n_ne = 0;
     bool built = false;
+    std::vector<BssCopy> copies;     // one per ipt in use
 };
 
 // ILU(0) preconditioner data (built on first use): factors in A's pattern
@@ -142,6 +176,7 @@ struct xb_plan {
     int *d_empty = nullptr;              // rows with no stored entry
     std::vector<xb::TilePart> tiles;     // cache by (block, ipt)
     std::vector<xb::SegPart> segs;       // cache by (block, ipt)
+    std::vector<xb::U2Part> u2;          // cache by ipt
     std::vector<xb::SellPart> sells;     // cache by sigma
     xb::BssData bss;
     xb::IluData ilu;
@@ -164,6 +199,10 @@ namespace xb {
 
 const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
 const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
+const U2Part *get_u2(xb_plan *p, int ipt, cudaStream_t s, int *err);
+// The U2 warp tiles on the host from the row pointer (n + 1 entries); returns
+// the number of flat tiles.  tiles: {r0, r1, ne0, kind | 4 * has_empty}.
+int u2_layout(int n, const int *rp, int ipt, std::vector<int4> &tiles, std::vector<int> &longs);
 // SELL-32-sigma copy (FP32 values too when f32); XB_EINVAL when the padding
 // would exceed 3 nnz + 32 per slice.
 const SellPart *get_sell(xb_plan *p, int sigma, bool f32, cudaStream_t s, int *err);
@@ -173,6 +212,10 @@ const SellPart *get_sell(xb_plan *p, int sigma, bool f32, cudaStream_t s, int *e
 int64_t sell_layout(int n, const int *rp, int sigma, std::vector<int> &perm,
                     std::vector<int> &slen, std::vector<int64_t> &off);
 const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err);
+// BSS data format copy for ipt (FP32 values too when f32), built on first use.
+const BssCopy *get_bss_copy(xb_plan *p, int ipt, bool f32, cudaStream_t s, int *err);
+// Free the BSS copies of every ipt but keep_ipt (0: all of them).
+void bss_trim(xb_plan *p, int keep_ipt);
 int ensure_val32(xb_plan *p, cudaStream_t s);
 int ensure_work(xb_plan *p, size_t bytes);
 // ILU(0): build (levels on the host from the pattern, factorization on the

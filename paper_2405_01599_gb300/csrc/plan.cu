@@ -114,6 +114,75 @@ const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *e
     return &p->tiles.back();
 }
 
+int u2_layout(int n, const int *rp, int ipt, std::vector<int4> &tiles, std::vector<int> &longs) {
+    tiles.clear();
+    longs.clear();
+    const int64_t W = 32LL * ipt;
+    int nflat = 0, r = 0, ne = 0;
+    while (r < n) {
+        const int64_t A = rp[r] - rp[r] % ipt;  // window start
+        if ((int64_t)rp[r + 1] - A > W) {        // the row alone overflows a window
+            longs.push_back(r);
+            ne += rp[r + 1] > rp[r];
+            r++;
+            continue;
+        }
+        const int r0 = r, ne0 = ne;
+        int maxlen = 0, empty = 0;
+        while (r < n && (int64_t)rp[r + 1] - A <= W) {
+            const int len = rp[r + 1] - rp[r];
+            const int nm = std::max(maxlen, len);
+            if (nm <= ipt && r - r0 == 32) break;  // a thread-per-row tile holds 32 rows
+            maxlen = nm;
+            empty |= (len == 0);
+            ne += (len > 0);
+            r++;
+        }
+        const int kind = maxlen <= ipt ? 0 : 1;
+        nflat += kind;
+        tiles.push_back(make_int4(r0, r, ne0, kind | (empty ? 4 : 0)));
+    }
+    return nflat;
+}
+
+const U2Part *get_u2(xb_plan *p, int ipt, cudaStream_t s, int *err) {
+    for (auto &t : p->u2)
+        if (t.ipt == ipt) return &t;
+    std::vector<int4> tiles;
+    std::vector<int> longs;
+    U2Part t;
+    t.ipt = ipt;
+    t.nflat = u2_layout(p->n, p->h_rowptr.data(), ipt, tiles, longs);
+    t.ntiles = (int)tiles.size();
+    t.nlong = (int)longs.size();
+    if (t.nflat > 0 && !get_bss(p, s, err)) return nullptr;  // flat tiles read the row-end bits
+    t.implicit = t.nlong == 0 && t.nflat == 0;
+    for (int i = 0; t.implicit && i < t.ntiles; i++)
+        t.implicit = tiles[i].x == 32 * i && tiles[i].y == std::min(p->n, 32 * i + 32);
+    cudaError_t e = cudaSuccess;
+    if (!t.implicit && t.ntiles > 0) {
+        e = cudaMalloc(&t.d_tile, tiles.size() * sizeof(int4));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t.d_tile, tiles.data(), tiles.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess && t.nlong > 0) {
+        e = cudaMalloc(&t.d_long, longs.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t.d_long, longs.data(), longs.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(t.d_tile);
+        cudaFree(t.d_long);
+        *err = cuda_error(e, "U2 tiles");
+        return nullptr;
+    }
+    p->u2.push_back(t);
+    return &p->u2.back();
+}
+
 // Index (over the rows of crp) of the row holding non-zero w*W, per warp w.
 __global__ void k_seg_rows(int nrows, const int *__restrict__ crp, long long W, int nw,
                            int *__restrict__ out) {
@@ -176,6 +245,91 @@ const BssData *get_bss(xb_plan *p, cudaStream_t s, int *err) {
     }
     d.built = true;
     return &d;
+}
+
+// Entry p of the BSS copy (VN-element vectors) comes from non-zero e.
+template <typename T, int VN>
+__global__ void k_bss_copy(int64_t total, int64_t nnz, int ipt, const T *__restrict__ src,
+                           T *__restrict__ dst) {
+    const int64_t W = 32LL * ipt;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = p / W;
+        const int off = (int)(p - g * W);
+        const int vec = off / VN, h = off - vec * VN;
+        const int q = vec >> 5, l = vec & 31;
+        const int64_t e = g * W + (int64_t)l * ipt + q * VN + h;
+        dst[p] = (e < nnz) ? src[e] : T(0);
+    }
+}
+
+const BssCopy *get_bss_copy(xb_plan *p, int ipt, bool f32, cudaStream_t s, int *err) {
+    BssCopy *c = nullptr;
+    for (auto &t : p->bss.copies)
+        if (t.ipt == ipt) c = &t;
+    const int64_t W = 32LL * ipt;
+    const int64_t total = (p->nnz + W - 1) / W * W;
+    const int grid = num_sms() * 8;
+    cudaError_t e = cudaSuccess;
+    if (!c) {
+        BssCopy t;
+        t.ipt = ipt;
+        t.total = total;
+        e = cudaMalloc(&t.d_col, std::max<int64_t>(total, 1) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_val, std::max<int64_t>(total, 1) * sizeof(double));
+        if (e == cudaSuccess && total > 0) {
+            k_bss_copy<int, 4><<<grid, 256, 0, s>>>(total, p->nnz, ipt, p->col, t.d_col);
+            k_bss_copy<double, 2><<<grid, 256, 0, s>>>(total, p->nnz, ipt, p->val, t.d_val);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(t.d_col);
+            cudaFree(t.d_val);
+            *err = cuda_error(e, "BSS data format copy");
+            return nullptr;
+        }
+        p->bss.copies.push_back(t);
+        c = &p->bss.copies.back();
+    }
+    if (f32 && !c->d_val32) {
+        int r = ensure_val32(p, s);
+        if (r != XB_OK) {
+            *err = r;
+            return nullptr;
+        }
+        e = cudaMalloc(&c->d_val32, std::max<int64_t>(total, 1) * sizeof(float));
+        if (e == cudaSuccess && total > 0) {
+            k_bss_copy<float, 4><<<grid, 256, 0, s>>>(total, p->nnz, ipt, p->val32, c->d_val32);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(c->d_val32);
+            c->d_val32 = nullptr;
+            *err = cuda_error(e, "BSS data format copy (FP32)");
+            return nullptr;
+        }
+    }
+    return c;
+}
+
+void bss_trim(xb_plan *p, int keep_ipt) {
+    auto &v = p->bss.copies;
+    bool any = false;
+    for (auto &t : v)
+        if (t.ipt != keep_ipt) any = true;
+    if (!any) return;
+    cudaDeviceSynchronize();  // no launch may still read a copy being freed
+    std::vector<BssCopy> kept;
+    for (auto &t : v) {
+        if (t.ipt == keep_ipt) {
+            kept.push_back(t);
+        } else {
+            cudaFree(t.d_col);
+            cudaFree(t.d_val);
+            cudaFree(t.d_val32);
+        }
+    }
+    v.swap(kept);
 }
 
 const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
@@ -463,6 +617,7 @@ void xb_options_default(xb_options *o) {
     o->policy = XB_POLICY_NONE;
     o->fault_check = 1;
     o->precond = XB_PRECOND_NONE;
+    o->ir_fallback = 1;
 }
 
 int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out) {
@@ -556,6 +711,10 @@ int xb_plan_destroy(xb_plan *p) {
     if (!p) return XB_OK;
     cudaDeviceSynchronize();
     for (auto &t : p->tiles) cudaFree(t.d_row);
+    for (auto &t : p->u2) {
+        cudaFree(t.d_tile);
+        cudaFree(t.d_long);
+    }
     for (auto &t : p->segs) {
         cudaFree(t.d_row);
         cudaFree(t.d_carry_row);
@@ -573,6 +732,11 @@ int xb_plan_destroy(xb_plan *p) {
     cudaFree(p->bss.d_endbits);
     cudaFree(p->bss.d_ne_rows);
     cudaFree(p->bss.d_crp);
+    for (auto &t : p->bss.copies) {
+        cudaFree(t.d_col);
+        cudaFree(t.d_val);
+        cudaFree(t.d_val32);
+    }
     cudaFree(p->d_empty);
     cudaFree(p->d_part);
     cudaFree(p->d_ticket);
@@ -659,5 +823,26 @@ extern "C" int xb_sell_layout(int32_t n, const int32_t *rowptr, int32_t sigma, i
     if (perm) std::copy(pv.begin(), pv.end(), perm);
     if (slen) std::copy(lv.begin(), lv.end(), slen);
     if (off) std::copy(ov.begin(), ov.end(), off);
+    return XB_OK;
+}
+
+extern "C" int xb_u2_layout(int32_t n, const int32_t *rowptr, int32_t ipt, int32_t *tiles,
+                            int32_t cap_tiles, int32_t *ntiles, int32_t *longs, int32_t cap_long,
+                            int32_t *nlong) {
+    if (n < 0 || !rowptr || ipt < 1 || ipt > 16 || !ntiles || !nlong || cap_tiles < 0 ||
+        cap_long < 0 || (cap_tiles > 0 && !tiles) || (cap_long > 0 && !longs))
+        return xb::set_error(XB_EINVAL, "u2_layout: bad argument");
+    std::vector<int4> tv;
+    std::vector<int> lv;
+    xb::u2_layout(n, rowptr, ipt, tv, lv);
+    *ntiles = (int32_t)tv.size();
+    *nlong = (int32_t)lv.size();
+    for (int i = 0; i < (int)tv.size() && i < cap_tiles; i++) {
+        tiles[4 * i] = tv[i].x;
+        tiles[4 * i + 1] = tv[i].y;
+        tiles[4 * i + 2] = tv[i].z;
+        tiles[4 * i + 3] = tv[i].w;
+    }
+    for (int i = 0; i < (int)lv.size() && i < cap_long; i++) longs[i] = lv[i];
     return XB_OK;
 }

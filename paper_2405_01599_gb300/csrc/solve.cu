@@ -348,7 +348,7 @@ int gmres_mixed(xb_plan *p, const double *b, double *x, const xb_options &o, xb_
             break;
         }
         slow = (rn > 0.5 * prev) ? slow + 1 : 0;
-        if (slow >= 2) {  // refinement stagnates: finish in FP64
+        if (o.ir_fallback && slow >= 2) {  // safeguard (option): finish in FP64
             xb_info fin;
             std::memset(&fin, 0, sizeof fin);
             inf.fallback = 1;
@@ -569,6 +569,8 @@ double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
                      (t.d_val32 ? 4.0 * t.total : 0.0);
     } else if (variant == XB_VAR_SEGSCAN) {
         b += 4.0 * ((p->nnz + 31) / 32 + 1);
+        for (const auto &c : p->bss.copies)  // the BSS data format copy
+            if (c.ipt == ipt) b += 12.0 * c.total + (c.d_val32 ? 4.0 * c.total : 0.0);
         if (p->bss.d_ne_rows) b += 4.0 * p->bss.n_ne + 4.0 * (p->bss.n_ne + 1);
         for (const auto &g : p->segs)
             if (g.block == block && g.ipt == ipt) b += 4.0 * (g.nblk + 1) + 12.0 * g.nblk;

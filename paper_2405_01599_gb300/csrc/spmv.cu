@@ -100,86 +100,206 @@ int launch_sell(xb_plan *p, int block, int ipt, V alpha, const V *x, V beta, int
     return XB_OK;
 }
 
+template <typename V>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using T = double2;
+    static constexpr int N = 2;
+};
+template <>
+struct Vec2<float> {
+    using T = float4;
+    static constexpr int N = 4;
+};
+
 // ---------------------------------------------------------------------------
-// U2: row-aligned, nnz-balanced tiles.  A tile holds at most T = B*IPT
-// non-zeros and B rows; its val and x[col] are staged into shared memory with
-// coalesced loads (IPT independent loads and gathers in flight per thread),
-// then each thread sums one row with FMAs from shared memory.  Tiles whose
-// rows average more than 32 non-zeros use a warp per row; a single row longer
-// than T is a tile of its own, summed by the whole CTA.
+// U2: non-zero-balanced row decomposition (Sec. 3.2.2, Fig. 3) at warp
+// granularity.  The plan cuts the rows into consecutive warp tiles of about
+// equal non-zero count (at most 32*IPT, rows never split); a row too long for
+// a tile gets a CTA.  Inside a tile the rows are binned by length:
+//   kind 0 (every row at most IPT long, at most 32 rows): a thread per row,
+//          operands straight from global memory -- on uniform short rows this
+//          is the row decomposition U1 with 32 rows per warp;
+//   kind 1 (some row longer): the tile's non-zeros are split flat over the
+//          lanes, IPT consecutive ones each from an IPT-aligned window (16-byte
+//          vector loads), row ends from the plan's bitmask, rows joined by a
+//          key-segmented warp scan.  No row leaves the tile, so there is no
+//          carry between warps and no fix-up launch.
+// Long-row CTAs come first in the grid (they are the longest-running).
 // ---------------------------------------------------------------------------
-template <typename V, int IPT>
-__global__ void __launch_bounds__(512) k_tile(const int *__restrict__ rowptr,
-                                              const int *__restrict__ col,
-                                              const V *__restrict__ val, const V *__restrict__ x,
-                                              V alpha, V beta, int mode, V *__restrict__ y,
-                                              const int *__restrict__ trow,
-                                              const V *__restrict__ adev) {
-    extern __shared__ __align__(16) unsigned char sm_[];
-    const int B = blockDim.x, tid = threadIdx.x;
-    const int T = B * IPT;
+template <typename V, int IPT, int M>
+__global__ void __launch_bounds__(512) k_u2(int ntiles, int implicit, int nlong, int n, int nnz,
+                                            const int4 *__restrict__ tiles,
+                                            const int *__restrict__ lrows,
+                                            const int *__restrict__ rowptr,
+                                            const int *__restrict__ col,
+                                            const V *__restrict__ val, const V *__restrict__ x,
+                                            V alpha, V beta, V *__restrict__ y,
+                                            const unsigned *__restrict__ endbits,
+                                            const int *__restrict__ ne_rows,
+                                            const V *__restrict__ adev, int vec) {
+    static_assert(IPT == 4 || IPT == 8 || IPT == 16, "IPT");
+    __shared__ V red[32];
+    const unsigned FULL = 0xffffffffu;
     if (adev) alpha = *adev;
-    const int r0 = trow[blockIdx.x], r1 = trow[blockIdx.x + 1];
-    const int k0 = rowptr[r0], k1 = rowptr[r1];
-    const int cnt = k1 - k0;
-    V *red = reinterpret_cast<V *>(sm_);  // 32
-    if (cnt > T) {  // one long row, whole CTA
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((int)blockIdx.x < nlong) {  // one long row, whole CTA (CTA-uniform branch)
+        const int r = lrows[blockIdx.x];
+        const int a = rowptr[r], b = rowptr[r + 1], B = blockDim.x;
         V s0 = V(0), s1 = V(0);
-        int e = k0 + tid;
-        for (; e + B < k1; e += 2 * B) {
-            const int c0 = col[e], c1 = col[e + B];
-            const V v0 = val[e], v1 = val[e + B];
-            s0 = fma(v0, x[c0], s0);
-            s1 = fma(v1, x[c1], s1);
+        int k = a + threadIdx.x;
+        for (; k + B < b; k += 2 * B) {
+            const int c0 = __ldg(col + k), c1 = __ldg(col + k + B);
+            const V v0 = __ldg(val + k), v1 = __ldg(val + k + B);
+            s0 = fma(v0, __ldg(x + c0), s0);
+            s1 = fma(v1, __ldg(x + c1), s1);
         }
-        if (e < k1) s0 = fma(val[e], x[col[e]], s0);
-        V s = xbd::block_sum(s0 + s1, red);
-        if (tid == 0) store_row(y, r0, s, alpha, beta, mode);
+        if (k < b) s0 = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s0);
+        const V sum = xbd::block_sum(s0 + s1, red);
+        if (threadIdx.x == 0) store_row(y, r, sum, alpha, beta, M);
         return;
     }
-    V *sv = red + 32;
-    V *sx = sv + T;
-    int *srp = reinterpret_cast<int *>(sx + T);
-    {
-        int c[IPT];
-        V v[IPT];
-#pragma unroll
-        for (int j = 0; j < IPT; j++) {
-            const int e = tid + j * B;
-            if (e < cnt) {
-                c[j] = col[k0 + e];
-                v[j] = val[k0 + e];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < IPT; j++) {
-            const int e = tid + j * B;
-            if (e < cnt) {
-                sx[e] = x[c[j]];
-                sv[e] = v[j];
-            }
-        }
+    const int t = ((int)blockIdx.x - nlong) * nw + wib;
+    if (t >= ntiles) return;  // warp-uniform
+    int r0, r1, ne0 = 0, kind = 0;
+    if (implicit) {
+        r0 = 32 * t;
+        r1 = min(n, r0 + 32);
+    } else {
+        const int4 d = __ldg(tiles + t);
+        r0 = d.x;
+        r1 = d.y;
+        ne0 = d.z;
+        kind = d.w;
     }
-    const int nr = r1 - r0;
-    for (int i = tid; i <= nr; i += B) srp[i] = rowptr[r0 + i] - k0;
-    __syncthreads();
-    if (cnt > 32 * nr) {  // long rows: a warp per row
-        const int lane = tid & 31, w = tid >> 5, nw = B >> 5;
-        for (int i = w; i < nr; i += nw) {
-            const int a = srp[i], b = srp[i + 1];
+    if ((kind & 3) == 0) {  // thread per row
+        const int r = r0 + lane;
+        if (r < r1) {
+            const int a = __ldg(rowptr + r), b = __ldg(rowptr + r + 1);
             V s = V(0);
-            for (int e = a + lane; e < b; e += 32) s = fma(sv[e], sx[e], s);
-            s = xbd::warp_sum(s);
-            if (lane == 0) store_row(y, r0 + i, s, alpha, beta, mode);
+            for (int k = a; k < b; k++) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+            store_row(y, r, s, alpha, beta, M);
         }
         return;
     }
-    for (int i = tid; i < nr; i += B) {
-        const int a = srp[i], b = srp[i + 1];
-        V s = V(0);
-        for (int e = a; e < b; e++) s = fma(sv[e], sx[e], s);
-        store_row(y, r0 + i, s, alpha, beta, mode);
+    // flat over the tile's IPT-aligned window
+    const int k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r1);
+    const int e0 = k0 - k0 % IPT + lane * IPT;
+    const int lo = max(0, k0 - e0), hi = min(IPT, k1 - e0);
+    const unsigned vm = (hi > lo) ? (((1u << hi) - 1u) & ~((1u << lo) - 1u)) : 0u;
+    unsigned fl = 0;
+    if (vm) {  // IPT divides 32 and e0 is a multiple of IPT: one bitmask word
+        const unsigned w = __ldg(endbits + (e0 >> 5));
+        fl = (w >> (unsigned)(e0 & 31)) & vm;
     }
+    const int cnt = __popc(fl);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += u;
+    }
+    int row = ne0 + incl - cnt;  // non-empty-row index of the lane's first entry
+    V v[IPT];
+    int c[IPT];
+    if (vm && vec && e0 + IPT <= nnz) {
+        using T2 = typename Vec2<V>::T;
+        constexpr int VN = Vec2<V>::N;
+        const T2 *vp = reinterpret_cast<const T2 *>(val + e0);
+#pragma unroll
+        for (int q = 0; q < IPT / VN; q++) {
+            const T2 u = __ldg(vp + q);
+            if constexpr (VN == 2) {
+                v[2 * q] = u.x;
+                v[2 * q + 1] = u.y;
+            } else {
+                v[4 * q] = u.x;
+                v[4 * q + 1] = u.y;
+                v[4 * q + 2] = u.z;
+                v[4 * q + 3] = u.w;
+            }
+        }
+        const int4 *cp = reinterpret_cast<const int4 *>(col + e0);
+#pragma unroll
+        for (int q = 0; q < IPT / 4; q++) {
+            const int4 u = __ldg(cp + q);
+            c[4 * q] = u.x;
+            c[4 * q + 1] = u.y;
+            c[4 * q + 2] = u.z;
+            c[4 * q + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < IPT; j++) {
+            const bool ok = (vm >> j) & 1u;
+            c[j] = ok ? __ldg(col + e0 + j) : 0;
+            v[j] = ok ? __ldg(val + e0 + j) : V(0);
+        }
+    }
+    V xv[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; j++) {  // window entries of other tiles count as 0
+        const bool ok = (vm >> j) & 1u;
+        xv[j] = ok ? __ldg(x + c[j]) : V(0);
+        v[j] = ok ? v[j] : V(0);
+    }
+    V sum = V(0), head = V(0);
+    int hrow = -1, hkey = -1;
+#pragma unroll
+    for (int j = 0; j < IPT; j++) {
+        sum = fma(v[j], xv[j], sum);
+        if ((fl >> j) & 1u) {
+            const int rid = ne_rows ? __ldg(ne_rows + row) : row;
+            if (hkey < 0) {
+                head = sum;
+                hrow = rid;
+                hkey = row;
+            } else {
+                store_row(y, rid, sum, alpha, beta, M);
+            }
+            sum = V(0);
+            row++;
+        }
+    }
+    // key-segmented inclusive scan of (row, sum); keys ascend with the lane
+    int k = vm ? row : INT_MAX;
+    V s = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ku = __shfl_up_sync(FULL, k, o);
+        const bool need = lane >= o && ku == k;
+        if (!__any_sync(FULL, need)) break;
+        const V su = __shfl_up_sync(FULL, s, o);
+        if (need) s += su;
+    }
+    const int kp = __shfl_up_sync(FULL, k, 1);
+    const V sp = __shfl_up_sync(FULL, s, 1);
+    const bool addc = lane > 0 && hkey >= 0 && kp == hkey;
+    if (__any_sync(FULL, addc))
+        if (addc) head += sp;
+    if (hkey >= 0) store_row(y, hrow, head, alpha, beta, M);
+    if (kind & 4)  // the tile's empty rows
+        for (int r = r0 + lane; r < r1; r += 32)
+            if (__ldg(rowptr + r) == __ldg(rowptr + r + 1))
+                y[r] = (M == 2) ? beta * y[r] : V(0);
+}
+
+// Thread-per-row U2 tiles when the balanced partition is 32-row blocks of
+// short rows (every tile kind 0, implicit): U1's loop with 32 rows per warp.
+template <typename V, int M>
+__global__ void __launch_bounds__(512) k_u2_rows(int n, const int *__restrict__ rowptr,
+                                                 const int *__restrict__ col,
+                                                 const V *__restrict__ val,
+                                                 const V *__restrict__ x, V alpha, V beta,
+                                                 V *__restrict__ y, const V *__restrict__ adev) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (adev) alpha = *adev;
+    const int a = __ldg(rowptr + r), b = __ldg(rowptr + r + 1);
+    V s = V(0);
+    for (int k = a; k < b; k++) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+    store_row(y, r, s, alpha, beta, M);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,7 +379,10 @@ __global__ void __launch_bounds__(512) k_seg(int n, int nnz, const int *__restri
         V xv[IPT];
 #pragma unroll
         for (int j = 0; j < IPT; j++)
-            if (j < ecnt) xv[j] = x[sc[p0 + j]];
+            if (j < ecnt) {  // unvalidated caller arrays: a column outside [0, n) adds 0
+                const int cj = sc[p0 + j];
+                xv[j] = ((unsigned)cj < (unsigned)n) ? x[cj] : V(0);
+            }
         int nend = RP(row + 1) - E0;
 #pragma unroll
         for (int j = 0; j < IPT; j++) {
@@ -270,7 +393,7 @@ __global__ void __launch_bounds__(512) k_seg(int n, int nnz, const int *__restri
                     if (hrow < 0) {
                         head = sum;
                         hrow = row;
-                    } else {
+                    } else if (row < n) {
                         store_row(y, row, sum, alpha, beta, mode);
                     }
                     sum = V(0);
@@ -329,7 +452,7 @@ __global__ void __launch_bounds__(512) k_seg(int n, int nnz, const int *__restri
             kp = -1;
         }
     }
-    if (hrow >= 0) store_row(y, hrow, head + (kp == hrow ? sp : V(0)), alpha, beta, mode);
+    if (hrow >= 0 && hrow < n) store_row(y, hrow, head + (kp == hrow ? sp : V(0)), alpha, beta, mode);
     if (cnt > 0 && tid == (cnt - 1) / IPT) {
         crow[blockIdx.x] = k;
         cval[blockIdx.x] = s;
@@ -339,44 +462,40 @@ __global__ void __launch_bounds__(512) k_seg(int n, int nnz, const int *__restri
 // ---------------------------------------------------------------------------
 // U3 (BSS) with the plan's row-end bitmask ("a data format representing the
 // continuous location", Sec. 3.2.2).  Warp w owns non-zeros [w*32*IPT, ...),
-// lane l the IPT consecutive ones from w*32*IPT + l*IPT.  A lane loads its
-// values and columns with 16-byte vector loads straight from global memory
-// (no staging, no row search): its start row is the warp's start row plus the
-// row ends that precede it (integer warp scan of popcounts of its flag bits).
-// The inner loop is IPT FMAs with row ends as predicated stores.  Row sums
-// that straddle lanes are joined by a key-segmented warp scan that stops as
-// soon as no lane needs another step (most steps cost no FP64 instruction);
-// rows that straddle warps go through one carry slot per warp and the fix-up.
+// lane l the IPT consecutive ones from w*32*IPT + l*IPT.  The lane's values
+// and columns come from the plan's BSS data format copy (values and columns in
+// the order the warps read them), so each 16-byte vector load of the warp
+// reads 512 consecutive bytes; no staging, no row search: the lane's start
+// row is the warp's start row plus the row ends that precede it (integer warp
+// scan of popcounts of its flag bits).  The inner loop is IPT FMAs with row
+// ends as predicated stores.  Row sums that straddle lanes are joined by a
+// key-segmented warp scan that stops as soon as no lane needs another step
+// (most steps cost no FP64 instruction); rows that straddle warps go through
+// one carry slot per warp and the fix-up.
+//
+// On GB300 this kernel is bound by the rate of L1 -> L2 requests (about one
+// per SM per clock): every x gather of a random column is one request, so
+// what is left to save is the streamed operands' requests.  With the copy a
+// warp's 256 values and columns (IPT = 8) take 24 line requests instead of
+// the 80 that lane-strided loads of the caller's arrays need.
 // ---------------------------------------------------------------------------
-template <typename V>
-struct Vec2;
-template <>
-struct Vec2<double> {
-    using T = double2;
-    static constexpr int N = 2;
-};
-template <>
-struct Vec2<float> {
-    using T = float4;
-    static constexpr int N = 4;
-};
-
-template <typename V, int IPT>
-__global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__restrict__ col,
-                                             const V *__restrict__ val, const V *__restrict__ x,
-                                             V alpha, V beta, int mode, V *__restrict__ y,
+template <typename V, int IPT, int M, bool NE>
+__global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__restrict__ col_il,
+                                             const V *__restrict__ val_il, const V *__restrict__ x,
+                                             V alpha, V beta, V *__restrict__ y,
                                              const unsigned *__restrict__ endbits,
                                              const int *__restrict__ wrow,
                                              const int *__restrict__ ne_rows, int n_ne, int n,
                                              V *__restrict__ cval, int *__restrict__ crow,
-                                             const V *__restrict__ adev, int vec) {
+                                             const V *__restrict__ adev) {
     static_assert(IPT == 4 || IPT == 8 || IPT == 16 || IPT == 32, "IPT");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= nwarps) return;  // warp-uniform
     if (adev) alpha = *adev;
-    const long long e0 = (gw * 32 + lane) * IPT;
+    const long long E = gw * 32 * IPT;
+    const long long e0 = E + lane * IPT;
     const int ecnt = (int)max(0LL, min((long long)IPT, (long long)nnz - e0));
     unsigned fl = 0;
     if (ecnt > 0) {
@@ -392,42 +511,34 @@ __global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__r
         if (lane >= o) incl += t;
     }
     int row = __ldg(wrow + gw) + incl - cnt;  // index over non-empty rows
-    // Each lane's run is one aligned block of IPT values and IPT columns: its
-    // 16-byte loads pair up inside 32-byte sectors, so the second load of each
-    // pair is an L1 hit and DRAM sees every byte once.
+    // The copy is padded to whole warp chunks: every load is a full vector.
     V v[IPT];
     int c[IPT];
-    if (vec && ecnt == IPT) {
+    {
         using T2 = typename Vec2<V>::T;
         constexpr int VN = Vec2<V>::N;
-        const T2 *vp = reinterpret_cast<const T2 *>(val + e0);
+        const T2 *vp = reinterpret_cast<const T2 *>(val_il + E);
 #pragma unroll
-        for (int j = 0; j < IPT / VN; j++) {
-            const T2 q = __ldg(vp + j);
+        for (int q = 0; q < IPT / VN; q++) {
+            const T2 t = __ldg(vp + q * 32 + lane);
             if constexpr (VN == 2) {
-                v[2 * j] = q.x;
-                v[2 * j + 1] = q.y;
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
             } else {
-                v[4 * j] = q.x;
-                v[4 * j + 1] = q.y;
-                v[4 * j + 2] = q.z;
-                v[4 * j + 3] = q.w;
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
             }
         }
-        const int4 *cp = reinterpret_cast<const int4 *>(col + e0);
+        const int4 *cp = reinterpret_cast<const int4 *>(col_il + E);
 #pragma unroll
-        for (int j = 0; j < IPT / 4; j++) {
-            const int4 q = __ldg(cp + j);
-            c[4 * j] = q.x;
-            c[4 * j + 1] = q.y;
-            c[4 * j + 2] = q.z;
-            c[4 * j + 3] = q.w;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < IPT; j++) {
-            c[j] = (j < ecnt) ? __ldg(col + e0 + j) : 0;
-            v[j] = (j < ecnt) ? __ldg(val + e0 + j) : V(0);
+        for (int q = 0; q < IPT / 4; q++) {
+            const int4 t = __ldg(cp + q * 32 + lane);
+            c[4 * q] = t.x;
+            c[4 * q + 1] = t.y;
+            c[4 * q + 2] = t.z;
+            c[4 * q + 3] = t.w;
         }
     }
     V xv[IPT];
@@ -439,13 +550,13 @@ __global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__r
     for (int j = 0; j < IPT; j++) {
         sum = fma(v[j], xv[j], sum);
         if ((fl >> j) & 1u) {
-            const int rid = ne_rows ? __ldg(ne_rows + row) : row;
+            const int rid = NE ? __ldg(ne_rows + row) : row;
             if (hkey < 0) {
                 head = sum;
                 hrow = rid;
                 hkey = row;
             } else {
-                store_row(y, rid, sum, alpha, beta, mode);
+                store_row(y, rid, sum, alpha, beta, M);
             }
             sum = V(0);
             row++;
@@ -467,12 +578,12 @@ __global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__r
     const bool addc = lane > 0 && hkey >= 0 && kp == hkey;
     if (__any_sync(FULL, addc))
         if (addc) head += sp;
-    if (hkey >= 0) store_row(y, hrow, head, alpha, beta, mode);
+    if (hkey >= 0) store_row(y, hrow, head, alpha, beta, M);
     // the warp's carry: the last lane holding a non-zero
     const long long left = (long long)nnz - gw * 32 * IPT;
     const int last = (int)min(31LL, (left - 1) / IPT);
     if (lane == last) {
-        crow[gw] = (k < n_ne) ? (ne_rows ? __ldg(ne_rows + k) : k) : n;
+        crow[gw] = (k < n_ne) ? (NE ? __ldg(ne_rows + k) : k) : n;
         cval[gw] = s;
     }
 }
@@ -642,32 +753,61 @@ int smem_optin(const void *fn, size_t need) {
 }
 
 template <typename V>
-int launch_tile(xb_plan *p, const int *rp, const int *ci, const V *va, int block, int ipt, V alpha,
-                const V *x, V beta, int mode, V *y, const V *adev, cudaStream_t s) {
+int launch_u2(xb_plan *p, const int *rp, const int *ci, const V *va, int block, int ipt, V alpha,
+              const V *x, V beta, int mode, V *y, const V *adev, cudaStream_t s) {
     int err = XB_OK;
-    const xb::TilePart *tp = xb::get_tiles(p, block, ipt, s, &err);
-    if (!tp) return err;
-    if (tp->ntiles == 0) return XB_OK;
-    const size_t sm = 32 * sizeof(V) + 2ull * block * ipt * sizeof(V) + (block + 1) * sizeof(int);
-#define XB_TILE(I)                                                                       \
-    case I:                                                                              \
-        XB_TRY(smem_optin((const void *)k_tile<V, I>, sm));                             \
-        k_tile<V, I><<<tp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, beta, mode, y,  \
-                                                   tp->d_row, adev);                     \
+    const xb::U2Part *up = xb::get_u2(p, ipt, s, &err);
+    if (!up) return err;
+    if (up->ntiles + up->nlong == 0) return XB_OK;
+    const int nw = block / 32;
+    const int grid = up->nlong + (up->ntiles + nw - 1) / nw;
+    const int vec = (((uintptr_t)va % 16) == 0 && ((uintptr_t)ci % 16) == 0) ? 1 : 0;
+    const xb::BssData &bd = p->bss;
+#define XB_U2(I)                                                                            \
+    case I:                                                                                 \
+        if (mode == 0) XB_U2M(I, 0) else if (mode == 1) XB_U2M(I, 1) else XB_U2M(I, 2)      \
         break;
-    switch (ipt) {
-        XB_TILE(1) XB_TILE(2) XB_TILE(4) XB_TILE(8) XB_TILE(16)
-        default: return xb::set_error(XB_EINVAL, "tile: unsupported ipt %d", ipt);
+#define XB_U2M(I, MM)                                                                       \
+    {                                                                                       \
+        k_u2<V, I, MM><<<grid, block, 0, s>>>(up->ntiles, up->implicit ? 1 : 0, up->nlong,    \
+                                              p->n, p->nnz, up->d_tile, up->d_long, rp, ci,  \
+                                              va, x, alpha, beta, y, bd.d_endbits,           \
+                                              bd.d_ne_rows, adev, vec);                      \
     }
-#undef XB_TILE
-    XB_LAUNCHED("k_tile");
+    if (up->implicit) {  // uniform short rows: the light thread-per-row kernel
+        const int g = (p->n + block - 1) / block;
+        if (mode == 0)
+            k_u2_rows<V, 0><<<g, block, 0, s>>>(p->n, rp, ci, va, x, alpha, beta, y, adev);
+        else if (mode == 1)
+            k_u2_rows<V, 1><<<g, block, 0, s>>>(p->n, rp, ci, va, x, alpha, beta, y, adev);
+        else
+            k_u2_rows<V, 2><<<g, block, 0, s>>>(p->n, rp, ci, va, x, alpha, beta, y, adev);
+        XB_LAUNCHED("k_u2_rows");
+        return XB_OK;
+    }
+    switch (ipt) {
+        XB_U2(4) XB_U2(8) XB_U2(16)
+        default: return xb::set_error(XB_EINVAL, "nnz-balanced: unsupported ipt %d", ipt);
+    }
+#undef XB_U2
+#undef XB_U2M
+    XB_LAUNCHED("k_u2");
     return XB_OK;
 }
+
+template <typename V>
+const V *bss_values(const xb::BssCopy *c);
+template <>
+const double *bss_values<double>(const xb::BssCopy *c) { return c->d_val; }
+template <>
+const float *bss_values<float>(const xb::BssCopy *c) { return c->d_val32; }
 
 template <typename V>
 int launch_seg(xb_plan *p, const int *rp, const int *ci, const V *va, int block, int ipt, V alpha,
                const V *x, V beta, int mode, V *y, const V *adev, cudaStream_t s) {
     (void)rp;
+    (void)ci;
+    (void)va;
     if (block > 256)
         return xb::set_error(XB_EINVAL, "segscan: block %d > 256", block);
     int err = XB_OK;
@@ -675,21 +815,33 @@ int launch_seg(xb_plan *p, const int *rp, const int *ci, const V *va, int block,
     if (!sp) return err;
     const xb::BssData &bd = p->bss;
     if (sp->nblk > 0) {
+        const xb::BssCopy *cp = xb::get_bss_copy(p, ipt, sizeof(V) == sizeof(float), s, &err);
+        if (!cp) return err;
+        const V *vil = bss_values<V>(cp);
         V *cv = reinterpret_cast<V *>(sp->d_carry_val);
         const int wpb = block / 32;
         const int grid = (sp->nblk + wpb - 1) / wpb;
-        const int vec = (((uintptr_t)va % 16) == 0 && ((uintptr_t)ci % 16) == 0) ? 1 : 0;
 #define XB_BSS(I)                                                                            \
     case I:                                                                                  \
-        k_bss<V, I><<<grid, block, 0, s>>>(p->nnz, sp->nblk, ci, va, x, alpha, beta, mode, y, \
-                                           bd.d_endbits, sp->d_row, bd.d_ne_rows, bd.n_ne,   \
-                                           p->n, cv, sp->d_carry_row, adev, vec);            \
+        if (mode == 0) XB_BSSM(I, 0) else if (mode == 1) XB_BSSM(I, 1) else XB_BSSM(I, 2)     \
         break;
+#define XB_BSSM(I, MM)                                                                       \
+    {                                                                                        \
+        if (bd.d_ne_rows)                                                                    \
+            k_bss<V, I, MM, true><<<grid, block, 0, s>>>(                                    \
+                p->nnz, sp->nblk, cp->d_col, vil, x, alpha, beta, y, bd.d_endbits, sp->d_row, \
+                bd.d_ne_rows, bd.n_ne, p->n, cv, sp->d_carry_row, adev);                     \
+        else                                                                                 \
+            k_bss<V, I, MM, false><<<grid, block, 0, s>>>(                                   \
+                p->nnz, sp->nblk, cp->d_col, vil, x, alpha, beta, y, bd.d_endbits, sp->d_row, \
+                bd.d_ne_rows, bd.n_ne, p->n, cv, sp->d_carry_row, adev);                     \
+    }
         switch (ipt) {
             XB_BSS(4) XB_BSS(8) XB_BSS(16) XB_BSS(32)
             default: return xb::set_error(XB_EINVAL, "segscan: unsupported ipt %d", ipt);
         }
 #undef XB_BSS
+#undef XB_BSSM
         XB_LAUNCHED("k_bss");
         k_seg_fix<V><<<(sp->nblk + 255) / 256, 256, 0, s>>>(sp->nblk, p->n, sp->d_carry_row, cv,
                                                              alpha, mode, y, adev);
@@ -768,8 +920,8 @@ int spmv_any(xb_plan *p, int variant, int block, int ipt, V alpha, const V *x, V
             XB_LAUNCHED("k_row");
             return XB_OK;
         case XB_VAR_NNZ:
-            return launch_tile<V>(p, p->rowptr, p->col, va, block, ipt, alpha, x, beta, mode, y, adev,
-                                  s);
+            return launch_u2<V>(p, p->rowptr, p->col, va, block, ipt, alpha, x, beta, mode, y, adev,
+                                s);
         case XB_VAR_SEGSCAN:
             return launch_seg<V>(p, p->rowptr, p->col, va, block, ipt, alpha, x, beta, mode, y, adev,
                                  s);
@@ -825,10 +977,13 @@ double spmv_alg_bytes(const xb_plan *p, bool beta_nonzero, int val_bytes) {
 // the free HBM at start-up and hands out sub-buffers), and code on a path
 // where an allocation's implicit device synchronisation and latency are not
 // allowed.  Such callers cannot create an xb_plan either, since a plan owns
-// device workspace.  spmv_segscan_noalloc runs the same U3 kernels with their
-// scratch (per-CTA start rows and carries) in one file-scope device array
-// instead of plan memory.  Every GPU that loads the library holds that array
-// until the process exits.
+// device workspace.  spmv_segscan_noalloc runs the staged per-CTA
+// segmented-scan kernel k_seg (nothing else launches it; spmv_segscan runs
+// the bitmask-driven k_bss, which needs plan data) with its scratch (per-CTA
+// start rows and carries) in one file-scope device array instead of plan
+// memory.  Its rows agree with spmv_segscan within the 1e-12 row tolerance,
+// not bit for bit.  Every GPU that loads the library holds that array until
+// the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -867,23 +1022,17 @@ __global__ void k_na_empty(int n, const int *__restrict__ rowptr, double beta, i
     y[r] = (mode == 2) ? beta * y[r] : 0.0;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array on the current device.  Looked up on
+// every call: once the library's module is loaded on the device this is a
+// host-side table lookup, and it stays right after cudaDeviceReset, which
+// reloads the module (a cached address could then be stale).  The first call
+// on a device loads the module, so it should come before any stream capture.
 int na_scratch(unsigned char **out) {
-    static std::mutex mu;
-    static unsigned char *addr[64] = {nullptr};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return xb::cuda_error(e, "spmv_segscan_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= 64) return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: device %d", dev);
-    std::lock_guard<std::mutex> g(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess)
-            return xb::cuda_error(e, "spmv_segscan_noalloc: cudaGetSymbolAddress(scratch)");
-        addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess)
+        return xb::cuda_error(e, "spmv_segscan_noalloc: cudaGetSymbolAddress(scratch)");
+    *out = static_cast<unsigned char *>(p);
     return XB_OK;
 }
 
@@ -896,8 +1045,11 @@ extern "C" int spmv_segscan_noalloc(int32_t n, int32_t nnz, const int32_t *rowpt
     if (n == 0) return XB_OK;
     if (!rowptr || !x || !y || (nnz > 0 && (!col || !val)))
         return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: NULL array");
-    if ((const void *)x == (const void *)y)
-        return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: x and y must not alias");
+    {  // y is written while other CTAs still read x: the ranges must be disjoint
+        const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y, len = (uintptr_t)n * sizeof(double);
+        if (xa < ya + len && ya < xa + len)
+            return xb::set_error(XB_EINVAL, "spmv_segscan_noalloc: x and y overlap");
+    }
     const long long T = (long long)kNaBlock * kNaIpt;
     const long long nblk = ((long long)nnz + T - 1) / T;
     if (nblk + 1 > kNaMaxCtas)

@@ -104,6 +104,8 @@ int xb_tune_exhaustive(xb_plan *p, xb_choice *out, void *stream) {
         p->ipt = best->ipt;
         p->tuned_ms = best->ms;
     }
+    // the sweep built a BSS data format copy per ipt tried: keep the chosen one
+    xb::bss_trim(p, p->variant == XB_VAR_SEGSCAN ? p->ipt : 0);
     if (out) xb_plan_get_choice(p, out);
     return XB_OK;
 }
@@ -112,6 +114,7 @@ int xb_tune_sweep(xb_plan *p, xb_choice *out, int32_t cap, int32_t *count, void 
     if (!p || !count || cap < 0 || (cap > 0 && !out)) return xb::set_error(XB_EINVAL, "tune_sweep: bad argument");
     std::vector<xb_choice> res;
     XB_TRY(sweep(p, res, (cudaStream_t)stream));
+    xb::bss_trim(p, p->variant == XB_VAR_SEGSCAN ? p->ipt : 0);
     *count = (int32_t)res.size();
     for (int i = 0; i < (int)res.size() && i < cap; i++) out[i] = res[i];
     return XB_OK;

@@ -134,17 +134,49 @@ def test_bicgstab_limits(env):
     ("random200", lambda: gen.random200()),
 ])
 def test_mixed_refinement_reaches_fp64(env, name, make):
+    """Plain refinement (ir_fallback = 0) against the oracle's loop: same
+    number of refinement steps (within one: the FP32 inner solves round
+    differently), both true residuals <= tol, no FP64 hand-over."""
     xb, dev = env
     A = make()
-    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, precision=xb.PREC_MIXED, tol_inner=1e-4)
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, precision=xb.PREC_MIXED,
+                        tol_inner=1e-4, ir_fallback=0)
     assert info["status"] == 0, info
+    assert info["fallback"] == 0 and info["iters"] == 0
     rel = _true_rel(A, x, b)
     assert rel <= TOL
     assert info["outer"] >= 2
     xo, io = oracle.gmres_ir(A, b, m=30, tol=TOL, tol_in=1e-4)
     assert io["status"] == 0
+    assert abs(info["outer"] - io["outer"]) <= 1, (info["outer"], io["outer"])
     # both solutions solve the system to the same accuracy class
     assert np.linalg.norm(x - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
+def test_mixed_refinement_fallback_continues_as_fp64_gmres(env):
+    """The library's safeguard (ir_fallback = 1, not part of the method):
+    with one inner Arnoldi step per refinement step on a 32 x 32 Poisson
+    matrix the residual ratios are ~0.46, ~0.71, ~0.82, so the third residual
+    check sees two steps in a row that failed to halve it and the solve goes
+    on as FP64 GMRES(30) from that x.  Checked against the oracle: three plain
+    refinement steps, then the oracle's FP64 GMRES(30) from the resulting x;
+    Arnoldi step counts within max(3, 5 %), both true residuals <= tol."""
+    xb, dev = env
+    A = gen.poisson2d(32)
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, precision=xb.PREC_MIXED,
+                        tol_inner=1e-4, maxiter_inner=1, ir_fallback=1)
+    assert info["status"] == 0, info
+    assert info["fallback"] == 1 and info["outer"] == 3 and info["inner_iters"] == 3, info
+    assert _true_rel(A, x, b) <= TOL
+    x3, i3 = oracle.gmres_ir(A, b, m=30, tol=TOL, tol_in=1e-4, maxit_in=1, max_outer=3)
+    assert i3["outer"] == 3
+    xo, io = oracle.gmres(A, b, x0=x3, m=30, tol=TOL)
+    assert io["status"] == 0
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
+    # without the safeguard the same settings keep refining to max_outer
+    info0, _, _ = _solve(xb, dev, A, "gmres", m=30, tol=TOL, precision=xb.PREC_MIXED,
+                         tol_inner=1e-4, maxiter_inner=1, ir_fallback=0, max_outer=6)
+    assert info0["status"] == -4 and info0["fallback"] == 0 and info0["outer"] == 6, info0
 
 
 def test_dot_and_axpy(env):

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 GENERAL = {
     "row": (0, [(64, 1), (256, 1)]),
-    "nnz": (1, [(64, 1), (128, 4), (256, 8), (512, 16), (256, 2)]),
+    "nnz": (1, [(64, 4), (128, 4), (256, 8), (512, 16), (128, 16)]),
     "segscan": (2, [(64, 4), (128, 4), (256, 8), (128, 16), (256, 16), (128, 32)]),
     "sell": (5, [(64, 1), (256, 1), (128, 8), (512, 32)]),
 }

@@ -1,5 +1,6 @@
 """The allocation-free SpMV entry point (spmv_segscan_noalloc), called through
-the C ABI, against the plan-based spmv_segscan on the same inputs.
+the C ABI, against the oracle and the plan-based spmv_segscan on the same
+inputs.
 
 It serves callers that cannot allocate device memory (their memory belongs
 to another allocator, or allocation is not allowed where they call), so it
@@ -43,7 +44,10 @@ def _adversarial():
 
 @pytest.mark.parametrize("make", [lambda: gen.powerlaw(n=300_000, seed=3), _adversarial,
                                   lambda: gen.poisson2d(64)])
-def test_noalloc_matches_plan_segscan_twice(make):
+def test_noalloc_matches_oracle_and_plan_segscan_twice(make):
+    """Two calls in a row (they share the scratch array) each match the
+    oracle row by row at 1e-12 * (|alpha| sum_j |a_ij||x_j| + |beta||y_i|), and
+    the plan-based spmv_segscan on the same inputs meets the same bound."""
     xb, dev = lib_and_device()
     import torch
     A = make()
@@ -58,16 +62,46 @@ def test_noalloc_matches_plan_segscan_twice(make):
     y0 = rng.uniform(-1, 1, n)
     xt = torch.tensor(x, device=dev)
     for alpha, beta in [(1.0, 0.0), (-2.0, 0.5)]:
+        want = oracle.spmv(A, x, alpha, beta, y0)
+        bound = row_bound(A, x, alpha, beta, y0)
         ref = torch.tensor(y0, device=dev)
         plan.spmv_segscan(xt, ref, alpha=alpha, beta=beta)
-        ref = ref.cpu().numpy()
-        bound = row_bound(A, x, alpha, beta, y0)
-        assert_rows_close(ref, oracle.spmv(A, x, alpha, beta, y0), bound, what="plan segscan")
-        for call in range(2):  # two calls in a row share the scratch array
+        assert_rows_close(ref.cpu().numpy(), want, bound, what="plan segscan")
+        for call in range(2):
             y = torch.tensor(y0, device=dev)
             assert _call(xb, f, rp, ci, va, alpha, xt, beta, y) == 0, xb.last_error()
-            got = y.cpu().numpy()
-            assert_rows_close(got, ref, bound, what=f"noalloc call {call}")
+            assert_rows_close(y.cpu().numpy(), want, bound, what=f"noalloc call {call}")
+
+
+def test_noalloc_matrix_without_entries():
+    """n > 0 rows and nnz = 0: only the empty-row pass runs; y = 0 when
+    beta = 0 and y = beta * y otherwise, exactly."""
+    xb, dev = lib_and_device()
+    import torch
+    f = _fn(xb)
+    n = 1000
+    rp = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    ci = torch.zeros(0, dtype=torch.int32, device=dev)
+    va = torch.zeros(0, dtype=torch.float64, device=dev)
+    y0 = np.random.default_rng(3).uniform(-1, 1, n)
+    xt = torch.ones(n, dtype=torch.float64, device=dev)
+    for alpha, beta in [(1.0, 0.0), (-2.0, 0.5)]:
+        y = torch.tensor(y0, device=dev)
+        assert _call(xb, f, rp, ci, va, alpha, xt, beta, y) == 0, xb.last_error()
+        np.testing.assert_array_equal(y.cpu().numpy(), beta * y0 if beta else np.zeros(n))
+
+
+def test_noalloc_rejects_overlapping_x_and_y():
+    xb, dev = lib_and_device()
+    import torch
+    f = _fn(xb)
+    A = gen.poisson2d(8)
+    rp = torch.as_tensor(A["rowptr"], device=dev)
+    ci = torch.as_tensor(A["col"], device=dev)
+    va = torch.as_tensor(A["val"], device=dev)
+    buf = torch.zeros(2 * A["n"], dtype=torch.float64, device=dev)
+    rc = _call(xb, f, rp, ci, va, 1.0, buf[: A["n"]], 0.0, buf[A["n"] // 2: A["n"] // 2 + A["n"]])
+    assert rc == xb.XB_EINVAL and "overlap" in xb.last_error()
 
 
 def test_noalloc_rejects_oversize_without_launching():
