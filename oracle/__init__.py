@@ -19,72 +19,91 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so if missing or stale."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".{os.getpid()}.tmp"
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so if missing or stale; with omp,
+    the OpenMP build _build/liboracle_omp.so used only for the benchmark's
+    all-cores CPU baseline (its dot products round differently)."""
+    out = _OUT_OMP if omp else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
                                "-ffp-contract=off", "-fno-fast-math",
+                               *(["-fopenmp"] if omp else []),
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+        os.replace(tmp, out)
+    return out
+
+
+def lib_omp():
+    """The OpenMP build (benchmark timing only; never for parity)."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _bind(C.CDLL(build(omp=True)))
+    return _lib_omp
 
 
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        vi, vd, vp = C.c_int, C.c_double, C.c_void_p
-        L.orc_spmv.argtypes = [vi, _i32p, _i32p, _f64p, vd, _f64p, vd, _f64p]
-        L.orc_spmv_sym.argtypes = [vi, _i32p, _i32p, _f64p, vd, _f64p, vd, _f64p]
-        L.orc_spmv_f32.argtypes = [vi, _i32p, _i32p, _f32p, C.c_float, _f32p, C.c_float, _f32p]
-        L.orc_dense_matvec.argtypes = [vi, vi, _f64p, _f64p, _f64p]
-        L.orc_lu_solve.argtypes = [vi, _f64p, _f64p]
-        L.orc_lu_solve.restype = vi
-        L.orc_mm_ratio.argtypes = [_f64p, vi, vi]
-        L.orc_mm_ratio.restype = vd
-        L.orc_dafrt.argtypes = [vi, _f64p, vd]
-        L.orc_dafrt.restype = vi
-        L.orc_arnoldi.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, vi, _f64p, _f64p]
-        L.orc_arnoldi.restype = vi
-        L.orc_arnoldi_ortho.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, vi, vi, vi, _f64p,
-                                        _f64p]
-        L.orc_arnoldi_ortho.restype = vi
-        L.orc_gs_qr.argtypes = [vi, vi, _f64p, vi, vi, _f64p, _f64p]
-        L.orc_gs_qr.restype = vi
-        L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
-                                vi, vd, vi, vi, vi, vi, vp, _i32p, _f64p, vp, vp, vi]
-        L.orc_sym_eig.argtypes = [vi, _f64p, _f64p, _f64p]
-        L.orc_lanczos.argtypes = [vi, vi, _i32p, _i32p, _f64p, vi, vi, vi, vd, vd, vi, _f64p,
-                                  _f64p, vp, _f64p, _i32p]
-        L.orc_lanczos.restype = vi
-        L.orc_ilu0.argtypes = [vi, _i32p, _i32p, _f64p, _f64p]
-        L.orc_ilu0.restype = vi
-        L.orc_ilu0_solve.argtypes = [vi, _i32p, _i32p, _f64p, _f64p, _f64p]
-        L.orc_gmres.restype = vi
-        L.orc_bicgstab.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vd, vi, vp,
-                                   _i32p, _f64p]
-        L.orc_bicgstab.restype = vi
-        L.orc_gmres_f32_inner.argtypes = [vi, _i32p, _i32p, _f32p, _f32p, _f32p, vi, vd, vi]
-        L.orc_gmres_f32_inner.restype = vi
-        L.orc_gmres_ir.argtypes = [vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vd, vd, vi, vi,
-                                   _i32p, _f64p]
-        L.orc_gmres_ir.restype = vi
-        L.orc_features.argtypes = [vi, _i32p, _i32p, _f64p, vi, _f64p, _f64p]
-        L.orc_mlp_forward.argtypes = [_f64p, vi, vi, vi, vi, _f64p, vi, _f64p]
-        L.orc_mlp_loss_grad.argtypes = [_f64p, vi, vi, vi, vi, _i32p, _f64p, _i32p, vi, _f64p]
-        L.orc_mlp_loss_grad.restype = vd
-        L.orc_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, vi, vi, vd, vd, vd, vd]
-        _lib = L
+        _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def _bind(L):
+    """argtypes / restypes of the exported routines."""
+    vi, vd, vp = C.c_int, C.c_double, C.c_void_p
+    L.orc_spmv.argtypes = [vi, _i32p, _i32p, _f64p, vd, _f64p, vd, _f64p]
+    L.orc_spmv_sym.argtypes = [vi, _i32p, _i32p, _f64p, vd, _f64p, vd, _f64p]
+    L.orc_spmv_f32.argtypes = [vi, _i32p, _i32p, _f32p, C.c_float, _f32p, C.c_float, _f32p]
+    L.orc_dense_matvec.argtypes = [vi, vi, _f64p, _f64p, _f64p]
+    L.orc_lu_solve.argtypes = [vi, _f64p, _f64p]
+    L.orc_lu_solve.restype = vi
+    L.orc_mm_ratio.argtypes = [_f64p, vi, vi]
+    L.orc_mm_ratio.restype = vd
+    L.orc_dafrt.argtypes = [vi, _f64p, vd]
+    L.orc_dafrt.restype = vi
+    L.orc_arnoldi.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, vi, _f64p, _f64p]
+    L.orc_arnoldi.restype = vi
+    L.orc_arnoldi_ortho.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, vi, vi, vi, _f64p,
+                                    _f64p]
+    L.orc_arnoldi_ortho.restype = vi
+    L.orc_gs_qr.argtypes = [vi, vi, _f64p, vi, vi, _f64p, _f64p]
+    L.orc_gs_qr.restype = vi
+    L.orc_gmres.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vi, vd, vi,
+                            vi, vd, vi, vi, vi, vi, vp, _i32p, _f64p, vp, vp, vi]
+    L.orc_sym_eig.argtypes = [vi, _f64p, _f64p, _f64p]
+    L.orc_lanczos.argtypes = [vi, vi, _i32p, _i32p, _f64p, vi, vi, vi, vd, vd, vi, _f64p,
+                              _f64p, vp, _f64p, _i32p]
+    L.orc_lanczos.restype = vi
+    L.orc_ilu0.argtypes = [vi, _i32p, _i32p, _f64p, _f64p]
+    L.orc_ilu0.restype = vi
+    L.orc_ilu0_solve.argtypes = [vi, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.orc_gmres.restype = vi
+    L.orc_bicgstab.argtypes = [vi, vi, _i32p, _i32p, _f64p, _f64p, _f64p, vd, vi, vp,
+                               _i32p, _f64p]
+    L.orc_bicgstab.restype = vi
+    L.orc_gmres_f32_inner.argtypes = [vi, _i32p, _i32p, _f32p, _f32p, _f32p, vi, vd, vi]
+    L.orc_gmres_f32_inner.restype = vi
+    L.orc_gmres_ir.argtypes = [vi, _i32p, _i32p, _f64p, _f64p, _f64p, vi, vd, vd, vi, vi,
+                               _i32p, _f64p]
+    L.orc_gmres_ir.restype = vi
+    L.orc_features.argtypes = [vi, _i32p, _i32p, _f64p, vi, _f64p, _f64p]
+    L.orc_mlp_forward.argtypes = [_f64p, vi, vi, vi, vi, _f64p, vi, _f64p]
+    L.orc_mlp_loss_grad.argtypes = [_f64p, vi, vi, vi, vi, _i32p, _f64p, _i32p, vi, _f64p]
+    L.orc_mlp_loss_grad.restype = vd
+    L.orc_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, vi, vi, vd, vd, vd, vd]
+    L.orc_num_threads.restype = vi
+    return L
 
 
 def _csr(A):
@@ -94,12 +113,14 @@ def _csr(A):
     return int(A["n"]), rp, ci, va
 
 
-def spmv(A, x, alpha=1.0, beta=0.0, y=None):
-    """y = alpha*A*x + beta*y (general CRS, or upper CRS when A['sym_upper'])."""
+def spmv(A, x, alpha=1.0, beta=0.0, y=None, omp=False):
+    """y = alpha*A*x + beta*y (general CRS, or upper CRS when A['sym_upper']);
+    omp: the OpenMP build's row-parallel loop (benchmark timing only)."""
     n, rp, ci, va = _csr(A)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.zeros(n) if y is None else np.array(y, dtype=np.float64, copy=True)
-    f = lib().orc_spmv_sym if A.get("sym_upper", False) else lib().orc_spmv
+    L = lib_omp() if omp else lib()
+    f = L.orc_spmv_sym if A.get("sym_upper", False) else L.orc_spmv
     f(n, rp, ci, va, float(alpha), x, float(beta), y)
     return y
 
@@ -220,9 +241,9 @@ def _prec(A, prec):
 
 def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
           dafrt=False, theta=10.0, window=5, dm=5, hist_cap=0, ortho=MGS, fault_check=True,
-          ilu=False):
+          ilu=False, omp=False):
     """Restarted GMRES(m), right-preconditioned by ILU(0) when ilu; returns
-    (x, info dict)."""
+    (x, info dict).  omp: run the OpenMP build (benchmark timing only)."""
     keep, mptr = _prec(A, ilu)
     n, rp, ci, va = _csr(A)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
@@ -230,7 +251,7 @@ def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
     dd = np.zeros(2)
     hist = np.zeros(max(hist_cap, 1))
     mh = np.zeros(max(hist_cap, 1), np.int32)
-    st = lib().orc_gmres(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
+    st = (lib_omp() if omp else lib()).orc_gmres(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
                          np.ascontiguousarray(b, np.float64), x, int(m),
                          int(m_max if m_max is not None else m), float(tol), int(maxiter),
                          1 if dafrt else 0, float(theta), int(window), int(dm), int(ortho),
@@ -247,13 +268,15 @@ def gmres(A, b, x0=None, m=30, m_max=None, tol=1e-8, maxiter=100000,
     return x, info
 
 
-def bicgstab(A, b, x0=None, tol=1e-8, maxiter=100000, ilu=False):
+def bicgstab(A, b, x0=None, tol=1e-8, maxiter=100000, ilu=False, omp=False):
+    """BiCGStab, right-preconditioned by ILU(0) when ilu; omp: the OpenMP
+    build (benchmark timing only)."""
     keep, mptr = _prec(A, ilu)
     n, rp, ci, va = _csr(A)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     ii = np.zeros(4, np.int32)
     dd = np.zeros(2)
-    st = lib().orc_bicgstab(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
+    st = (lib_omp() if omp else lib()).orc_bicgstab(n, 1 if A.get("sym_upper", False) else 0, rp, ci, va,
                             np.ascontiguousarray(b, np.float64), x, float(tol), int(maxiter),
                             mptr, ii, dd)
     return x, dict(status=st, iters=int(ii[0]), restarts=int(ii[1]), faults=int(ii[3]),

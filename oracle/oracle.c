@@ -28,6 +28,34 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The same source is also compiled with -fopenmp for the benchmark's
+ * all-cores CPU baseline (the paper's row-parallel decomposition, U1 of
+ * Sec. 3.2.2, run over the host's cores).  ORC_PAR marks the row loop of the
+ * SpMV and the streaming vector loops of the solvers; ORC_PAR_SUM a dot
+ * product.  Without -fopenmp both expand to nothing: the single-thread build
+ * the tests check is exactly the plain loops.  In the OpenMP build the dot
+ * products are summed in per-thread pieces, so its results differ by
+ * rounding; it is used for timing only. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_STR_(x) #x
+#define ORC_PAR _Pragma("omp parallel for schedule(static)")
+#define ORC_PAR_SUM(v) _Pragma(ORC_STR_(omp parallel for schedule(static) reduction(+:v)))
+#else
+#define ORC_PAR
+#define ORC_PAR_SUM(v)
+#endif
+
+/* Threads the loops above use (1 in the single-thread build). */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 #define ORC_OK 0
 #define ORC_ENOCONV (-4)
 #define ORC_EBREAKDOWN (-5)
@@ -43,6 +71,7 @@
 void orc_spmv(int n, const int *rowptr, const int *col, const double *val,
               double alpha, const double *x, double beta, double *y)
 {
+    ORC_PAR
     for (int i = 0; i < n; i++) {
         double s = 0.0;
         for (int k = rowptr[i]; k < rowptr[i + 1]; k++)
@@ -142,6 +171,7 @@ int orc_lu_solve(int n, double *A, double *b)
 static double dot(int n, const double *a, const double *b)
 {
     double s = 0.0;
+    ORC_PAR_SUM(s)
     for (int i = 0; i < n; i++)
         s += a[i] * b[i];
     return s;
@@ -214,6 +244,7 @@ static void orth(int ortho, int bl, int n, int j, const double *V, double *w, do
     if (ortho == ORC_MGS) {
         for (int i = 0; i <= j; i++) {
             h[i] = dot(n, w, V + (size_t)i * n);
+            ORC_PAR
             for (int q = 0; q < n; q++)
                 w[q] -= h[i] * V[(size_t)i * n + q];
         }
@@ -227,6 +258,7 @@ static void orth(int ortho, int bl, int n, int j, const double *V, double *w, do
             for (int i = 0; i <= j; i++)
                 h2[i] = dot(n, w, V + (size_t)i * n);
             for (int i = 0; i <= j; i++) {
+                ORC_PAR
                 for (int q = 0; q < n; q++)
                     w[q] -= h2[i] * V[(size_t)i * n + q];
                 h[i] += h2[i];
@@ -241,9 +273,11 @@ static void orth(int ortho, int bl, int n, int j, const double *V, double *w, do
         if (i1 > j) i1 = j;
         for (int i = i0; i <= i1; i++)
             h[i] = dot(n, w, V + (size_t)i * n);
-        for (int i = i0; i <= i1; i++)
+        for (int i = i0; i <= i1; i++) {
+            ORC_PAR
             for (int q = 0; q < n; q++)
                 w[q] -= h[i] * V[(size_t)i * n + q];
+        }
     }
 }
 
@@ -467,6 +501,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
     for (;;) {
         /* r = b - A x, true residual */
         matvec(kind, n, rp, ci, va, x, r);
+        ORC_PAR
         for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
         double beta = nrm2(n, r);
         res_true = beta / bnorm;
@@ -492,6 +527,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
         }
         if (mhist && restarts < hist_cap) mhist[restarts] = m; /* m this cycle uses */
         /* one cycle */
+        ORC_PAR
         for (int i = 0; i < n; i++) V[i] = r[i] / beta;
         for (int i = 0; i <= m; i++) g[i] = 0.0;
         g[0] = beta;
@@ -532,6 +568,7 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
             res_impl = fabs(g[j + 1]) / bnorm;
             k = j + 1;
             if (hn <= ORC_BREAKDOWN_REL * sqrt(len2)) { broke = 1; break; }
+            ORC_PAR
             for (int q = 0; q < n; q++)
                 V[(size_t)(j + 1) * n + q] = w[q] / hn;
             if (res_impl <= tau) { claimed = 1; break; }
@@ -554,9 +591,11 @@ int orc_gmres(int n, int kind, const int *rp, const int *ci, const double *va,
             orc_ilu0_solve(n, rp, ci, M, w, tz);
             for (int q = 0; q < n; q++) x[q] += tz[q];
         } else {
-            for (int i = 0; i < k; i++)
+            for (int i = 0; i < k; i++) {
+                ORC_PAR
                 for (int q = 0; q < n; q++)
                     x[q] += y[i] * V[(size_t)i * n + q];
+            }
         }
         restarts++;
     }
@@ -614,6 +653,7 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
     double *ph = (double *)malloc(bytes), *sh = (double *)malloc(bytes);
     for (;;) {
         matvec(kind, n, rp, ci, va, x, r);
+        ORC_PAR
         for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
         res_true = nrm2(n, r) / bnorm;
         if (res_true <= tol) { status = ORC_OK; break; }
@@ -621,6 +661,7 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
         if (claimed) { faults++; tau *= tol / res_true; restarts++; }
         else if (iters > 0) restarts++;
         claimed = 0;
+        ORC_PAR
         for (int i = 0; i < n; i++) { rh[i] = r[i]; p[i] = 0.0; v[i] = 0.0; }
         double rho = 1.0, alpha = 1.0, omega = 1.0;
         int broke = 0;
@@ -629,13 +670,18 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
             double rho1 = dot(n, rh, r);
             if (rho1 == 0.0) { broke = 1; break; }
             double beta = (rho1 / rho) * (alpha / omega);
+            ORC_PAR
             for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
             if (M) orc_ilu0_solve(n, rp, ci, M, p, ph);
-            else for (int i = 0; i < n; i++) ph[i] = p[i];
+            else {
+                ORC_PAR
+                for (int i = 0; i < n; i++) ph[i] = p[i];
+            }
             matvec(kind, n, rp, ci, va, ph, v);
             double sigma = dot(n, rh, v);
             if (sigma == 0.0) { broke = 1; break; }
             alpha = rho1 / sigma;
+            ORC_PAR
             for (int i = 0; i < n; i++) s[i] = r[i] - alpha * v[i];
             double sn = nrm2(n, s) / bnorm;
             if (sn <= tau) {
@@ -645,12 +691,17 @@ int orc_bicgstab(int n, int kind, const int *rp, const int *ci, const double *va
                 break;
             }
             if (M) orc_ilu0_solve(n, rp, ci, M, s, sh);
-            else for (int i = 0; i < n; i++) sh[i] = s[i];
+            else {
+                ORC_PAR
+                for (int i = 0; i < n; i++) sh[i] = s[i];
+            }
             matvec(kind, n, rp, ci, va, sh, t);
             double tt = dot(n, t, t);
             if (tt == 0.0) { broke = 1; break; }
             omega = dot(n, t, s) / tt;
+            ORC_PAR
             for (int i = 0; i < n; i++) x[i] += alpha * ph[i] + omega * sh[i];
+            ORC_PAR
             for (int i = 0; i < n; i++) r[i] = s[i] - omega * t[i];
             rho = rho1;
             res_rec = nrm2(n, r) / bnorm;
