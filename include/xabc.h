@@ -56,7 +56,24 @@ extern "C" {
                              /*   in windows of sigma = 32 * ipt rows; a thread */
                              /*   per row, coalesced slice columns; built on   */
                              /*   first use (general storage only)             */
-#define XB_NUM_VARIANTS 6
+#define XB_VAR_SYM_PART 6    /* S3: S2 tiles; transposes beyond the tile summed */
+                             /*   in per-CTA partial vectors over only the     */
+                             /*   256-row granules they reach, then one pass   */
+                             /*   adds each reached granule's partials in tile */
+                             /*   order (granules nothing reaches are skipped);*/
+                             /*   no device atomics.  XB_EINVAL when a tile    */
+                             /*   reaches more than 8 granules beyond itself   */
+#define XB_VAR_SYM_WAGG 7    /* S1 with warp-aggregated atomics: lanes whose   */
+                             /*   transpose terms target the same row add them */
+                             /*   first, one device atomic per distinct row    */
+#define XB_VAR_BCSR 8        /* format conversion (Sec. 5): block CRS with     */
+                             /*   r x r blocks, r = ipt in {2, 3, 4}, zero-   */
+                             /*   filled; a thread per row walks its block    */
+                             /*   row (one column index per block, x read r   */
+                             /*   at a time); built on first use, rejected    */
+                             /*   when the blocks hold more than 2 nnz + 16 r */
+                             /*   entries (general storage only)              */
+#define XB_NUM_VARIANTS 9
 
 /* Re-orthogonalisation in the Arnoldi step (Sec. 3.2.2) and the accuracy
  * policy choosing it (Sec. 3.3.2). */
@@ -157,6 +174,12 @@ typedef struct xb_options {
                              /*   resolve the system: kappa * 6e-8 near 1),    */
                              /*   the solve continues as FP64 GMRES(m) from    */
                              /*   the current x and xb_info.fallback = 1       */
+    int32_t small_n;         /* GMRES: systems with n <= small_n and nnz +   */
+                             /*   m n <= 32 small_n run as one persistent     */
+                             /*   launch when the options allow it (see       */
+                             /*   gmres_solve); default 8192 (the environment */
+                             /*   variable XB_SMALL_N changes the default),   */
+                             /*   0 = never                                    */
 } xb_options;
 
 typedef struct xb_info {
@@ -181,6 +204,8 @@ typedef struct xb_info {
     double mem_bytes;        /* device memory the solve used: workspace it    */
                              /*   requested, the SpMV variant's plan data and */
                              /*   the FP32 matrix copy (mixed precision)      */
+    int32_t persistent;      /* 1: GMRES ran as one persistent launch (small  */
+                             /*   systems, see gmres_solve)                   */
 } xb_info;
 
 typedef struct xb_plan xb_plan;
@@ -304,6 +329,16 @@ int xb_sell_layout(int32_t n, const int32_t *rowptr, int32_t sigma, int32_t *per
 int xb_u2_layout(int32_t n, const int32_t *rowptr, int32_t ipt, int32_t *tiles, int32_t cap_tiles,
                  int32_t *ntiles, int32_t *longs, int32_t cap_long, int32_t *nlong);
 
+/* The block-CRS structure that XB_VAR_BCSR builds for r x r blocks (host
+ * logic, no device work; exposed for testing): block row b covers rows
+ * [r b, r b + r); its blocks are the distinct col / r of those rows' entries,
+ * ascending.  HOST arrays: rowptr (n + 1), col (nnz); bptr (ceil(n / r) + 1)
+ * receives the block-row offsets, bcol (capacity cap) the block columns;
+ * *nblocks the block count (always set).  bptr and bcol may be NULL (cap 0)
+ * to query the count. */
+int xb_bcsr_layout(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t r, int32_t *bptr,
+                   int32_t *bcol, int64_t cap, int64_t *nblocks);
+
 /* Any variant (XB_VAR_*; XB_VAR_AUTO = plan choice) with an explicit launch
  * shape (block/ipt 0 = plan choice).  XB_VAR_SELL builds the SELL-32-sigma
  * copy of the matrix on its first use with that sigma (device memory held by
@@ -329,15 +364,30 @@ int xb_spmv_f32(xb_plan *plan, int32_t variant, float alpha, const float *x, flo
  * b == 0 gives x = 0.  The host synchronises `stream` every
  * opt->check_every steps to read the residual. */
 
-/* Restarted GMRES(m) (Sec. 2.2, Sec. 4.3) with MGS (or CGS2) Arnoldi and
- * Givens least squares; opt->dafrt enables the MM-ratio restart rule of
- * Eq. (1) / Fig. 2 / Sec. 4.3 (m += dafrt_dm, at most m_max).
- * opt->precision == XB_PREC_MIXED runs FP32 GMRES(m) (FP32 SpMV and basis,
- * FP64 Hessenberg/Givens/least squares) inside FP64 iterative refinement. */
+/* Restarted GMRES(m) (Sec. 2.2, Sec. 4.3): Arnoldi with the
+ * orthogonalisation opt->ortho -- MGS, CGS, DGKS (CGS run twice) or BCGS
+ * (blocks of 4), Sec. 3.2.2, or XB_ORTHO_AUTO, the accuracy policy of
+ * Sec. 3.3.2 (MGS for tol <= 1e-10, else BCGS; DGKS after a fault
+ * convergence) -- and Givens least squares; opt->dafrt enables the MM-ratio
+ * restart rule of Eq. (1) / Fig. 2 / Sec. 4.3 (m += dafrt_dm, at most m_max).
+ * opt->precond == XB_PRECOND_ILU0 preconditions on the right with ILU(0)
+ * (Sec. 4.3; FP64 only, general storage).  opt->precision == XB_PREC_MIXED
+ * runs FP32 GMRES(m) (FP32 SpMV and basis, FP64 Hessenberg/Givens/least
+ * squares) inside FP64 iterative refinement (see opt->ir_fallback).
+ * Small systems -- n <= opt->small_n (default 8192) and nnz + m n <= 32
+ * small_n, general storage, FP64, no preconditioner,
+ * MGS or BCGS, m (and m_max with the restart rule, whose window and
+ * increment must then be the default 5) <= XB_BATCH_MAX_M,
+ * fault_check on -- run the same GMRES(m) as one persistent launch of the
+ * batched kernel (one CTA solves the system), because each Arnoldi step of
+ * the multi-launch path is bound by launch and synchronisation latency at
+ * that size; xb_info.persistent = 1 then, spmv_ms and res_implicit are 0. */
 int gmres_solve(xb_plan *plan, const double *b, double *x, const xb_options *opt,
                 xb_info *info, void *stream);
 
-/* BiCGStab (Sec. 2.2, Sec. 4.3), unpreconditioned, two SpMVs per step. */
+/* BiCGStab (Sec. 2.2, Sec. 4.3; van der Vorst's iteration), two SpMVs per
+ * step, optionally right-preconditioned with ILU(0) (opt->precond ==
+ * XB_PRECOND_ILU0: two preconditioner applications per step). */
 int bicgstab_solve(xb_plan *plan, const double *b, double *x, const xb_options *opt,
                    xb_info *info, void *stream);
 
@@ -445,6 +495,17 @@ int xb_ilu0_setup(xb_plan *plan, void *stream);
 /* z = (L U)^{-1} r: forward then backward substitution, one launch per
  * dependency level.  r and z: DEVICE, n doubles, distinct. */
 int xb_ilu0_apply(xb_plan *plan, const double *r, double *z, void *stream);
+/* Which substitution path the plan's ILU(0) applications take, and the
+ * persistent path's barrier poll limit (a control for tests and diagnosis).
+ * mode: -1 = automatic (the default; the environment variable XB_ILU_MODE
+ * = 0/1 overrides it), 0 = the captured graph of level launches, 1 = one
+ * cooperative launch with a grid barrier between levels (used only when the
+ * device supports cooperative launches).  barrier_polls: how many times a CTA
+ * polls a level barrier before it gives up (0 = default, about 0.5 s of
+ * polling); a CTA that gives up sets an error flag and returns, every other
+ * CTA returns at its next barrier, and the apply or solve reports
+ * XB_ETIMEOUT.  XB_EINVAL for mode outside -1..1 or barrier_polls < 0. */
+int xb_ilu0_config(xb_plan *plan, int32_t mode, int32_t barrier_polls);
 /* Copy the factors (aligned with the plan's col array: strict lower part = L
  * with unit diagonal not stored, the rest = U) to the DEVICE array lu (nnz). */
 int xb_ilu0_factors(xb_plan *plan, double *lu, void *stream);

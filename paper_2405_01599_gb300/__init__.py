@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libxabc.so")
 XB_OK, XB_EINVAL, XB_ENOMEM, XB_ECUDA, XB_ENOCONV, XB_EBREAKDOWN, XB_ETIMEOUT, XB_EFAULT = \
     0, -1, -2, -3, -4, -5, -6, -7
 VAR_AUTO, VAR_ROW, VAR_NNZ, VAR_SEGSCAN, VAR_SYM_ATOMIC, VAR_SYM_TILE, VAR_SELL = -1, 0, 1, 2, 3, 4, 5
-VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile", 5: "sell"}
+VAR_SYM_PART, VAR_SYM_WAGG, VAR_BCSR = 6, 7, 8
+VARIANT_NAMES = {0: "row", 1: "nnz", 2: "segscan", 3: "sym_atomic", 4: "sym_tile", 5: "sell",
+                 6: "sym_part", 7: "sym_wagg", 8: "bcsr"}
 ORTHO_MGS, ORTHO_CGS, ORTHO_DGKS, ORTHO_BCGS, ORTHO_AUTO = 0, 1, 2, 3, 4
 POLICY_NONE, POLICY_TIME, POLICY_ACCURACY, POLICY_MEMORY, POLICY_STABLE = 0, 1, 2, 3, 4
 PRECOND_NONE, PRECOND_ILU0 = 0, 1
@@ -49,7 +51,7 @@ class Options(C.Structure):
                 ("max_outer", C.c_int32), ("variant", C.c_int32), ("block", C.c_int32),
                 ("ipt", C.c_int32), ("tuner", C.c_int32), ("check_every", C.c_int32),
                 ("timing", C.c_int32), ("policy", C.c_int32), ("fault_check", C.c_int32),
-                ("precond", C.c_int32), ("ir_fallback", C.c_int32)]
+                ("precond", C.c_int32), ("ir_fallback", C.c_int32), ("small_n", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -58,7 +60,8 @@ class Info(C.Structure):
                                          "block_used", "ipt_used", "spmv_calls",
                                          "ortho_used")] + \
                [(k, C.c_double) for k in ("res_implicit", "res_true", "t_solve_s", "spmv_ms",
-                                          "bytes_alg", "mem_bytes")]
+                                          "bytes_alg", "mem_bytes")] + \
+               [("persistent", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +128,8 @@ def lib():
         "xb_dense_restart_basis": (i32, [i32, P(f64), i32, i32, P(f64), P(i32)]),
         "xb_policy_parse": (i32, [C.c_char_p, P(Options), P(i32), P(f64), P(i32)]),
         "xb_u2_layout": (i32, [i32, P(i32), i32, P(i32), i32, P(i32), P(i32), i32, P(i32)]),
+        "xb_bcsr_layout": (i32, [i32, P(i32), P(i32), i32, P(i32), P(i32), C.c_int64,
+                                 P(C.c_int64)]),
         "xb_sell_layout": (i32, [i32, P(i32), i32, P(i32), P(i32), P(C.c_int64),
                                  P(C.c_int64)]),
         "xb_ilu_levels": (i32, [i32, P(i32), P(i32), P(i32), P(i32), P(i32)]),
@@ -132,6 +137,7 @@ def lib():
         "xb_ilu0_setup": (i32, [vp, vp]),
         "xb_ilu0_apply": (i32, [vp, vp, vp, vp]),
         "xb_ilu0_factors": (i32, [vp, vp, vp]),
+        "xb_ilu0_config": (i32, [vp, i32, i32]),
         "xb_tune_exhaustive": (i32, [vp, P(Choice), vp]),
         "xb_mm_ratio": (f64, [P(f64), i32, i32]),
         "xb_dafrt": (i32, [i32, P(f64), f64]),
@@ -240,6 +246,22 @@ def u2_layout(rowptr, ipt):
     _check(lib().xb_u2_layout(n, f(rp), int(ipt), f(tiles), nt.value, C.byref(nt), f(longs),
                               nl.value, C.byref(nl)))
     return tiles[:4 * nt.value].reshape(-1, 4), longs[:nl.value]
+
+
+def bcsr_layout(rowptr, col, r):
+    """The block-CRS structure the BCSR variant builds for r x r blocks:
+    (bptr, bcol) as numpy arrays (host logic)."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    n = rp.size - 1
+    f = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    nb = C.c_int64()
+    bptr = np.zeros((n + r - 1) // r + 1, np.int32)
+    _check(lib().xb_bcsr_layout(n, f(rp), f(ci), int(r), f(bptr), None, 0, C.byref(nb)))
+    bcol = np.zeros(max(nb.value, 1), np.int32)
+    _check(lib().xb_bcsr_layout(n, f(rp), f(ci), int(r), f(bptr), f(bcol), nb.value, C.byref(nb)))
+    return bptr, bcol[:nb.value]
 
 
 def ilu_levels(rowptr, col):
@@ -488,6 +510,11 @@ class Plan:
         self._vec(r, z)
         _check(lib().xb_ilu0_apply(self._h, _ptr(r), _ptr(z), _stream(stream)))
         return z
+
+    def ilu0_config(self, mode=-1, barrier_polls=0):
+        """ILU(0) substitution path (-1 automatic, 0 graph, 1 persistent) and
+        the persistent path's barrier poll limit (0 = default)."""
+        _check(lib().xb_ilu0_config(self._h, int(mode), int(barrier_polls)))
 
     def ilu0_factors(self, stream=None):
         import torch

@@ -551,6 +551,78 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 1)
 
 }  // namespace
 
+namespace xb {
+
+// One system through the persistent kernel: a single 8-CTA cluster (rank 0's
+// CTA solves a system below the cluster threshold alone), the system's basis
+// and Hessenberg, its descriptor, queue and result in the plan's workspace;
+// no graph capture, no allocation after the workspace has grown.  Used by
+// gmres_solve for small systems, whose multi-launch Arnoldi steps are bound by
+// launch and synchronisation latency.
+int batch_single(xb_plan *p, const double *b, double *x, const xb_options &o, int mode,
+                 xb_info &inf, double *alg_bytes, cudaStream_t s) {
+    xb_batch_dev d;
+    std::memset(&d, 0, sizeof d);
+    d.n = p->n;
+    d.nnz = p->nnz;
+    d.m = o.m;
+    d.m_max = o.dafrt ? std::max(o.m, std::min(o.m_max, XB_BATCH_MAX_M)) : o.m;
+    d.mode = mode;
+    d.zero_x = 0;
+    long coop_min = kLargeN;
+    if (const char *env = std::getenv("XB_BATCH_COOP_MIN_N")) coop_min = std::max(1L, std::atol(env));
+    d.coop = d.n >= coop_min ? 1 : 0;
+    d.ld = ((int64_t)d.n + 31) / 32 * 32;
+    d.rowptr = p->rowptr;
+    d.col = p->col;
+    d.val = p->val;
+    d.b = b;
+    d.x = x;
+    const size_t nv = (size_t)(d.m_max + 1) * d.ld;
+    const size_t nh = (size_t)(d.coop ? kCl : 1) * (d.m_max + 1) * d.m_max + 32;
+    const size_t meta = 4096;  // descriptor, result, order, queue
+    XB_TRY(ensure_work(p, (nv + nh) * sizeof(double) + meta));
+    char *w = static_cast<char *>(p->d_work);
+    d.V = reinterpret_cast<double *>(w);
+    d.H = d.V + nv;
+    char *m0 = w + (nv + nh) * sizeof(double);
+    xb_batch_dev *d_sys = reinterpret_cast<xb_batch_dev *>(m0);
+    xb_batch_info *d_info = reinterpret_cast<xb_batch_info *>(m0 + 1024);
+    int *d_order = reinterpret_cast<int *>(m0 + 2048);
+    int *d_queue = d_order + 1;
+    static_assert(sizeof(xb_batch_dev) <= 1024 && sizeof(xb_batch_info) <= 1024, "meta layout");
+    const int zero = 0;
+    XB_CUDA(cudaMemcpyAsync(d_sys, &d, sizeof d, cudaMemcpyHostToDevice, s));
+    XB_CUDA(cudaMemcpyAsync(d_order, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
+    XB_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+    const unsigned long long budget = (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
+    const double theta = o.dafrt ? o.dafrt_theta : 0.0;
+    const int bcgs = o.ortho == XB_ORTHO_BCGS ? 1 : 0;
+    k_batch_gmres<<<kCl, kBT, 0, s>>>(d_sys, d_info, d_order, 1, d_queue, o.tol, o.maxiter, budget,
+                                      theta, bcgs);
+    XB_LAUNCHED("k_batch_gmres (single system)");
+    xb_batch_info r;
+    XB_CUDA(cudaMemcpyAsync(&r, d_info, sizeof r, cudaMemcpyDeviceToHost, s));
+    XB_CUDA(cudaStreamSynchronize(s));
+    inf.iters = r.iters;
+    inf.restarts = r.restarts;
+    inf.m_final = r.m;
+    inf.res_true = r.res_true;
+    inf.ortho_used = bcgs ? XB_ORTHO_BCGS : XB_ORTHO_MGS;
+    inf.persistent = 1;
+    // algorithmic bytes: per Arnoldi step one SpMV and the Gram-Schmidt passes
+    // at the cycle's mean basis size, plus a residual per restart
+    const double jm = (r.m + 1) / 2.0, n = d.n;
+    *alg_bytes = r.iters * (spmv_alg_bytes(p, false, 8) + (4.0 * jm + 5.0) * 8.0 * n) +
+                 (r.restarts + 1) * (spmv_alg_bytes(p, true, 8) + 16.0 * n);
+    if (r.status == XB_ENOCONV)
+        return set_error(XB_ENOCONV, "not converged: ||b-Ax||/||b|| = %.3e > tol %.1e", r.res_true,
+                         o.tol);
+    return r.status;
+}
+
+}  // namespace xb
+
 extern "C" {
 
 int xb_batch_destroy(xb_batch *bt) {

@@ -40,7 +40,7 @@ int spmv_crs(xb_plan *p, double alpha, const double *x, double beta, double *y, 
 int spmv_sym(xb_plan *p, double alpha, const double *x, double beta, double *y, void *stream) {
     XB_TRY(need_plan(p, x, y));
     if (!p->sym) return xb::set_error(XB_EINVAL, "spmv_sym: plan is not symmetric upper storage");
-    const int v = (p->variant == XB_VAR_SYM_ATOMIC) ? XB_VAR_SYM_ATOMIC : XB_VAR_SYM_TILE;
+    const int v = xb::variant_fits(p, p->variant) ? p->variant : XB_VAR_SYM_TILE;
     int b, i;
     shape_for(p, v, &b, &i);
     return xb::spmv_launch(p, v, b, i, alpha, x, beta, y, (cudaStream_t)stream);

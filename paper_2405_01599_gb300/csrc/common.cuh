@@ -71,6 +71,32 @@ struct U2Part {
                              //  non-empty row >= r0), kind | 4 if it has empty rows}
     int *d_long = nullptr;
 };
+// S3 partial vectors (XB_VAR_SYM_PART) over the S2 tiles (TilePart with the
+// same block, ipt): slots tslot[t] .. tslot[t+1]-1 of tile t hold the granules
+// (kS3Gran rows each, sgran[slot]) its transposes reach beyond the tile, at
+// most kS3Max per tile; reached granule c (gid[c]) adds slots
+// gslot[gptr[c] .. gptr[c+1]-1] (tile order).  part: nslots * kS3Gran values.
+constexpr int kS3Gran = 256;
+constexpr int kS3Max = 8;
+struct S3Part {
+    int block = 0, ipt = 0;
+    int ntiles = 0, nslots = 0, ngran = 0;
+    int *d_tslot = nullptr, *d_sgran = nullptr;
+    int *d_gid = nullptr, *d_gptr = nullptr, *d_gslot = nullptr;
+    double *d_part = nullptr;  // FP32 use reads it as floats
+};
+// Block CRS copy (format conversion, XB_VAR_BCSR): r x r blocks, block row
+// b = rows [r b, r b + r), blocks ascending by block column, values row-major
+// inside a block and zero where A has no entry.
+struct BcsrPart {
+    int r = 0;
+    int nbr = 0;                     // block rows
+    int64_t nblocks = 0;
+    int *d_bptr = nullptr;           // nbr + 1
+    int *d_bcol = nullptr;           // nblocks
+    double *d_val = nullptr;         // nblocks * r * r
+    float *d_val32 = nullptr;        // built on the first FP32 use
+};
 // Flat nnz segments (U3, BSS): warp w owns non-zeros [w*W, (w+1)*W), W =
 // 32*ipt; d_row[w] is the (non-empty-row) index of the row holding non-zero
 // w*W; one carry slot per warp feeds the fix-up.
@@ -177,9 +203,13 @@ struct xb_plan {
     std::vector<xb::TilePart> tiles;     // cache by (block, ipt)
     std::vector<xb::SegPart> segs;       // cache by (block, ipt)
     std::vector<xb::U2Part> u2;          // cache by ipt
+    std::vector<xb::S3Part> s3;          // cache by (block, ipt)
+    std::vector<xb::BcsrPart> bcsr;      // cache by block size r
     std::vector<xb::SellPart> sells;     // cache by sigma
     xb::BssData bss;
     xb::IluData ilu;
+    int ilu_mode = -1;                   // substitution path: -1 auto, 0 graph, 1 persistent
+    int ilu_polls = 0;                   // persistent barrier poll limit (0: default)
     bool vec_ok = false;                 // val and col 16-byte aligned
     // reduction scratch
     double *d_part = nullptr;            // kRedSlots * kRedValues partials
@@ -200,6 +230,18 @@ namespace xb {
 const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
 const SegPart *get_segs(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
 const U2Part *get_u2(xb_plan *p, int ipt, cudaStream_t s, int *err);
+// Row starts of the S2 / U2-CTA tiles (host): at most block rows and
+// block*ipt non-zeros per tile, a longer row alone.
+std::vector<int> tile_rows(int n, const int *rp, int block, int ipt);
+// The S3 slots and cover lists (XB_EINVAL when a tile reaches more than
+// kS3Max granules beyond itself).
+const S3Part *get_s3(xb_plan *p, int block, int ipt, cudaStream_t s, int *err);
+// Block CRS structure on the host from the pattern; returns the block count.
+int64_t bcsr_layout(int n, const int *rp, const int *col, int r, std::vector<int> &bptr,
+                    std::vector<int> &bcol);
+// BCSR copy with r x r blocks (FP32 values too when f32); XB_EINVAL when the
+// blocks would hold more than 2 nnz + 16 r entries.
+const BcsrPart *get_bcsr(xb_plan *p, int r, bool f32, cudaStream_t s, int *err);
 // The U2 warp tiles on the host from the row pointer (n + 1 entries); returns
 // the number of flat tiles.  tiles: {r0, r1, ne0, kind | 4 * has_empty}.
 int u2_layout(int n, const int *rp, int ipt, std::vector<int4> &tiles, std::vector<int> &longs);
@@ -229,6 +271,10 @@ int ensure_ilu(xb_plan *p, cudaStream_t s);
 int ilu_levels(int n, const int *rp, const int *ci, std::vector<int> &dpos, std::vector<int> &lev,
                std::vector<int> &ulev, int *nl, int *nu);
 int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s);
+// GMRES(m) of the plan's system in one persistent launch (the batched
+// kernel with a single system): FP64, general storage, MGS or BCGS, m <= 128.
+int batch_single(xb_plan *p, const double *b, double *x, const xb_options &o, int mode,
+                 xb_info &inf, double *alg_bytes, cudaStream_t s);
 double ilu_apply_bytes(const xb_plan *p);
 int ilu_check(xb_plan *p);  // XB_ETIMEOUT if a substitution's barrier wait ran out
 void ilu_free(xb_plan *p);

@@ -178,8 +178,10 @@ __global__ void k_diag_fill(int n, const int *__restrict__ rows, const int *__re
 // Both substitutions in one cooperative launch (every CTA resident, one per
 // SM): each level is processed by the whole grid, then a grid barrier.  The
 // barrier is a counter and a generation word in global memory; a CTA that
-// waits longer than kBarSpins polls sets the error flag and leaves (every
-// wait is bounded).  Values of z written by other CTAs are read at L2.
+// waits longer than `polls` polls (kernel argument; default kBarSpins) sets
+// the error flag and leaves, so every wait is bounded, and every CTA then
+// leaves at its next barrier too.  Values of z written by other CTAs are read
+// at L2.
 constexpr unsigned kBarSpins = 1u << 20;  // polls of ~0.5 us: a wait gives up after ~0.5 s
 
 struct TriDev {
@@ -190,7 +192,7 @@ struct TriDev {
     const double *eval, *diag;
 };
 
-__device__ __forceinline__ bool grid_bar(unsigned *bar, int *err) {
+__device__ __forceinline__ bool grid_bar(unsigned *bar, int *err, unsigned polls) {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
@@ -204,9 +206,9 @@ __device__ __forceinline__ bool grid_bar(unsigned *bar, int *err) {
             ok = 1;
         } else {
             unsigned it = 0;
-            while (*gen == g && ++it < kBarSpins) {
+            while (*gen == g && ++it < polls) {
             }
-            ok = (it < kBarSpins);
+            ok = (*gen != g);
             if (!ok) atomicExch(err, 1);
         }
         __threadfence();
@@ -292,15 +294,16 @@ __device__ void persist_level(const TriDev &t, int l, const int *__restrict__ rp
 __global__ void __launch_bounds__(512, 1) k_ilu_persist(TriDev L, TriDev U, const int *rp,
                                                      const int *ci, const int *dpos,
                                                      const double *lu, const double *r,
-                                                     double *z, unsigned *bar, int *err) {
+                                                     double *z, unsigned *bar, int *err,
+                                                     unsigned polls) {
     __shared__ double sh[16];
     for (int l = 0; l < L.nlev; l++) {
         persist_level<true>(L, l, rp, ci, dpos, lu, r, z, sh);
-        if (!grid_bar(bar, err)) return;
+        if (!grid_bar(bar, err, polls)) return;
     }
     for (int l = 0; l < U.nlev; l++) {
         persist_level<false>(U, l, rp, ci, dpos, lu, r, z, sh);
-        if (l + 1 < U.nlev && !grid_bar(bar, err)) return;
+        if (l + 1 < U.nlev && !grid_bar(bar, err, polls)) return;
     }
 }
 
@@ -582,11 +585,12 @@ int ensure_ilu(xb_plan *p, cudaStream_t s) {
 // (measured: ~6 us per barrier, ~4 us per graph kernel), so the persistent
 // launch wins when levels hold several tiers (power-law rows) and the graph
 // when every level is one ELL kernel (stencils).  XB_ILU_MODE=0/1 forces one.
-int ilu_mode(const IluData &u) {
+int ilu_mode(const xb_plan *p, const IluData &u) {
     static const int env = [] {
         const char *e = std::getenv("XB_ILU_MODE");
         return e ? std::atoi(e) : -1;
     }();
+    if (p->ilu_mode >= 0) return p->ilu_mode;
     if (env >= 0) return env;
     long long levels = (long long)u.ln0.size() + (long long)u.un0.size(), kernels = 0;
     auto tiers = [](const std::vector<int> &off, const std::vector<int> &n0,
@@ -616,15 +620,16 @@ int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s) {
     IluData &u = p->ilu;
     XB_TRY(ensure_ilu(p, s));
     if (p->n == 0) return XB_OK;
-    if (u.pgrid > 0 && ilu_mode(u) == 1) {
+    if (u.pgrid > 0 && ilu_mode(p, u) == 1) {
         TriDev L{(int)u.ln0.size(), u.d_lmeta, u.d_leo, u.d_lrows, u.d_lecol, u.d_leval, u.d_udiag};
         TriDev U{(int)u.un0.size(), u.d_umeta, u.d_ueo, u.d_urows, u.d_uecol, u.d_ueval, u.d_udiag};
         const int *rp = p->rowptr, *ci = p->col, *dp = u.d_dpos;
         const double *lu = u.d_lu;
         unsigned *bar = u.d_bar;
         int *err = u.d_err;
+        unsigned polls = p->ilu_polls > 0 ? (unsigned)p->ilu_polls : kBarSpins;
         void *args[] = {&L, &U, (void *)&rp, (void *)&ci, (void *)&dp, (void *)&lu, (void *)&r,
-                        (void *)&z, (void *)&bar, (void *)&err};
+                        (void *)&z, (void *)&bar, (void *)&err, (void *)&polls};
         XB_CUDA(cudaMemsetAsync(u.d_bar, 0, 2 * sizeof(unsigned), s));
         XB_CUDA(cudaLaunchCooperativeKernel((const void *)k_ilu_persist, u.pgrid, 512, args, 0, s));
         return XB_OK;
@@ -661,6 +666,15 @@ int xb_ilu0_apply(xb_plan *p, const double *r, double *z, void *stream) {
     XB_TRY(xb::ilu_apply(p, r, z, s));
     XB_CUDA(cudaStreamSynchronize(s));
     return xb::ilu_check(p);
+}
+
+int xb_ilu0_config(xb_plan *p, int32_t mode, int32_t barrier_polls) {
+    if (!p || mode < -1 || mode > 1 || barrier_polls < 0)
+        return xb::set_error(XB_EINVAL, "ilu0_config: plan %p mode %d polls %d", (void *)p, mode,
+                             barrier_polls);
+    p->ilu_mode = mode;
+    p->ilu_polls = barrier_polls;
+    return XB_OK;
 }
 
 int xb_ilu0_factors(xb_plan *p, double *lu, void *stream) {

@@ -70,18 +70,17 @@ int resident_grid(const void *fn, int block, int64_t n, int per_thread) {
 }
 
 bool variant_fits(const xb_plan *p, int v) {
-    if (p->sym) return v == XB_VAR_SYM_ATOMIC || v == XB_VAR_SYM_TILE;
-    return v == XB_VAR_ROW || v == XB_VAR_NNZ || v == XB_VAR_SEGSCAN || v == XB_VAR_SELL;
+    if (p->sym)
+        return v == XB_VAR_SYM_ATOMIC || v == XB_VAR_SYM_TILE || v == XB_VAR_SYM_PART ||
+               v == XB_VAR_SYM_WAGG;
+    return v == XB_VAR_ROW || v == XB_VAR_NNZ || v == XB_VAR_SEGSCAN || v == XB_VAR_SELL ||
+           v == XB_VAR_BCSR;
 }
 
 // ---- partitions -------------------------------------------------------------
 
-const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
-    for (auto &t : p->tiles)
-        if (t.block == block && t.ipt == ipt) return &t;
-    const int n = p->n;
+std::vector<int> tile_rows(int n, const int *rp, int block, int ipt) {
     const int64_t T = (int64_t)block * ipt;
-    const int *rp = p->h_rowptr.data();
     std::vector<int> rows;
     rows.reserve(n / std::max(1, block / 2) + 16);
     rows.push_back(0);
@@ -94,6 +93,13 @@ const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *e
         rows.push_back(r1);
         r = r1;
     }
+    return rows;
+}
+
+const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
+    for (auto &t : p->tiles)
+        if (t.block == block && t.ipt == ipt) return &t;
+    std::vector<int> rows = tile_rows(p->n, p->h_rowptr.data(), block, ipt);
     TilePart t;
     t.block = block;
     t.ipt = ipt;
@@ -112,6 +118,200 @@ const TilePart *get_tiles(xb_plan *p, int block, int ipt, cudaStream_t s, int *e
     }
     p->tiles.push_back(t);
     return &p->tiles.back();
+}
+
+const S3Part *get_s3(xb_plan *p, int block, int ipt, cudaStream_t s, int *err) {
+    for (auto &t : p->s3)
+        if (t.block == block && t.ipt == ipt) return &t;
+    const TilePart *tp = get_tiles(p, block, ipt, s, err);
+    if (!tp) return nullptr;
+    const int n = p->n;
+    const int *rp = p->h_rowptr.data();
+    std::vector<int> rows = tile_rows(n, rp, block, ipt);
+    std::vector<int> hcol(p->nnz);
+    cudaError_t e = cudaSuccess;
+    if (p->nnz > 0)
+        e = cudaMemcpy(hcol.data(), p->col, (size_t)p->nnz * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        *err = cuda_error(e, "S3 layout: columns to host");
+        return nullptr;
+    }
+    const int ngr = (n + kS3Gran - 1) / kS3Gran;
+    std::vector<int> tslot(1, 0), sgran;
+    std::vector<std::vector<int>> cover(ngr);
+    for (size_t t = 0; t + 1 < rows.size(); t++) {
+        const int r1 = rows[t + 1];
+        std::vector<int> g;  // granules reached beyond the tile, ascending
+        for (int k = rp[rows[t]]; k < rp[r1]; k++)
+            if (hcol[k] >= r1) {
+                const int q = hcol[k] / kS3Gran;
+                if (std::find(g.begin(), g.end(), q) == g.end()) {
+                    if ((int)g.size() == kS3Max) {
+                        *err = set_error(XB_EINVAL,
+                                         "S3 layout: tile %zu reaches more than %d granules of "
+                                         "%d rows beyond itself", t, kS3Max, kS3Gran);
+                        return nullptr;
+                    }
+                    g.push_back(q);
+                }
+            }
+        std::sort(g.begin(), g.end());
+        for (int q : g) {
+            cover[q].push_back((int)sgran.size());
+            sgran.push_back(q);
+        }
+        tslot.push_back((int)sgran.size());
+    }
+    std::vector<int> gid, gptr(1, 0), gslot;
+    for (int q = 0; q < ngr; q++)
+        if (!cover[q].empty()) {
+            gid.push_back(q);
+            gslot.insert(gslot.end(), cover[q].begin(), cover[q].end());
+            gptr.push_back((int)gslot.size());
+        }
+    S3Part t;
+    t.block = block;
+    t.ipt = ipt;
+    t.ntiles = (int)rows.size() - 1;
+    t.nslots = (int)sgran.size();
+    t.ngran = (int)gid.size();
+    auto up = [&](int **d, const std::vector<int> &h) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(int));
+        if (e == cudaSuccess && !h.empty())
+            e = cudaMemcpy(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice);
+    };
+    up(&t.d_tslot, tslot);
+    up(&t.d_sgran, sgran);
+    up(&t.d_gid, gid);
+    up(&t.d_gptr, gptr);
+    up(&t.d_gslot, gslot);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&t.d_part, std::max<size_t>(1, (size_t)t.nslots * kS3Gran) * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(t.d_tslot);
+        cudaFree(t.d_sgran);
+        cudaFree(t.d_gid);
+        cudaFree(t.d_gptr);
+        cudaFree(t.d_gslot);
+        cudaFree(t.d_part);
+        *err = cuda_error(e, "S3 layout");
+        return nullptr;
+    }
+    p->s3.push_back(t);
+    return &p->s3.back();
+}
+
+int64_t bcsr_layout(int n, const int *rp, const int *col, int r, std::vector<int> &bptr,
+                    std::vector<int> &bcol) {
+    const int nbr = (n + r - 1) / r;
+    bptr.assign(1, 0);
+    bcol.clear();
+    std::vector<int> cur;
+    for (int b = 0; b < nbr; b++) {
+        cur.clear();
+        for (int i = b * r; i < std::min(n, b * r + r); i++)
+            for (int k = rp[i]; k < rp[i + 1]; k++) cur.push_back(col[k] / r);
+        std::sort(cur.begin(), cur.end());
+        cur.erase(std::unique(cur.begin(), cur.end()), cur.end());
+        bcol.insert(bcol.end(), cur.begin(), cur.end());
+        bptr.push_back((int)bcol.size());
+    }
+    return (int64_t)bcol.size();
+}
+
+// Places A's entries in the zero-filled blocks: thread per row, merging the
+// row's block columns (ascending) with its block row's block list (ascending).
+template <typename T>
+__global__ void k_bcsr_fill(int n, int r, const int *__restrict__ rowptr,
+                            const int *__restrict__ col, const T *__restrict__ val,
+                            const int *__restrict__ bptr, const int *__restrict__ bcol,
+                            T *__restrict__ bval) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = i / r, li = i - b * r;
+    int q = bptr[b];
+    const int qe = bptr[b + 1];
+    for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+        const int c = col[k], cb = c / r;
+        while (q < qe && bcol[q] < cb) q++;
+        if (q < qe && bcol[q] == cb) bval[((int64_t)q * r + li) * r + (c - cb * r)] = val[k];
+    }
+}
+
+const BcsrPart *get_bcsr(xb_plan *p, int r, bool f32, cudaStream_t s, int *err) {
+    if (r < 2 || r > 4) {
+        *err = set_error(XB_EINVAL, "BCSR: block size %d not in {2, 3, 4}", r);
+        return nullptr;
+    }
+    BcsrPart *bp = nullptr;
+    for (auto &t : p->bcsr)
+        if (t.r == r) bp = &t;
+    cudaError_t e = cudaSuccess;
+    if (!bp) {
+        std::vector<int> hcol(p->nnz), bptr, bcol;
+        if (p->nnz > 0)
+            e = cudaMemcpy(hcol.data(), p->col, (size_t)p->nnz * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            *err = cuda_error(e, "BCSR: columns to host");
+            return nullptr;
+        }
+        BcsrPart t;
+        t.r = r;
+        t.nbr = (p->n + r - 1) / r;
+        t.nblocks = bcsr_layout(p->n, p->h_rowptr.data(), hcol.data(), r, bptr, bcol);
+        const int64_t entries = t.nblocks * r * r;
+        if (entries > 2LL * p->nnz + 16LL * r) {
+            *err = set_error(XB_EINVAL, "BCSR %dx%d: blocks hold %lld entries for %d non-zeros", r,
+                             r, (long long)entries, p->nnz);
+            return nullptr;
+        }
+        const size_t ent = (size_t)std::max<int64_t>(entries, 1);
+        e = cudaMalloc(&t.d_bptr, bptr.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_bcol, std::max<size_t>(bcol.size(), 1) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&t.d_val, ent * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t.d_bptr, bptr.data(), bptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !bcol.empty())
+            e = cudaMemcpy(t.d_bcol, bcol.data(), bcol.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.d_val, 0, ent * sizeof(double), s);
+        if (e == cudaSuccess && p->n > 0) {
+            k_bcsr_fill<double><<<(p->n + 255) / 256, 256, 0, s>>>(p->n, r, p->rowptr, p->col, p->val,
+                                                                  t.d_bptr, t.d_bcol, t.d_val);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(t.d_bptr);
+            cudaFree(t.d_bcol);
+            cudaFree(t.d_val);
+            *err = cuda_error(e, "BCSR copy");
+            return nullptr;
+        }
+        p->bcsr.push_back(t);
+        bp = &p->bcsr.back();
+    }
+    if (f32 && !bp->d_val32) {
+        int rc = ensure_val32(p, s);
+        if (rc != XB_OK) {
+            *err = rc;
+            return nullptr;
+        }
+        const size_t ent = (size_t)std::max<int64_t>(bp->nblocks * r * r, 1);
+        e = cudaMalloc(&bp->d_val32, ent * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemsetAsync(bp->d_val32, 0, ent * sizeof(float), s);
+        if (e == cudaSuccess && p->n > 0) {
+            k_bcsr_fill<float><<<(p->n + 255) / 256, 256, 0, s>>>(p->n, r, p->rowptr, p->col, p->val32,
+                                                                 bp->d_bptr, bp->d_bcol, bp->d_val32);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(bp->d_val32);
+            bp->d_val32 = nullptr;
+            *err = cuda_error(e, "BCSR FP32 copy");
+            return nullptr;
+        }
+    }
+    return bp;
 }
 
 int u2_layout(int n, const int *rp, int ipt, std::vector<int4> &tiles, std::vector<int> &longs) {
@@ -618,6 +818,8 @@ void xb_options_default(xb_options *o) {
     o->fault_check = 1;
     o->precond = XB_PRECOND_NONE;
     o->ir_fallback = 1;
+    o->small_n = 8192;
+    if (const char *e = std::getenv("XB_SMALL_N")) o->small_n = std::max(0, std::atoi(e));
 }
 
 int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out) {
@@ -714,6 +916,20 @@ int xb_plan_destroy(xb_plan *p) {
     for (auto &t : p->u2) {
         cudaFree(t.d_tile);
         cudaFree(t.d_long);
+    }
+    for (auto &t : p->bcsr) {
+        cudaFree(t.d_bptr);
+        cudaFree(t.d_bcol);
+        cudaFree(t.d_val);
+        cudaFree(t.d_val32);
+    }
+    for (auto &t : p->s3) {
+        cudaFree(t.d_tslot);
+        cudaFree(t.d_sgran);
+        cudaFree(t.d_gid);
+        cudaFree(t.d_gptr);
+        cudaFree(t.d_gslot);
+        cudaFree(t.d_part);
     }
     for (auto &t : p->segs) {
         cudaFree(t.d_row);
@@ -844,5 +1060,17 @@ extern "C" int xb_u2_layout(int32_t n, const int32_t *rowptr, int32_t ipt, int32
         tiles[4 * i + 3] = tv[i].w;
     }
     for (int i = 0; i < (int)lv.size() && i < cap_long; i++) longs[i] = lv[i];
+    return XB_OK;
+}
+
+extern "C" int xb_bcsr_layout(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t r,
+                              int32_t *bptr, int32_t *bcol, int64_t cap, int64_t *nblocks) {
+    if (n < 0 || !rowptr || (n > 0 && rowptr[n] > 0 && !col) || r < 1 || !nblocks || cap < 0 ||
+        (cap > 0 && !bcol))
+        return xb::set_error(XB_EINVAL, "bcsr_layout: bad argument");
+    std::vector<int> bp, bc;
+    *nblocks = xb::bcsr_layout(n, rowptr, col, r, bp, bc);
+    if (bptr) std::copy(bp.begin(), bp.end(), bptr);
+    for (int64_t i = 0; i < *nblocks && i < cap; i++) bcol[i] = bc[i];
     return XB_OK;
 }

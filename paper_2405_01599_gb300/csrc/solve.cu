@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 namespace {
@@ -135,6 +136,7 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
         XB_TRY(xb::gm_cycle_init(p, st, n, V, tau, s));
         ac.bytes += 8.0 * n;
         XB_TRY(peek(p, st.misc, xb::GM_NMISC, s));
+        if (prec) XB_TRY(xb::ilu_check(p));  // a preconditioner wait ran out: stop here
         res_true = p->h_pin[xb::GM_RES];
         if (res_true <= o.tol) {
             status = XB_OK;
@@ -233,7 +235,7 @@ int gmres_fp64(xb_plan *p, const double *b, double *x, const xb_options &o, xb_i
 
 int gmres_f32_inner(xb_plan *p, const float *r32, float *d, float *V, int64_t ld, xb::GmDev st,
                     int m, double tol_in, int maxit, int ortho, const xb_options &o, Acct &ac,
-                    int *steps, cudaStream_t s) {
+                    SpmvTimer &tm, int *steps, cudaStream_t s) {
     const int64_t n = p->n;
     const double spmv_b = xb::spmv_alg_bytes(p, false, 4);
     *steps = 0;
@@ -245,7 +247,9 @@ int gmres_f32_inner(xb_plan *p, const float *r32, float *d, float *V, int64_t ld
         XB_CUDA(cudaMemcpyAsync(V, r32, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
         ac.bytes += 8.0 * n;
         if (!first) {
+            tm.begin();
             XB_TRY(xb::spmv_launch_f32(p, o.variant, o.block, o.ipt, -1.0f, d, 1.0f, V, s));
+            tm.end();
             ac.bytes += xb::spmv_alg_bytes(p, true, 4);
             ac.spmv++;
         }
@@ -264,8 +268,10 @@ int gmres_f32_inner(xb_plan *p, const float *r32, float *d, float *V, int64_t ld
         int launched = 0;
         double stop = 0.0;
         for (int j = 0; j < m; j++) {
+            tm.begin();
             XB_TRY(xb::spmv_launch_dalpha_f32(p, o.variant, o.block, o.ipt, st.scf + j,
                                               V + (size_t)j * ld, V + (size_t)(j + 1) * ld, s));
+            tm.end();
             ac.bytes += spmv_b;
             ac.spmv++;
             XB_TRY(xb::gm_ortho_step<float>(p, st, n, V, ld, V + (size_t)(j + 1) * ld, j, ortho,
@@ -368,7 +374,7 @@ int gmres_mixed(xb_plan *p, const double *b, double *x, const xb_options &o, xb_
         const int ortho_in = xb::ortho_choice(o.ortho, o.tol_inner, inf.faults > 0);
         inf.ortho_used = ortho_in;
         XB_TRY(gmres_f32_inner(p, r32, d, V, ld, st, m, o.tol_inner, o.maxiter_inner, ortho_in, o,
-                               ac, &steps, s));
+                               ac, tm, &steps, s));
         inner_total += steps;
         XB_TRY(xb::add_scaled_f32(n, x, sc + 1, d, s));
         ac.bytes += 20.0 * n;
@@ -419,6 +425,7 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
         XB_TRY(xb::vnrm2(p, n, r, sc + xb::BI_N + 1, s));
         ac.bytes += 8.0 * n;
         XB_TRY(peek(p, sc + xb::BI_N + 1, 1, s));
+        if (prec) XB_TRY(xb::ilu_check(p));  // a preconditioner wait ran out: stop here
         res_true = p->h_pin[0] / bnorm;
         if (res_true <= o.tol) {
             status = XB_OK;
@@ -468,6 +475,7 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
             ac.spmv += 2;
             if (iters % check == 0 || iters >= o.maxiter) {
                 XB_TRY(peek(p, sc, xb::BI_N, s));
+                if (prec) XB_TRY(xb::ilu_check(p));
                 flag = (int)p->h_pin[xb::BI_FLAG];
                 res_rec = std::sqrt(p->h_pin[xb::BI_RNORM2]) / bnorm;
                 if (flag != 0) break;
@@ -495,6 +503,23 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
     inf.res_true = res_true;
     inf.res_implicit = res_rec;
     return status;
+}
+
+// Whether gmres_solve runs the system as one persistent launch: small, and
+// options the persistent kernel implements exactly as gmres_fp64 does.
+bool small_system(const xb_plan *p, const xb_options &o) {
+    if (p->n < 1 || p->n > o.small_n || p->sym) return false;
+    // one CTA does a step's SpMV and Gram-Schmidt passes alone: only while that
+    // work (about nnz + m n) stays small does it beat the multi-launch step
+    // (measured: n = 4096 stencil 76 vs 148 us per step; n = 20,000 power-law
+    // rows 592 vs 168 us)
+    if ((double)p->nnz + (double)o.m * p->n > 32.0 * o.small_n) return false;
+    if (o.precision != XB_PREC_FP64 || o.precond != XB_PRECOND_NONE || !o.fault_check) return false;
+    if (o.ortho != XB_ORTHO_MGS && o.ortho != XB_ORTHO_BCGS) return false;
+    // the persistent kernel's restart rule judges windows of 5 samples, m += 5
+    if (o.dafrt && (o.dafrt_window != 5 || o.dafrt_dm != 5)) return false;
+    const int mmax = o.dafrt ? std::max(o.m, o.m_max) : o.m;
+    return o.m >= 1 && mmax <= XB_BATCH_MAX_M;
 }
 
 int check_args(xb_plan *p, const double *b, double *x, const xb_options &o) {
@@ -562,6 +587,18 @@ double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
     if (variant == XB_VAR_NNZ || variant == XB_VAR_SYM_TILE) {
         for (const auto &t : p->tiles)
             if (t.block == block && t.ipt == ipt) b += 4.0 * (t.ntiles + 1);
+    } else if (variant == XB_VAR_SYM_PART) {
+        for (const auto &t : p->tiles)
+            if (t.block == block && t.ipt == ipt) b += 4.0 * (t.ntiles + 1);
+        for (const auto &t : p->s3)
+            if (t.block == block && t.ipt == ipt)
+                b += 4.0 * (t.ntiles + 1 + 2.0 * t.nslots + 2.0 * t.ngran + 1) +
+                     8.0 * t.nslots * xb::kS3Gran;
+    } else if (variant == XB_VAR_BCSR) {
+        for (const auto &t : p->bcsr)
+            if (t.r == ipt)
+                b += 4.0 * (t.nbr + 1) + 4.0 * t.nblocks + 8.0 * t.nblocks * t.r * t.r +
+                     (t.d_val32 ? 4.0 * t.nblocks * t.r * t.r : 0.0);
     } else if (variant == XB_VAR_SELL) {
         for (const auto &t : p->sells)
             if (t.sigma == 32 * ipt)
@@ -648,6 +685,14 @@ int gmres_solve(xb_plan *p, const double *b, double *x, const xb_options *opt, x
                           }
                           if (o.precision == XB_PREC_MIXED)
                               return gmres_mixed(p, b, x, o, inf, s, ac, tm, t0);
+                          if (small_system(p, o)) {
+                              // thread per row, or warp-sized row blocks when rows are long
+                              const int mode = p->max_row > 32 ? 1 : 0;
+                              double by = 0.0;
+                              const int r = xb::batch_single(p, b, x, o, mode, inf, &by, s);
+                              ac.bytes += by;
+                              return r;
+                          }
                           return gmres_fp64(p, b, x, o, inf, s, ac, tm, t0, o.maxiter);
                       });
 }

@@ -78,6 +78,73 @@ __global__ void __launch_bounds__(512) k_sell(int nslices, const int64_t *__rest
     store_row(y, r, s, alpha, beta, mode);
 }
 
+// ---------------------------------------------------------------------------
+// BCSR (format conversion, R x R blocks): a thread per row walks its block
+// row's blocks; the R threads of a block row share each block's column index
+// and x segment and read consecutive rows of the block.  Zero-filled entries
+// add fma(0, x, s) = s, and the entries come in ascending column order, so the
+// row sum is the one k_row forms, bit for bit.
+// ---------------------------------------------------------------------------
+template <typename V, int R>
+__global__ void __launch_bounds__(512) k_bcsr(int n, const int *__restrict__ bptr,
+                                              const int *__restrict__ bcol,
+                                              const V *__restrict__ bval, const V *__restrict__ x,
+                                              V alpha, V beta, int mode, V *__restrict__ y,
+                                              const V *__restrict__ adev) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (adev) alpha = *adev;
+    const int b = r / R, li = r - b * R;
+    const int q0 = __ldg(bptr + b), q1 = __ldg(bptr + b + 1);
+    V s = V(0);
+    for (int q = q0; q < q1; q++) {
+        const int c0 = __ldg(bcol + q) * R;
+        const V *blk = bval + ((int64_t)q * R + li) * R;
+        if (c0 + R <= n) {
+#pragma unroll
+            for (int j = 0; j < R; j++) s = fma(__ldg(blk + j), __ldg(x + c0 + j), s);
+        } else {  // last block column of a matrix whose n is not a multiple of R
+            for (int j = 0; c0 + j < n; j++) s = fma(__ldg(blk + j), __ldg(x + c0 + j), s);
+        }
+    }
+    store_row(y, r, s, alpha, beta, mode);
+}
+
+template <typename V>
+const V *bcsr_values(const xb::BcsrPart *bp);
+template <>
+const double *bcsr_values<double>(const xb::BcsrPart *bp) { return bp->d_val; }
+template <>
+const float *bcsr_values<float>(const xb::BcsrPart *bp) { return bp->d_val32; }
+
+template <typename V>
+int launch_bcsr(xb_plan *p, int block, int ipt, V alpha, const V *x, V beta, int mode, V *y,
+                const V *adev, cudaStream_t s) {
+    int err = XB_OK;
+    const xb::BcsrPart *bp = xb::get_bcsr(p, ipt, sizeof(V) == sizeof(float), s, &err);
+    if (!bp) return err;
+    const int grid = (p->n + block - 1) / block;
+    const V *bv = bcsr_values<V>(bp);
+    switch (ipt) {
+        case 2:
+            k_bcsr<V, 2><<<grid, block, 0, s>>>(p->n, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
+                                                mode, y, adev);
+            break;
+        case 3:
+            k_bcsr<V, 3><<<grid, block, 0, s>>>(p->n, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
+                                                mode, y, adev);
+            break;
+        case 4:
+            k_bcsr<V, 4><<<grid, block, 0, s>>>(p->n, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
+                                                mode, y, adev);
+            break;
+        default:
+            return xb::set_error(XB_EINVAL, "BCSR: block size %d not in {2, 3, 4}", ipt);
+    }
+    XB_LAUNCHED("k_bcsr");
+    return XB_OK;
+}
+
 template <typename V>
 const V *sell_values(const xb::SellPart *sp);
 template <>
@@ -129,7 +196,8 @@ struct Vec2<float> {
 // Long-row CTAs come first in the grid (they are the longest-running).
 // ---------------------------------------------------------------------------
 template <typename V, int IPT, int M>
-__global__ void __launch_bounds__(512) k_u2(int ntiles, int implicit, int nlong, int n, int nnz,
+__global__ void __launch_bounds__(512, (IPT <= 8 ? 3 : 1)) k_u2(int ntiles, int implicit, int nlong,
+                                                               int n, int nnz,
                                             const int4 *__restrict__ tiles,
                                             const int *__restrict__ lrows,
                                             const int *__restrict__ rowptr,
@@ -726,6 +794,175 @@ __global__ void __launch_bounds__(512) k_sym_tile(const int *__restrict__ rowptr
     if (tid < nr) atomicAdd(&y[r0 + tid], A1 ? s + acc[tid] : fma(alpha, s, acc[tid]));
 }
 
+// ---------------------------------------------------------------------------
+// S3: zero-element omission (Sec. 3.2.2, S3).  The S2 tile partition; each
+// CTA sums the transpose terms of its rows into shared-memory partial vectors
+// that cover only where they land: the tile's own rows, and the granules of
+// kS3Gran rows beyond the tile that the plan listed for it (at most kS3Max).
+// The CTA writes each of its rows once (alpha * (row sum + in-tile transposes)
+// + beta * y) and its granule partials to its slots in device memory; the
+// reduction launch then adds, for every granule some tile reaches, its slots
+// in tile order.  Granules no tile reaches -- the all-zero parts of the
+// partial vectors -- are neither stored nor read.  No device atomics; the
+// shared-memory sums are atomic (their order varies between launches).
+// ---------------------------------------------------------------------------
+template <typename V, int IPT, bool A1>
+__global__ void __launch_bounds__(512) k_sym_s3(const int *__restrict__ rowptr,
+                                                const int *__restrict__ col,
+                                                const V *__restrict__ val, const V *__restrict__ x,
+                                                V alpha, V beta, int mode, V *__restrict__ y,
+                                                const int *__restrict__ trow,
+                                                const int *__restrict__ tslot,
+                                                const int *__restrict__ sgran, V *__restrict__ part,
+                                                const V *__restrict__ adev) {
+    extern __shared__ __align__(16) unsigned char sm_[];
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int T = B * IPT;
+    if (!A1 && adev) alpha = *adev;
+    const int t = blockIdx.x;
+    const int r0 = trow[t], r1 = trow[t + 1];
+    const int k0 = rowptr[r0], k1 = rowptr[r1];
+    const int cnt = k1 - k0, nr = r1 - r0;
+    const int s0 = tslot[t], ns = tslot[t + 1] - s0;
+    V *gp = reinterpret_cast<V *>(sm_);      // kS3Max * kS3Gran
+    V *acc = gp + xb::kS3Max * xb::kS3Gran;  // B
+    V *red = acc + B;                        // 32
+    V *sv = red + 32;                        // T
+    int *sc = reinterpret_cast<int *>(sv + T);  // T
+    int *srp = sc + T;                       // B + 1
+    int *gid = srp + B + 1;                  // kS3Max
+    for (int i = tid; i < ns * xb::kS3Gran; i += B) gp[i] = V(0);
+    for (int i = tid; i < B; i += B) acc[i] = V(0);
+    if (tid < ns) gid[tid] = sgran[s0 + tid];
+    // transpose term u * x_r of stored (r, j, u), j != r: in-tile row or granule slot
+    auto scatter = [&](int j, V tv) {
+        if (j < r1) {
+            atomicAdd(&acc[j - r0], tv);
+        } else {
+            const int g = j / xb::kS3Gran;
+            int q = 0;
+            while (q + 1 < ns && gid[q] != g) q++;
+            atomicAdd(&gp[q * xb::kS3Gran + (j - g * xb::kS3Gran)], tv);
+        }
+    };
+    if (cnt > T) {  // one long row r0, whole CTA
+        __syncthreads();
+        const V xr = x[r0];
+        V sr = V(0);
+        for (int e = k0 + tid; e < k1; e += B) {
+            const int j = col[e];
+            const V u = val[e];
+            sr = fma(u, x[j], sr);
+            if (j != r0) scatter(j, u * xr);
+        }
+        sr = xbd::block_sum(sr, red);
+        __syncthreads();
+        if (tid == 0) store_row(y, r0, sr + acc[0], alpha, beta, mode);
+    } else {
+        {
+            int c[IPT];
+            V v[IPT];
+#pragma unroll
+            for (int j = 0; j < IPT; j++) {
+                const int e = tid + j * B;
+                if (e < cnt) {
+                    c[j] = col[k0 + e];
+                    v[j] = val[k0 + e];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < IPT; j++) {
+                const int e = tid + j * B;
+                if (e < cnt) {
+                    sc[e] = c[j];
+                    sv[e] = v[j];
+                }
+            }
+        }
+        for (int i = tid; i <= nr; i += B) srp[i] = rowptr[r0 + i] - k0;
+        __syncthreads();
+        V sr = V(0);
+        if (tid < nr) {
+            const int r = r0 + tid;
+            const V xr = x[r];
+            for (int e = srp[tid]; e < srp[tid + 1]; e++) {
+                const int j = sc[e];
+                const V u = sv[e];
+                sr = fma(u, x[j], sr);
+                if (j != r) scatter(j, u * xr);
+            }
+        }
+        __syncthreads();
+        if (tid < nr) store_row(y, r0 + tid, sr + acc[tid], alpha, beta, mode);
+    }
+    __syncthreads();
+    for (int i = tid; i < ns * xb::kS3Gran; i += B) part[(size_t)s0 * xb::kS3Gran + i] = gp[i];
+}
+
+// Adds the partials of one reached granule (one CTA of kS3Gran threads).
+template <typename V>
+__global__ void __launch_bounds__(xb::kS3Gran) k_sym_s3_red(int n, const int *__restrict__ gid,
+                                                            const int *__restrict__ gptr,
+                                                            const int *__restrict__ gslot,
+                                                            const V *__restrict__ part, V alpha,
+                                                            V *__restrict__ y,
+                                                            const V *__restrict__ adev) {
+    if (adev) alpha = *adev;
+    const int c = blockIdx.x;
+    const int i = gid[c] * xb::kS3Gran + threadIdx.x;
+    if (i >= n) return;
+    V sum = V(0);
+    for (int q = gptr[c]; q < gptr[c + 1]; q++)
+        sum += part[(size_t)gslot[q] * xb::kS3Gran + threadIdx.x];
+    y[i] += alpha * sum;
+}
+
+// ---------------------------------------------------------------------------
+// S1 with warp-aggregated atomics: a thread per upper row; the warp walks its
+// rows' entries in lock step, and lanes whose transpose terms go to the same
+// row add them (in lane order) before one device atomic per distinct row.
+// y must hold beta*y beforehand.
+// ---------------------------------------------------------------------------
+template <typename V, bool A1>
+__global__ void __launch_bounds__(512) k_sym_wagg(int n, const int *__restrict__ rowptr,
+                                                  const int *__restrict__ col,
+                                                  const V *__restrict__ val,
+                                                  const V *__restrict__ x, V alpha,
+                                                  V *__restrict__ y, const V *__restrict__ adev) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!A1 && adev) alpha = *adev;
+    const bool has = r < n;
+    const int a = has ? rowptr[r] : 0, b = has ? rowptr[r + 1] : 0;
+    int len = b - a, L = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) L = max(L, __shfl_xor_sync(FULL, L, o));
+    const V axi = has ? (A1 ? x[r] : alpha * x[r]) : V(0);
+    V s = V(0);
+    for (int q = 0; q < L; q++) {  // warp-uniform trip count
+        const bool act = q < len;
+        int j = -1;
+        V tv = V(0);
+        if (act) {
+            j = col[a + q];
+            const V u = val[a + q];
+            s = fma(u, x[j], s);
+            if (j != r) tv = u * axi;
+            else j = -1;
+        }
+        const int key = (j >= 0) ? j : -1 - lane;  // lanes with no transpose term: own key
+        const unsigned m = __match_any_sync(FULL, key);
+        V tot = tv;
+        if (__popc(m) > 1) {  // add the group's terms in lane order
+            tot = V(0);
+            for (unsigned mm = m; mm; mm &= mm - 1) tot += __shfl_sync(m, tv, __ffs(mm) - 1);
+        }
+        if (j >= 0 && lane == __ffs(m) - 1) atomicAdd(&y[j], tot);
+    }
+    if (has) atomicAdd(&y[r], A1 ? s : alpha * s);
+}
+
 // Opt every kernel instantiation into the device's full shared-memory
 // capacity once (the launch size decides the occupancy).
 int smem_limit() {
@@ -860,9 +1097,55 @@ int launch_sym(xb_plan *p, int variant, const int *rp, const int *ci, const V *v
                int ipt, V alpha, const V *x, V beta, V *y, const V *adev, cudaStream_t s) {
     const int n = p->n;
     if (n == 0) return XB_OK;
+    const bool a1 = (adev == nullptr && alpha == V(1));
+    if (variant == XB_VAR_SYM_PART) {
+        int err = XB_OK;
+        const xb::TilePart *tp = xb::get_tiles(p, block, ipt, s, &err);
+        if (!tp) return err;
+        const xb::S3Part *sp = xb::get_s3(p, block, ipt, s, &err);
+        if (!sp) return err;
+        const int mode = adev ? 1 : (beta == V(0)) ? (alpha == V(1) ? 0 : 1) : 2;
+        const size_t sm = ((size_t)xb::kS3Max * xb::kS3Gran + block + 32 + (size_t)block * ipt) *
+                              sizeof(V) +
+                          (size_t)block * ipt * 4 + (block + 1) * 4 + xb::kS3Max * 4;
+        V *part = reinterpret_cast<V *>(sp->d_part);
+#define XB_S3(I)                                                                                \
+    case I:                                                                                     \
+        if (a1) {                                                                               \
+            XB_TRY(smem_optin((const void *)k_sym_s3<V, I, true>, sm));                          \
+            k_sym_s3<V, I, true><<<sp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, beta, mode,  \
+                                                              y, tp->d_row, sp->d_tslot,        \
+                                                              sp->d_sgran, part, adev);         \
+        } else {                                                                                \
+            XB_TRY(smem_optin((const void *)k_sym_s3<V, I, false>, sm));                         \
+            k_sym_s3<V, I, false><<<sp->ntiles, block, sm, s>>>(rp, ci, va, x, alpha, beta,      \
+                                                               mode, y, tp->d_row, sp->d_tslot, \
+                                                               sp->d_sgran, part, adev);        \
+        }                                                                                       \
+        break;
+        switch (ipt) {
+            XB_S3(1) XB_S3(2) XB_S3(4) XB_S3(8) XB_S3(16)
+            default: return xb::set_error(XB_EINVAL, "sym S3: unsupported ipt %d", ipt);
+        }
+#undef XB_S3
+        XB_LAUNCHED("k_sym_s3");
+        if (sp->ngran > 0) {
+            k_sym_s3_red<V><<<sp->ngran, xb::kS3Gran, 0, s>>>(n, sp->d_gid, sp->d_gptr, sp->d_gslot,
+                                                              part, alpha, y, adev);
+            XB_LAUNCHED("k_sym_s3_red");
+        }
+        return XB_OK;
+    }
     k_yscale<V><<<(n + 255) / 256, 256, 0, s>>>(n, beta, y);
     XB_LAUNCHED("k_yscale");
-    const bool a1 = (adev == nullptr && alpha == V(1));
+    if (variant == XB_VAR_SYM_WAGG) {
+        if (a1)
+            k_sym_wagg<V, true><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
+        else
+            k_sym_wagg<V, false><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
+        XB_LAUNCHED("k_sym_wagg");
+        return XB_OK;
+    }
     if (variant == XB_VAR_SYM_ATOMIC) {
         if (a1)
             k_sym_atomic<V, true><<<(n + block - 1) / block, block, 0, s>>>(n, rp, ci, va, x, alpha, y, adev);
@@ -927,10 +1210,14 @@ int spmv_any(xb_plan *p, int variant, int block, int ipt, V alpha, const V *x, V
                                  s);
         case XB_VAR_SYM_ATOMIC:
         case XB_VAR_SYM_TILE:
+        case XB_VAR_SYM_PART:
+        case XB_VAR_SYM_WAGG:
             return launch_sym<V>(p, variant, p->rowptr, p->col, va, block, ipt, alpha, x, beta, y,
                                  adev, s);
         case XB_VAR_SELL:
             return launch_sell<V>(p, block, ipt, alpha, x, beta, mode, y, adev, s);
+        case XB_VAR_BCSR:
+            return launch_bcsr<V>(p, block, ipt, alpha, x, beta, mode, y, adev, s);
     }
     return xb::set_error(XB_EINVAL, "unknown SpMV variant %d", variant);
 }

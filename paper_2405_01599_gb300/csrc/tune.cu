@@ -17,6 +17,11 @@ std::vector<Cand> candidates(const xb_plan *p) {
         for (int b : {128, 256, 512}) c.push_back({XB_VAR_SYM_ATOMIC, b, 1});
         for (int b : {128, 256, 512})
             for (int i : {4, 8, 16}) c.push_back({XB_VAR_SYM_TILE, b, i});
+        // S3 partial vectors (skipped when a tile reaches too many granules)
+        // and S1 with warp-aggregated atomics
+        for (int b : {128, 256, 512})
+            for (int i : {4, 8}) c.push_back({XB_VAR_SYM_PART, b, i});
+        for (int b : {128, 256, 512}) c.push_back({XB_VAR_SYM_WAGG, b, 1});
         return c;
     }
     for (int b : {64, 128, 256, 512}) c.push_back({XB_VAR_ROW, b, 1});
@@ -28,6 +33,10 @@ std::vector<Cand> candidates(const xb_plan *p) {
     // across slices) or 1024 rows; skipped when its padding is too large
     for (int b : {128, 256, 512})
         for (int i : {1, 32}) c.push_back({XB_VAR_SELL, b, i});
+    // format conversion: block CRS with 2x2, 3x3, 4x4 blocks (the block-size
+    // AT); skipped when the zero fill is too large
+    for (int b : {128, 256})
+        for (int i : {2, 3, 4}) c.push_back({XB_VAR_BCSR, b, i});
     return c;
 }
 

@@ -124,6 +124,47 @@ def convdiff3d(N=256, pe=10.0, dims=None):
     return _mat(n, rp, c, v, kind="convdiff3d", side=N, pe=pe)
 
 
+def block_stencil3d(N, dof=3, seed=0):
+    """A 7-point 3D grid (N^3 nodes) with `dof` unknowns per node and a dense
+    dof x dof coupling block for every stencil neighbour pair: the pattern of
+    vector-valued PDEs such as 3D elasticity (3 displacements per node).  Node
+    (i, j, k) is index (i * N + j) * N + k; its unknowns are consecutive rows.
+    Off-diagonal blocks U[-1, 0]; the diagonal block U[-1, 1] off its diagonal
+    and 1 + the row's absolute sum on it (strictly diagonally dominant)."""
+    rng = np.random.default_rng(seed)
+    nodes = N ** 3
+    n = nodes * dof
+    idx = np.arange(nodes, dtype=np.int64)
+    i, j, k = idx // (N * N), (idx // N) % N, idx % N
+    nb = [idx]
+    ok = [np.ones(nodes, bool)]
+    for d, (di, dj, dk) in enumerate(((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1))):
+        ii, jj, kk = i + di, j + dj, k + dk
+        ok.append((ii >= 0) & (ii < N) & (jj >= 0) & (jj < N) & (kk >= 0) & (kk < N))
+        nb.append(np.clip(ii, 0, N - 1) * N * N + np.clip(jj, 0, N - 1) * N + np.clip(kk, 0, N - 1))
+    nb = np.stack(nb, axis=1)   # nodes x 7 (0: the node itself)
+    ok = np.stack(ok, axis=1)
+    order = np.argsort(np.where(ok, nb, np.iinfo(np.int64).max), axis=1, kind="stable")
+    nbs = np.take_along_axis(nb, order, axis=1)
+    oks = np.take_along_axis(ok, order, axis=1)
+    deg = oks.sum(axis=1)
+    # every row of a node has the node's neighbours' unknowns, ascending
+    cols = (nbs[:, None, :, None] * dof + np.arange(dof)[None, None, None, :])  # node, -, t, b
+    cols = np.broadcast_to(cols, (nodes, dof, 7, dof))
+    mask = np.broadcast_to(oks[:, None, :, None], cols.shape)
+    same = np.broadcast_to((nbs == idx[:, None])[:, None, :, None], cols.shape)
+    v = np.where(same, rng.uniform(-1, 1, cols.shape), rng.uniform(-1, 0, cols.shape))
+    rows = idx[:, None] * dof + np.arange(dof)[None, :]                         # node, a
+    diag = cols == rows[:, :, None, None]
+    v = np.where(diag | ~mask, 0.0, v)
+    v = np.where(diag, 1.0 + np.abs(v).sum(axis=(2, 3), keepdims=True), v)
+    col = cols[mask]
+    val = v[mask]
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.repeat(deg * dof, dof), out=rowptr[1:])
+    return _mat(n, rowptr, col, val, kind="block_stencil3d", side=N, dof=dof)
+
+
 def quasi_triangular(n=400, per_row=4, seed=0, pair_frac=0.5, top=10.0, ratio=0.995,
                      signed=False, off=1.0):
     """Block upper-triangular n x n with a spectrum known by construction.

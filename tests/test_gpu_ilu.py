@@ -2,7 +2,10 @@
 (same IKJ order per row; the device contracts a*b+c into FMAs, so entries
 agree to rounding, 1e-11 relative to the row's largest factor), the two
 substitutions (1e-10 of max |z|), and right-preconditioned GMRES and
-BiCGStab (true residual <= 1e-8, iteration counts within max(3, 10 %))."""
+BiCGStab (true residual <= 1e-8, iteration counts within max(3, 10 %)).
+Both substitution paths run every case: the captured graph of level
+launches (mode 0) and the persistent cooperative launch (mode 1); a test
+makes the persistent path's bounded barrier wait run out."""
 import numpy as np
 import pytest
 
@@ -22,14 +25,16 @@ def env():
     return lib_and_device()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name,make", MATS)
-def test_factors_and_apply_match_oracle(env, name, make):
+def test_factors_and_apply_match_oracle(env, name, make, mode):
     xb, dev = env
     import torch
     A = make()
     lu_o, st = oracle.ilu0(A)
     assert st == 0
     plan = xb.Plan.from_host(A, dev)
+    plan.ilu0_config(mode)
     lu = plan.ilu0_factors().cpu().numpy()
     rp = A["rowptr"]
     for i in range(A["n"]):
@@ -43,14 +48,16 @@ def test_factors_and_apply_match_oracle(env, name, make):
     assert np.max(np.abs(z - zo)) <= 1e-10 * np.max(np.abs(zo))
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name,make", MATS)
 @pytest.mark.parametrize("which", ["gmres", "bicgstab"])
-def test_preconditioned_solvers_match_oracle(env, name, make, which):
+def test_preconditioned_solvers_match_oracle(env, name, make, which, mode):
     xb, dev = env
     import torch
     A = make()
     b = oracle.spmv(A, np.ones(A["n"]))
     plan = xb.Plan.from_host(A, dev)
+    plan.ilu0_config(mode)
     x = torch.zeros(A["n"], dtype=torch.float64, device=dev)
     fn = plan.gmres if which == "gmres" else plan.bicgstab
     info = fn(torch.tensor(b, device=dev), x, tol=1e-8, precond=xb.PRECOND_ILU0)
@@ -80,3 +87,40 @@ def test_ilu_argument_errors(env):
     with pytest.raises(xb.XbError) as e:
         xb.Plan.from_host(Z, dev).ilu0_setup()
     assert e.value.code == xb.XB_EBREAKDOWN
+
+
+def test_persistent_barrier_wait_runs_out(env):
+    """The persistent substitution's level barrier with a one-poll limit: a
+    CTA that finds the barrier not yet released gives up, flags the error and
+    returns, the rest return at their next barrier, and the host reports
+    XB_ETIMEOUT (a bounded wait, no fault).  The plan stays usable: with the
+    default limit the next application matches the oracle."""
+    xb, dev = env
+    import torch
+    A = gen.poisson2d(40)  # 79 dependency levels per triangle
+    plan = xb.Plan.from_host(A, dev)
+    plan.ilu0_setup()
+    r = np.random.default_rng(3).standard_normal(A["n"])
+    rt = torch.tensor(r, device=dev)
+    z = torch.empty_like(rt)
+    plan.ilu0_config(1, barrier_polls=1)
+    with pytest.raises(xb.XbError) as e:
+        plan.ilu0_apply(rt, z)
+    assert e.value.code == xb.XB_ETIMEOUT
+    b = torch.tensor(oracle.spmv(A, np.ones(A["n"])), device=dev)
+    for fn in (plan.gmres, plan.bicgstab):  # both stop at their next check of the flag
+        info = fn(b, torch.zeros_like(b), tol=1e-8, precond=xb.PRECOND_ILU0, maxiter=2000)
+        assert info["status"] == xb.XB_ETIMEOUT, info
+        assert info["iters"] <= 60, info  # stopped early, not at maxiter
+    plan.ilu0_config(1, barrier_polls=0)
+    zo = oracle.ilu0_solve(A, oracle.ilu0(A)[0], r)
+    z = plan.ilu0_apply(rt, z).cpu().numpy()
+    assert np.max(np.abs(z - zo)) <= 1e-10 * np.max(np.abs(zo))
+
+
+def test_ilu_config_rejects_bad_arguments(env):
+    xb, dev = env
+    plan = xb.Plan.from_host(gen.poisson2d(6), dev)
+    for mode, polls in ((2, 0), (-2, 0), (0, -1)):
+        with pytest.raises(xb.XbError):
+            plan.ilu0_config(mode, polls)

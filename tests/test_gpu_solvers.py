@@ -35,17 +35,22 @@ def _solve(xb, dev, A, which, b=None, x0=None, **opt):
     return info, xt.cpu().numpy(), b
 
 
+@pytest.mark.parametrize("small_n", [8192, 0])
 @pytest.mark.parametrize("name,make,m", [
     ("poisson64", lambda: gen.poisson2d(64), 30),
     ("random200", lambda: gen.random200(), 30),
     ("convdiff10", lambda: gen.convdiff3d(N=10), 20),
     ("laplace3d_10_upper", lambda: gen.laplace3d(10, upper=True), 25),
 ])
-def test_gmres_matches_oracle(env, name, make, m):
+def test_gmres_matches_oracle(env, name, make, m, small_n):
+    """Both GMRES paths: one persistent launch for small general systems
+    (small_n = 8192, the default) and the multi-launch path (small_n = 0;
+    symmetric storage always takes it)."""
     xb, dev = env
     A = make()
-    info, x, b = _solve(xb, dev, A, "gmres", m=m, tol=TOL)
+    info, x, b = _solve(xb, dev, A, "gmres", m=m, tol=TOL, small_n=small_n)
     xo, io = oracle.gmres(A, b, m=m, tol=TOL)
+    assert info["persistent"] == (1 if small_n and not A["sym_upper"] else 0)
     assert info["status"] == 0, info
     assert _true_rel(A, x, b) <= TOL
     assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
@@ -56,7 +61,8 @@ def test_gmres_matches_oracle(env, name, make, m):
 def test_gmres_each_spmv_variant(env, variant):
     xb, dev = env
     A = gen.powerlaw(n=4000, seed=4)
-    info, x, b = _solve(xb, dev, A, "gmres", m=40, tol=TOL, variant=variant, maxiter=20000)
+    info, x, b = _solve(xb, dev, A, "gmres", m=40, tol=TOL, variant=variant, maxiter=20000,
+                        small_n=0)
     assert info["status"] == 0 and _true_rel(A, x, b) <= TOL
     assert info["variant_used"] == variant
 
@@ -64,17 +70,19 @@ def test_gmres_each_spmv_variant(env, variant):
 def test_gmres_check_every_is_transparent(env):
     xb, dev = env
     A = gen.poisson2d(40)
-    i1, x1, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, check_every=1)
-    i4, x4, _ = _solve(xb, dev, A, "gmres", m=30, tol=TOL, check_every=7)
+    i1, x1, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, check_every=1, small_n=0)
+    i4, x4, _ = _solve(xb, dev, A, "gmres", m=30, tol=TOL, check_every=7, small_n=0)
     assert i1["iters"] == i4["iters"] and i1["restarts"] == i4["restarts"]
     np.testing.assert_array_equal(x1, x4)
 
 
-def test_gmres_dafrt_matches_oracle(env):
+@pytest.mark.parametrize("small_n", [8192, 0])
+def test_gmres_dafrt_matches_oracle(env, small_n):
     xb, dev = env
     A = gen.poisson2d(24)
     info, x, b = _solve(xb, dev, A, "gmres", m=2, m_max=17, tol=TOL, dafrt=1, dafrt_theta=10.0,
-                        dafrt_window=5, dafrt_dm=5, maxiter=3000)
+                        dafrt_window=5, dafrt_dm=5, maxiter=3000, small_n=small_n)
+    assert info["persistent"] == (1 if small_n else 0)
     xo, io = oracle.gmres(A, b, m=2, m_max=17, tol=TOL, maxiter=3000, dafrt=True, theta=10.0,
                           window=5, dm=5)
     assert info["m_final"] == io["m_final"] and info["m_final"] > 2
@@ -82,22 +90,24 @@ def test_gmres_dafrt_matches_oracle(env):
     assert info["status"] == io["status"]
 
 
-def test_gmres_edge_cases(env):
+@pytest.mark.parametrize("small_n", [8192, 0])
+def test_gmres_edge_cases(env, small_n):
     xb, dev = env
     A = gen.poisson2d(10)
     n = A["n"]
-    info, x, _ = _solve(xb, dev, A, "gmres", b=np.zeros(n), x0=np.ones(n))
+    info, x, _ = _solve(xb, dev, A, "gmres", b=np.zeros(n), x0=np.ones(n), small_n=small_n)
     assert info["status"] == 0 and np.all(x == 0)
-    info, x, b = _solve(xb, dev, A, "gmres", m=5, tol=1e-12, maxiter=20)
+    info, x, b = _solve(xb, dev, A, "gmres", m=5, tol=1e-12, maxiter=20, small_n=small_n)
     assert info["status"] == xb.XB_ENOCONV and info["iters"] == 20 and info["res_true"] > 1e-12
     I = dict(n=50, nnz=50, rowptr=np.arange(51, dtype=np.int32), col=np.arange(50, dtype=np.int32),
              val=np.ones(50), sym_upper=False)
-    info, x, b = _solve(xb, dev, I, "gmres", b=np.random.default_rng(0).standard_normal(50))
+    info, x, b = _solve(xb, dev, I, "gmres", b=np.random.default_rng(0).standard_normal(50),
+                        small_n=small_n)
     assert info["status"] == 0 and info["iters"] == 1
     np.testing.assert_allclose(x, b, rtol=1e-15)
     Z = dict(n=6, nnz=0, rowptr=np.zeros(7, np.int32), col=np.zeros(0, np.int32), val=np.zeros(0),
              sym_upper=False)
-    info, x, b = _solve(xb, dev, Z, "gmres", b=np.ones(6))
+    info, x, b = _solve(xb, dev, Z, "gmres", b=np.ones(6), small_n=small_n)
     assert info["status"] == xb.XB_EBREAKDOWN
     info, x, b = _solve(xb, dev, Z, "bicgstab", b=np.ones(6))
     assert info["status"] == xb.XB_EBREAKDOWN

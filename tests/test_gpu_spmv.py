@@ -19,7 +19,19 @@ GENERAL = {
     "nnz": (1, [(64, 4), (128, 4), (256, 8), (512, 16), (128, 16)]),
     "segscan": (2, [(64, 4), (128, 4), (256, 8), (128, 16), (256, 16), (128, 32)]),
     "sell": (5, [(64, 1), (256, 1), (128, 8), (512, 32)]),
+    "bcsr": (8, [(128, 2), (256, 3), (64, 4)]),
 }
+
+
+def bcsr_accepts(A, r):
+    """The BCSR copy is built unless its r x r blocks hold more than 2 nnz +
+    16 r entries (blocks = distinct column blocks of each block row)."""
+    rp = np.asarray(A["rowptr"], np.int64)
+    col = np.asarray(A["col"], np.int64)
+    n = A["n"]
+    nb = sum(np.unique(col[rp[b * r]:rp[min(n, b * r + r)]] // r).size
+             for b in range((n + r - 1) // r))
+    return nb * r * r <= 2 * A["nnz"] + 16 * r
 
 
 def sell_accepts(A, sigma):
@@ -63,6 +75,8 @@ MATS = {
     "laplace3d_20": lambda: gen.laplace3d(20),
     "convdiff12": lambda: gen.convdiff3d(N=12),
     "powerlaw30k": lambda: gen.powerlaw(n=30000, seed=3),
+    "block3d_10_dof3": lambda: gen.block_stencil3d(10, 3),
+    "block3d_7_dof2": lambda: gen.block_stencil3d(7, 2),
     "adversarial": _adversarial,
     "one_huge_row": _one_huge_row,
     "n1": lambda: dict(n=1, nnz=1, rowptr=np.array([0, 1], np.int32), col=np.array([0], np.int32),
@@ -94,7 +108,8 @@ def test_general_variants_match_oracle(env, mname):
         for vname, (v, shapes) in GENERAL.items():
             for block, ipt in shapes:
                 y = torch.tensor(y0, device=dev) if beta != 0 else torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
-                if v == xb.VAR_SELL and not sell_accepts(A, 32 * ipt):
+                if ((v == xb.VAR_SELL and not sell_accepts(A, 32 * ipt)) or
+                        (v == xb.VAR_BCSR and not bcsr_accepts(A, ipt))):
                     with pytest.raises(xb.XbError):
                         plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
                     continue
@@ -135,6 +150,28 @@ def test_segscan_deterministic(env):
     np.testing.assert_array_equal(ys[0], ys[2])
 
 
+def _arrow(U):
+    """Upper storage plus a dense last column (every row couples to row n-1):
+    all lanes of a warp send a transpose term to the same row, the case the
+    warp-aggregated atomics combine."""
+    n = U["n"]
+    rp = np.asarray(U["rowptr"], np.int64)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        a, b = rp[i], rp[i + 1]
+        c = list(U["col"][a:b])
+        v = list(U["val"][a:b])
+        if i < n - 1 and c[-1] != n - 1:
+            c.append(n - 1)
+            v.append(0.01)
+        rows.append(len(c))
+        cols += c
+        vals += v
+    rp2 = np.concatenate([[0], np.cumsum(rows)])
+    return dict(n=n, nnz=int(rp2[-1]), rowptr=rp2.astype(np.int32), col=np.array(cols, np.int32),
+                val=np.array(vals), sym_upper=True)
+
+
 def _sym_long_row():
     n = 4000
     U = gen.random_sym_upper(n, per_row=3, seed=21)
@@ -151,8 +188,29 @@ def _sym_long_row():
                 val=val2, sym_upper=True)
 
 
+def s3_accepts(U, block, ipt):
+    """The S3 layout exists unless some tile (at most `block` rows and
+    block*ipt entries, a longer row alone) reaches more than 8 granules of 256
+    rows beyond its last row."""
+    rp = np.asarray(U["rowptr"], np.int64)
+    col = np.asarray(U["col"], np.int64)
+    n = U["n"]
+    r = 0
+    while r < n:
+        r1 = r + 1
+        if rp[r + 1] - rp[r] <= block * ipt:
+            while r1 < n and r1 - r < block and rp[r1 + 1] - rp[r] <= block * ipt:
+                r1 += 1
+        c = col[rp[r]:rp[r1]]
+        if np.unique(c[c >= r1] // 256).size > 8:
+            return False
+        r = r1
+    return True
+
+
 SYM = {
     "laplace3d_20_upper": lambda: gen.laplace3d(20, upper=True),
+    "laplace3d_24_upper_arrow": lambda: _arrow(gen.laplace3d(24, upper=True)),
     "randsym3000": lambda: gen.random_sym_upper(3000, per_row=6, seed=3),
     "sym_long_row": _sym_long_row,
     "poisson2d_50_upper": lambda: gen.poisson2d(50, upper=True),
@@ -176,9 +234,14 @@ def test_sym_variants_match_oracle(env, mname):
         bound = row_bound(F, x, alpha, beta, y0)
         # the symmetric-storage identity: oracle sym == oracle full
         assert_rows_close(oracle.spmv(F, x, alpha, beta, y0), yref, bound, what="oracle sym==full")
-        for v, shapes in ((3, [(128, 1), (256, 1)]), (4, [(128, 4), (256, 8), (512, 16), (64, 1)])):
+        for v, shapes in ((3, [(128, 1), (256, 1)]), (4, [(128, 4), (256, 8), (512, 16), (64, 1)]),
+                          (6, [(128, 4), (256, 8), (512, 16), (64, 1)]), (7, [(64, 1), (256, 1)])):
             for block, ipt in shapes:
                 y = torch.tensor(y0, device=dev)
+                if v == 6 and not s3_accepts(U, block, ipt):
+                    with pytest.raises(xb.XbError):
+                        plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
+                    continue
                 plan.spmv(xt, y, alpha=alpha, beta=beta, variant=v, block=block, ipt=ipt)
                 assert_rows_close(y.cpu().numpy(), yref, bound, what=f"{mname}/v{v}/b{block}i{ipt}")
         y = torch.tensor(y0, device=dev)
@@ -327,3 +390,34 @@ def test_sell_layout_and_solvers(env):
         assert info["variant_used"] == xb.VAR_SELL
         if prec == xb.PREC_FP64:
             assert abs(info["iters"] - oinfo["iters"]) <= max(3, 0.05 * oinfo["iters"])
+
+
+def test_bcsr_is_bit_identical_to_row_kernel_and_solves(env):
+    """BCSR adds its zero fill as fma(0, x, s) and walks columns in ascending
+    order, so y equals the row kernel's bit for bit; GMRES runs on it in FP64
+    and mixed precision; the exhaustive tuner may pick it."""
+    xb, dev = env
+    import torch
+    A = gen.block_stencil3d(12, 3)
+    plan = xb.Plan.from_host(A, dev)
+    xt = torch.tensor(np.random.default_rng(3).uniform(-1, 1, A["n"]), device=dev)
+    y_row = torch.empty_like(xt)
+    plan.spmv(xt, y_row, variant=xb.VAR_ROW, block=256, ipt=1)
+    for r in (2, 3, 4):
+        y = torch.empty_like(xt)
+        plan.spmv(xt, y, variant=xb.VAR_BCSR, block=128, ipt=r)
+        assert torch.equal(y, y_row), r
+    b_h = oracle.spmv(A, np.ones(A["n"]))
+    b = torch.tensor(b_h, device=dev)
+    _, oinfo = oracle.gmres(A, b_h, m=30, tol=1e-8)
+    for prec in (xb.PREC_FP64, xb.PREC_MIXED):
+        x = torch.zeros_like(b)
+        info = plan.gmres(b, x, m=30, tol=1e-8, precision=prec, variant=xb.VAR_BCSR, block=128,
+                          ipt=3, small_n=0)
+        rel = np.linalg.norm(b_h - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b_h)
+        assert info["status"] == 0 and rel <= 1e-8, info
+        assert info["variant_used"] == xb.VAR_BCSR
+        if prec == xb.PREC_FP64:
+            assert abs(info["iters"] - oinfo["iters"]) <= max(3, 0.05 * oinfo["iters"])
+    ch = plan.tune()
+    assert ch["variant"] in (xb.VAR_ROW, xb.VAR_NNZ, xb.VAR_SEGSCAN, xb.VAR_SELL, xb.VAR_BCSR)
