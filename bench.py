@@ -9,8 +9,9 @@ SpMV y = A x on the power-law matrix of the unbalanced-rows workload
 the 129 MB L2).  GB/s counts algorithmic bytes: 12 B per non-zero (value +
 column index), rowptr once, x once, y once.
 
---impl reference times the CPU oracle (plain C, one host core) on a bounded
-row sample of the same matrix with the same metric.
+--impl reference times the CPU oracle's SpMV on the same matrix with the same
+metric: its OpenMP build, the rows split statically over all host cores (the
+paper's row decomposition U1 on the CPU).
 """
 from __future__ import annotations
 
@@ -42,8 +43,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip per-variant/sym/solver lines")
     ap.add_argument("--no-solvers", action="store_true",
                     help="skip the GMRES time-to-1e-8 comparison (256^3 convection-diffusion)")
-    ap.add_argument("--batch", action="store_true",
-                    help="also run the 512-system batched solve (default / learned / exhaustive)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 512-system batch (config 5)")
+    ap.add_argument("--batch-rule-arms", action="store_true",
+                    help="batch: also the arms with the restart-frequency rule (Eq. 1)")
     ap.add_argument("--variant", default=None,
                     choices=["row", "nnz", "segscan", "sym-atomic", "sym-tile", "sell"],
                     help="fixed SpMV variant instead of the exhaustive tuner")
@@ -171,15 +174,16 @@ def alg_bytes(A, vb=8, beta=False):
     return (vb + 4) * nnz + 4 * (n + 1) + 2 * vb * n + (vb * n if beta else 0)
 
 
-# DRAM bytes (read + write) of one headline SpMV launch from an ncu capture, keyed by
-# (variant, block, ipt, n, nnz) and valid only while the code that launch ran is
-# unchanged: the sha256 of the segmented-scan kernels, their launcher and the
-# row-store helper (csrc/spmv.cu) and of the plan builders of their row-end bitmask
-# and warp start rows (csrc/plan.cu), as cut out by HEADLINE_SRC below.  The
+# DRAM bytes (read + write) of one headline SpMV launch (k_bss) from an ncu capture,
+# keyed by (variant, block, ipt, n, nnz) and valid only while the code that launch
+# ran is unchanged: the sha256 of the segmented-scan kernels, their launcher and the
+# row-store helper (csrc/spmv.cu) and of the plan builders of their row-end bitmask,
+# warp start rows and BSS data format copy (csrc/plan.cu), as cut out by
+# HEADLINE_SRC below.  The
 # capture and its command are summarised in profiles/.
 NCU_TRAFFIC = {
     ("segscan", 128, 8, 4_000_000, 52_238_581):
-        (706.63e6, "e754fb61fd997d69e722bc8923891f434d2c502a07d577334435fb08ac5baff7"),
+        (707.49e6, "b0c6609017e1496a9746e8702269a5e1dffcb01b66783f81a9d5ea616ce3f896"),
 }
 HEADLINE_SRC = [
     ("spmv.cu", "__device__ __forceinline__ void store_row(", "// U1: one thread per row"),
@@ -210,8 +214,35 @@ def ncu_traffic(choice_name, block, ipt, n, nnz):
     return ent[0]
 
 
-def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None):
-    """Time the oracle's SpMV (plain C, one core) on a bounded row block."""
+def host_cpu():
+    """The host's CPU model, vendor and logical core count (lscpu, else
+    /proc/cpuinfo)."""
+    info = {"model": None, "vendor": None, "nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name" and info["model"] is None:
+                info["model"] = val.strip()
+            elif key.strip() == "Vendor ID" and info["vendor"] is None:
+                info["vendor"] = val.strip()
+    except Exception:
+        pass
+    if info["model"] is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        info["model"] = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return info
+
+
+def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None, omp=False):
+    """Time the oracle's SpMV on a row block (one core, or the OpenMP build's
+    row-parallel loop over every host core); median of the runs."""
     import oracle
     rp = A["rowptr"]
     n = A["n"]
@@ -224,7 +255,7 @@ def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None):
                col=A["col"], val=A["val"], sym_upper=False)
     x = np.random.default_rng(0).uniform(-1, 1, n)
     y = np.zeros(r1)
-    L = oracle.lib()
+    L = oracle.lib_omp() if omp else oracle.lib()
     times = []
     t_end = time.perf_counter() + budget_s
     while True:
@@ -234,35 +265,37 @@ def cpu_oracle_rate(A, budget_s=10.0, max_nnz=None):
         if time.perf_counter() > t_end or len(times) >= 50:
             break
     t = float(np.median(times))
-    return alg_bytes(sub) / t / 1e9, t, sub, len(times)
+    return alg_bytes(sub) / t / 1e9, t, sub, len(times), L.orc_num_threads()
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    A = make_c3(args.n)
-    # each step: the oracle SpMV over a row block of ~8M non-zeros
-    budget_nnz = 8_000_000
-    gbs, t, sub, reps = cpu_oracle_rate(A, budget_s=0.0, max_nnz=budget_nnz)
     import oracle
-    L = oracle.lib()
-    x = np.random.default_rng(0).uniform(-1, 1, A["n"])
-    y = np.zeros(sub["n"])
+    A = make_c3(args.n)
+    L = oracle.lib_omp()
+    n = A["n"]
+    x = np.random.default_rng(0).uniform(-1, 1, n)
+    y = np.zeros(n)
+    # one step: the oracle's SpMV over the whole matrix, rows split over all host
+    # cores (the OpenMP build of the plain loops)
     for _ in range(args.warmup):
-        L.orc_spmv(sub["n"], sub["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
+        L.orc_spmv(n, A["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        L.orc_spmv(sub["n"], sub["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
+        L.orc_spmv(n, A["rowptr"], A["col"], A["val"], 1.0, x, 0.0, y)
     el = time.perf_counter() - t0
-    val = alg_bytes(sub) * args.steps / el / 1e9
-    sample = f"rows 0..{sub['n']} of the n=4M power-law matrix ({sub['nnz']} non-zeros) per step"
+    val = alg_bytes(A) * args.steps / el / 1e9
+    threads = L.orc_num_threads()
+    sample = (f"the whole n=4M power-law SpMV per step ({A['nnz']} non-zeros), rows split "
+              f"statically over {threads} OpenMP threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": sample, "cpu": host_cpu()},
         "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -461,10 +494,17 @@ def main():
         "clocks": clk,
     }
     if ws == 1:
-        gbs, t, sub, reps = cpu_oracle_rate(A, budget_s=10.0)
-        out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                               "sample": f"full n=4M SpMV, median of {reps} runs"}
+        gbs, t, sub, reps, thr = cpu_oracle_rate(A, budget_s=6.0, omp=True)
+        g1, t1, _, reps1, _ = cpu_oracle_rate(A, budget_s=6.0)
+        out["cpu_baseline"] = {
+            "value": gbs, "unit": "GB/s", "cores": thr, "kind": "oracle",
+            "sample": f"the whole n=4M SpMV, rows split over {thr} OpenMP threads "
+                      f"(the oracle's OpenMP build), median of {reps} runs",
+            "single_core": {"value": g1, "unit": "GB/s", "cores": 1,
+                            "sample": f"the whole n=4M SpMV, plain oracle, median of {reps1} runs"},
+            "cpu": host_cpu()}
     if not args.no_extras:
+        args.sm_mhz = clk.get("sm_mhz")
         out["extras"] = extras(xb, torch, dev, plan, A, x, y, args)
     print(json.dumps(out))
     if pg:
@@ -491,11 +531,19 @@ def extras(xb, torch, dev, plan, A, x, y, args):
     res = {}
     b3 = alg_bytes(A)
     var = {}
-    for name, v, blk, ipt in [("row_U1", 0, 256, 1), ("nnz_U2", 1, 256, 8),
-                              ("segscan_U3", 2, 256, 8), ("segscan_U3_i16", 2, 128, 16)]:
+    for name, v, blk, ipt in [("row_U1", 0, 256, 1), ("nnz_U2", 1, 128, 8),
+                              ("nnz_U2_b256", 1, 256, 8), ("segscan_U3", 2, 128, 8),
+                              ("segscan_U3_b256", 2, 256, 8), ("segscan_U3_i16", 2, 128, 16)]:
         ms = _time_spmv(torch, lambda: plan.spmv(x, y, variant=v, block=blk, ipt=ipt))
         var[name] = {"ms": ms, "GBs": b3 / ms / 1e6}
+    var["ratios"] = {"segscan_U3_vs_row_U1": var["row_U1"]["ms"] / var["segscan_U3"]["ms"],
+                     "nnz_U2_vs_row_U1": var["row_U1"]["ms"] / var["nnz_U2"]["ms"],
+                     "paper_T2K_16_threads": "U3/U1 4.62x on trans4 (Sec. 4.4.1.3), "
+                                             "U2/U1 2.8x on epb3 (Sec. 4.4.1.2)"}
     res["c3_variants"] = var
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (args.sm_mhz or 2070.0)
+    fp64_peak = 2.0 * nsm * mhz * 1e6  # FP64 FMA lanes per second: 2 per clock per SM
     # config 2: 3D 7-point Laplacian 128^3, symmetric upper storage vs full
     U = gen.laplace3d(128, upper=True)
     F = gen.laplace3d(128)
@@ -513,11 +561,23 @@ def extras(xb, torch, dev, plan, A, x, y, args):
     bs = 12 * U["nnz"] + 4 * (n2 + 1) + 16 * n2
     bf = alg_bytes(F)
     flops = 2 * F["nnz"]
+    # FP64 pipe operations per SpMV: symmetric (alpha = 1) = one FMA per stored
+    # entry for the row sum plus one multiply per stored off-diagonal for its
+    # transpose term; full storage = one FMA per entry.  Equal counts.
+    ops_sym = 2 * U["nnz"] - n2
+    ops_full = F["nnz"]
+    fp = lambda ops, ms: {"ops": ops, "achieved_G": ops / ms / 1e6, "peak_G": fp64_peak / 1e9,
+                          "frac": ops / (ms * 1e-3) / fp64_peak}
     res["c2_sym_vs_full"] = {
-        "sym_tuned": {"choice": cu, "ms": ms_sym, "GBs": bs / ms_sym / 1e6, "GFLOPs": flops / ms_sym / 1e6},
-        "sym_atomic_S1": {"ms": ms_sym_atomic, "GBs": bs / ms_sym_atomic / 1e6},
-        "full_tuned": {"choice": cf, "ms": ms_full, "GBs": bf / ms_full / 1e6, "GFLOPs": flops / ms_full / 1e6},
+        "sym_tuned": {"choice": cu, "ms": ms_sym, "GBs": bs / ms_sym / 1e6, "GFLOPs": flops / ms_sym / 1e6,
+                      "fp64": fp(ops_sym, ms_sym)},
+        "sym_atomic_S1": {"ms": ms_sym_atomic, "GBs": bs / ms_sym_atomic / 1e6,
+                          "fp64": fp(ops_sym, ms_sym_atomic)},
+        "full_tuned": {"choice": cf, "ms": ms_full, "GBs": bf / ms_full / 1e6, "GFLOPs": flops / ms_full / 1e6,
+                       "fp64": fp(ops_full, ms_full)},
         "200_spmv_ms": {"sym": 200 * ms_sym, "full": 200 * ms_full},
+        "sym_speedup_vs_full": ms_full / ms_sym,
+        "fp64_peak_note": f"2 FMA lanes/clk/SM x {nsm} SMs x {mhz:.0f} MHz (sampled SM clock)",
     }
     # format-conversion AT (Sec. 5): a 27-point stencil (128^3, 56M nnz), where
     # the tuner converts to SELL-32-sigma; every general variant's throughput
@@ -599,19 +659,69 @@ def extras(xb, torch, dev, plan, A, x, y, args):
                      "lambda_max_err_vs_closed_form": float(abs(ev[0] - lam_top))}
     res["c2_arnoldi_convdiff_box_policies"] = pol
     del pc, CB
+    # FP64 roof of the block Gram-Schmidt pass kernel: one BCGS orthogonalisation
+    # of a vector against 32 basis rows at the 256^3 size (n = 16.8M) through the
+    # library's xb_orth; FMA lanes = n (2k + 1) (k dots, k updates, the norm)
+    ng = 256 ** 3
+    kk = 32
+    # random unit rows of length 16.8M are orthogonal to ~1/sqrt(n) = 2.4e-4:
+    # orthonormal enough for a timing
+    Vb = torch.randn(kk, ng, dtype=torch.float64, device=dev)
+    Vb /= Vb.norm(dim=1, keepdim=True)
+    w0 = torch.randn(ng, dtype=torch.float64, device=dev)
+    wk = torch.empty_like(w0)
+    ms_o = {}
+    for nm, code in (("bcgs", xb.ORTHO_BCGS), ("cgs", xb.ORTHO_CGS), ("mgs", xb.ORTHO_MGS)):
+        def one():
+            wk.copy_(w0)
+            plan.orth(Vb, wk, code)
+        for _ in range(2):
+            one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ec0, ec1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            one()
+        e1.record()
+        ec0.record()
+        for _ in range(reps):
+            wk.copy_(w0)
+        ec1.record()
+        torch.cuda.synchronize()
+        ms = (e0.elapsed_time(e1) - ec0.elapsed_time(ec1)) / reps
+        ops = ng * (2 * kk + 1)
+        ms_o[nm] = {"ms": ms, "fp64": fp(ops, ms)}
+    res["orth_fp64_roof_n16.8M_k32"] = ms_o
+    del Vb, w0, wk
     # config 1: 64x64 Poisson GMRES(30) to 1e-8, b = A*ones, x0 = 0
     P = gen.poisson2d(64)
     pp = xb.Plan.from_host(P, dev)
     bp_h = oracle.spmv(P, np.ones(P["n"]))
     bp = torch.tensor(bp_h, device=dev)
+    t_c1 = time.perf_counter()
     xo, io = oracle.gmres(P, bp_h, m=30, tol=1e-8)
-    for ce in (1, 8):
+    t_c1 = time.perf_counter() - t_c1
+    cpu = {"c1_gmres30": {"s": t_c1, "iters": io["iters"], "cores": 1,
+                          "kind": "plain oracle, run to convergence"}}
+    res["cpu_oracle"] = cpu
+    # the library's default path for a system this small is one persistent
+    # launch; small_n = 0 forces the multi-launch path (host checks every
+    # check_every Arnoldi steps)
+    for label, kw in (("c1_gmres30_persistent", {}),
+                      ("c1_gmres30_multilaunch_check1", dict(small_n=0, check_every=1)),
+                      ("c1_gmres30_multilaunch_check8", dict(small_n=0, check_every=8))):
         xs = torch.zeros(P["n"], dtype=torch.float64, device=dev)
+        pp.gmres(bp, xs, m=30, tol=1e-8, **kw)  # warm-up (workspace, module load)
+        xs.zero_()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info = pp.gmres(bp, xs, m=30, tol=1e-8, check_every=ce)
-        res[f"c1_gmres30_check{ce}"] = {"s": time.perf_counter() - t0, "iters": info["iters"],
-                                        "oracle_iters": io["iters"],
-                                        "res_true": info["res_true"], "status": info["status"]}
+        info = pp.gmres(bp, xs, m=30, tol=1e-8, **kw)
+        torch.cuda.synchronize()
+        res[label] = {"s": time.perf_counter() - t0, "iters": info["iters"],
+                      "oracle_iters": io["iters"], "persistent": info["persistent"],
+                      "res_true": info["res_true"], "status": info["status"]}
     xs = torch.zeros(P["n"], dtype=torch.float64, device=dev)
     info = pp.gmres(bp, xs, m=30, tol=1e-8, precision=xb.PREC_MIXED, check_every=8)
     res["c1_gmres30_mixed"] = {"iters_inner": info["inner_iters"], "outer": info["outer"],
@@ -619,14 +729,18 @@ def extras(xb, torch, dev, plan, A, x, y, args):
                                "err_vs_fp64_oracle": float(np.max(np.abs(xs.cpu().numpy() - xo)) /
                                                            np.max(np.abs(xo)))}
     if not args.no_solvers:
-        res.update(solvers(xb, torch, dev, plan, A, args))
-    if args.batch:
-        res["c5_batch"] = batch(xb, torch, dev, args)
+        res.update(solvers(xb, torch, dev, plan, A, args, cpu))
+    if not args.no_batch:
+        res["c5_batch"] = batch(xb, torch, dev, args, cpu)
     return res
 
 
-def solvers(xb, torch, dev, plan3, A3, args):
-    """Time to true ||b - A x|| / ||b|| <= 1e-8 (b = A*ones, x0 = 0)."""
+def solvers(xb, torch, dev, plan3, A3, args, cpu):
+    """Time to true ||b - A x|| / ||b|| <= 1e-8 (b = A*ones, x0 = 0); the CPU
+    oracle's time for the same solves (OpenMP build, all host cores) where it
+    finishes in seconds, else per-iteration times scaled to the GPU's
+    iteration counts (labelled extrapolated)."""
+    import oracle
     from paper_2405_01599_gb300 import gen, tuner
     out = {}
     # config 3: BiCGStab on the power-law matrix (tuned SpMV)
@@ -654,6 +768,23 @@ def solvers(xb, torch, dev, plan3, A3, args):
     out["c3_bicgstab_ilu0"] = {"s": time.perf_counter() - t0, "setup_s": t_ilu,
                                "iters": info["iters"], "res_true": info["res_true"],
                                "status": info["status"]}
+    # CPU oracle, BiCGStab on the same matrix: a bounded number of iterations
+    # of the OpenMP build, per-iteration time x the GPU's iteration count
+    b3h = oracle.spmv(A3, np.ones(n3), omp=True)
+    k, el = 2, 0.0
+    while True:
+        t0 = time.perf_counter()
+        _, ci = oracle.bicgstab(A3, b3h, tol=1e-30, maxiter=k, omp=True)
+        el = time.perf_counter() - t0
+        if el > 4.0 or k >= 256:
+            break
+        k *= 4
+    per_it = el / max(1, ci["iters"])
+    cpu["c3_bicgstab"] = {"per_iteration_s": per_it, "iterations_timed": ci["iters"],
+                          "s_extrapolated": per_it * out["c3_bicgstab"]["iters"],
+                          "gpu_iters": out["c3_bicgstab"]["iters"],
+                          "cores": oracle.lib_omp().orc_num_threads(),
+                          "kind": "extrapolated: OpenMP oracle per-iteration time x GPU iterations"}
     # config 4: 256^3 convection-diffusion, Peclet 10, upwind
     A = gen.convdiff3d(N=256, pe=10.0)
     n = A["n"]
@@ -670,11 +801,16 @@ def solvers(xb, torch, dev, plan3, A3, args):
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         err = float((x - ones).abs().max().item())
+        mixed = kw.get("precision") == xb.PREC_MIXED
+        timed = info["inner_iters"] + info["outer"] if mixed else info["spmv_calls"]
         out[label] = {"s": el, "status": info["status"], "iters": info["iters"] or info["inner_iters"],
-                      "outer": info["outer"], "res_true": info["res_true"],
+                      "outer": info["outer"], "inner_iters": info["inner_iters"],
+                      "fallback": info["fallback"], "fp64_iters_after_fallback": info["iters"] if mixed else None,
+                      "res_true": info["res_true"],
                       "err_vs_exact_solution": err, "spmv_calls": info["spmv_calls"],
                       "GBs_solve": info["bytes_alg"] / el / 1e9,
-                      "spmv_ms_avg": info["spmv_ms"] / max(1, info["spmv_calls"]),
+                      "spmv_ms_avg": info["spmv_ms"] / max(1, timed),
+                      "spmv_timed": "FP32 inner SpMVs" if mixed else "every SpMV",
                       "variant": xb.VARIANT_NAMES.get(info["variant_used"], "?"),
                       "ortho_used": ["mgs", "cgs", "dgks", "bcgs"][info["ortho_used"]],
                       "block": info["block_used"], "ipt": info["ipt_used"], **kw}
@@ -706,6 +842,29 @@ def solvers(xb, torch, dev, plan3, A3, args):
     t_ilu4 = time.perf_counter() - t0
     run("c4_exhaustive_fp64_m30_ilu0", p_ex, m=30, ortho=xb.ORTHO_AUTO, precond=xb.PRECOND_ILU0)
     out["c4_exhaustive_fp64_m30_ilu0"]["setup_s"] = t_ilu4
+    # ILU(0)-preconditioned BiCGStab (FP64): the fastest FP64 solve of this problem
+    b4 = torch.empty(n, dtype=torch.float64, device=dev)
+    p_ex.spmv(ones, b4)
+    x4 = torch.zeros(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = p_ex.bicgstab(b4, x4, tol=1e-8, maxtime_s=120.0, check_every=1,
+                         precond=xb.PRECOND_ILU0)
+    torch.cuda.synchronize()
+    out["c4_exhaustive_bicgstab_ilu0"] = {"s": time.perf_counter() - t0, "iters": info["iters"],
+                                          "res_true": info["res_true"], "status": info["status"],
+                                          "setup_s": t_ilu4}
+    # CPU oracle: one GMRES(30) cycle (30 Arnoldi steps with MGS) of the OpenMP
+    # build, x the cycles the untuned FP64 GPU solve needed
+    b4h = b4.cpu().numpy()
+    t0 = time.perf_counter()
+    _, c4i = oracle.gmres(A, b4h, m=30, tol=1e-30, maxiter=30, omp=True)
+    t_cyc = time.perf_counter() - t0
+    cyc = out["c4_plain_fp64_m30"]["iters"] / 30.0
+    cpu["c4_gmres30"] = {"cycle_s": t_cyc, "steps_timed": c4i["iters"], "gpu_cycles": cyc,
+                         "s_extrapolated": t_cyc * cyc, "cores": oracle.lib_omp().orc_num_threads(),
+                         "kind": "extrapolated: one OpenMP oracle GMRES(30) cycle x the GPU's cycles"}
+    del b4h
     # numerical computation policies (Sec. 2.3.2, 3.3) on the 128^3 problem: time,
     # memory and accuracy of each
     A2 = gen.convdiff3d(N=128, pe=10.0)
@@ -732,17 +891,34 @@ def solvers(xb, torch, dev, plan3, A3, args):
     out["c4_speedup_vs_plain_fp64"] = {k: base / out[k]["s"] for k in
                                        ("c4_exhaustive_fp64_m30", "c4_exhaustive_fp64_m30_policy",
                                         "c4_mlp_fp64", "c4_mlp_mixed")}
+    fp64_runs = ("c4_plain_fp64_m30", "c4_exhaustive_fp64_m30", "c4_exhaustive_fp64_m30_policy",
+                 "c4_mlp_fp64", "c4_exhaustive_fp64_m30_ilu0", "c4_exhaustive_bicgstab_ilu0")
+    ok64 = [k for k in fp64_runs if out[k]["status"] == 0]
+    fastest = min(ok64, key=lambda k: out[k]["s"]) if ok64 else None
+    mx = out["c4_mlp_mixed"]["s"]
+    out["c4_mixed_speedup"] = {
+        "vs_plain_fp64_untuned": base / mx,
+        "vs_exhaustive_fp64_mgs": out["c4_exhaustive_fp64_m30"]["s"] / mx,
+        "vs_exhaustive_fp64_policy": out["c4_exhaustive_fp64_m30_policy"]["s"] / mx,
+        "vs_mlp_fp64_same_m_and_ortho": out["c4_mlp_fp64"]["s"] / mx,
+        "vs_fastest_fp64": (out[fastest]["s"] / mx) if fastest else None,
+        "fastest_fp64": fastest,
+        "mixed_fallback": out["c4_mlp_mixed"]["fallback"]}
     return out
 
 
-def batch(xb, torch, dev, args):
+def batch(xb, torch, dev, args, cpu):
     """512 uneven systems in one persistent graph-captured launch: untuned
     default vs the exhaustive run-time tuner (each system's SpMV candidates
-    timed, Sec. 3.1; m fixed at 30) vs the learned tuner (SpMV choice and m)."""
+    timed, Sec. 3.1; m fixed at 30) vs the learned tuner (SpMV choice and m).
+    Throughput of a launch: algorithmic bytes and flops summed over the
+    systems' Arnoldi steps (one SpMV plus the MGS passes of the step at the
+    cycle's mean basis size) over the launch time."""
+    import oracle
     from paper_2405_01599_gb300 import gen, tuner
     specs = gen.batch_specs(512, seed=5)
     model = xb.Mlp.load(tuner.MODEL_PATH)
-    systems, plans = [], []
+    systems, plans, shapes = [], [], []
     t_ml = t_ex = 0.0
     mode_of = lambda v: 1 if v == xb.VAR_SEGSCAN else 0
     for sp in specs:
@@ -761,6 +937,7 @@ def batch(xb, torch, dev, args):
                             x=torch.zeros(n, dtype=torch.float64, device=dev),
                             m_ml=m, mode_ml=mode_of(ch["variant"]), mode_ex=mode_of(ce["variant"])))
         plans.append(pl)
+        shapes.append((n, A["nnz"]))
     # per-system cap: the power-law systems of this mix stagnate without a
     # preconditioner; the cap bounds their share of the launch
     opts = dict(tol=1e-8, maxiter=3000, maxtime_s=60.0)
@@ -778,26 +955,53 @@ def batch(xb, torch, dev, args):
         return e0.elapsed_time(e1), r
 
     N = len(systems)
+
+    def thru(r, t_ms):
+        by = fl = 0.0
+        for (n, nnz), q in zip(shapes, r):
+            jm = (q["m"] + 1) / 2.0  # mean basis size of a cycle's step
+            steps = q["iters"]
+            by += steps * ((12 * nnz + 4 * (n + 1) + 16 * n) + (4 * jm + 5) * 8 * n)
+            fl += steps * (2 * nnz + 4 * n * (jm + 1))
+        return {"GBs": by / (t_ms * 1e-3) / 1e9, "GFLOPs": fl / (t_ms * 1e-3) / 1e9,
+                "alg_GB": by / 1e9, "arnoldi_steps": int(sum(q["iters"] for q in r))}
+
     # MGS in every arm: inside the batched kernel (one SM per small system,
     # latency-bound) BCGS measured no faster than MGS
     t_def, r_def = run([30] * N, [0] * N)
     t_exh, r_exh = run([30] * N, [q["mode_ex"] for q in systems])
     t_mlp, r_mlp = run([q["m_ml"] for q in systems], [q["mode_ml"] for q in systems])
-    # the paper's full run-time AT: SpMV choice before execution plus the
-    # restart-frequency rule during it (m starts at 30, grows by 5 up to 128)
-    t_exr, r_exr = run([30] * N, [q["mode_ex"] for q in systems], dafrt=1, m_max=128,
-                       dafrt_theta=10.0)
-    # the learned choices as the starting point of the same rule
-    t_mlr, r_mlr = run([q["m_ml"] for q in systems], [q["mode_ml"] for q in systems], dafrt=1,
-                       m_max=128, dafrt_theta=10.0)
     ok = lambda r: int(sum(1 for q in r if q["status"] == 0))
     # systems every arm solved: their summed per-system device times compare the
     # tuners on work that finished (systems that hit the cap all ran 3000 steps)
     both = [k for k in range(N) if r_def[k]["status"] == 0 and r_exh[k]["status"] == 0
             and r_mlp[k]["status"] == 0]
     cs = lambda r: float(sum(r[k]["ms"] for k in both))
-    return {"systems": N, "sum_n": int(sum(q["b"].numel() for q in systems)),
+    # CPU oracle on a seeded sample of the same systems (one core, GMRES(30),
+    # the same 3000-step cap), scaled by the summed row counts to all 512
+    rng = np.random.default_rng(55)
+    order = rng.permutation(N)
+    t_cpu, n_cpu, solved, done = 0.0, 0, 0, []
+    for k in order:
+        if t_cpu > 15.0:
+            break
+        A = gen.from_spec(specs[k])
+        bh = oracle.spmv(A, np.ones(A["n"]))
+        t0 = time.perf_counter()
+        _, oi = oracle.gmres(A, bh, m=30, tol=1e-8, maxiter=3000)
+        t_cpu += time.perf_counter() - t0
+        n_cpu += A["n"]
+        solved += oi["status"] == 0
+        done.append(int(k))
+    sum_n = int(sum(q["b"].numel() for q in systems))
+    cpu["c5_batch"] = {"systems_timed": len(done), "s_timed": t_cpu, "converged_timed": int(solved),
+                       "s_extrapolated": t_cpu * sum_n / max(n_cpu, 1), "cores": 1,
+                       "kind": "extrapolated: plain oracle GMRES(30) on a seeded sample, "
+                               "scaled by summed rows to all 512 systems"}
+    res = {"systems": N, "sum_n": sum_n,
             "launch_ms": {"default": t_def, "exhaustive": t_exh, "learned": t_mlp},
+            "throughput": {"default": thru(r_def, t_def), "exhaustive": thru(r_exh, t_exh),
+                           "learned": thru(r_mlp, t_mlp)},
             "learned_tune_s": t_ml, "exhaustive_tune_s": t_ex,
             "converged": {"default": ok(r_def), "exhaustive": ok(r_exh), "learned": ok(r_mlp)},
             "solved_by_all": len(both),
@@ -808,11 +1012,20 @@ def batch(xb, torch, dev, args):
             "launch_speedup_learned": {"vs_default": t_def / t_mlp, "vs_exhaustive": t_exh / t_mlp},
             "max_system_ms": {"default": max(q["ms"] for q in r_def),
                               "exhaustive": max(q["ms"] for q in r_exh),
-                              "learned": max(q["ms"] for q in r_mlp)},
-            "exhaustive_with_restart_rule": {"launch_ms": t_exr, "converged": ok(r_exr),
-                                             "solved_by_all_sum_ms": cs(r_exr)},
-            "learned_with_restart_rule": {"launch_ms": t_mlr, "converged": ok(r_mlr),
-                                          "solved_by_all_sum_ms": cs(r_mlr)}}
+                              "learned": max(q["ms"] for q in r_mlp)}}
+    if args.batch_rule_arms:
+        # the paper's full run-time AT: SpMV choice before execution plus the
+        # restart-frequency rule during it (m starts at 30, grows by 5 up to 128),
+        # and the learned choices as the starting point of the same rule
+        t_exr, r_exr = run([30] * N, [q["mode_ex"] for q in systems], dafrt=1, m_max=128,
+                           dafrt_theta=10.0)
+        t_mlr, r_mlr = run([q["m_ml"] for q in systems], [q["mode_ml"] for q in systems],
+                           dafrt=1, m_max=128, dafrt_theta=10.0)
+        res["exhaustive_with_restart_rule"] = {"launch_ms": t_exr, "converged": ok(r_exr),
+                                               "solved_by_all_sum_ms": cs(r_exr)}
+        res["learned_with_restart_rule"] = {"launch_ms": t_mlr, "converged": ok(r_mlr),
+                                            "solved_by_all_sum_ms": cs(r_mlr)}
+    return res
 
 
 if __name__ == "__main__":
