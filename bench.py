@@ -601,6 +601,35 @@ def extras(xb, torch, dev, plan, A, x, y, args):
         del p27, S27, x27, y27
     except xb.XbError as e:
         res["stencil27_128_spmv"] = {"error": str(e)}
+    # format-conversion AT with blocks: a 3D 7-point grid with 3 unknowns per
+    # node and dense 3 x 3 coupling blocks (elasticity-like; 80^3 nodes, n =
+    # 1.5M, 32M non-zeros), where the tuner may convert to BCSR
+    try:
+        B3 = gen.block_stencil3d(80, 3)
+        pb = xb.Plan.from_host(B3, dev)
+        cb = pb.tune()
+        xb3 = torch.ones(B3["n"], dtype=torch.float64, device=dev)
+        yb3 = torch.empty_like(xb3)
+        bb = alg_bytes(B3)
+        tb = {}
+        for lab, (v, b, i) in {"row": (xb.VAR_ROW, 128, 1), "nnz": (xb.VAR_NNZ, 128, 8),
+                               "segscan": (xb.VAR_SEGSCAN, 128, 8), "sell_s32": (xb.VAR_SELL, 128, 1),
+                               "bcsr_2x2": (xb.VAR_BCSR, 128, 2), "bcsr_3x3": (xb.VAR_BCSR, 128, 3),
+                               "bcsr_4x4": (xb.VAR_BCSR, 128, 4)}.items():
+            try:
+                ms = _time_spmv(torch, lambda: pb.spmv(xb3, yb3, variant=v, block=b, ipt=i), 50)
+                tb[lab] = {"ms": ms, "GBs_crs_bytes": bb / ms / 1e6}
+            except xb.XbError as e:
+                tb[lab] = {"rejected": str(e)}
+        res["block3d_dof3_80_spmv"] = {
+            "n": B3["n"], "nnz": B3["nnz"],
+            "tuned": {"variant": xb.VARIANT_NAMES[cb["variant"]], "block": cb["block"], "ipt": cb["ipt"]},
+            "variants": tb,
+            "note": "GB/s over the CRS algorithmic bytes (12 B per non-zero); a 3x3 BCSR copy reads "
+                    "8 B per non-zero plus one column index per 9"}
+        del pb, B3, xb3, yb3
+    except xb.XbError as e:
+        res["block3d_dof3_80_spmv"] = {"error": str(e)}
     # restarted Lanczos (OpenATI_EIGENSOLVE): the 10 largest eigenvalues of the
     # 128^3 Laplacian (upper storage), as the paper asks for 10 eigenpairs
     torch.cuda.synchronize()

@@ -225,17 +225,50 @@ void xb_options_default(xb_options *opt);
 const char *xb_last_error(void);
 
 /* Build a plan for A (the paper's *_Setup functions, Table 1): validates
- * sizes, copies rowptr to the host once, and builds on the device the
- * row-aligned nnz-balanced tile partition (U2/S2), the flat segment
- * partition with per-CTA start rows (U3) and, for sym_upper, the per-tile
- * non-zero region bounds (S3).  opt may be NULL (defaults).  The plan keeps
- * A's pointers: A's arrays must outlive the plan and stay unmodified.
+ * sizes, copies rowptr to the host once, picks the default SpMV variant and
+ * allocates the reduction scratch.  Each variant's plan data (tile
+ * partitions, the segmented scan's row-end bitmask, warp start rows and data
+ * format copy, the S3 granule lists, the SELL and BCSR copies) is built on the
+ * variant's first use.  opt may be NULL (defaults).  The plan keeps A's
+ * pointers: A's arrays must outlive the plan and stay unmodified.
  * XB_EINVAL: n < 0, nnz < 0, NULL arrays with n > 0, rowptr[0] != 0,
- * rowptr[n] != nnz or rowptr decreasing.  Columns are checked
- * (0 <= col < n, ascending, and col >= row when sym_upper) only when the
- * environment variable XB_VALIDATE=1 is set. */
+ * rowptr[n] != nnz or rowptr decreasing, n or nnz >= 2^31 - 64 (use
+ * xb_plan_create64).  Columns are checked (0 <= col < n, ascending, and
+ * col >= row when sym_upper) only when the environment variable
+ * XB_VALIDATE=1 is set. */
 int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out);
 int xb_plan_destroy(xb_plan *plan);
+
+/* A in CRS with 64-bit row offsets (nnz up to 2^62; n, the columns and every
+ * row's length stay below 2^31 - 64).  Same rules as xb_csr otherwise. */
+typedef struct xb_csr64 {
+    int32_t n;
+    int64_t nnz;
+    const int64_t *rowptr;   /* device, n+1                                    */
+    const int32_t *col;      /* device, nnz                                    */
+    const double *val;       /* device, nnz                                    */
+    int32_t sym_upper;
+} xb_csr64;
+/* Plan for A with 64-bit row offsets.  When nnz < 2^31 - 64 the plan narrows
+ * rowptr to an int32 copy it owns and is an ordinary plan.  Larger matrices
+ * (general storage only) are cut into consecutive row blocks of at most
+ * 2^31 - 64 non-zeros each (xb_split_rows64; the environment variable
+ * XB_PLAN_SPLIT_NNZ lowers the block limit, for testing); each block is
+ * planned with int32 offsets into A's col/val from the block's first entry,
+ * and every SpMV runs the chosen variant block by block on the whole x.  Such
+ * a plan supports the general SpMV variants (ROW, NNZ, SEGSCAN, SELL, BCSR),
+ * the tuner and the FP64 / mixed-precision GMRES and BiCGStab solvers; ILU(0)
+ * and the symmetric storage return XB_EINVAL.  Errors as xb_plan_create, plus
+ * XB_EINVAL for a row longer than the block limit. */
+int xb_plan_create64(const xb_csr64 *A, const xb_options *opt, void *stream, xb_plan **out);
+/* The row blocks xb_plan_create64 cuts (host logic, no device work; exposed
+ * for testing): consecutive rows, each block at most max_nnz non-zeros,
+ * greedily as many rows as fit.  HOST rowptr (n + 1 int64); starts receives
+ * the first row of each block and then n (capacity cap entries); *nblocks the
+ * block count (always set).  XB_EINVAL when a row alone has more than max_nnz
+ * non-zeros, max_nnz < 1 or rowptr is not non-decreasing from 0. */
+int xb_split_rows64(int32_t n, const int64_t *rowptr, int64_t max_nnz, int32_t *starts,
+                    int32_t cap, int32_t *nblocks);
 
 /* Set the SpMV variant and launch shape used by XB_VAR_AUTO calls and by the
  * solvers.  block in {64,128,256,512}; ipt in [1,32].  XB_EINVAL for a
@@ -379,7 +412,7 @@ int xb_spmv_f32(xb_plan *plan, int32_t variant, float alpha, const float *x, flo
  * MGS or BCGS, m (and m_max with the restart rule, whose window and
  * increment must then be the default 5) <= XB_BATCH_MAX_M,
  * fault_check on -- run the same GMRES(m) as one persistent launch of the
- * batched kernel (one CTA solves the system), because each Arnoldi step of
+ * batched kernel (one 8-CTA cluster solves the system), because each Arnoldi step of
  * the multi-launch path is bound by launch and synchronisation latency at
  * that size; xb_info.persistent = 1 then, spmv_ms and res_implicit are 0. */
 int gmres_solve(xb_plan *plan, const double *b, double *x, const xb_options *opt,

@@ -42,6 +42,11 @@ class Csr(C.Structure):
                 ("col", C.c_void_p), ("val", C.c_void_p), ("sym_upper", C.c_int32)]
 
 
+class Csr64(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("sym_upper", C.c_int32)]
+
+
 class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int32), ("maxtime_s", C.c_double),
                 ("m", C.c_int32), ("m_max", C.c_int32), ("dafrt", C.c_int32),
@@ -107,6 +112,8 @@ def lib():
         "xb_last_error": (C.c_char_p, []),
         "xb_plan_create": (i32, [P(Csr), P(Options), vp, P(vp)]),
         "xb_plan_destroy": (i32, [vp]),
+        "xb_plan_create64": (i32, [P(Csr64), P(Options), vp, P(vp)]),
+        "xb_split_rows64": (i32, [i32, P(C.c_int64), C.c_int64, P(i32), i32, P(i32)]),
         "xb_plan_set_choice": (i32, [vp, i32, i32, i32]),
         "xb_plan_get_choice": (i32, [vp, P(Choice)]),
         "spmv_crs": (i32, [vp, f64, vp, f64, vp, vp]),
@@ -248,6 +255,19 @@ def u2_layout(rowptr, ipt):
     return tiles[:4 * nt.value].reshape(-1, 4), longs[:nl.value]
 
 
+def split_rows64(rowptr, max_nnz):
+    """The row blocks of a 64-bit row pointer that xb_plan_create64 plans
+    separately (host logic): the first row of each block, then n."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    n = rp.size - 1
+    nb = C.c_int32()
+    st = np.zeros(n + 2, np.int32)
+    _check(lib().xb_split_rows64(n, rp.ctypes.data_as(C.POINTER(C.c_int64)), int(max_nnz),
+                                 st.ctypes.data_as(C.POINTER(C.c_int32)), n + 2, C.byref(nb)))
+    return st[:nb.value + 1]
+
+
 def bcsr_layout(rowptr, col, r):
     """The block-CRS structure the BCSR variant builds for r x r blocks:
     (bptr, bcol) as numpy arrays (host logic)."""
@@ -306,17 +326,24 @@ class Plan:
     """A matrix in CRS on the device plus the library's setup data."""
 
     def __init__(self, rowptr, col, val, sym_upper=False, stream=None):
+        """rowptr int32 (xb_plan_create) or int64 (xb_plan_create64: 64-bit row
+        offsets, split into row blocks beyond 2^31 - 64 non-zeros)."""
         import torch
-        _need(rowptr, torch.int32, "rowptr")
+        wide = rowptr.dtype == torch.int64
+        _need(rowptr, torch.int64 if wide else torch.int32, "rowptr")
         _need(col, torch.int32, "col")
         _need(val, torch.float64, "val")
         self.n = rowptr.numel() - 1
         self.nnz = col.numel()
         self.sym_upper = bool(sym_upper)
         self._keep = (rowptr, col, val)
-        self._csr = Csr(self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val), int(sym_upper))
         h = C.c_void_p()
-        _check(lib().xb_plan_create(C.byref(self._csr), None, _stream(stream), C.byref(h)))
+        if wide:
+            self._csr = Csr64(self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val), int(sym_upper))
+            _check(lib().xb_plan_create64(C.byref(self._csr), None, _stream(stream), C.byref(h)))
+        else:
+            self._csr = Csr(self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val), int(sym_upper))
+            _check(lib().xb_plan_create(C.byref(self._csr), None, _stream(stream), C.byref(h)))
         self._h = h
 
     @classmethod

@@ -193,6 +193,14 @@ struct IluData {
 
 struct xb_plan {
     int n = 0, nnz = 0, sym = 0;
+    int ncols = 0;                       // columns (= n but for the row blocks of a split plan)
+    int64_t nnz64 = 0;                   // non-zeros (nnz saturates in a split plan)
+    int *d_rp32_own = nullptr;           // int32 row offsets the plan narrowed from 64-bit ones
+    struct Sub {
+        int r0;
+        xb_plan *plan;
+    };
+    std::vector<Sub> subs;               // row blocks of a plan with more than 2^31 - 64 non-zeros
     const int *rowptr = nullptr, *col = nullptr;
     const double *val = nullptr;
     float *val32 = nullptr;              // FP32 copy (mixed precision)
@@ -279,6 +287,10 @@ double ilu_apply_bytes(const xb_plan *p);
 int ilu_check(xb_plan *p);  // XB_ETIMEOUT if a substitution's barrier wait ran out
 void ilu_free(xb_plan *p);
 bool variant_fits(const xb_plan *p, int variant);
+// Consecutive row blocks of a 64-bit row pointer, each holding at most
+// max_nnz non-zeros (rows never split): starts[b] = first row of block b,
+// plus n at the end.  XB_EINVAL when one row alone has more than max_nnz.
+int split_rows64(int n, const int64_t *rp, int64_t max_nnz, std::vector<int> &starts);
 
 // SpMV dispatch: y = alpha*A*x + beta*y in value type double or float.
 int spmv_launch(xb_plan *p, int variant, int block, int ipt, double alpha, const double *x,

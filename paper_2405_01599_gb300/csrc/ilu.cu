@@ -455,6 +455,8 @@ int ilu_levels(int n, const int *rp, const int *ci, std::vector<int> &dpos, std:
 }
 
 int ensure_ilu(xb_plan *p, cudaStream_t s) {
+    if (!p->subs.empty())
+        return set_error(XB_EINVAL, "ILU(0): not available for a plan split into row blocks");
     IluData &u = p->ilu;
     if (u.built) return u.status == XB_OK ? XB_OK : set_error(u.status, "ILU(0): zero pivot");
     if (p->sym) return set_error(XB_EINVAL, "ILU(0) needs full (general) CRS storage");

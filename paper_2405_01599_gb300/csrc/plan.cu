@@ -513,6 +513,7 @@ const BssCopy *get_bss_copy(xb_plan *p, int ipt, bool f32, cudaStream_t s, int *
 }
 
 void bss_trim(xb_plan *p, int keep_ipt) {
+    for (auto &sb : p->subs) bss_trim(sb.plan, keep_ipt);
     auto &v = p->bss.copies;
     bool any = false;
     for (auto &t : v)
@@ -571,7 +572,8 @@ __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restr
 }
 
 int ensure_val32(xb_plan *p, cudaStream_t s) {
-    if (p->val32 || p->nnz == 0) return XB_OK;
+    for (auto &sb : p->subs) XB_TRY(ensure_val32(sb.plan, s));  // a split plan's blocks
+    if (!p->subs.empty() || p->val32 || p->nnz == 0) return XB_OK;
     XB_CUDA(cudaMalloc(&p->val32, (size_t)p->nnz * sizeof(float)));
     k_to_f32<<<num_sms() * 8, 256, 0, s>>>(p->nnz, p->val, p->val32);
     XB_LAUNCHED("k_to_f32");
@@ -787,6 +789,104 @@ __global__ void k_feat_sym(int n, const int *__restrict__ rowptr, const int *__r
 
 using namespace xb;
 
+namespace xb {
+// Reduction scratch, pinned host mirror and timing events of a plan.
+int plan_scratch(xb_plan *p, cudaStream_t s) {
+    cudaError_t e = cudaMalloc(&p->d_part, (size_t)kRedSlots * kRedValues * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ticket, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_scal, (size_t)kScalars * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ticket, 0, 64 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_scal, 0, (size_t)kScalars * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->h_pin, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[1]);
+    return e == cudaSuccess ? XB_OK : cuda_error(e, "plan_create: scratch");
+}
+
+// A plan over A whose columns index an x of ncols entries (ncols = n except
+// for the row blocks of a split plan).
+int plan_create_impl(const xb_csr *A, int ncols, cudaStream_t s, xb_plan **out) {
+    const int n = A->n, nnz = A->nnz;
+    if (n < 0 || nnz < 0 || n > INT_MAX - 64 || nnz > INT_MAX - 64)
+        return set_error(XB_EINVAL, "plan_create: n=%d nnz=%d (int32 indices, < 2^31 - 64)", n,
+                         nnz);
+    if (n > 0 && (!A->rowptr || (nnz > 0 && (!A->col || !A->val))))
+        return set_error(XB_EINVAL, "plan_create: NULL CRS array");
+    xb_plan *p = new (std::nothrow) xb_plan();
+    if (!p) return set_error(XB_ENOMEM, "plan_create: host allocation");
+    p->n = n;
+    p->nnz = nnz;
+    p->ncols = ncols;
+    p->nnz64 = nnz;
+    p->sym = A->sym_upper ? 1 : 0;
+    p->rowptr = A->rowptr;
+    p->col = A->col;
+    p->val = A->val;
+    auto fail = [&](int code) {
+        xb_plan_destroy(p);
+        return code;
+    };
+    p->h_rowptr.resize((size_t)n + 1, 0);
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(p->h_rowptr.data(), A->rowptr, ((size_t)n + 1) * sizeof(int),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: read rowptr"));
+    }
+    const int *rp = p->h_rowptr.data();
+    if (rp[0] != 0 || rp[n] != nnz)
+        return fail(set_error(XB_EINVAL, "plan_create: rowptr[0]=%d rowptr[n]=%d nnz=%d", rp[0],
+                              rp[n], nnz));
+    std::vector<int> empty;
+    for (int i = 0; i < n; i++) {
+        const int L = rp[i + 1] - rp[i];
+        if (L < 0) return fail(set_error(XB_EINVAL, "plan_create: rowptr decreases at row %d", i));
+        p->max_row = std::max(p->max_row, L);
+        if (L == 0) empty.push_back(i);
+    }
+    const char *val_env = std::getenv("XB_VALIDATE");
+    if (val_env && val_env[0] == '1' && nnz > 0) {
+        std::vector<int> hc(nnz);
+        cudaError_t e = cudaMemcpy(hc.data(), A->col, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: read col"));
+        for (int i = 0; i < n; i++)
+            for (int k = rp[i]; k < rp[i + 1]; k++) {
+                const int c = hc[k];
+                if (c < 0 || c >= ncols || (k > rp[i] && c <= hc[k - 1]) || (p->sym && c < i))
+                    return fail(set_error(XB_EINVAL, "plan_create: bad column %d at row %d (k=%d)",
+                                          c, i, k));
+            }
+    }
+    p->n_empty = (int)empty.size();
+    if (p->n_empty) {
+        cudaError_t e = cudaMalloc(&p->d_empty, empty.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_empty, empty.data(), empty.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: empty rows"));
+    }
+    {
+        const int r = plan_scratch(p, s);
+        if (r != XB_OK) return fail(r);
+    }
+    // default choice (Sec. 3.3.1 STABLE policy: no tuning): power-law rows go to
+    // the segmented scan, everything else to the nnz-balanced tiles.
+    if (p->sym) {
+        p->variant = XB_VAR_SYM_TILE;
+    } else {
+        const double mean = n > 0 ? (double)nnz / n : 0.0;
+        p->variant = (p->max_row > 64 && p->max_row > 16.0 * mean) ? XB_VAR_SEGSCAN : XB_VAR_NNZ;
+    }
+    p->block = 256;
+    p->ipt = 8;
+    p->vec_ok = ((uintptr_t)A->val % 16 == 0) && ((uintptr_t)A->col % 16 == 0);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_error(e, "plan_create"));
+    *out = p;
+    return XB_OK;
+}
+
+}  // namespace xb
+
 extern "C" {
 
 const char *xb_last_error(void) { return g_err.c_str(); }
@@ -822,96 +922,20 @@ void xb_options_default(xb_options *o) {
     if (const char *e = std::getenv("XB_SMALL_N")) o->small_n = std::max(0, std::atoi(e));
 }
 
+
 int xb_plan_create(const xb_csr *A, const xb_options *opt, void *stream, xb_plan **out) {
     (void)opt;
     if (!A || !out) return set_error(XB_EINVAL, "plan_create: NULL argument");
     *out = nullptr;
-    const int n = A->n, nnz = A->nnz;
-    if (n < 0 || nnz < 0 || n > INT_MAX - 64 || nnz > INT_MAX - 64)
-        return set_error(XB_EINVAL, "plan_create: n=%d nnz=%d (int32 indices, < 2^31 - 64)", n,
-                         nnz);
-    if (n > 0 && (!A->rowptr || (nnz > 0 && (!A->col || !A->val))))
-        return set_error(XB_EINVAL, "plan_create: NULL CRS array");
-    cudaStream_t s = (cudaStream_t)stream;
-    xb_plan *p = new (std::nothrow) xb_plan();
-    if (!p) return set_error(XB_ENOMEM, "plan_create: host allocation");
-    p->n = n;
-    p->nnz = nnz;
-    p->sym = A->sym_upper ? 1 : 0;
-    p->rowptr = A->rowptr;
-    p->col = A->col;
-    p->val = A->val;
-    auto fail = [&](int code) {
-        xb_plan_destroy(p);
-        return code;
-    };
-    p->h_rowptr.resize((size_t)n + 1, 0);
-    if (n > 0) {
-        cudaError_t e = cudaMemcpyAsync(p->h_rowptr.data(), A->rowptr, ((size_t)n + 1) * sizeof(int),
-                                        cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: read rowptr"));
-    }
-    const int *rp = p->h_rowptr.data();
-    if (rp[0] != 0 || rp[n] != nnz)
-        return fail(set_error(XB_EINVAL, "plan_create: rowptr[0]=%d rowptr[n]=%d nnz=%d", rp[0],
-                              rp[n], nnz));
-    std::vector<int> empty;
-    for (int i = 0; i < n; i++) {
-        const int L = rp[i + 1] - rp[i];
-        if (L < 0) return fail(set_error(XB_EINVAL, "plan_create: rowptr decreases at row %d", i));
-        p->max_row = std::max(p->max_row, L);
-        if (L == 0) empty.push_back(i);
-    }
-    const char *val_env = std::getenv("XB_VALIDATE");
-    if (val_env && val_env[0] == '1' && nnz > 0) {
-        std::vector<int> hc(nnz);
-        cudaError_t e = cudaMemcpy(hc.data(), A->col, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: read col"));
-        for (int i = 0; i < n; i++)
-            for (int k = rp[i]; k < rp[i + 1]; k++) {
-                const int c = hc[k];
-                if (c < 0 || c >= n || (k > rp[i] && c <= hc[k - 1]) || (p->sym && c < i))
-                    return fail(set_error(XB_EINVAL, "plan_create: bad column %d at row %d (k=%d)",
-                                          c, i, k));
-            }
-    }
-    p->n_empty = (int)empty.size();
-    if (p->n_empty) {
-        cudaError_t e = cudaMalloc(&p->d_empty, empty.size() * sizeof(int));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_empty, empty.data(), empty.size() * sizeof(int), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: empty rows"));
-    }
-    cudaError_t e = cudaMalloc(&p->d_part, (size_t)kRedSlots * kRedValues * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_ticket, 64 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_scal, (size_t)kScalars * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ticket, 0, 64 * sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_scal, 0, (size_t)kScalars * sizeof(double), s);
-    if (e == cudaSuccess) e = cudaMallocHost(&p->h_pin, 64 * sizeof(double));
-    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[0]);
-    if (e == cudaSuccess) e = cudaEventCreate(&p->ev[1]);
-    if (e != cudaSuccess) return fail(cuda_error(e, "plan_create: scratch"));
-    // default choice (Sec. 3.3.1 STABLE policy: no tuning): power-law rows go to
-    // the segmented scan, everything else to the nnz-balanced tiles.
-    if (p->sym) {
-        p->variant = XB_VAR_SYM_TILE;
-    } else {
-        const double mean = n > 0 ? (double)nnz / n : 0.0;
-        p->variant = (p->max_row > 64 && p->max_row > 16.0 * mean) ? XB_VAR_SEGSCAN : XB_VAR_NNZ;
-    }
-    p->block = 256;
-    p->ipt = 8;
-    p->vec_ok = ((uintptr_t)A->val % 16 == 0) && ((uintptr_t)A->col % 16 == 0);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(cuda_error(e, "plan_create"));
-    *out = p;
-    return XB_OK;
+    return xb::plan_create_impl(A, A->n, (cudaStream_t)stream, out);
 }
+
 
 int xb_plan_destroy(xb_plan *p) {
     if (!p) return XB_OK;
     cudaDeviceSynchronize();
+    for (auto &sb : p->subs) xb_plan_destroy(sb.plan);
+    cudaFree(p->d_rp32_own);
     for (auto &t : p->tiles) cudaFree(t.d_row);
     for (auto &t : p->u2) {
         cudaFree(t.d_tile);
@@ -1072,5 +1096,144 @@ extern "C" int xb_bcsr_layout(int32_t n, const int32_t *rowptr, const int32_t *c
     *nblocks = xb::bcsr_layout(n, rowptr, col, r, bp, bc);
     if (bptr) std::copy(bp.begin(), bp.end(), bptr);
     for (int64_t i = 0; i < *nblocks && i < cap; i++) bcol[i] = bc[i];
+    return XB_OK;
+}
+
+namespace xb {
+
+int split_rows64(int n, const int64_t *rp, int64_t max_nnz, std::vector<int> &starts) {
+    starts.clear();
+    if (max_nnz < 1) return set_error(XB_EINVAL, "split_rows64: max_nnz %lld", (long long)max_nnz);
+    if (n > 0 && rp[0] != 0) return set_error(XB_EINVAL, "split_rows64: rowptr[0] = %lld", (long long)rp[0]);
+    int r = 0;
+    while (r < n) {
+        if (rp[r + 1] < rp[r])
+            return set_error(XB_EINVAL, "split_rows64: rowptr decreases at row %d", r);
+        if (rp[r + 1] - rp[r] > max_nnz)
+            return set_error(XB_EINVAL, "split_rows64: row %d holds %lld non-zeros (> %lld)", r,
+                             (long long)(rp[r + 1] - rp[r]), (long long)max_nnz);
+        starts.push_back(r);
+        int rb = r + 1;
+        while (rb < n && rp[rb + 1] >= rp[rb] && rp[rb + 1] - rp[r] <= max_nnz) rb++;
+        r = rb;
+    }
+    starts.push_back(n);
+    return XB_OK;
+}
+
+// rp32[i] = rp64[i] - base, i < count
+__global__ void k_rp_narrow(int64_t count, const int64_t *__restrict__ rp64, int64_t base,
+                            int *__restrict__ rp32) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) rp32[i] = (int)(rp64[i] - base);
+}
+
+}  // namespace xb
+
+extern "C" int xb_split_rows64(int32_t n, const int64_t *rowptr, int64_t max_nnz, int32_t *starts,
+                               int32_t cap, int32_t *nblocks) {
+    if (n < 0 || !rowptr || !nblocks || cap < 0 || (cap > 0 && !starts))
+        return xb::set_error(XB_EINVAL, "split_rows64: bad argument");
+    std::vector<int> st;
+    XB_TRY(xb::split_rows64(n, rowptr, max_nnz, st));
+    *nblocks = (int32_t)st.size() - 1;
+    for (int i = 0; i < (int)st.size() && i < cap; i++) starts[i] = st[i];
+    return XB_OK;
+}
+
+extern "C" int xb_plan_create64(const xb_csr64 *A, const xb_options *opt, void *stream,
+                                xb_plan **out) {
+    (void)opt;
+    if (!A || !out) return xb::set_error(XB_EINVAL, "plan_create64: NULL argument");
+    *out = nullptr;
+    const int n = A->n;
+    const int64_t nnz = A->nnz;
+    if (n < 0 || nnz < 0 || n > INT_MAX - 64)
+        return xb::set_error(XB_EINVAL, "plan_create64: n=%d nnz=%lld", n, (long long)nnz);
+    if (n > 0 && (!A->rowptr || (nnz > 0 && (!A->col || !A->val))))
+        return xb::set_error(XB_EINVAL, "plan_create64: NULL CRS array");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> rp((size_t)n + 1, 0);
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(rp.data(), A->rowptr, ((size_t)n + 1) * sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return xb::cuda_error(e, "plan_create64: read rowptr");
+    }
+    if (rp[0] != 0 || rp[n] != nnz)
+        return xb::set_error(XB_EINVAL, "plan_create64: rowptr[0]=%lld rowptr[n]=%lld nnz=%lld",
+                             (long long)rp[0], (long long)rp[n], (long long)nnz);
+    int64_t limit = INT_MAX - 64;
+    if (const char *e = std::getenv("XB_PLAN_SPLIT_NNZ")) limit = std::max(1LL, std::atoll(e));
+    std::vector<int> starts;
+    XB_TRY(xb::split_rows64(n, rp.data(), std::min<int64_t>(limit, INT_MAX - 64), starts));
+    // one row block (or none): an ordinary plan on an int32 copy of rowptr
+    auto narrow = [&](int r0, int r1, int **d32) -> int {
+        const int64_t cnt = (int64_t)(r1 - r0) + 1;
+        cudaError_t e = cudaMalloc(d32, cnt * sizeof(int));
+        if (e == cudaSuccess) {
+            xb::k_rp_narrow<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, A->rowptr + r0, rp[r0],
+                                                                         *d32);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(*d32);
+            *d32 = nullptr;
+            return xb::cuda_error(e, "plan_create64: narrow rowptr");
+        }
+        return XB_OK;
+    };
+    if (starts.size() <= 2) {
+        int *d32 = nullptr;
+        XB_TRY(narrow(0, n, &d32));
+        xb_csr c{n, (int32_t)nnz, d32, A->col, A->val, A->sym_upper};
+        const int r = xb::plan_create_impl(&c, n, s, out);
+        if (r != XB_OK) {
+            cudaFree(d32);
+            return r;
+        }
+        (*out)->d_rp32_own = d32;
+        return XB_OK;
+    }
+    if (A->sym_upper)
+        return xb::set_error(XB_EINVAL, "plan_create64: symmetric storage beyond 2^31 - 64 non-zeros");
+    xb_plan *p = new (std::nothrow) xb_plan();
+    if (!p) return xb::set_error(XB_ENOMEM, "plan_create64: host allocation");
+    auto fail = [&](int code) {
+        xb_plan_destroy(p);
+        return code;
+    };
+    p->n = n;
+    p->ncols = n;
+    p->nnz64 = nnz;
+    p->nnz = INT_MAX - 64;  // saturated; nnz64 holds the count
+    {
+        const int r = xb::plan_scratch(p, s);
+        if (r != XB_OK) return fail(r);
+    }
+    for (size_t b = 0; b + 1 < starts.size(); b++) {
+        const int r0 = starts[b], r1 = starts[b + 1];
+        int *d32 = nullptr;
+        {
+            const int r = narrow(r0, r1, &d32);
+            if (r != XB_OK) return fail(r);
+        }
+        xb_csr c{r1 - r0, (int32_t)(rp[r1] - rp[r0]), d32, A->col + rp[r0], A->val + rp[r0], 0};
+        xb_plan *q = nullptr;
+        const int r = xb::plan_create_impl(&c, n, s, &q);
+        if (r != XB_OK) {
+            cudaFree(d32);
+            return fail(r);
+        }
+        q->d_rp32_own = d32;
+        p->subs.push_back({r0, q});
+        p->max_row = std::max(p->max_row, q->max_row);
+        p->n_empty += q->n_empty;
+    }
+    p->variant = p->subs[0].plan->variant;
+    p->block = p->subs[0].plan->block;
+    p->ipt = p->subs[0].plan->ipt;
+    *out = p;
     return XB_OK;
 }

@@ -533,8 +533,9 @@ int check_args(xb_plan *p, const double *b, double *x, const xb_options &o) {
         return xb::set_error(XB_EINVAL, "solve: unknown orthogonalisation %d", o.ortho);
     if (o.precond != XB_PRECOND_NONE && o.precond != XB_PRECOND_ILU0)
         return xb::set_error(XB_EINVAL, "solve: unknown preconditioner %d", o.precond);
-    if (o.precond == XB_PRECOND_ILU0 && (p->sym || o.precision != XB_PREC_FP64))
-        return xb::set_error(XB_EINVAL, "solve: ILU(0) needs general CRS and FP64 precision");
+    if (o.precond == XB_PRECOND_ILU0 && (p->sym || o.precision != XB_PREC_FP64 || !p->subs.empty()))
+        return xb::set_error(XB_EINVAL, "solve: ILU(0) needs general CRS (below 2^31 - 64 "
+                                        "non-zeros) and FP64 precision");
     return XB_OK;
 }
 
@@ -584,6 +585,7 @@ namespace xb {
 // Device bytes of the plan data the SpMV variant reads besides the matrix.
 double spmv_meta_bytes(const xb_plan *p, int variant, int block, int ipt) {
     double b = 0.0;
+    for (const auto &sb : p->subs) b += spmv_meta_bytes(sb.plan, variant, block, ipt);
     if (variant == XB_VAR_NNZ || variant == XB_VAR_SYM_TILE) {
         for (const auto &t : p->tiles)
             if (t.block == block && t.ipt == ipt) b += 4.0 * (t.ntiles + 1);
@@ -656,8 +658,8 @@ int run_solver(xb_plan *p, const double *b, double *x, const xb_options *opt, xb
         inf.block_used = o.block > 0 ? o.block : p->block;
         inf.ipt_used = o.ipt > 0 ? o.ipt : p->ipt;
         inf.mem_bytes = ac.mem + xb::spmv_meta_bytes(p, inf.variant_used, inf.block_used, inf.ipt_used) +
-                        (o.precision == XB_PREC_MIXED ? 4.0 * p->nnz : 0.0) +
-                        (o.precond == XB_PRECOND_ILU0 ? 8.0 * p->nnz + 12.0 * p->n : 0.0);
+                        (o.precision == XB_PREC_MIXED ? 4.0 * p->nnz64 : 0.0) +
+                        (o.precond == XB_PRECOND_ILU0 ? 8.0 * p->nnz64 + 12.0 * p->n : 0.0);
         if (st == XB_EFAULT)
             xb::set_error(XB_EFAULT, "fault convergence: implicit residual met tol, "
                                      "||b-Ax||/||b|| = %.3e", inf.res_true);

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(512) k_sell(int nslices, const int64_t *__rest
 // row sum is the one k_row forms, bit for bit.
 // ---------------------------------------------------------------------------
 template <typename V, int R>
-__global__ void __launch_bounds__(512) k_bcsr(int n, const int *__restrict__ bptr,
+__global__ void __launch_bounds__(512) k_bcsr(int n, int ncols, const int *__restrict__ bptr,
                                               const int *__restrict__ bcol,
                                               const V *__restrict__ bval, const V *__restrict__ x,
                                               V alpha, V beta, int mode, V *__restrict__ y,
@@ -100,11 +100,11 @@ __global__ void __launch_bounds__(512) k_bcsr(int n, const int *__restrict__ bpt
     for (int q = q0; q < q1; q++) {
         const int c0 = __ldg(bcol + q) * R;
         const V *blk = bval + ((int64_t)q * R + li) * R;
-        if (c0 + R <= n) {
+        if (c0 + R <= ncols) {
 #pragma unroll
             for (int j = 0; j < R; j++) s = fma(__ldg(blk + j), __ldg(x + c0 + j), s);
-        } else {  // last block column of a matrix whose n is not a multiple of R
-            for (int j = 0; c0 + j < n; j++) s = fma(__ldg(blk + j), __ldg(x + c0 + j), s);
+        } else {  // last block column when the column count is not a multiple of R
+            for (int j = 0; c0 + j < ncols; j++) s = fma(__ldg(blk + j), __ldg(x + c0 + j), s);
         }
     }
     store_row(y, r, s, alpha, beta, mode);
@@ -127,15 +127,15 @@ int launch_bcsr(xb_plan *p, int block, int ipt, V alpha, const V *x, V beta, int
     const V *bv = bcsr_values<V>(bp);
     switch (ipt) {
         case 2:
-            k_bcsr<V, 2><<<grid, block, 0, s>>>(p->n, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
+            k_bcsr<V, 2><<<grid, block, 0, s>>>(p->n, p->ncols, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
                                                 mode, y, adev);
             break;
         case 3:
-            k_bcsr<V, 3><<<grid, block, 0, s>>>(p->n, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
+            k_bcsr<V, 3><<<grid, block, 0, s>>>(p->n, p->ncols, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
                                                 mode, y, adev);
             break;
         case 4:
-            k_bcsr<V, 4><<<grid, block, 0, s>>>(p->n, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
+            k_bcsr<V, 4><<<grid, block, 0, s>>>(p->n, p->ncols, bp->d_bptr, bp->d_bcol, bv, x, alpha, beta,
                                                 mode, y, adev);
             break;
         default:
@@ -1194,6 +1194,14 @@ int spmv_any(xb_plan *p, int variant, int block, int ipt, V alpha, const V *x, V
         return xb::set_error(XB_EINVAL, "SpMV block %d not in {64,128,256,512}", block);
     const int n = p->n;
     if (n == 0) return XB_OK;
+    if (!p->subs.empty()) {  // a split plan: the variant on each row block, the whole x
+        for (const auto &sb : p->subs) {
+            const V *vs = sizeof(V) == sizeof(float) ? reinterpret_cast<const V *>(sb.plan->val32)
+                                                     : reinterpret_cast<const V *>(sb.plan->val);
+            XB_TRY(spmv_any<V>(sb.plan, variant, block, ipt, alpha, x, beta, y + sb.r0, vs, adev, s));
+        }
+        return XB_OK;
+    }
     if (adev) beta = V(0);
     const int mode = adev ? 1 : (beta == V(0)) ? (alpha == V(1) ? 0 : 1) : 2;
     switch (variant) {
@@ -1249,7 +1257,7 @@ int spmv_launch_f32(xb_plan *p, int variant, int block, int ipt, float alpha, co
 }
 
 double spmv_alg_bytes(const xb_plan *p, bool beta_nonzero, int val_bytes) {
-    const double n = p->n, nnz = p->nnz;
+    const double n = p->n, nnz = (double)p->nnz64;
     const int vb = val_bytes;
     return (vb + 4.0) * nnz + 4.0 * (n + 1) + vb * n + vb * n + (beta_nonzero ? vb * n : 0.0);
 }
