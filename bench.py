@@ -178,18 +178,19 @@ def alg_bytes(A, vb=8, beta=False):
 # keyed by (variant, block, ipt, n, nnz) and valid only while the code that launch
 # ran is unchanged: the sha256 of the segmented-scan kernels, their launcher and the
 # row-store helper (csrc/spmv.cu) and of the plan builders of their row-end bitmask,
-# warp start rows and BSS data format copy (csrc/plan.cu), as cut out by
-# HEADLINE_SRC below.  The
+# warp start rows and BSS data format copy (csrc/plan.cu; not the host-side
+# clean-up of unused copies), as cut out by HEADLINE_SRC below.  The
 # capture and its command are summarised in profiles/.
 NCU_TRAFFIC = {
     ("segscan", 128, 8, 4_000_000, 52_238_581):
-        (707.49e6, "b0c6609017e1496a9746e8702269a5e1dffcb01b66783f81a9d5ea616ce3f896"),
+        (707.49e6, "41407b9c258b0451900bd06265626c276f4454c5be5032b6a12c948e9297630a"),
 }
 HEADLINE_SRC = [
     ("spmv.cu", "__device__ __forceinline__ void store_row(", "// U1: one thread per row"),
     ("spmv.cu", "// U3 (BSS) with the plan's row-end bitmask", "// S1-like baseline"),
     ("spmv.cu", "int launch_seg(", "int launch_sym("),
-    ("plan.cu", "__global__ void k_seg_rows(", "__global__ void k_to_f32("),
+    ("plan.cu", "__global__ void k_seg_rows(", "void bss_trim("),
+    ("plan.cu", "const SegPart *get_segs(", "__global__ void k_to_f32("),
 ]
 
 

@@ -208,6 +208,50 @@ def resweep(D, dev="cuda", log_every=100):
     return out
 
 
+def remeasure_m(D, cap_s=4.0, kinds=("poisson2d", "laplace3d", "convdiff3d", "fixedrows",
+                                      "poisson2d_sym", "laplace3d_sym", "randsym"),
+                dev="cuda", log_every=10):
+    """Re-time GMRES(m) for every m of the saved records of the given kinds
+    with a per-solve cap of cap_s (SpMV choice: the record's fastest
+    candidate), marking which runs converged; other records are kept.
+    Returns a new dataset with an "m_full" flag per record (1 = re-timed, its
+    converged runs are labels whatever the matrix size)."""
+    import ast
+
+    import torch
+
+    import paper_2405_01599_gb300 as xb
+    xb.build()
+    out = {k: np.array(v, copy=True) for k, v in D.items()}
+    out["m_full"] = np.zeros(len(D["specs"]), np.int32)
+    t0 = time.perf_counter()
+    done = 0
+    for s, spec in enumerate(D["specs"]):
+        sp = ast.literal_eval(re.sub(r"np\.\w+\(([^()]*)\)", r"\1", str(spec)))
+        if sp[0] not in kinds:
+            continue
+        A = make(sp)
+        plan = xb.Plan.from_host(A, torch.device(dev))
+        t = D["times"][s]
+        plan.set_choice(*ALL_CANDS[int(np.nanargmin(t))])
+        n = A["n"]
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        plan.spmv(torch.ones(n, dtype=torch.float64, device=dev), b)
+        for k, m in enumerate(RESTARTS):
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            info = plan.gmres(b, x, m=m, tol=1e-8, maxiter=1_000_000, maxtime_s=cap_s,
+                              check_every=10)
+            conv = info["status"] == 0
+            out["mconv"][s, k] = conv
+            out["mtimes"][s, k] = info["t_solve_s"] if conv else np.inf
+        out["m_full"][s] = 1
+        del plan
+        done += 1
+        if log_every and done % log_every == 0:
+            print(f"[tuner m] {done} matrices re-timed, {time.perf_counter() - t0:.0f}s", flush=True)
+    return out
+
+
 M_LABEL_MAX_N = 200_000  # above this the m timings are capped extrapolations
 
 
@@ -228,7 +272,8 @@ def m_label(D, s):
     """Fastest restart length among the runs that converged within the cap
     (capped runs are extrapolations, which favour small m); -1 when none did
     or the matrix is above M_LABEL_MAX_N."""
-    if D["raw"][s][0] > M_LABEL_MAX_N:
+    full = "m_full" in D and D["m_full"][s]
+    if D["raw"][s][0] > M_LABEL_MAX_N and not full:
         return -1
     mt = D["mtimes"][s]
     conv = D["mconv"][s] if "mconv" in D else (mt < SMALL_CAP_S)
@@ -318,12 +363,18 @@ def main():
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--resweep", nargs="*", default=None,
                     help="re-time the SpMV candidates of saved datasets in place")
+    ap.add_argument("--remeasure-m", nargs="*", default=None,
+                    help="re-time GMRES(m) of saved large-matrix records (4 s cap) in place")
     a = ap.parse_args()
     D = None
     for f in a.resweep or ():
         R = resweep(dict(np.load(f)))
         np.savez_compressed(f, **R)
         print(f"[tuner resweep] {f}: {len(R['feat'])} matrices re-timed")
+    for f in a.remeasure_m or ():
+        R = remeasure_m(dict(np.load(f)))
+        np.savez_compressed(f, **R)
+        print(f"[tuner m] {f}: {int(R['m_full'].sum())} records re-timed")
     if a.make_data:
         D = make_data(a.make_data, a.seed, large=a.large)
         print(f"[tuner data] {n_records(D)} timing records from {len(D['feat'])} matrices")
@@ -335,6 +386,9 @@ def main():
             if "mconv" not in p_:
                 p_["mconv"] = p_["mtimes"] < (SMALL_CAP_S if p_["raw"][:, 0].max() <= M_LABEL_MAX_N
                                               else 0.6)
+        for p_ in parts:
+            if "m_full" not in p_:
+                p_["m_full"] = np.zeros(len(p_["feat"]), np.int32)
         Dt = {k: np.concatenate([p_[k] for p_ in parts]) for k in parts[0]}
         print(f"[tuner train] {n_records(Dt)} timing records from {len(Dt['feat'])} matrices")
         model, loss = train_model(Dt, epochs=a.epochs)
