@@ -223,6 +223,8 @@ def remeasure_m(D, cap_s=4.0, kinds=("poisson2d", "laplace3d", "convdiff3d", "fi
     import paper_2405_01599_gb300 as xb
     xb.build()
     out = {k: np.array(v, copy=True) for k, v in D.items()}
+    if "mconv" not in out:  # older sweeps: a run converged when it beat the 0.6 s cap
+        out["mconv"] = np.isfinite(out["mtimes"]) & (out["mtimes"] < 0.6)
     out["m_full"] = np.zeros(len(D["specs"]), np.int32)
     t0 = time.perf_counter()
     done = 0

@@ -157,3 +157,19 @@ def test_powerlaw_recipe_properties():
         v = val[rp[i]:rp[i + 1]]
         d = v[c == i][0]
         assert d == pytest.approx(2.0 * np.abs(v[c != i]).sum(), rel=1e-12)
+
+
+def test_openmp_build_matches_the_plain_oracle():
+    """The benchmark's all-cores baseline runs the OpenMP build of the same
+    source: its row-parallel SpMV keeps each row's summation order (bit for
+    bit), and its solvers, whose dot products sum in per-thread pieces, reach
+    the same iteration counts on a well-conditioned problem."""
+    A = gen.powerlaw(n=20000, seed=3)
+    x = np.random.default_rng(1).uniform(-1, 1, A["n"])
+    np.testing.assert_array_equal(oracle.spmv(A, x, omp=True), oracle.spmv(A, x))
+    P = gen.poisson2d(40)
+    b = oracle.spmv(P, np.ones(P["n"]))
+    _, i1 = oracle.gmres(P, b, m=30, tol=1e-8)
+    _, i2 = oracle.gmres(P, b, m=30, tol=1e-8, omp=True)
+    assert abs(i1["iters"] - i2["iters"]) <= 3 and i2["res_true"] <= 1e-8
+    assert oracle.lib_omp().orc_num_threads() >= 1
