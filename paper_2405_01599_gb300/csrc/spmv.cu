@@ -557,6 +557,9 @@ __global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__r
                                              V *__restrict__ cval, int *__restrict__ crow,
                                              const V *__restrict__ adev) {
     static_assert(IPT == 4 || IPT == 8 || IPT == 16 || IPT == 32, "IPT");
+    // the carry fix-up may be scheduled as soon as every CTA of this grid has
+    // started (it waits for this grid's completion before reading anything)
+    asm volatile("griddepcontrol.launch_dependents;");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -656,10 +659,13 @@ __global__ void __launch_bounds__(256) k_bss(int nnz, int nwarps, const int *__r
     }
 }
 
-// Adds each run of equal carry rows, in CTA order (deterministic).
+// Adds each run of equal carry rows, in CTA order (deterministic).  Launched
+// as a programmatic dependent of k_bss, it waits here until k_bss has
+// finished and its writes are visible (a no-op for an ordinary launch).
 template <typename V>
 __global__ void k_seg_fix(int nblk, int n, const int *__restrict__ crow, const V *__restrict__ cval,
                           V alpha, int mode, V *__restrict__ y, const V *__restrict__ adev) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblk) return;
     if (adev) alpha = *adev;
@@ -1080,8 +1086,21 @@ int launch_seg(xb_plan *p, const int *rp, const int *ci, const V *va, int block,
 #undef XB_BSS
 #undef XB_BSSM
         XB_LAUNCHED("k_bss");
-        k_seg_fix<V><<<(sp->nblk + 255) / 256, 256, 0, s>>>(sp->nblk, p->n, sp->d_carry_row, cv,
-                                                             alpha, mode, y, adev);
+        {  // programmatic dependent launch: no idle gap between the two kernels
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)((sp->nblk + 255) / 256));
+            cfg.blockDim = dim3(256);
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            const int *cr = sp->d_carry_row;
+            const V *cvc = cv;
+            XB_CUDA(cudaLaunchKernelEx(&cfg, k_seg_fix<V>, sp->nblk, p->n, cr, cvc, alpha, mode, y,
+                                       adev));
+        }
         XB_LAUNCHED("k_seg_fix");
     }
     if (p->n_empty > 0) {
