@@ -174,12 +174,12 @@ typedef struct xb_options {
                              /*   resolve the system: kappa * 6e-8 near 1),    */
                              /*   the solve continues as FP64 GMRES(m) from    */
                              /*   the current x and xb_info.fallback = 1       */
-    int32_t small_n;         /* GMRES: systems with n <= small_n and nnz +   */
-                             /*   m n <= 32 small_n run as one persistent     */
-                             /*   launch when the options allow it (see       */
-                             /*   gmres_solve); default 8192 (the environment */
-                             /*   variable XB_SMALL_N changes the default),   */
-                             /*   0 = never                                    */
+    int32_t small_n;         /* GMRES: systems with n <= small_n run as one  */
+                             /*   persistent launch when the options allow it */
+                             /*   and one of the persistent kernels takes     */
+                             /*   the size (see gmres_solve); default 8192    */
+                             /*   (the environment variable XB_SMALL_N        */
+                             /*   changes the default), 0 = never             */
 } xb_options;
 
 typedef struct xb_info {
@@ -204,8 +204,10 @@ typedef struct xb_info {
     double mem_bytes;        /* device memory the solve used: workspace it    */
                              /*   requested, the SpMV variant's plan data and */
                              /*   the FP32 matrix copy (mixed precision)      */
-    int32_t persistent;      /* 1: GMRES ran as one persistent launch (small  */
-                             /*   systems, see gmres_solve)                   */
+    int32_t persistent;      /* GMRES ran as one persistent launch (small     */
+                             /*   systems, see gmres_solve): 2 = from one     */
+                             /*   cluster's shared memory, 1 = the batched    */
+                             /*   kernel's single-system path; 0 = neither    */
 } xb_info;
 
 typedef struct xb_plan xb_plan;
@@ -407,14 +409,23 @@ int xb_spmv_f32(xb_plan *plan, int32_t variant, float alpha, const float *x, flo
  * (Sec. 4.3; FP64 only, general storage).  opt->precision == XB_PREC_MIXED
  * runs FP32 GMRES(m) (FP32 SpMV and basis, FP64 Hessenberg/Givens/least
  * squares) inside FP64 iterative refinement (see opt->ir_fallback).
- * Small systems -- n <= opt->small_n (default 8192) and nnz + m n <= 32
- * small_n, general storage, FP64, no preconditioner,
+ * Small systems -- n <= opt->small_n (default 8192), general storage, FP64,
+ * no preconditioner,
  * MGS or BCGS, m (and m_max with the restart rule, whose window and
  * increment must then be the default 5) <= XB_BATCH_MAX_M,
- * fault_check on -- run the same GMRES(m) as one persistent launch of the
- * batched kernel (one 8-CTA cluster solves the system), because each Arnoldi step of
- * the multi-launch path is bound by launch and synchronisation latency at
- * that size; xb_info.persistent = 1 then, spmv_ms and res_implicit are 0. */
+ * fault_check on -- run the same GMRES(m) as one persistent launch, because
+ * each Arnoldi step of the multi-launch path is bound by launch and
+ * synchronisation latency at that size.  When a cluster of 2, 4, 8 or 16
+ * CTAs can hold the system in shared memory (at most 512 rows per CTA, rows
+ * at most 64 long, the basis slice, the ELL copy of the rows and the
+ * Hessenberg matrix within the opt-in shared memory of a CTA) that cluster
+ * runs it with no global-memory traffic per step (xb_info.persistent = 2;
+ * the environment variable XB_RESIDENT_CL = 0 turns this off, a cluster size
+ * forces it); otherwise, while nnz + m n <= 32 small_n, the batched kernel's
+ * single-system path does (one 8-CTA cluster, basis in global memory;
+ * xb_info.persistent = 1), and beyond that the multi-launch path.  spmv_ms
+ * and res_implicit are 0 on both.  A column index outside [0, n) makes the
+ * shared-memory path return XB_EINVAL without touching x. */
 int gmres_solve(xb_plan *plan, const double *b, double *x, const xb_options *opt,
                 xb_info *info, void *stream);
 

@@ -283,6 +283,10 @@ int ilu_apply(xb_plan *p, const double *r, double *z, cudaStream_t s);
 // kernel with a single system): FP64, general storage, MGS or BCGS, m <= 128.
 int batch_single(xb_plan *p, const double *b, double *x, const xb_options &o, int mode,
                  xb_info &inf, double *alg_bytes, cudaStream_t s);
+// The same solve from one cluster's shared memory when the system fits
+// (resident.cu); *ran = false when it does not (nothing launched).
+int resident_gmres(xb_plan *p, const double *b, double *x, const xb_options &o, xb_info &inf,
+                   double *alg_bytes, cudaStream_t s, bool *ran);
 double ilu_apply_bytes(const xb_plan *p);
 int ilu_check(xb_plan *p);  // XB_ETIMEOUT if a substitution's barrier wait ran out
 void ilu_free(xb_plan *p);

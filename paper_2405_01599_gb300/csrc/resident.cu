@@ -1,0 +1,680 @@
+// GMRES(m) for a small system held entirely in the shared memory of one
+// thread-block cluster: restarted GMRES (Sec. 2.2) with the fused MGS or the
+// blocked (length 4) Gram-Schmidt pass, Givens least squares, the
+// restart-frequency rule of Eq. (1) / Sec. 4.3 and the fault-convergence
+// check of Sec. 3.3.2 -- the same iteration as the multi-launch FP64 solver
+// and the batched kernel, with a different data layout and schedule.
+//
+// Cost model.  On this GPU an FP64 add or FMA issued by a warp occupies its
+// SM sub-partition's FP64 pipe for about 80 cycles whatever the number of
+// active lanes, so at this size a Krylov step is bound by the count of FP64
+// warp instructions on its critical path (and by cluster barriers, about 400
+// cycles).  Hence: one warp per sub-partition (4 warps per CTA, R rows per
+// thread), the largest cluster that keeps R smallest, reductions shaped to
+// use few FP64 instructions, and the Givens work of the previous entry run
+// between a barrier's arrive and its wait.
+//
+// Layout.  CTA r of the cluster owns rows [r rpc, (r+1) rpc); thread t holds
+// the local rows t, t + 128, ... (R of them).  The thread's entries of the
+// Krylov basis sit in the CTA's shared memory (basis vector i, local row l at
+// V[i rpp + l], rpp = 128 R, so a warp's accesses are consecutive), its rows
+// of A in an ELL copy there (column k at [k rpp + l]: the value, and the
+// owning CTA and local offset of the column), and w, x, b in registers, so an
+// Arnoldi step touches no global memory.
+//
+// Exchange.  The vector an SpMV multiplies (x at a restart, the unnormalised
+// w of the previous step otherwise, the 1 / ||w|| scale applied to the
+// product) is published in one of two shared buffers; every thread gathers
+// the entries of its rows from the owning CTAs with ld.shared::cluster.  The
+// buffers alternate, and a buffer is rewritten only after a cluster barrier
+// that follows every read of it.
+//
+// Reductions.  One, or four at once, sums over the cluster cost one cluster
+// barrier: each warp reduces its lanes' partials with shuffles (four sums in
+// a transposed tree: 6 adds rather than 20), and lanes store the warp's sums
+// into the same slot of every CTA's slot array (st.shared::cluster); after the
+// barrier every warp sums the P = 4 ncl slots in one fixed order, so every
+// thread of the cluster holds the same bits and takes the same branches.  Two
+// slot arrays alternate: one is rewritten only after the barrier of the
+// reduction that follows its last read.  Every barrier sits on a path whose
+// conditions are such reduced values or step counts, so all threads of the
+// cluster reach the same barriers in the same order, and no CTA touches
+// another's shared memory after the last barrier.
+
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+namespace {
+
+constexpr int kMaxRow = 64;  // longest row the ELL copy takes
+constexpr int kW = 4;        // warps per CTA: one per SM sub-partition
+constexpr int kBT = 32 * kW;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct ResArgs {
+    int n, rpc, ncl, lmax, m, m_max, maxiter, bcgs;
+    double tol, theta;
+    unsigned long long budget_ns;
+    const int *rowptr, *col;
+    const double *val, *b;
+    double *x;
+    xb_batch_info *out;
+};
+
+// Byte offsets of the dynamic shared memory regions (doubles first).
+struct ResLayout {
+    size_t V, W, ev, red, H, cs, sn, g, y, ea, total;
+};
+
+__host__ __device__ inline ResLayout res_layout(int rpp, int lmax, int mmax, int P) {
+    ResLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 15) / 16 * 16;
+        return at;
+    };
+    L.V = take((size_t)(mmax + 1) * rpp * 8);
+    L.W = take((size_t)2 * rpp * 8);
+    L.ev = take((size_t)lmax * rpp * 8);
+    L.red = take((size_t)2 * 4 * P * 8);
+    L.H = take((size_t)(mmax + 1) * mmax * 8);
+    L.cs = take((size_t)mmax * 8);
+    L.sn = take((size_t)mmax * 8);
+    L.g = take((size_t)(mmax + 1) * 8);
+    L.y = take((size_t)mmax * 8);
+    L.ea = take((size_t)lmax * rpp * 4);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// The shared::cluster address of local shared address a in CTA `rank`.
+__device__ __forceinline__ unsigned map_rank(unsigned a, unsigned rank) {
+    unsigned d;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(rank));
+    return d;
+}
+
+__device__ __forceinline__ double ld_cluster(unsigned a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void st_cluster(unsigned a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// Cluster barrier in two halves: stores before the arrive are visible to
+// loads after the wait in every CTA; work between them overlaps the barrier.
+__device__ __forceinline__ void cl_arrive() {
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cl_wait() {
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Sum of four values over the warp, transposed: every lane returns the sum
+// of value (lane >> 3) (6 adds in all).
+__device__ __forceinline__ double warp_sum4(const double (&v)[4]) {
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    double k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
+    const double s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
+    k0 += __shfl_xor_sync(kFull, s0, 16);
+    k1 += __shfl_xor_sync(kFull, s1, 16);
+    double k = h8 ? k1 : k0;
+    k += __shfl_xor_sync(kFull, h8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(kFull, k, 4);
+    k += __shfl_xor_sync(kFull, k, 2);
+    k += __shfl_xor_sync(kFull, k, 1);
+    return k;
+}
+
+struct Red {
+    double *slots;  // 2 phases x 4 sums x P partials
+    int P, slot, ncl, phase;
+};
+
+// Stage 1 of one cluster sum: the warp's sum into every CTA's slot, arrive.
+__device__ __forceinline__ void put1(double v, const Red &R) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int lane = threadIdx.x & 31;
+    if (lane < R.ncl)
+        st_cluster(map_rank(smem_addr(R.slots + (size_t)R.phase * 4 * R.P + R.slot), (unsigned)lane),
+                   v);
+    cl_arrive();
+}
+
+// Stage 2: wait, then the P slots summed in a fixed order (log2 P adds).
+__device__ __forceinline__ double get1(Red &R) {
+    cl_wait();
+    const double *base = R.slots + (size_t)R.phase * 4 * R.P;
+    const int lane = threadIdx.x & 31;
+    double s = lane < R.P ? base[lane] : 0.0;
+    if (R.P > 32) s += base[32 + lane];
+    for (int o = min(R.P, 32) >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    R.phase ^= 1;
+    return __shfl_sync(kFull, s, 0);
+}
+
+// The same for four sums at once.
+__device__ __forceinline__ void put4(const double (&v)[4], const Red &R) {
+    const double k = warp_sum4(v);  // sum of value lane >> 3
+    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+    double *dst = R.slots + (size_t)R.phase * 4 * R.P + q * R.P + R.slot;
+    if (r < R.ncl) st_cluster(map_rank(smem_addr(dst), (unsigned)r), k);
+    if (r + 8 < R.ncl) st_cluster(map_rank(smem_addr(dst), (unsigned)(r + 8)), k);
+    cl_arrive();
+}
+
+__device__ __forceinline__ void get4(double (&v)[4], Red &R) {
+    cl_wait();
+    const double *base = R.slots + (size_t)R.phase * 4 * R.P;
+    const int lane = threadIdx.x & 31;
+    double a[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        a[q] = lane < R.P ? base[q * R.P + lane] : 0.0;
+        if (R.P > 32) a[q] += base[q * R.P + 32 + lane];
+    }
+    const double k = warp_sum4(a);
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = __shfl_sync(kFull, k, 8 * q);
+    R.phase ^= 1;
+}
+
+// (A u)_row for the published vector u in shared buffer `buf` (local shared
+// address), row entries in storage order.
+__device__ __forceinline__ double row_spmv(const double *__restrict__ ev, const int *__restrict__ ea,
+                                           int len, int rpp, int l, unsigned buf) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < len; k++) {
+        const int e = ea[k * rpp + l];
+        const double u = ld_cluster(map_rank(buf + (unsigned)(e & 0xffff) * 8u, (unsigned)e >> 16));
+        s = fma(ev[k * rpp + l], u, s);
+    }
+    return s;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int rpp = kBT * R;
+    const int mmax = A.m_max, ldh = mmax + 1;
+    const ResLayout L = res_layout(rpp, A.lmax, mmax, A.ncl * kW);
+    double *V = reinterpret_cast<double *>(smem + L.V);
+    double *W = reinterpret_cast<double *>(smem + L.W);
+    double *ev = reinterpret_cast<double *>(smem + L.ev);
+    double *H = reinterpret_cast<double *>(smem + L.H);
+    double *cs = reinterpret_cast<double *>(smem + L.cs);
+    double *sn = reinterpret_cast<double *>(smem + L.sn);
+    double *g = reinterpret_cast<double *>(smem + L.g);
+    double *yv = reinterpret_cast<double *>(smem + L.y);
+    int *ea = reinterpret_cast<int *>(smem + L.ea);
+    const unsigned rank = cluster_rank();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    Red Rd{reinterpret_cast<double *>(smem + L.red), A.ncl * kW, (int)rank * kW + warp, A.ncl, 0};
+    const bool lead = rank == 0 && t == 0;
+    const unsigned long long ts = gtimer(), deadline = ts + A.budget_ns;
+
+    // this thread's rows into the ELL copy; a column outside [0, n) is
+    // counted and fails the solve (nothing is read through it)
+    int len[R];
+    double bi[R], x[R], w[R];
+    double bad = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int l = r * kBT + t, row = (int)rank * A.rpc + l;
+        len[r] = 0;
+        bi[r] = 0.0;
+        x[r] = 0.0;
+        if (l < A.rpc && row < A.n) {
+            const int ka = A.rowptr[row];
+            len[r] = A.rowptr[row + 1] - ka;
+            for (int k = 0; k < len[r]; k++) {
+                int c = A.col[ka + k];
+                if (c < 0 || c >= A.n) {
+                    bad = 1.0;
+                    c = row;
+                }
+                const int o = c / A.rpc;
+                ea[k * rpp + l] = (o << 16) | (c - o * A.rpc);
+                ev[k * rpp + l] = A.val[ka + k];
+            }
+            bi[r] = A.b[row];
+            x[r] = A.x[row];
+        }
+    }
+    const unsigned wbuf[2] = {smem_addr(W), smem_addr(W + rpp)};
+
+    int iters = 0, restarts = 0, status = XB_OK, claimed = 0, m = A.m, K = 0;
+    double tau = A.tol, res_true = 0.0, samp[5];
+    double q4[4] = {0.0, bad, 0.0, 0.0};
+#pragma unroll
+    for (int r = 0; r < R; r++) q4[0] = fma(bi[r], bi[r], q4[0]);
+    put4(q4, Rd);  // the barrier also orders the ELL copy before any gather
+    get4(q4, Rd);
+    const double bnorm = sqrt(q4[0]);
+    int wb = 0;  // buffer the next publication goes to
+    if (q4[1] > 0.0) {
+        status = XB_EINVAL;
+    } else if (bnorm == 0.0) {
+#pragma unroll
+        for (int r = 0; r < R; r++) x[r] = 0.0;
+    } else {
+        for (;;) {
+            // r = b - A x
+#pragma unroll
+            for (int r = 0; r < R; r++) W[wb * rpp + r * kBT + t] = x[r];
+            cl_arrive();
+            cl_wait();
+            double rs[R];
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                rs[r] = fma(-1.0, row_spmv(ev, ea, len[r], rpp, r * kBT + t, wbuf[wb]), bi[r]);
+            wb ^= 1;
+            q4[0] = 0.0;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                W[wb * rpp + r * kBT + t] = rs[r];  // v_0 unnormalised, for the first SpMV
+                q4[0] = fma(rs[r], rs[r], q4[0]);
+            }
+            q4[1] = (lead && gtimer() > deadline) ? 1.0 : 0.0;
+            q4[2] = q4[3] = 0.0;
+            put4(q4, Rd);
+            get4(q4, Rd);
+            const double beta = sqrt(q4[0]);
+            res_true = beta / bnorm;
+            if (res_true <= A.tol) {
+                status = XB_OK;
+                break;
+            }
+            if (iters >= A.maxiter || q4[1] > 0.0) {
+                status = XB_ENOCONV;
+                break;
+            }
+            if (claimed) tau *= A.tol / res_true;  // fault convergence: narrow the threshold
+            claimed = 0;
+            if (restarts > 0) {  // restart-frequency rule (Eq. 1): judge every 5 samples
+                samp[K++] = res_true;
+                if (K == 5) {
+                    double mx = samp[0], mn = samp[0];
+                    for (int z = 1; z < 5; z++) {
+                        mx = fmax(mx, samp[z]);
+                        mn = fmin(mn, samp[z]);
+                    }
+                    if (mn > 0.0 && mx / mn < A.theta) m = min(m + 5, mmax);
+                    K = 0;
+                }
+            }
+            double sc = 1.0 / beta;  // scale of the published vector
+#pragma unroll
+            for (int r = 0; r < R; r++) V[r * kBT + t] = rs[r] * sc;
+            const double tol_g = tau * bnorm;  // |g_{j+1}| <= tau ||b||
+            double gj = beta;                  // g_j of the least-squares right-hand side
+            int k = 0;
+            for (int j = 0; j < m; j++) {
+                iters++;
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    w[r] = row_spmv(ev, ea, len[r], rpp, r * kBT + t, wbuf[wb]) * sc;
+                double len2 = 0.0, tt = 0.0;
+                // Givens rotations of the previous columns, applied as the
+                // column's entries arrive (each between the arrive and the
+                // wait of the next barrier): tt is entry i rotated by
+                // G_0..G_{i-1}
+                auto take = [&](int i, double h) {
+                    len2 = fma(h, h, len2);
+                    if (i == 0) {
+                        tt = h;
+                    } else {
+                        const double c = cs[i - 1], s = sn[i - 1];
+                        if (t == 0) H[(size_t)j * ldh + i - 1] = fma(c, tt, s * h);
+                        tt = fma(-s, tt, c * h);
+                    }
+                };
+                const double *Vj = V + (size_t)j * rpp;
+                double *wn = W + (wb ^ 1) * rpp;
+                double last[4];
+                int nlast;
+                int i_last;
+                if (A.bcgs) {
+                    // blocks of 4: one barrier per block takes the block's dots
+                    // after the previous block's projection
+                    double c4[4] = {0.0, 0.0, 0.0, 0.0};
+                    int u0 = 0, nu = 0;
+                    for (int d0 = 0; d0 <= j; d0 += 4) {
+                        const int nd = min(4, j + 1 - d0);
+                        double a4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                        for (int r = 0; r < R; r++) {
+                            const int l = r * kBT + t;
+#pragma unroll
+                            for (int q = 0; q < 4; q++)
+                                if (q < nu) w[r] = fma(-c4[q], V[(size_t)(u0 + q) * rpp + l], w[r]);
+#pragma unroll
+                            for (int q = 0; q < 4; q++)
+                                if (q < nd) a4[q] = fma(w[r], V[(size_t)(d0 + q) * rpp + l], a4[q]);
+                        }
+                        put4(a4, Rd);
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (q < nu) take(u0 + q, c4[q]);
+                        get4(a4, Rd);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) c4[q] = a4[q];
+                        u0 = d0;
+                        nu = nd;
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int l = r * kBT + t;
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (q < nu) w[r] = fma(-c4[q], V[(size_t)(u0 + q) * rpp + l], w[r]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; q++) last[q] = c4[q];
+                    nlast = nu;
+                    i_last = u0;
+                } else {
+                    // fused MGS: pass i applies the projection on v_{i-1} and
+                    // takes (w, v_i)
+                    double hprev = 0.0;
+                    for (int i = 0; i <= j; i++) {
+                        double a = 0.0;
+#pragma unroll
+                        for (int r = 0; r < R; r++) {
+                            const int l = r * kBT + t;
+                            if (i > 0) w[r] = fma(-hprev, V[(size_t)(i - 1) * rpp + l], w[r]);
+                            a = fma(w[r], V[(size_t)i * rpp + l], a);
+                        }
+                        put1(a, Rd);
+                        if (i > 0) take(i - 1, hprev);
+                        hprev = get1(Rd);
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; r++) w[r] = fma(-hprev, Vj[r * kBT + t], w[r]);
+                    last[0] = hprev;
+                    nlast = 1;
+                    i_last = j;
+                }
+                wb ^= 1;
+                double a = 0.0;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    wn[r * kBT + t] = w[r];  // published by the norm's barrier
+                    a = fma(w[r], w[r], a);
+                }
+                put1(a, Rd);
+                for (int q = 0; q < nlast; q++) take(i_last + q, last[q]);
+                const double hn2 = get1(Rd);
+                // the new rotation, from values every thread holds alike
+                // (|h| <= ||A|| sqrt(m): no overflow in tt^2 + hn^2)
+                int flag = 0;
+                const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0, hn = hn2 * ihn;
+                const double rr2 = fma(tt, tt, hn2);
+                if (rr2 == 0.0) {
+                    flag = 2;
+                } else {
+                    const double irr = rsqrt(rr2), c = tt * irr, s = hn * irr;
+                    if (t == 0) {
+                        cs[j] = c;
+                        sn[j] = s;
+                        H[(size_t)j * ldh + j] = rr2 * irr;
+                        g[j] = c * gj;
+                    }
+                    gj = -s * gj;
+                    if (hn2 <= 1e-28 * (len2 + hn2)) flag = 1;  // hn <= 1e-14 |column|
+                    else if (fabs(gj) <= tol_g) flag = 3;
+                }
+                if (flag == 2) {
+                    k = j;
+                    status = XB_EBREAKDOWN;
+                    break;
+                }
+                k = j + 1;
+                if (flag == 1) {
+                    claimed = 1;
+                    break;
+                }
+                sc = ihn;
+                double *Vn = V + (size_t)(j + 1) * rpp;
+#pragma unroll
+                for (int r = 0; r < R; r++) Vn[r * kBT + t] = w[r] * sc;
+                if (flag == 3) {
+                    claimed = 1;
+                    break;
+                }
+                if (iters >= A.maxiter) break;
+            }
+            if (status == XB_EBREAKDOWN) break;
+            // R y = g by columns on warp 0 (lane c holds g_c and 1 / R_cc;
+            // every CTA holds the same R and g), then x += V y
+            if (warp == 0) {
+                __syncwarp();
+                constexpr int QM = (XB_BATCH_MAX_M + 31) / 32;
+                double gl[QM], dl[QM];
+#pragma unroll
+                for (int q = 0; q < QM; q++) {
+                    const int c = lane + 32 * q;
+                    gl[q] = c < k ? g[c] : 0.0;
+                    dl[q] = c < k ? 1.0 / H[(size_t)c * ldh + c] : 0.0;
+                }
+                for (int i = k - 1; i >= 0; i--) {
+                    const int qi = i >> 5, li = i & 31;
+                    double gs = gl[0], ds = dl[0];
+#pragma unroll
+                    for (int q = 1; q < QM; q++)
+                        if (qi == q) {
+                            gs = gl[q];
+                            ds = dl[q];
+                        }
+                    const double yi = __shfl_sync(kFull, gs, li) * __shfl_sync(kFull, ds, li);
+                    if (lane == 0) yv[i] = yi;
+#pragma unroll
+                    for (int q = 0; q < QM; q++) {
+                        const int c = lane + 32 * q;
+                        if (32 * q < i && c < i) gl[q] = fma(-H[(size_t)i * ldh + c], yi, gl[q]);
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                double s0 = 0.0;
+                for (int i = 0; i < k; i++) s0 = fma(yv[i], V[(size_t)i * rpp + r * kBT + t], s0);
+                x[r] += s0;
+            }
+            restarts++;
+        }
+    }
+    if (status != XB_EINVAL) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int l = r * kBT + t, row = (int)rank * A.rpc + l;
+            if (l < A.rpc && row < A.n) A.x[row] = x[r];
+        }
+    }
+    if (lead) {
+        xb_batch_info inf;
+        inf.status = status;
+        inf.iters = iters;
+        inf.restarts = restarts;
+        inf.m = m;
+        inf.mode = 2;
+        inf.res_true = res_true;
+        inf.ms = (double)(gtimer() - ts) * 1e-6;
+        *A.out = inf;
+    }
+}
+
+typedef void (*ResKernel)(const ResArgs);
+
+ResKernel res_kernel(int R) {
+    switch (R) {
+        case 1: return k_gmres_resident<1>;
+        case 2: return k_gmres_resident<2>;
+        case 4: return k_gmres_resident<4>;
+        case 8: return k_gmres_resident<8>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+namespace xb {
+
+// Runs gmres_solve's FP64 GMRES(m) for plan p as one launch of the
+// shared-memory-resident kernel when a cluster of 2, 4, 8 or 16 CTAs holds
+// the system (at most 1024 rows per CTA, rows at most 64 long, the basis
+// slice, ELL copy, Hessenberg and slots within the opt-in shared memory);
+// *ran = false otherwise (nothing launched).  The cluster is the smallest
+// whose CTAs hold at most 128 rows (one row per thread), else the largest
+// that fits (fewest rows per thread).  The environment variable
+// XB_RESIDENT_CL = 0 turns the path off, a cluster size forces it.
+int resident_gmres(xb_plan *p, const double *b, double *x, const xb_options &o, xb_info &inf,
+                   double *alg_bytes, cudaStream_t s, bool *ran) {
+    *ran = false;
+    int force = -1;
+    if (const char *env = std::getenv("XB_RESIDENT_CL")) force = std::atoi(env);
+    if (force == 0 || p->n < 1 || p->max_row > kMaxRow || p->n > 16 * 8 * kBT) return XB_OK;
+    const int mmax = o.dafrt ? std::max(o.m, std::min(o.m_max, XB_BATCH_MAX_M)) : o.m;
+    if (mmax > XB_BATCH_MAX_M) return XB_OK;
+    int dev = 0, optin = 0;
+    XB_CUDA(cudaGetDevice(&dev));
+    XB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int lmax = std::max(1, p->max_row);
+    // candidates in order of preference
+    int order[4], no = 0;
+    if (force > 0) {
+        order[no++] = force;
+    } else {
+        int first = 16;
+        for (int c : {2, 4, 8, 16})
+            if ((p->n + c - 1) / c <= kBT) {
+                first = c;
+                break;
+            }
+        order[no++] = first;
+        for (int c : {16, 8, 4, 2})
+            if (c != first) order[no++] = c;
+    }
+    ResArgs a;
+    std::memset(&a, 0, sizeof a);
+    size_t bytes = 0;
+    ResKernel kern = nullptr;
+    for (int z = 0; z < no; z++) {
+        const int ncl = order[z];
+        if (ncl != 2 && ncl != 4 && ncl != 8 && ncl != 16) continue;
+        const int rpc = (p->n + ncl - 1) / ncl;
+        int R = 1;
+        while (R * kBT < rpc) R *= 2;
+        ResKernel kf = res_kernel(R);
+        if (!kf) continue;
+        const ResLayout L = res_layout(kBT * R, lmax, mmax, ncl * kW);
+        if (L.total > (size_t)optin) continue;
+        XB_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        if (ncl > 8) XB_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = ncl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(ncl);
+        cfg.blockDim = dim3(kBT);
+        cfg.dynamicSmemBytes = L.total;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, (void *)kf, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        a.ncl = ncl;
+        a.rpc = rpc;
+        bytes = L.total;
+        kern = kf;
+        break;
+    }
+    if (!kern) return XB_OK;
+    XB_TRY(ensure_work(p, sizeof(xb_batch_info)));
+    xb_batch_info *d_info = static_cast<xb_batch_info *>(p->d_work);
+    a.n = p->n;
+    a.lmax = lmax;
+    a.m = o.m;
+    a.m_max = mmax;
+    a.maxiter = o.maxiter;
+    a.bcgs = o.ortho == XB_ORTHO_BCGS ? 1 : 0;
+    a.tol = o.tol;
+    a.theta = o.dafrt ? o.dafrt_theta : 0.0;
+    a.budget_ns = (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
+    a.rowptr = p->rowptr;
+    a.col = p->col;
+    a.val = p->val;
+    a.b = b;
+    a.x = x;
+    a.out = d_info;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = a.ncl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(a.ncl);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    XB_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    XB_LAUNCHED("k_gmres_resident");
+    xb_batch_info r;
+    XB_CUDA(cudaMemcpyAsync(&r, d_info, sizeof r, cudaMemcpyDeviceToHost, s));
+    XB_CUDA(cudaStreamSynchronize(s));
+    *ran = true;
+    inf.iters = r.iters;
+    inf.restarts = r.restarts;
+    inf.m_final = r.m;
+    inf.res_true = r.res_true;
+    inf.ortho_used = a.bcgs ? XB_ORTHO_BCGS : XB_ORTHO_MGS;
+    inf.persistent = 2;
+    // algorithmic bytes, counted as for the multi-launch step: per Arnoldi
+    // step one SpMV and the Gram-Schmidt passes at the cycle's mean basis
+    // size, plus a residual per restart
+    const double jm = (r.m + 1) / 2.0, n = a.n;
+    *alg_bytes = r.iters * (spmv_alg_bytes(p, false, 8) + (4.0 * jm + 5.0) * 8.0 * n) +
+                 (r.restarts + 1) * (spmv_alg_bytes(p, true, 8) + 16.0 * n);
+    if (r.status == XB_EINVAL)
+        return set_error(XB_EINVAL, "gmres: column index outside [0, n) in the matrix");
+    if (r.status == XB_ENOCONV)
+        return set_error(XB_ENOCONV, "not converged: ||b-Ax||/||b|| = %.3e > tol %.1e", r.res_true,
+                         o.tol);
+    return r.status;
+}
+
+}  // namespace xb

@@ -505,15 +505,10 @@ int bicgstab_run(xb_plan *p, const double *b, double *x, const xb_options &o, xb
     return status;
 }
 
-// Whether gmres_solve runs the system as one persistent launch: small, and
-// options the persistent kernel implements exactly as gmres_fp64 does.
+// Whether gmres_solve may run the system as one persistent launch: small, and
+// options the persistent kernels implement exactly as gmres_fp64 does.
 bool small_system(const xb_plan *p, const xb_options &o) {
     if (p->n < 1 || p->n > o.small_n || p->sym) return false;
-    // one CTA does a step's SpMV and Gram-Schmidt passes alone: only while that
-    // work (about nnz + m n) stays small does it beat the multi-launch step
-    // (measured: n = 4096 stencil 76 vs 148 us per step; n = 20,000 power-law
-    // rows 592 vs 168 us)
-    if ((double)p->nnz + (double)o.m * p->n > 32.0 * o.small_n) return false;
     if (o.precision != XB_PREC_FP64 || o.precond != XB_PRECOND_NONE || !o.fault_check) return false;
     if (o.ortho != XB_ORTHO_MGS && o.ortho != XB_ORTHO_BCGS) return false;
     // the persistent kernel's restart rule judges windows of 5 samples, m += 5
@@ -688,12 +683,27 @@ int gmres_solve(xb_plan *p, const double *b, double *x, const xb_options *opt, x
                           if (o.precision == XB_PREC_MIXED)
                               return gmres_mixed(p, b, x, o, inf, s, ac, tm, t0);
                           if (small_system(p, o)) {
-                              // thread per row, or warp-sized row blocks when rows are long
-                              const int mode = p->max_row > 32 ? 1 : 0;
                               double by = 0.0;
-                              const int r = xb::batch_single(p, b, x, o, mode, inf, &by, s);
-                              ac.bytes += by;
-                              return r;
+                              // the whole system in one cluster's shared memory
+                              bool ran = false;
+                              int r = xb::resident_gmres(p, b, x, o, inf, &by, s, &ran);
+                              if (ran || r != XB_OK) {
+                                  ac.bytes += by;
+                                  return r;
+                              }
+                              // else the batched kernel's single-system path (thread
+                              // per row, or warp-sized row blocks when rows are long),
+                              // whose cluster streams the basis from L2: only while a
+                              // step's work (about nnz + m n) stays small does it beat
+                              // the multi-launch step (measured: n = 4096 stencil 57
+                              // vs 148 us per step; n = 20,000 power-law rows 592 vs
+                              // 168 us on one CTA)
+                              if ((double)p->nnz + (double)o.m * p->n <= 32.0 * o.small_n) {
+                                  const int mode = p->max_row > 32 ? 1 : 0;
+                                  r = xb::batch_single(p, b, x, o, mode, inf, &by, s);
+                                  ac.bytes += by;
+                                  return r;
+                              }
                           }
                           return gmres_fp64(p, b, x, o, inf, s, ac, tm, t0, o.maxiter);
                       });

@@ -24,6 +24,26 @@ def _true_rel(A, x, b):
     return np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
 
 
+# the three GMRES paths: one launch from one cluster's shared memory, one
+# launch of the batched kernel (basis in global memory), and the multi-launch
+# Arnoldi loop
+PATHS = ["resident", "batched", "multi"]
+
+
+def _path(monkeypatch, path):
+    """Select a GMRES path; returns the small_n option for it."""
+    monkeypatch.setenv("XB_RESIDENT_CL", "0" if path == "batched" else "")
+    if path != "batched":
+        monkeypatch.delenv("XB_RESIDENT_CL")
+    return 0 if path == "multi" else 8192
+
+
+def _persistent(path, A):
+    if path == "multi" or A["sym_upper"]:
+        return 0
+    return 2 if path == "resident" else 1
+
+
 def _solve(xb, dev, A, which, b=None, x0=None, **opt):
     import torch
     plan = xb.Plan.from_host(A, dev)
@@ -35,22 +55,24 @@ def _solve(xb, dev, A, which, b=None, x0=None, **opt):
     return info, xt.cpu().numpy(), b
 
 
-@pytest.mark.parametrize("small_n", [8192, 0])
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("name,make,m", [
     ("poisson64", lambda: gen.poisson2d(64), 30),
     ("random200", lambda: gen.random200(), 30),
     ("convdiff10", lambda: gen.convdiff3d(N=10), 20),
     ("laplace3d_10_upper", lambda: gen.laplace3d(10, upper=True), 25),
 ])
-def test_gmres_matches_oracle(env, name, make, m, small_n):
-    """Both GMRES paths: one persistent launch for small general systems
-    (small_n = 8192, the default) and the multi-launch path (small_n = 0;
-    symmetric storage always takes it)."""
+def test_gmres_matches_oracle(env, monkeypatch, name, make, m, path):
+    """Every GMRES path: one persistent launch for small general systems
+    (small_n = 8192, the default), from shared memory or through the batched
+    kernel, and the multi-launch path (small_n = 0; symmetric storage always
+    takes it)."""
     xb, dev = env
     A = make()
+    small_n = _path(monkeypatch, path)
     info, x, b = _solve(xb, dev, A, "gmres", m=m, tol=TOL, small_n=small_n)
     xo, io = oracle.gmres(A, b, m=m, tol=TOL)
-    assert info["persistent"] == (1 if small_n and not A["sym_upper"] else 0)
+    assert info["persistent"] == _persistent(path, A)
     assert info["status"] == 0, info
     assert _true_rel(A, x, b) <= TOL
     assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
@@ -76,13 +98,14 @@ def test_gmres_check_every_is_transparent(env):
     np.testing.assert_array_equal(x1, x4)
 
 
-@pytest.mark.parametrize("small_n", [8192, 0])
-def test_gmres_dafrt_matches_oracle(env, small_n):
+@pytest.mark.parametrize("path", PATHS)
+def test_gmres_dafrt_matches_oracle(env, monkeypatch, path):
     xb, dev = env
     A = gen.poisson2d(24)
+    small_n = _path(monkeypatch, path)
     info, x, b = _solve(xb, dev, A, "gmres", m=2, m_max=17, tol=TOL, dafrt=1, dafrt_theta=10.0,
                         dafrt_window=5, dafrt_dm=5, maxiter=3000, small_n=small_n)
-    assert info["persistent"] == (1 if small_n else 0)
+    assert info["persistent"] == _persistent(path, A)
     xo, io = oracle.gmres(A, b, m=2, m_max=17, tol=TOL, maxiter=3000, dafrt=True, theta=10.0,
                           window=5, dm=5)
     assert info["m_final"] == io["m_final"] and info["m_final"] > 2
@@ -90,9 +113,10 @@ def test_gmres_dafrt_matches_oracle(env, small_n):
     assert info["status"] == io["status"]
 
 
-@pytest.mark.parametrize("small_n", [8192, 0])
-def test_gmres_edge_cases(env, small_n):
+@pytest.mark.parametrize("path", PATHS)
+def test_gmres_edge_cases(env, monkeypatch, path):
     xb, dev = env
+    small_n = _path(monkeypatch, path)
     A = gen.poisson2d(10)
     n = A["n"]
     info, x, _ = _solve(xb, dev, A, "gmres", b=np.zeros(n), x0=np.ones(n), small_n=small_n)
@@ -111,6 +135,41 @@ def test_gmres_edge_cases(env, small_n):
     assert info["status"] == xb.XB_EBREAKDOWN
     info, x, b = _solve(xb, dev, Z, "bicgstab", b=np.ones(6))
     assert info["status"] == xb.XB_EBREAKDOWN
+
+
+@pytest.mark.parametrize("ncl,mat,m", [
+    (2, "convdiff9", 23), (4, "convdiff9", 23), (8, "convdiff9", 23), (16, "convdiff9", 23),
+    (2, "poisson44", 10), (16, "poisson44", 10)])
+@pytest.mark.parametrize("ortho", ["mgs", "bcgs"])
+def test_gmres_resident_cluster_sizes(env, monkeypatch, ncl, mat, m, ortho):
+    """The shared-memory path on each cluster size and rows-per-thread count
+    (convdiff9, n = 729: 365 / 183 / 92 / 46 rows per CTA, 4 / 2 / 1 / 1 rows
+    per thread; poisson44, n = 1936: 968 rows per CTA, 8 per thread, or 121;
+    the last CTA holds fewer rows than the others), both Gram-Schmidt forms,
+    against the oracle's GMRES with the same orthogonalisation."""
+    xb, dev = env
+    monkeypatch.setenv("XB_RESIDENT_CL", str(ncl))
+    A = gen.convdiff3d(N=9) if mat == "convdiff9" else gen.poisson2d(44)
+    oc = xb.ORTHO_MGS if ortho == "mgs" else xb.ORTHO_BCGS
+    info, x, b = _solve(xb, dev, A, "gmres", m=m, tol=1e-10, ortho=oc, maxiter=20000)
+    xo, io = oracle.gmres(A, b, m=m, tol=1e-10, maxiter=20000,
+                          ortho=oracle.MGS if ortho == "mgs" else oracle.BCGS)
+    assert info["persistent"] == 2 and info["status"] == 0, info
+    assert _true_rel(A, x, b) <= 1e-10
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
+    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+def test_gmres_resident_declines_long_rows(env, monkeypatch):
+    """Rows longer than 64 entries do not take the shared-memory path: the
+    batched kernel runs the system instead."""
+    xb, dev = env
+    monkeypatch.delenv("XB_RESIDENT_CL", raising=False)
+    A = gen.powerlaw(n=3000, seed=9)
+    assert np.diff(A["rowptr"]).max() > 64
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, maxiter=20000)
+    assert info["persistent"] == 1 and info["status"] == 0
+    assert _true_rel(A, x, b) <= TOL
 
 
 @pytest.mark.parametrize("name,make", [
