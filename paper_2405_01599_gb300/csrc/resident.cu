@@ -29,17 +29,26 @@
 // buffers alternate, and a buffer is rewritten only after a cluster barrier
 // that follows every read of it.
 //
-// Reductions.  One, or four at once, sums over the cluster cost one cluster
-// barrier: each warp reduces its lanes' partials with shuffles (four sums in
-// a transposed tree: 6 adds rather than 20), and lanes store the warp's sums
-// into the same slot of every CTA's slot array (st.shared::cluster); after the
-// barrier every warp sums the P = 4 ncl slots in one fixed order, so every
-// thread of the cluster holds the same bits and takes the same branches.  Two
-// slot arrays alternate: one is rewritten only after the barrier of the
-// reduction that follows its last read.  Every barrier sits on a path whose
-// conditions are such reduced values or step counts, so all threads of the
-// cluster reach the same barriers in the same order, and no CTA touches
-// another's shared memory after the last barrier.
+// Reductions.  One, or four at once, sums over the cluster: each warp
+// reduces its lanes' partials with shuffles (four sums in a transposed tree:
+// 6 adds rather than 20), and lanes store the warp's sums into the same slot
+// of every CTA's slot array; every warp then sums the P = 4 ncl slots in one
+// fixed order, so every thread of the cluster holds the same bits and takes
+// the same branches.  The inner products of the Gram-Schmidt passes complete
+// through mbarriers: the stores are st.async with complete-tx on the
+// receiving CTA's mbarrier, and each CTA waits on its own mbarrier for all P
+// contributions -- no fence and no cluster barrier.  Two slot arrays and two
+// mbarriers alternate; a CTA can send the sums of reduction k + 2 only after
+// receiving every warp's sums of k + 1, which each warp sends only after it
+// has read its slots of k, and thread 0 re-arms an mbarrier right after its
+// wait, so the expected byte count is set before any contribution to the next
+// use can arrive.  Sums that must also publish a vector (the norm of w, the
+// residual) use a cluster barrier (release / acquire) over a second pair of
+// slot arrays.  Every barrier sits on a path whose conditions are such
+// reduced values or step counts, so all threads of the cluster reach the same
+// barriers in the same order; a final cluster barrier keeps every CTA's
+// shared memory alive until no CTA can write to it.  An mbarrier wait gives
+// up after 2 s (XB_ETIMEOUT), which a correct exchange never reaches.
 
 #include "common.cuh"
 
@@ -56,7 +65,7 @@ constexpr int kBT = 32 * kW;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct ResArgs {
-    int n, rpc, ncl, lmax, m, m_max, maxiter, bcgs;
+    int n, rpc, lmax, m, m_max, maxiter, bcgs;
     double tol, theta;
     unsigned long long budget_ns;
     const int *rowptr, *col;
@@ -67,7 +76,7 @@ struct ResArgs {
 
 // Byte offsets of the dynamic shared memory regions (doubles first).
 struct ResLayout {
-    size_t V, W, ev, red, H, cs, sn, g, y, ea, total;
+    size_t V, W, ev, bs, ms, H, cs, sn, g, y, ea, mb, total;
 };
 
 __host__ __device__ inline ResLayout res_layout(int rpp, int lmax, int mmax, int P) {
@@ -81,13 +90,15 @@ __host__ __device__ inline ResLayout res_layout(int rpp, int lmax, int mmax, int
     L.V = take((size_t)(mmax + 1) * rpp * 8);
     L.W = take((size_t)2 * rpp * 8);
     L.ev = take((size_t)lmax * rpp * 8);
-    L.red = take((size_t)2 * 4 * P * 8);
+    L.bs = take((size_t)2 * 4 * P * 8);  // barrier-completed slots
+    L.ms = take((size_t)2 * 4 * P * 8);  // mbarrier-completed slots
     L.H = take((size_t)(mmax + 1) * mmax * 8);
     L.cs = take((size_t)mmax * 8);
     L.sn = take((size_t)mmax * 8);
     L.g = take((size_t)(mmax + 1) * 8);
     L.y = take((size_t)mmax * 8);
     L.ea = take((size_t)lmax * rpp * 4);
+    L.mb = take(2 * 8 + 4);  // two mbarriers, the abort flag
     L.total = o;
     return L;
 }
@@ -119,6 +130,36 @@ __device__ __forceinline__ void st_cluster(unsigned a, double v) {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
+// Store v at shared::cluster address a and complete 8 bytes of the
+// transaction count of the mbarrier at shared::cluster address mb (same CTA).
+__device__ __forceinline__ void st_async(unsigned a, double v, unsigned mb) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(a),
+                 "l"(__double_as_longlong(v)), "r"(mb)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mb_init(unsigned a) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+}
+
+// The one arrival of a phase, expecting `bytes` of transactions.
+__device__ __forceinline__ void mb_arm(unsigned a, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mb_test(unsigned a, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Cluster barrier in two halves: stores before the arrive are visible to
 // loads after the wait in every CTA; work between them overlaps the barrier.
 __device__ __forceinline__ void cl_arrive() {
@@ -132,6 +173,12 @@ __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
     asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
+}
+
+__device__ __forceinline__ double warp_sum1(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
 }
 
 // Sum of four values over the warp, transposed: every lane returns the sum
@@ -151,57 +198,116 @@ __device__ __forceinline__ double warp_sum4(const double (&v)[4]) {
     return k;
 }
 
-struct Red {
-    double *slots;  // 2 phases x 4 sums x P partials
-    int P, slot, ncl, phase;
-};
-
-// Stage 1 of one cluster sum: the warp's sum into every CTA's slot, arrive.
-__device__ __forceinline__ void put1(double v, const Red &R) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+// Sum over the P = 4 NCL slots at `base` (one value), in a fixed order:
+// lane l holds slots l (and l + 32), then log2 P levels of the tree.
+template <int NCL>
+__device__ __forceinline__ double slots_sum1(const double *base) {
+    constexpr int P = 4 * NCL;
     const int lane = threadIdx.x & 31;
-    if (lane < R.ncl)
-        st_cluster(map_rank(smem_addr(R.slots + (size_t)R.phase * 4 * R.P + R.slot), (unsigned)lane),
-                   v);
-    cl_arrive();
-}
-
-// Stage 2: wait, then the P slots summed in a fixed order (log2 P adds).
-__device__ __forceinline__ double get1(Red &R) {
-    cl_wait();
-    const double *base = R.slots + (size_t)R.phase * 4 * R.P;
-    const int lane = threadIdx.x & 31;
-    double s = lane < R.P ? base[lane] : 0.0;
-    if (R.P > 32) s += base[32 + lane];
-    for (int o = min(R.P, 32) >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    R.phase ^= 1;
+    double s = lane < P ? base[lane] : 0.0;
+    if (P > 32) s += base[32 + lane];
+#pragma unroll
+    for (int o = (P < 32 ? P : 32) >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     return __shfl_sync(kFull, s, 0);
 }
 
-// The same for four sums at once.
-__device__ __forceinline__ void put4(const double (&v)[4], const Red &R) {
-    const double k = warp_sum4(v);  // sum of value lane >> 3
-    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
-    double *dst = R.slots + (size_t)R.phase * 4 * R.P + q * R.P + R.slot;
-    if (r < R.ncl) st_cluster(map_rank(smem_addr(dst), (unsigned)r), k);
-    if (r + 8 < R.ncl) st_cluster(map_rank(smem_addr(dst), (unsigned)(r + 8)), k);
-    cl_arrive();
-}
-
-__device__ __forceinline__ void get4(double (&v)[4], Red &R) {
-    cl_wait();
-    const double *base = R.slots + (size_t)R.phase * 4 * R.P;
+// Four sums over the P slots of each of base[q P ...].
+template <int NCL>
+__device__ __forceinline__ void slots_sum4(const double *base, double (&v)[4]) {
+    constexpr int P = 4 * NCL;
     const int lane = threadIdx.x & 31;
     double a[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        a[q] = lane < R.P ? base[q * R.P + lane] : 0.0;
-        if (R.P > 32) a[q] += base[q * R.P + 32 + lane];
+        a[q] = lane < P ? base[q * P + lane] : 0.0;
+        if (P > 32) a[q] += base[q * P + 32 + lane];
     }
     const double k = warp_sum4(a);
 #pragma unroll
     for (int q = 0; q < 4; q++) v[q] = __shfl_sync(kFull, k, 8 * q);
-    R.phase ^= 1;
+}
+
+template <int NCL>
+struct Red {
+    static constexpr int P = 4 * NCL;
+    double *bs, *ms;       // barrier / mbarrier slots: 2 phases x 4 sums x P
+    unsigned mb;           // shared address of the two mbarriers
+    volatile int *abort;   // set when an mbarrier wait gave up
+    int slot, bph, mk, K;  // this warp's slot, phases, sums per mbarrier exchange
+};
+
+// Barrier-completed sum of one value (also publishes the caller's earlier
+// shared stores to the cluster): put, then the work between, then get.
+template <int NCL>
+__device__ __forceinline__ void bput1(double v, const Red<NCL> &R) {
+    v = warp_sum1(v);
+    const int lane = threadIdx.x & 31;
+    if (lane < NCL)
+        st_cluster(map_rank(smem_addr(R.bs + R.bph * 4 * R.P + R.slot), (unsigned)lane), v);
+    cl_arrive();
+}
+template <int NCL>
+__device__ __forceinline__ double bget1(Red<NCL> &R) {
+    cl_wait();
+    const double s = slots_sum1<NCL>(R.bs + R.bph * 4 * R.P);
+    R.bph ^= 1;
+    return s;
+}
+template <int NCL>
+__device__ __forceinline__ void bput4(const double (&v)[4], const Red<NCL> &R) {
+    const double k = warp_sum4(v);  // sum of value lane >> 3
+    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7;
+    const unsigned dst = smem_addr(R.bs + R.bph * 4 * R.P + q * R.P + R.slot);
+    if (r < NCL) st_cluster(map_rank(dst, (unsigned)r), k);
+    if (r + 8 < NCL) st_cluster(map_rank(dst, (unsigned)(r + 8)), k);
+    cl_arrive();
+}
+template <int NCL>
+__device__ __forceinline__ void bget4(double (&v)[4], Red<NCL> &R) {
+    cl_wait();
+    slots_sum4<NCL>(R.bs + R.bph * 4 * R.P, v);
+    R.bph ^= 1;
+}
+
+// mbarrier-completed sums (R.K values: 1 for MGS, 4 for BCGS).
+template <int NCL>
+__device__ __forceinline__ void mput1(double v, const Red<NCL> &R) {
+    v = warp_sum1(v);
+    const int lane = threadIdx.x & 31, p = R.mk & 1;
+    if (lane < NCL)
+        st_async(map_rank(smem_addr(R.ms + p * 4 * R.P + R.slot), (unsigned)lane), v,
+                 map_rank(R.mb + 8 * p, (unsigned)lane));
+}
+template <int NCL>
+__device__ __forceinline__ void mput4(const double (&v)[4], const Red<NCL> &R) {
+    const double k = warp_sum4(v);
+    const int lane = threadIdx.x & 31, q = lane >> 3, r = lane & 7, p = R.mk & 1;
+    const unsigned dst = smem_addr(R.ms + p * 4 * R.P + q * R.P + R.slot), mb = R.mb + 8 * p;
+    if (r < NCL) st_async(map_rank(dst, (unsigned)r), k, map_rank(mb, (unsigned)r));
+    if (r + 8 < NCL) st_async(map_rank(dst, (unsigned)(r + 8)), k, map_rank(mb, (unsigned)(r + 8)));
+}
+// Wait for this CTA's mbarrier of the current exchange (2 s limit), re-arm it
+// for the exchange after next, return the slots.
+template <int NCL>
+__device__ __forceinline__ const double *mwait(Red<NCL> &R) {
+    const int p = R.mk & 1;
+    const unsigned a = R.mb + 8 * p, par = (unsigned)(R.mk >> 1) & 1u;
+    bool done = mb_test(a, par);
+    if (!done) {
+        const unsigned long long t0 = gtimer();
+        while (!(done = mb_test(a, par))) {
+            if (*R.abort) break;
+            if (gtimer() - t0 > 2000000000ull) {
+                *R.abort = 1;
+                break;
+            }
+        }
+    }
+    // re-arm only a completed phase (after a timeout the exchange is lost and
+    // every later wait returns at once)
+    if (threadIdx.x == 0 && done) mb_arm(a, (unsigned)(R.K * R.P * 8));
+    R.mk++;
+    return R.ms + p * 4 * R.P;
 }
 
 // (A u)_row for the published vector u in shared buffer `buf` (local shared
@@ -218,12 +324,12 @@ __device__ __forceinline__ double row_spmv(const double *__restrict__ ev, const 
     return s;
 }
 
-template <int R>
+template <int R, int NCL>
 __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int rpp = kBT * R;
     const int mmax = A.m_max, ldh = mmax + 1;
-    const ResLayout L = res_layout(rpp, A.lmax, mmax, A.ncl * kW);
+    const ResLayout L = res_layout(rpp, A.lmax, mmax, 4 * NCL);
     double *V = reinterpret_cast<double *>(smem + L.V);
     double *W = reinterpret_cast<double *>(smem + L.W);
     double *ev = reinterpret_cast<double *>(smem + L.ev);
@@ -235,7 +341,23 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
     int *ea = reinterpret_cast<int *>(smem + L.ea);
     const unsigned rank = cluster_rank();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    Red Rd{reinterpret_cast<double *>(smem + L.red), A.ncl * kW, (int)rank * kW + warp, A.ncl, 0};
+    Red<NCL> Rd;
+    Rd.bs = reinterpret_cast<double *>(smem + L.bs);
+    Rd.ms = reinterpret_cast<double *>(smem + L.ms);
+    Rd.mb = smem_addr(smem + L.mb);
+    Rd.abort = reinterpret_cast<volatile int *>(smem + L.mb + 16);
+    Rd.slot = (int)rank * kW + warp;
+    Rd.bph = 0;
+    Rd.mk = 0;
+    Rd.K = A.bcgs ? 4 : 1;
+    if (t == 0) {
+        *Rd.abort = 0;
+        mb_init(Rd.mb);
+        mb_init(Rd.mb + 8);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mb_arm(Rd.mb, (unsigned)(Rd.K * Rd.P * 8));
+        mb_arm(Rd.mb + 8, (unsigned)(Rd.K * Rd.P * 8));
+    }
     const bool lead = rank == 0 && t == 0;
     const unsigned long long ts = gtimer(), deadline = ts + A.budget_ns;
 
@@ -274,8 +396,10 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
     double q4[4] = {0.0, bad, 0.0, 0.0};
 #pragma unroll
     for (int r = 0; r < R; r++) q4[0] = fma(bi[r], bi[r], q4[0]);
-    put4(q4, Rd);  // the barrier also orders the ELL copy before any gather
-    get4(q4, Rd);
+    // the first barrier also orders the mbarrier set-up and the ELL copy
+    // before any exchange or gather
+    bput4(q4, Rd);
+    bget4(q4, Rd);
     const double bnorm = sqrt(q4[0]);
     int wb = 0;  // buffer the next publication goes to
     if (q4[1] > 0.0) {
@@ -302,11 +426,16 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                 q4[0] = fma(rs[r], rs[r], q4[0]);
             }
             q4[1] = (lead && gtimer() > deadline) ? 1.0 : 0.0;
-            q4[2] = q4[3] = 0.0;
-            put4(q4, Rd);
-            get4(q4, Rd);
+            q4[2] = *Rd.abort ? 1.0 : 0.0;
+            q4[3] = 0.0;
+            bput4(q4, Rd);
+            bget4(q4, Rd);
             const double beta = sqrt(q4[0]);
             res_true = beta / bnorm;
+            if (q4[2] > 0.0) {
+                status = XB_ETIMEOUT;
+                break;
+            }
             if (res_true <= A.tol) {
                 status = XB_OK;
                 break;
@@ -342,27 +471,24 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     w[r] = row_spmv(ev, ea, len[r], rpp, r * kBT + t, wbuf[wb]) * sc;
                 double len2 = 0.0, tt = 0.0;
                 // Givens rotations of the previous columns, applied as the
-                // column's entries arrive (each between the arrive and the
-                // wait of the next barrier): tt is entry i rotated by
-                // G_0..G_{i-1}
+                // column's entries arrive (while the next exchange is in
+                // flight): tt is entry i rotated by G_0..G_{i-1}
                 auto take = [&](int i, double h) {
                     len2 = fma(h, h, len2);
                     if (i == 0) {
                         tt = h;
                     } else {
                         const double c = cs[i - 1], s = sn[i - 1];
-                        if (t == 0) H[(size_t)j * ldh + i - 1] = fma(c, tt, s * h);
+                        if (t == 0) H[j * ldh + i - 1] = fma(c, tt, s * h);
                         tt = fma(-s, tt, c * h);
                     }
                 };
-                const double *Vj = V + (size_t)j * rpp;
                 double *wn = W + (wb ^ 1) * rpp;
                 double last[4];
-                int nlast;
-                int i_last;
+                int nlast, i_last;
                 if (A.bcgs) {
-                    // blocks of 4: one barrier per block takes the block's dots
-                    // after the previous block's projection
+                    // blocks of 4: one exchange per block takes the block's
+                    // dots after the previous block's projection
                     double c4[4] = {0.0, 0.0, 0.0, 0.0};
                     int u0 = 0, nu = 0;
                     for (int d0 = 0; d0 <= j; d0 += 4) {
@@ -373,16 +499,16 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                             const int l = r * kBT + t;
 #pragma unroll
                             for (int q = 0; q < 4; q++)
-                                if (q < nu) w[r] = fma(-c4[q], V[(size_t)(u0 + q) * rpp + l], w[r]);
+                                if (q < nu) w[r] = fma(-c4[q], V[(u0 + q) * rpp + l], w[r]);
 #pragma unroll
                             for (int q = 0; q < 4; q++)
-                                if (q < nd) a4[q] = fma(w[r], V[(size_t)(d0 + q) * rpp + l], a4[q]);
+                                if (q < nd) a4[q] = fma(w[r], V[(d0 + q) * rpp + l], a4[q]);
                         }
-                        put4(a4, Rd);
+                        mput4(a4, Rd);
 #pragma unroll
                         for (int q = 0; q < 4; q++)
                             if (q < nu) take(u0 + q, c4[q]);
-                        get4(a4, Rd);
+                        slots_sum4<NCL>(mwait(Rd), a4);
 #pragma unroll
                         for (int q = 0; q < 4; q++) c4[q] = a4[q];
                         u0 = d0;
@@ -393,7 +519,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                         const int l = r * kBT + t;
 #pragma unroll
                         for (int q = 0; q < 4; q++)
-                            if (q < nu) w[r] = fma(-c4[q], V[(size_t)(u0 + q) * rpp + l], w[r]);
+                            if (q < nu) w[r] = fma(-c4[q], V[(u0 + q) * rpp + l], w[r]);
                     }
 #pragma unroll
                     for (int q = 0; q < 4; q++) last[q] = c4[q];
@@ -408,15 +534,15 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
 #pragma unroll
                         for (int r = 0; r < R; r++) {
                             const int l = r * kBT + t;
-                            if (i > 0) w[r] = fma(-hprev, V[(size_t)(i - 1) * rpp + l], w[r]);
-                            a = fma(w[r], V[(size_t)i * rpp + l], a);
+                            if (i > 0) w[r] = fma(-hprev, V[(i - 1) * rpp + l], w[r]);
+                            a = fma(w[r], V[i * rpp + l], a);
                         }
-                        put1(a, Rd);
+                        mput1(a, Rd);
                         if (i > 0) take(i - 1, hprev);
-                        hprev = get1(Rd);
+                        hprev = slots_sum1<NCL>(mwait(Rd));
                     }
 #pragma unroll
-                    for (int r = 0; r < R; r++) w[r] = fma(-hprev, Vj[r * kBT + t], w[r]);
+                    for (int r = 0; r < R; r++) w[r] = fma(-hprev, V[j * rpp + r * kBT + t], w[r]);
                     last[0] = hprev;
                     nlast = 1;
                     i_last = j;
@@ -428,9 +554,9 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     wn[r * kBT + t] = w[r];  // published by the norm's barrier
                     a = fma(w[r], w[r], a);
                 }
-                put1(a, Rd);
+                bput1(a, Rd);
                 for (int q = 0; q < nlast; q++) take(i_last + q, last[q]);
-                const double hn2 = get1(Rd);
+                const double hn2 = bget1(Rd);
                 // the new rotation, from values every thread holds alike
                 // (|h| <= ||A|| sqrt(m): no overflow in tt^2 + hn^2)
                 int flag = 0;
@@ -443,7 +569,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     if (t == 0) {
                         cs[j] = c;
                         sn[j] = s;
-                        H[(size_t)j * ldh + j] = rr2 * irr;
+                        H[j * ldh + j] = rr2 * irr;
                         g[j] = c * gj;
                     }
                     gj = -s * gj;
@@ -461,7 +587,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     break;
                 }
                 sc = ihn;
-                double *Vn = V + (size_t)(j + 1) * rpp;
+                double *Vn = V + (j + 1) * rpp;
 #pragma unroll
                 for (int r = 0; r < R; r++) Vn[r * kBT + t] = w[r] * sc;
                 if (flag == 3) {
@@ -481,7 +607,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                 for (int q = 0; q < QM; q++) {
                     const int c = lane + 32 * q;
                     gl[q] = c < k ? g[c] : 0.0;
-                    dl[q] = c < k ? 1.0 / H[(size_t)c * ldh + c] : 0.0;
+                    dl[q] = c < k ? 1.0 / H[c * ldh + c] : 0.0;
                 }
                 for (int i = k - 1; i >= 0; i--) {
                     const int qi = i >> 5, li = i & 31;
@@ -497,7 +623,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
 #pragma unroll
                     for (int q = 0; q < QM; q++) {
                         const int c = lane + 32 * q;
-                        if (32 * q < i && c < i) gl[q] = fma(-H[(size_t)i * ldh + c], yi, gl[q]);
+                        if (32 * q < i && c < i) gl[q] = fma(-H[i * ldh + c], yi, gl[q]);
                     }
                 }
             }
@@ -505,13 +631,13 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 double s0 = 0.0;
-                for (int i = 0; i < k; i++) s0 = fma(yv[i], V[(size_t)i * rpp + r * kBT + t], s0);
+                for (int i = 0; i < k; i++) s0 = fma(yv[i], V[i * rpp + r * kBT + t], s0);
                 x[r] += s0;
             }
             restarts++;
         }
     }
-    if (status != XB_EINVAL) {
+    if (status != XB_EINVAL && status != XB_ETIMEOUT) {
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int l = r * kBT + t, row = (int)rank * A.rpc + l;
@@ -529,16 +655,30 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
         inf.ms = (double)(gtimer() - ts) * 1e-6;
         *A.out = inf;
     }
+    // no CTA leaves while another may still write to its shared memory
+    cl_arrive();
+    cl_wait();
 }
 
 typedef void (*ResKernel)(const ResArgs);
 
-ResKernel res_kernel(int R) {
+template <int R>
+ResKernel res_kernel_r(int ncl) {
+    switch (ncl) {
+        case 2: return k_gmres_resident<R, 2>;
+        case 4: return k_gmres_resident<R, 4>;
+        case 8: return k_gmres_resident<R, 8>;
+        case 16: return k_gmres_resident<R, 16>;
+        default: return nullptr;
+    }
+}
+
+ResKernel res_kernel(int R, int ncl) {
     switch (R) {
-        case 1: return k_gmres_resident<1>;
-        case 2: return k_gmres_resident<2>;
-        case 4: return k_gmres_resident<4>;
-        case 8: return k_gmres_resident<8>;
+        case 1: return res_kernel_r<1>(ncl);
+        case 2: return res_kernel_r<2>(ncl);
+        case 4: return res_kernel_r<4>(ncl);
+        case 8: return res_kernel_r<8>(ncl);
         default: return nullptr;
     }
 }
@@ -586,13 +726,14 @@ int resident_gmres(xb_plan *p, const double *b, double *x, const xb_options &o, 
     std::memset(&a, 0, sizeof a);
     size_t bytes = 0;
     ResKernel kern = nullptr;
+    int chosen = 0;
     for (int z = 0; z < no; z++) {
         const int ncl = order[z];
         if (ncl != 2 && ncl != 4 && ncl != 8 && ncl != 16) continue;
         const int rpc = (p->n + ncl - 1) / ncl;
         int R = 1;
         while (R * kBT < rpc) R *= 2;
-        ResKernel kf = res_kernel(R);
+        ResKernel kf = res_kernel(R, ncl);
         if (!kf) continue;
         const ResLayout L = res_layout(kBT * R, lmax, mmax, ncl * kW);
         if (L.total > (size_t)optin) continue;
@@ -615,7 +756,7 @@ int resident_gmres(xb_plan *p, const double *b, double *x, const xb_options &o, 
             cudaGetLastError();
             continue;
         }
-        a.ncl = ncl;
+        chosen = ncl;
         a.rpc = rpc;
         bytes = L.total;
         kern = kf;
@@ -642,10 +783,10 @@ int resident_gmres(xb_plan *p, const double *b, double *x, const xb_options &o, 
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = a.ncl;
+    at[0].val.clusterDim.x = chosen;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(a.ncl);
+    cfg.gridDim = dim3(chosen);
     cfg.blockDim = dim3(kBT);
     cfg.dynamicSmemBytes = bytes;
     cfg.stream = s;
@@ -671,6 +812,8 @@ int resident_gmres(xb_plan *p, const double *b, double *x, const xb_options &o, 
                  (r.restarts + 1) * (spmv_alg_bytes(p, true, 8) + 16.0 * n);
     if (r.status == XB_EINVAL)
         return set_error(XB_EINVAL, "gmres: column index outside [0, n) in the matrix");
+    if (r.status == XB_ETIMEOUT)
+        return set_error(XB_ETIMEOUT, "gmres: an inner-product exchange of the cluster timed out");
     if (r.status == XB_ENOCONV)
         return set_error(XB_ENOCONV, "not converged: ||b-Ax||/||b|| = %.3e > tol %.1e", r.res_true,
                          o.tol);
