@@ -208,7 +208,8 @@ __device__ __forceinline__ double slots_sum1(const double *base) {
     if (P > 32) s += base[32 + lane];
 #pragma unroll
     for (int o = (P < 32 ? P : 32) >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    return __shfl_sync(kFull, s, 0);
+    // P >= 32: every lane took part, the butterfly left the total everywhere
+    return P >= 32 ? s : __shfl_sync(kFull, s, 0);
 }
 
 // Four sums over the P slots of each of base[q P ...].
@@ -576,6 +577,9 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     if (hn2 <= 1e-28 * (len2 + hn2)) flag = 1;  // hn <= 1e-14 |column|
                     else if (fabs(gj) <= tol_g) flag = 3;
                 }
+                // thread 0's rotation, g and the column's entries (stored by
+                // the warps in turn) visible to the CTA before their next use
+                __syncthreads();
                 if (flag == 2) {
                     k = j;
                     status = XB_EBREAKDOWN;

@@ -160,6 +160,21 @@ def test_gmres_resident_cluster_sizes(env, monkeypatch, ncl, mat, m, ortho):
     assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("ortho", ["mgs", "bcgs"])
+def test_gmres_resident_is_repeatable(env, monkeypatch, ortho):
+    """The shared-memory path sums in one fixed order whatever the timing of
+    the exchanges, so repeated solves give the same iterate bit for bit."""
+    xb, dev = env
+    monkeypatch.delenv("XB_RESIDENT_CL", raising=False)
+    A = gen.poisson2d(64)
+    oc = xb.ORTHO_MGS if ortho == "mgs" else xb.ORTHO_BCGS
+    runs = [_solve(xb, dev, A, "gmres", m=30, tol=1e-8, ortho=oc) for _ in range(4)]
+    assert all(i["persistent"] == 2 and i["status"] == 0 for i, _, _ in runs)
+    assert len({i["iters"] for i, _, _ in runs}) == 1
+    for _, x, _ in runs[1:]:
+        np.testing.assert_array_equal(x, runs[0][1])
+
+
 def test_gmres_resident_declines_long_rows(env, monkeypatch):
     """Rows longer than 64 entries do not take the shared-memory path: the
     batched kernel runs the system instead."""
