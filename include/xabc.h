@@ -676,7 +676,9 @@ int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, i
  * else MGS; others are rejected).  Per system:
  * m in [1, XB_BATCH_MAX_M] and the SpMV mode inside the CTA (0: thread per
  * row; 1: thread per row in warp-sized row blocks, rows longer than 32
- * non-zeros taken by the whole warp), as chosen by a tuner; zero_x = 1 makes the kernel
+ * non-zeros taken by the whole warp, rows longer than 1024 by the whole CTA
+ * after the blocks -- xb_batch_create reads each mode-1 system's row pointer
+ * once to list them), as chosen by a tuner; zero_x = 1 makes the kernel
  * start from x = 0 (so a replay repeats the same solve). */
 #define XB_BATCH_MAX_M 128
 typedef struct xb_batch_sys {

@@ -39,6 +39,7 @@ namespace {
 constexpr int kCl = 8;          // CTAs per cluster
 constexpr int kBT = 512;        // threads per CTA
 constexpr int kLargeN = 30000;  // systems this large are solved by a whole cluster
+constexpr int kCtaRow = 1024;   // mode 1: rows longer than this are summed by the whole CTA
 }  // namespace
 
 struct xb_batch_dev {
@@ -49,6 +50,8 @@ struct xb_batch_dev {
     double *x;
     double *V;  // (m_max+1) * ld basis
     double *H;  // per cooperating CTA: (m_max+1) * m_max Hessenberg (column-major)
+    const int *lrows;  // mode 1: the rows longer than kCtaRow, ascending
+    int nl;
 };
 
 struct xb_batch {
@@ -57,6 +60,7 @@ struct xb_batch {
     xb_batch_info *d_info = nullptr;
     int *d_order = nullptr, *d_queue = nullptr;
     double *d_ws = nullptr;
+    int *d_lrows = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
@@ -169,25 +173,33 @@ __device__ __forceinline__ void coop_barrier(const Part &P) {
 //   mode 0: one thread per row;
 //   mode 1: rows in warp-sized blocks, one thread per row, except that rows
 //           longer than 32 non-zeros are taken by the whole warp in turn
-//           (lanes stride over the row, shuffle reduction), so a power-law
-//           row of thousands of entries does not serialise one thread.
+//           (lanes stride over the row, shuffle reduction), and rows longer
+//           than kCtaRow (the system's list, ascending) by the whole CTA
+//           after the blocks, so a power-law row of thousands of entries
+//           neither serialises one thread nor one warp.
+// Every row's sum has one fixed order (its stride and four interleaved
+// partial sums), so results do not depend on scheduling.
 __device__ __forceinline__ double row_dot(const int *__restrict__ col,
                                           const double *__restrict__ val, const double *x,
                                           int ka, int kb, int step) {
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int k = ka;
-    for (; k + step < kb; k += 2 * step) {
-        const int c0 = __ldg(col + k), c1 = __ldg(col + k + step);
-        const double v0 = __ldg(val + k), v1 = __ldg(val + k + step);
+    for (; k + 3 * step < kb; k += 4 * step) {  // four gathers in flight
+        const int c0 = __ldg(col + k), c1 = __ldg(col + k + step), c2 = __ldg(col + k + 2 * step),
+                  c3 = __ldg(col + k + 3 * step);
+        const double v0 = __ldg(val + k), v1 = __ldg(val + k + step), v2 = __ldg(val + k + 2 * step),
+                     v3 = __ldg(val + k + 3 * step);
         s0 = fma(v0, __ldcg(x + c0), s0);
         s1 = fma(v1, __ldcg(x + c1), s1);
+        s2 = fma(v2, __ldcg(x + c2), s2);
+        s3 = fma(v3, __ldcg(x + c3), s3);
     }
-    if (k < kb) s0 = fma(__ldg(val + k), __ldcg(x + __ldg(col + k)), s0);
-    return s0 + s1;
+    for (; k < kb; k += step) s0 = fma(__ldg(val + k), __ldcg(x + __ldg(col + k)), s0);
+    return (s0 + s1) + (s2 + s3);
 }
 
-__device__ void part_spmv(const xb_batch_dev &D, const Part &P, double alpha, const double *x,
-                          double beta, double *y) {
+__device__ void part_spmv(const xb_batch_dev &D, const Part &P, Smem &S, double alpha,
+                          const double *x, double beta, double *y) {
     const int *__restrict__ rp = D.rowptr;
     if (D.mode == 0) {
         for (int r = P.r0 + threadIdx.x; r < P.r1; r += blockDim.x) {
@@ -203,8 +215,9 @@ __device__ void part_spmv(const xb_batch_dev &D, const Part &P, double alpha, co
                 ka = __ldg(rp + r);
                 kb = __ldg(rp + r + 1);
             }
-            const bool lng = kb - ka > 32;
-            double s = lng ? 0.0 : row_dot(D.col, D.val, x, ka, kb, 1);
+            const bool cta = kb - ka > kCtaRow;
+            const bool lng = kb - ka > 32 && !cta;
+            double s = (lng || cta) ? 0.0 : row_dot(D.col, D.val, x, ka, kb, 1);
             unsigned todo = __ballot_sync(0xffffffffu, lng);
             while (todo) {
                 const int src = __ffs(todo) - 1;
@@ -215,7 +228,24 @@ __device__ void part_spmv(const xb_batch_dev &D, const Part &P, double alpha, co
                 for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
                 if (lane == src) s = t;
             }
-            if (r < P.r1) y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
+            if (r < P.r1 && !cta) y[r] = beta == 0.0 ? alpha * s : fma(alpha, s, beta * y[r]);
+        }
+        if (D.nl > 0) {
+            // the CTA's long rows: first list entry >= r0 (binary search), up to r1
+            int lo = 0, hi = D.nl;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(D.lrows + mid) < P.r0) lo = mid + 1;
+                else hi = mid;
+            }
+            for (int q = lo; q < D.nl; q++) {  // CTA-uniform
+                const int r = __ldg(D.lrows + q);
+                if (r >= P.r1) break;
+                const int ka = __ldg(rp + r), kb = __ldg(rp + r + 1);
+                const double t = cta_sum(row_dot(D.col, D.val, x, ka + (int)threadIdx.x, kb,
+                                                 (int)blockDim.x), S);
+                if (threadIdx.x == 0) y[r] = beta == 0.0 ? alpha * t : fma(alpha, t, beta * y[r]);
+            }
         }
     }
     // rows were stored by other threads than the ones that read them next,
@@ -335,7 +365,7 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
             coop_barrier(P);  // x complete before A x
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) V[i] = D.b[i];
             __syncthreads();  // the SpMV reads V_0 rows through other threads
-            part_spmv(D, P, -1.0, D.x, 1.0, V);
+            part_spmv(D, P, S, -1.0, D.x, 1.0, V);
             a = 0.0;
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) a = fma(V[i], V[i], a);
             const double beta = sqrt(coop_sum(a, S, P));
@@ -375,7 +405,7 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
                 iters++;
                 double *w = V + (size_t)(j + 1) * ld;
                 coop_barrier(P);  // v_j complete
-                part_spmv(D, P, 1.0, V + (size_t)j * ld, 0.0, w);
+                part_spmv(D, P, S, 1.0, V + (size_t)j * ld, 0.0, w);
                 double len2 = 0.0, hn;
                 if (bcgs) {
                     // BCGS, block length 4: one pass per block applies the previous
@@ -583,7 +613,12 @@ int batch_single(xb_plan *p, const double *b, double *x, const xb_options &o, in
     const size_t nv = (size_t)(d.m_max + 1) * d.ld;
     const size_t nh = (size_t)(d.coop ? kCl : 1) * (d.m_max + 1) * d.m_max + 32;
     const size_t meta = 4096;  // descriptor, result, order, queue
-    XB_TRY(ensure_work(p, (nv + nh) * sizeof(double) + meta));
+    // mode 1: the rows longer than kCtaRow, from the plan's host row pointer
+    std::vector<int> lr;
+    if (mode == 1 && p->nnz > kCtaRow && (int)p->h_rowptr.size() == p->n + 1)
+        for (int r = 0; r < p->n; r++)
+            if (p->h_rowptr[r + 1] - p->h_rowptr[r] > kCtaRow) lr.push_back(r);
+    XB_TRY(ensure_work(p, (nv + nh) * sizeof(double) + meta + lr.size() * sizeof(int)));
     char *w = static_cast<char *>(p->d_work);
     d.V = reinterpret_cast<double *>(w);
     d.H = d.V + nv;
@@ -593,6 +628,13 @@ int batch_single(xb_plan *p, const double *b, double *x, const xb_options &o, in
     int *d_order = reinterpret_cast<int *>(m0 + 2048);
     int *d_queue = d_order + 1;
     static_assert(sizeof(xb_batch_dev) <= 1024 && sizeof(xb_batch_info) <= 1024, "meta layout");
+    d.nl = (int)lr.size();
+    d.lrows = nullptr;
+    if (!lr.empty()) {
+        int *d_lr = reinterpret_cast<int *>(m0 + meta);
+        XB_CUDA(cudaMemcpyAsync(d_lr, lr.data(), lr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        d.lrows = d_lr;
+    }
     const int zero = 0;
     XB_CUDA(cudaMemcpyAsync(d_sys, &d, sizeof d, cudaMemcpyHostToDevice, s));
     XB_CUDA(cudaMemcpyAsync(d_order, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
@@ -637,6 +679,7 @@ int xb_batch_destroy(xb_batch *bt) {
     cudaFree(bt->d_order);
     cudaFree(bt->d_queue);
     cudaFree(bt->d_ws);
+    cudaFree(bt->d_lrows);
     delete bt;
     return XB_OK;
 }
@@ -680,6 +723,23 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
         d.x = q.x;
         ws += (size_t)(d.m_max + 1) * d.ld + (size_t)(d.coop ? kCl : 1) * (d.m_max + 1) * d.m_max + 32;
     }
+    // mode 1: each system's rows longer than kCtaRow (summed by a whole CTA),
+    // from a host copy of its row pointer
+    std::vector<int> lr_all, rp_h;
+    std::vector<size_t> lr_off(count, 0);
+    for (int i = 0; i < count; i++) {
+        h[i].lrows = nullptr;
+        h[i].nl = 0;
+        if (h[i].mode != 1 || h[i].n < 1 || h[i].nnz <= kCtaRow) continue;
+        rp_h.resize((size_t)h[i].n + 1);
+        cudaError_t e = cudaMemcpy(rp_h.data(), h[i].rowptr, rp_h.size() * sizeof(int),
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return xb::cuda_error(e, "batch_create: read rowptr");
+        lr_off[i] = lr_all.size();
+        for (int r = 0; r < h[i].n; r++)
+            if (rp_h[r + 1] - rp_h[r] > kCtaRow) lr_all.push_back(r);
+        h[i].nl = (int)(lr_all.size() - lr_off[i]);
+    }
     xb_batch *bt = new xb_batch();
     bt->count = count;
     auto fail = [&](int code) {
@@ -690,6 +750,15 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(xb::set_error(XB_ENOMEM, "batch_create: %zu bytes of workspace", ws * 8));
+    }
+    if (!lr_all.empty()) {
+        e = cudaMalloc(&bt->d_lrows, lr_all.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(bt->d_lrows, lr_all.data(), lr_all.size() * sizeof(int),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(xb::cuda_error(e, "batch_create: long-row lists"));
+        for (int i = 0; i < count; i++)
+            if (h[i].nl > 0) h[i].lrows = bt->d_lrows + lr_off[i];
     }
     size_t off = 0;
     for (int i = 0; i < count; i++) {

@@ -79,6 +79,36 @@ def poisson2d(N, upper=False):
     return _mat(n, rp, c, v, upper, kind="poisson2d", side=N)
 
 
+def poisson2d_dense_rows(N, count=4, length=3000, seed=0):
+    """2D 5-point Poisson on an N x N grid with `count` rows (seeded choice)
+    widened to about `length` entries: each added entry (a distinct random
+    column) holds -1 / length, and those rows' diagonal grows by 1, so the
+    matrix stays diagonally dominant.  Skewed rows on a well-conditioned
+    system (for the long-row paths of the SpMV kernels)."""
+    A = poisson2d(N)
+    n = A["n"]
+    rng = np.random.default_rng(seed)
+    wide = set(int(r) for r in rng.choice(n, size=min(count, n), replace=False))
+    rp, ci, va = A["rowptr"], A["col"], A["val"]
+    rows_c, rows_v = [], []
+    for r in range(n):
+        c = ci[rp[r]:rp[r + 1]].astype(np.int64)
+        v = va[rp[r]:rp[r + 1]].copy()
+        if r in wide:
+            extra = np.setdiff1d(rng.choice(n, size=min(length, n), replace=False), c)
+            v = np.where(c == r, v + 1.0, v)
+            c = np.concatenate([c, extra])
+            v = np.concatenate([v, np.full(extra.size, -1.0 / length)])
+            o = np.argsort(c, kind="stable")
+            c, v = c[o], v[o]
+        rows_c.append(c)
+        rows_v.append(v)
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in rows_c])
+    return _mat(n, rowptr, np.concatenate(rows_c), np.concatenate(rows_v),
+                kind="poisson2d_dense_rows", side=N)
+
+
 def laplace3d(N, upper=False):
     """3D 7-point Laplacian on an N^3 grid: diagonal 6, neighbours -1."""
     co = {(0, 0, 0): 6.0}

@@ -65,6 +65,33 @@ def test_batch_matches_oracle_and_replays(coop_min, monkeypatch):
         assert r["iters"] == r2["iters"]
 
 
+@pytest.mark.parametrize("coop_min", ["16384", "1000000000"])
+def test_batch_long_rows_summed_by_the_cta(coop_min, monkeypatch):
+    """Mode 1 with rows longer than 1024 entries: the CTA (or each CTA of a
+    cluster, for the long rows in its slice) sums them after its warp blocks;
+    the solves match the oracle and replays are bit-identical."""
+    monkeypatch.setenv("XB_BATCH_COOP_MIN_N", coop_min)
+    xb, dev = lib_and_device()
+    specs = [(gen.poisson2d_dense_rows(60, count=3, length=1500, seed=1), 30, 1),
+             (gen.poisson2d_dense_rows(130, count=5, length=3000, seed=3), 30, 1),
+             (gen.poisson2d_dense_rows(45, count=2, length=1100, seed=5), 20, 1)]
+    assert all(np.diff(A["rowptr"]).max() > 1024 for A, _, _ in specs)
+    systems, mats = _systems(dev, specs)
+    bt = xb.Batch(systems, tol=1e-8, maxiter=20000, maxtime_s=60.0)
+    bt.run()
+    res = bt.results()
+    xs = [q["x"].cpu().numpy().copy() for q in systems]
+    for (A, b), r, x, (_, m, _) in zip(mats, res, xs, specs):
+        assert r["status"] == 0, r
+        rel = np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+        assert rel <= 1e-8
+        _, io = oracle.gmres(A, b, m=m, tol=1e-8)
+        assert abs(r["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (r, io["iters"])
+    bt.run()
+    for q, x in zip(systems, xs):
+        np.testing.assert_array_equal(q["x"].cpu().numpy(), x)
+
+
 def test_batch_restart_rule_grows_m(monkeypatch):
     """With the MM-ratio rule on, a stagnating GMRES(5) grows its restart
     length at run time (Eq. 1, Sec. 4.3) and still converges; the same

@@ -185,6 +185,13 @@ def test_gmres_resident_declines_long_rows(env, monkeypatch):
     info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, maxiter=20000)
     assert info["persistent"] == 1 and info["status"] == 0
     assert _true_rel(A, x, b) <= TOL
+    # rows longer than 1024 entries: summed by the whole cluster CTA
+    A = gen.poisson2d_dense_rows(60, count=3, length=1500, seed=1)
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=TOL, maxiter=20000)
+    _, io = oracle.gmres(A, b, m=30, tol=TOL)
+    assert info["persistent"] == 1 and info["status"] == 0
+    assert _true_rel(A, x, b) <= TOL
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
 
 
 @pytest.mark.parametrize("name,make", [
