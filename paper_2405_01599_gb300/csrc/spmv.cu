@@ -671,8 +671,26 @@ __global__ void k_seg_fix(int nblk, int n, const int *__restrict__ crow, const V
     if (adev) alpha = *adev;
     const int r = crow[b];
     if (r >= n || (b > 0 && crow[b - 1] == r)) return;
+    // the run of carries of row r, added in storage order; eight carries are
+    // loaded per round, so a row spanning many warps costs few round trips
     V s = cval[b];
-    for (int q = b + 1; q < nblk && crow[q] == r; q++) s += cval[q];
+    for (int q = b + 1; q < nblk; q += 8) {
+        int rr[8];
+        V cc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const bool in = q + u < nblk;
+            rr[u] = in ? crow[q + u] : -1;
+            cc[u] = in ? cval[q + u] : V(0);
+        }
+        bool more = true;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            more = more && rr[u] == r;
+            if (more) s += cc[u];
+        }
+        if (!more) break;
+    }
     y[r] += (mode == 0) ? s : alpha * s;
 }
 
