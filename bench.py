@@ -967,7 +967,11 @@ def batch(xb, torch, dev, args, cpu):
     model = xb.Mlp.load(tuner.MODEL_PATH)
     systems, plans, shapes = [], [], []
     t_ml = t_ex = 0.0
-    mode_of = lambda v: 1 if v == xb.VAR_SEGSCAN else 0
+    # the batched kernel's two in-CTA SpMV forms: thread per row (the U1
+    # counterpart) and warp-sized row blocks with warp- and CTA-wide long rows
+    # (the counterpart of the nnz-balanced U2 and U3); a tuned system takes
+    # the form of the family its tuner chose
+    mode_of = lambda v: 1 if v in (xb.VAR_NNZ, xb.VAR_SEGSCAN) else 0
     for sp in specs:
         A = gen.from_spec(sp)
         pl = xb.Plan.from_host(A, dev)
