@@ -473,14 +473,17 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                 double len2 = 0.0, tt = 0.0;
                 // Givens rotations of the previous columns, applied as the
                 // column's entries arrive (while the next exchange is in
-                // flight): tt is entry i rotated by G_0..G_{i-1}
+                // flight): tt is entry i rotated by G_0..G_{i-1}.  The column
+                // keeps the raw entries; the rotated ones are formed again at
+                // the restart, where the triangular solve needs them, so no
+                // warp carries that work on the path of every exchange
                 auto take = [&](int i, double h) {
                     len2 = fma(h, h, len2);
+                    if (t == 0) H[j * ldh + i] = h;
                     if (i == 0) {
                         tt = h;
                     } else {
                         const double c = cs[i - 1], s = sn[i - 1];
-                        if (t == 0) H[j * ldh + i - 1] = fma(c, tt, s * h);
                         tt = fma(-s, tt, c * h);
                     }
                 };
@@ -570,7 +573,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     if (t == 0) {
                         cs[j] = c;
                         sn[j] = s;
-                        H[j * ldh + j] = rr2 * irr;
+                        H[j * ldh + j + 1] = rr2 * irr;  // the diagonal, until the restart
                         g[j] = c * gj;
                     }
                     gj = -s * gj;
@@ -606,6 +609,24 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
             if (warp == 0) {
                 __syncwarp();
                 constexpr int QM = (XB_BATCH_MAX_M + 31) / 32;
+                // lane c rotates column c's raw entries with G_0..G_{c-1} (the
+                // arithmetic of the steps' running value) and moves its
+                // diagonal into place
+#pragma unroll
+                for (int q = 0; q < QM; q++) {
+                    const int c = lane + 32 * q;
+                    if (c < k) {
+                        double *col = H + c * ldh;
+                        double tr = col[0];
+                        for (int i = 1; i <= c; i++) {
+                            const double hi = col[i], cc = cs[i - 1], ss = sn[i - 1];
+                            col[i - 1] = fma(cc, tr, ss * hi);
+                            tr = fma(-ss, tr, cc * hi);
+                        }
+                        col[c] = col[c + 1];
+                    }
+                }
+                __syncwarp();
                 double gl[QM], dl[QM];
 #pragma unroll
                 for (int q = 0; q < QM; q++) {
