@@ -665,11 +665,12 @@ int xb_tune_mlp(xb_plan *plan, const xb_csr *A, xb_mlp *model, xb_choice *out, i
  * xb_csr rules with sym_upper = 0) solved by restarted GMRES(m) with MGS,
  * the same algorithm as gmres_solve.  One persistent kernel (captured once in
  * a CUDA graph, replayed by xb_batch_run) holds as many CTAs as fit on the
- * GPU, in 8-CTA clusters; work comes from an atomic queue (largest systems
- * first).  A system with n >= 30000 (XB_BATCH_COOP_MIN_N in the environment
- * overrides the threshold) is solved by a whole cluster, its dot products
- * combined through distributed shared memory; smaller systems take one CTA
- * each and need no inter-CTA synchronisation.  opt: tol, maxiter (per
+ * GPU, in 8-CTA clusters; work comes from two atomic queues.  A system with
+ * n >= 30000 (XB_BATCH_COOP_MIN_N in the environment overrides the
+ * threshold) is solved by a whole cluster, its dot products combined through
+ * distributed shared memory; these are taken first, largest first.  Once
+ * they are all taken, every CTA pulls the smaller systems (largest first)
+ * one at a time as soon as it is free, with no inter-CTA synchronisation.  opt: tol, maxiter (per
  * system), maxtime_s (whole launch; checked at every restart), dafrt /
  * dafrt_theta / m_max (the restart-length rule, per system), ortho
  * (XB_ORTHO_MGS, XB_ORTHO_BCGS, or XB_ORTHO_AUTO: BCGS for tol > 1e-10,

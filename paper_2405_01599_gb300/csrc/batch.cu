@@ -80,7 +80,7 @@ struct Smem {
     double sh4[4][kBT / 32], slot4[2][4], tot4[4];  // the same for 4 sums at once
     double g[XB_BATCH_MAX_M + 1], cs[XB_BATCH_MAX_M], sn[XB_BATCH_MAX_M], yv[XB_BATCH_MAX_M];
     unsigned long long t_start;
-    int q, q2, big;
+    int q;
     int flag;
 };
 
@@ -540,8 +540,9 @@ __device__ void solve_one(const xb_batch_dev &D, Part &P, Smem &S, double tol, i
 
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 1)
     k_batch_gmres(const xb_batch_dev *__restrict__ sys, xb_batch_info *__restrict__ out,
-                  const int *__restrict__ order, int count, int *__restrict__ queue, double tol,
-                  int maxiter, unsigned long long budget_ns, double theta, int bcgs) {
+                  const int *__restrict__ order, int count, int nbig, int nsmall_cl,
+                  int *__restrict__ queue, double tol, int maxiter, unsigned long long budget_ns,
+                  double theta, int bcgs) {
     __shared__ Smem S;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -550,32 +551,48 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 1)
     cl.sync();
     const unsigned long long deadline = cl.map_shared_rank(&S, 0)->t_start + budget_ns;
     cl.sync();
-    for (;;) {
-        if (rank == 0 && threadIdx.x == 0) {
-            const int q = atomicAdd(queue, 1);
-            S.q = q;
-            S.big = (q < count && sys[order[q]].coop) ? 1 : 0;
-            S.q2 = (q < count && !S.big) ? atomicAdd(queue, kCl - 1) : count;
-        }
-        cl.sync();
-        const Smem *L = cl.map_shared_rank(&S, 0);
-        const int q = L->q, q2 = L->q2, big = L->big;
-        cl.sync();  // the leader may overwrite q only after every CTA has read it
-        if (q >= count) return;  // cluster-uniform
-        if (big) {
+    // phase 1: the systems a whole cluster solves (order[0, nbig), largest
+    // first), one per pull of the cluster's leader; phase 2: the single-CTA
+    // systems (order[nbig, count), largest first), every CTA pulling its next
+    // system as soon as it is free (no cluster barrier and no distributed
+    // shared memory inside phase 2, so the CTAs of a cluster run apart).  The
+    // first nsmall_cl clusters start with phase 2, so the longest single-CTA
+    // solves do not wait for the end of phase 1, and join phase 1 when the
+    // single-CTA queue is empty (their last systems are the smallest, so the
+    // regrouping barrier waits little); the others run phase 1, then phase 2.
+    const bool small_first = (int)(blockIdx.x / kCl) < nsmall_cl;  // cluster-uniform
+    auto phase1 = [&]() {
+        for (;;) {
+            if (rank == 0 && threadIdx.x == 0) S.q = atomicAdd(queue, 1);
+            cl.sync();
+            const int q = cl.map_shared_rank(&S, 0)->q;
+            cl.sync();  // the leader may overwrite q only after every CTA has read it
+            if (q >= nbig) return;  // cluster-uniform
             const xb_batch_dev D = sys[order[q]];
             const int per = (D.n + kCl - 1) / kCl;
             Part P{min(D.n, rank * per), min(D.n, (rank + 1) * per), 1, 0};
             solve_one(D, P, S, tol, maxiter, deadline, rank, theta, bcgs, out + order[q]);
-        } else {
-            const int mine = rank == 0 ? q : q2 + rank - 1;
-            if (mine < count) {
-                const xb_batch_dev D = sys[order[mine]];
-                Part P{0, D.n, 0, 0};
-                solve_one(D, P, S, tol, maxiter, deadline, 0, theta, bcgs, out + order[mine]);
-            }
         }
-        cl.sync();  // regroup before the next pull
+    };
+    auto phase2 = [&]() {
+        for (;;) {
+            if (threadIdx.x == 0) S.q = atomicAdd(queue + 1, 1);
+            __syncthreads();
+            const int q = nbig + S.q;
+            __syncthreads();  // S.q is rewritten only after every thread has read it
+            if (q >= count) return;  // CTA-uniform
+            const xb_batch_dev D = sys[order[q]];
+            Part P{0, D.n, 0, 0};
+            solve_one(D, P, S, tol, maxiter, deadline, 0, theta, bcgs, out + order[q]);
+        }
+    };
+    if (small_first) {
+        phase2();
+        cl.sync();  // every CTA of the cluster is free: take cluster systems
+        phase1();
+    } else {
+        phase1();
+        phase2();
     }
 }
 
@@ -638,12 +655,12 @@ int batch_single(xb_plan *p, const double *b, double *x, const xb_options &o, in
     const int zero = 0;
     XB_CUDA(cudaMemcpyAsync(d_sys, &d, sizeof d, cudaMemcpyHostToDevice, s));
     XB_CUDA(cudaMemcpyAsync(d_order, &zero, sizeof zero, cudaMemcpyHostToDevice, s));
-    XB_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+    XB_CUDA(cudaMemsetAsync(d_queue, 0, 2 * sizeof(int), s));
     const unsigned long long budget = (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
     const double theta = o.dafrt ? o.dafrt_theta : 0.0;
     const int bcgs = o.ortho == XB_ORTHO_BCGS ? 1 : 0;
-    k_batch_gmres<<<kCl, kBT, 0, s>>>(d_sys, d_info, d_order, 1, d_queue, o.tol, o.maxiter, budget,
-                                      theta, bcgs);
+    k_batch_gmres<<<kCl, kBT, 0, s>>>(d_sys, d_info, d_order, 1, 1, 0, d_queue, o.tol, o.maxiter,
+                                      budget, theta, bcgs);
     XB_LAUNCHED("k_batch_gmres (single system)");
     xb_batch_info r;
     XB_CUDA(cudaMemcpyAsync(&r, d_info, sizeof r, cudaMemcpyDeviceToHost, s));
@@ -767,16 +784,20 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
         h[i].H = bt->d_ws + off;
         off += (size_t)(h[i].coop ? kCl : 1) * (h[i].m_max + 1) * h[i].m_max + 32;
     }
+    // the cluster systems first, then the single-CTA ones, each part
     // largest first: the long solves start in the first wave
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (h[a].coop != h[b].coop) return h[a].coop > h[b].coop;
         return (int64_t)h[a].nnz + h[a].n > (int64_t)h[b].nnz + h[b].n;
     });
+    int nbig = 0;
+    for (int i = 0; i < count; i++) nbig += h[i].coop ? 1 : 0;
     e = cudaMalloc(&bt->d_sys, std::max(count, 1) * sizeof(xb_batch_dev));
     if (e == cudaSuccess) e = cudaMalloc(&bt->d_info, std::max(count, 1) * sizeof(xb_batch_info));
     if (e == cudaSuccess) e = cudaMalloc(&bt->d_order, std::max(count, 1) * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_queue, 2 * sizeof(int));
     if (e == cudaSuccess && count > 0)
         e = cudaMemcpy(bt->d_sys, h.data(), count * sizeof(xb_batch_dev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && count > 0)
@@ -794,6 +815,18 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
         clusters = std::max(1, xb::num_sms() / kCl);
     }
     bt->grid = kCl * std::max(1, clusters);
+    // clusters that take the single-CTA systems from the start: their share
+    // of the work, with nnz + m n (one step's SpMV and Gram-Schmidt) as the
+    // per-system weight; none without cluster systems to balance against
+    double w_big = 0.0, w_small = 0.0;
+    for (int i = 0; i < count; i++) {
+        const double wi = (double)h[i].nnz + (double)h[i].m * h[i].n;
+        (h[i].coop ? w_big : w_small) += wi;
+    }
+    const int ncl = std::max(1, clusters);
+    int nsmall_cl = 0;
+    if (nbig > 0 && w_small > 0.0)
+        nsmall_cl = std::min(ncl - 1, (int)std::lround(ncl * w_small / (w_big + w_small)));
     const unsigned long long budget = (unsigned long long)(std::min(o.maxtime_s, 3600.0) * 1e9);
     const double theta = o.dafrt ? o.dafrt_theta : 0.0;  // theta 0: the rule never fires
     // orthogonalisation: MGS or BCGS (block length 4); the accuracy policy's
@@ -811,8 +844,9 @@ int xb_batch_create(int32_t count, const xb_batch_sys *sys, const xb_options *op
         cudaStreamDestroy(cs);
         return fail(xb::cuda_error(e, "batch_create: begin capture"));
     }
-    cudaMemsetAsync(bt->d_queue, 0, sizeof(int), cs);
-    k_batch_gmres<<<bt->grid, kBT, 0, cs>>>(bt->d_sys, bt->d_info, bt->d_order, count, bt->d_queue,
+    cudaMemsetAsync(bt->d_queue, 0, 2 * sizeof(int), cs);
+    k_batch_gmres<<<bt->grid, kBT, 0, cs>>>(bt->d_sys, bt->d_info, bt->d_order, count, nbig,
+                                             nsmall_cl, bt->d_queue,
                                              o.tol, o.maxiter, budget, theta, bcgs);
     cudaError_t el = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &bt->graph);

@@ -175,6 +175,25 @@ def test_gmres_resident_is_repeatable(env, monkeypatch, ortho):
         np.testing.assert_array_equal(x, runs[0][1])
 
 
+def test_gmres_resident_fault_convergence_and_time_budget(env, monkeypatch):
+    """The shared-memory path's true-residual check after an implicit
+    convergence claim (Sec. 3.3.2: at tol 1e-14 the oracle claims once too
+    early and narrows its threshold) and its time budget (a deadline the
+    first restart check already sees ends the solve with XB_ENOCONV)."""
+    xb, dev = env
+    monkeypatch.delenv("XB_RESIDENT_CL", raising=False)
+    A = gen.poisson2d(64)
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=1e-14, maxiter=20000, ortho=xb.ORTHO_MGS)
+    _, io = oracle.gmres(A, b, m=30, tol=1e-14, maxiter=20000)
+    assert io["faults"] >= 1
+    assert info["persistent"] == 2 and info["status"] == 0, info
+    assert _true_rel(A, x, b) <= 1e-14
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=1e-8, maxtime_s=1e-6)
+    assert info["persistent"] == 2 and info["status"] == xb.XB_ENOCONV, info
+    assert info["iters"] <= 30
+
+
 def test_gmres_resident_declines_long_rows(env, monkeypatch):
     """Rows longer than 64 entries do not take the shared-memory path: the
     batched kernel runs the system instead."""
