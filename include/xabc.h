@@ -416,7 +416,7 @@ int xb_spmv_f32(xb_plan *plan, int32_t variant, float alpha, const float *x, flo
  * fault_check on -- run the same GMRES(m) as one persistent launch, because
  * each Arnoldi step of the multi-launch path is bound by launch and
  * synchronisation latency at that size.  When a cluster of 2, 4, 8 or 16
- * CTAs can hold the system in shared memory (at most 512 rows per CTA, rows
+ * CTAs can hold the system in shared memory (at most 1024 rows per CTA, rows
  * at most 64 long, the basis slice, the ELL copy of the rows and the
  * Hessenberg matrix within the opt-in shared memory of a CTA) that cluster
  * runs it with no global-memory traffic per step (xb_info.persistent = 2;

@@ -11,8 +11,9 @@
 // warp instructions on its critical path (and by cluster barriers, about 400
 // cycles).  Hence: one warp per sub-partition (4 warps per CTA, R rows per
 // thread), the largest cluster that keeps R smallest, reductions shaped to
-// use few FP64 instructions, and the Givens work of the previous entry run
-// between a barrier's arrive and its wait.
+// use few FP64 instructions, the running Givens rotation of the previous
+// entry computed while an exchange is in flight, and the rotated Hessenberg
+// entries formed only at the restart, where the triangular solve needs them.
 //
 // Layout.  CTA r of the cluster owns rows [r rpc, (r+1) rpc); thread t holds
 // the local rows t, t + 128, ... (R of them).  The thread's entries of the
