@@ -534,17 +534,50 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     // fused MGS: pass i applies the projection on v_{i-1} and
                     // takes (w, v_i)
                     double hprev = 0.0;
-                    for (int i = 0; i <= j; i++) {
-                        double a = 0.0;
+                    if constexpr (R <= 2) {
+                        // the thread's part of (w - h_{i-1} v_{i-1}, v_i) as
+                        // (w, v_i) - h_{i-1} (v_{i-1}, v_i): both parts are
+                        // formed while the previous exchange is in flight,
+                        // so one FMA separates h_{i-1} from the next send
+                        // (with more rows per thread that work outgrows the
+                        // exchange, and the direct form below is faster)
+                        double p1 = 0.0, p2 = 0.0;
 #pragma unroll
-                        for (int r = 0; r < R; r++) {
-                            const int l = r * kBT + t;
-                            if (i > 0) w[r] = fma(-hprev, V[(i - 1) * rpp + l], w[r]);
-                            a = fma(w[r], V[i * rpp + l], a);
+                        for (int r = 0; r < R; r++) p1 = fma(w[r], V[r * kBT + t], p1);
+                        for (int i = 0; i <= j; i++) {
+                            mput1(i == 0 ? p1 : fma(-hprev, p2, p1), Rd);
+                            if (i > 0) {
+#pragma unroll
+                                for (int r = 0; r < R; r++)
+                                    w[r] = fma(-hprev, V[(i - 1) * rpp + r * kBT + t], w[r]);
+                            }
+                            if (i < j) {
+                                p1 = 0.0;
+                                p2 = 0.0;
+#pragma unroll
+                                for (int r = 0; r < R; r++) {
+                                    const int l = r * kBT + t;
+                                    const double vi = V[i * rpp + l], vn = V[(i + 1) * rpp + l];
+                                    p1 = fma(w[r], vn, p1);
+                                    p2 = fma(vi, vn, p2);
+                                }
+                            }
+                            if (i > 0) take(i - 1, hprev);
+                            hprev = slots_sum1<NCL>(mwait(Rd));
                         }
-                        mput1(a, Rd);
-                        if (i > 0) take(i - 1, hprev);
-                        hprev = slots_sum1<NCL>(mwait(Rd));
+                    } else {
+                        for (int i = 0; i <= j; i++) {
+                            double a = 0.0;
+#pragma unroll
+                            for (int r = 0; r < R; r++) {
+                                const int l = r * kBT + t;
+                                if (i > 0) w[r] = fma(-hprev, V[(i - 1) * rpp + l], w[r]);
+                                a = fma(w[r], V[i * rpp + l], a);
+                            }
+                            mput1(a, Rd);
+                            if (i > 0) take(i - 1, hprev);
+                            hprev = slots_sum1<NCL>(mwait(Rd));
+                        }
                     }
 #pragma unroll
                     for (int r = 0; r < R; r++) w[r] = fma(-hprev, V[j * rpp + r * kBT + t], w[r]);
