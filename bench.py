@@ -1064,6 +1064,20 @@ def batch(xb, torch, dev, args, cpu):
             "max_system_ms": {"default": max(q["ms"] for q in r_def),
                               "exhaustive": max(q["ms"] for q in r_exh),
                               "learned": max(q["ms"] for q in r_mlp)}}
+    # tuning included: each arm's tuning time plus its launch
+    res["launch_plus_tune_s"] = {"default": t_def * 1e-3, "exhaustive": t_ex + t_exh * 1e-3,
+                                 "learned": t_ml + t_mlp * 1e-3}
+    res["launch_plus_tune_speedup_learned"] = {
+        "vs_exhaustive": (t_ex + t_exh * 1e-3) / (t_ml + t_mlp * 1e-3),
+        "vs_default": (t_def * 1e-3) / (t_ml + t_mlp * 1e-3)}
+    # per-system regret of the learned choice against the exhaustive one on
+    # the systems both solve (device time of the system's solve)
+    ratios = np.array([r_mlp[i]["ms"] / max(r_exh[i]["ms"], 1e-9) for i in both])
+    if ratios.size:
+        res["learned_regret_vs_exhaustive_per_system"] = {
+            "systems": int(ratios.size), "geomean": float(np.exp(np.mean(np.log(ratios)))),
+            "median": float(np.median(ratios)), "p90": float(np.percentile(ratios, 90)),
+            "faster_or_equal": int(np.sum(ratios <= 1.0))}
     if args.batch_rule_arms:
         # the paper's full run-time AT: SpMV choice before execution plus the
         # restart-frequency rule during it (m starts at 30, grows by 5 up to 128),
