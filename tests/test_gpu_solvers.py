@@ -194,6 +194,31 @@ def test_gmres_resident_fault_convergence_and_time_budget(env, monkeypatch):
     assert info["iters"] <= 30
 
 
+def test_gmres_resident_cta_without_rows_and_tiny_systems(env, monkeypatch):
+    """A cluster CTA that owns no rows still takes part in every exchange
+    (n = 130 on 16 CTAs: 9 rows per CTA, the last CTA none); a 1 x 1 system
+    and a 2 x 2 one converge in one and two steps."""
+    xb, dev = env
+    monkeypatch.setenv("XB_RESIDENT_CL", "16")
+    A = gen.laplace1d(130)
+    info, x, b = _solve(xb, dev, A, "gmres", m=30, tol=1e-10, maxiter=5000)
+    _, io = oracle.gmres(A, b, m=30, tol=1e-10, maxiter=5000)
+    assert info["persistent"] == 2 and info["status"] == 0, info
+    assert _true_rel(A, x, b) <= 1e-10
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.05 * io["iters"]), (info["iters"], io["iters"])
+    monkeypatch.delenv("XB_RESIDENT_CL")
+    one = dict(n=1, nnz=1, rowptr=np.array([0, 1], np.int32), col=np.array([0], np.int32),
+               val=np.array([3.0]), sym_upper=False)
+    info, x, b = _solve(xb, dev, one, "gmres", b=np.array([6.0]))
+    assert info["persistent"] == 2 and info["status"] == 0 and info["iters"] == 1
+    np.testing.assert_allclose(x, [2.0], rtol=1e-15)
+    two = dict(n=2, nnz=3, rowptr=np.array([0, 2, 3], np.int32), col=np.array([0, 1, 1], np.int32),
+               val=np.array([2.0, 1.0, 3.0]), sym_upper=False)
+    info, x, b = _solve(xb, dev, two, "gmres", b=np.array([3.0, 3.0]), tol=1e-12)
+    assert info["persistent"] == 2 and info["status"] == 0 and info["iters"] <= 2
+    np.testing.assert_allclose(x, [1.0, 1.0], rtol=1e-12)
+
+
 def test_gmres_resident_declines_long_rows(env, monkeypatch):
     """Rows longer than 64 entries do not take the shared-memory path: the
     batched kernel runs the system instead."""
