@@ -1,15 +1,17 @@
 // Batched solve of many independent systems in ONE persistent kernel launch,
 // captured in a CUDA graph and replayed.
 //
-// The launch is a grid of 8-CTA thread-block clusters.  Each cluster pulls
-// work from an atomic queue (systems ordered largest first):
-//   - a system with n >= kLargeN is solved by the whole cluster: every CTA
+// The launch is a grid of 8-CTA thread-block clusters, fed by two atomic
+// queues (each ordered largest first):
+//   - a system with n >= kLargeN is solved by a whole cluster: every CTA
 //     owns a slice of the rows, dot products are combined across the cluster
 //     through distributed shared memory (every CTA sums the 8 partials in rank
 //     order, so all CTAs hold identical values), and hardware cluster
-//     barriers order the shared vectors;
-//   - smaller systems are taken one per CTA and solved with block-level
-//     reductions only.
+//     barriers order the shared vectors; a cluster's leader pulls these;
+//   - smaller systems are pulled by each CTA on its own, as soon as it is
+//     free, and solved with block-level reductions only.
+// Most clusters take the cluster queue first and then the other; the first
+// few start on the single-CTA queue and join the cluster queue after it.
 // Every cluster barrier sits on a path whose branch conditions are
 // cluster-uniform (iteration counts, reduced values, and a time-budget flag
 // that rank 0 decides and broadcasts through a reduction), so all CTAs of a
