@@ -77,7 +77,7 @@ struct ResArgs {
 
 // Byte offsets of the dynamic shared memory regions (doubles first).
 struct ResLayout {
-    size_t V, W, ev, bs, ms, H, cs, sn, g, y, ea, mb, total;
+    size_t V, W, ev, bs, ms, H, cs, sn, g, y, ea, p2, mb, total;
 };
 
 __host__ __device__ inline ResLayout res_layout(int rpp, int lmax, int mmax, int P) {
@@ -99,6 +99,8 @@ __host__ __device__ inline ResLayout res_layout(int rpp, int lmax, int mmax, int
     L.g = take((size_t)(mmax + 1) * 8);
     L.y = take((size_t)mmax * 8);
     L.ea = take((size_t)lmax * rpp * 4);
+    // R <= 2: each thread's part of (v_{i-1}, v_i), formed once per basis vector
+    L.p2 = take(rpp <= 2 * 128 ? (size_t)(mmax + 1) * 128 * 8 : 0);
     L.mb = take(2 * 8 + 4);  // two mbarriers, the abort flag
     L.total = o;
     return L;
@@ -341,6 +343,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
     double *g = reinterpret_cast<double *>(smem + L.g);
     double *yv = reinterpret_cast<double *>(smem + L.y);
     int *ea = reinterpret_cast<int *>(smem + L.ea);
+    double *P2 = reinterpret_cast<double *>(smem + L.p2);  // R <= 2 only
     const unsigned rank = cluster_rank();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     Red<NCL> Rd;
@@ -553,14 +556,10 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                             }
                             if (i < j) {
                                 p1 = 0.0;
-                                p2 = 0.0;
 #pragma unroll
-                                for (int r = 0; r < R; r++) {
-                                    const int l = r * kBT + t;
-                                    const double vi = V[i * rpp + l], vn = V[(i + 1) * rpp + l];
-                                    p1 = fma(w[r], vn, p1);
-                                    p2 = fma(vi, vn, p2);
-                                }
+                                for (int r = 0; r < R; r++)
+                                    p1 = fma(w[r], V[(i + 1) * rpp + r * kBT + t], p1);
+                                p2 = P2[(i + 1) * kBT + t];
                             }
                             if (i > 0) take(i - 1, hprev);
                             hprev = slots_sum1<NCL>(mwait(Rd));
@@ -631,6 +630,15 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                 double *Vn = V + (j + 1) * rpp;
 #pragma unroll
                 for (int r = 0; r < R; r++) Vn[r * kBT + t] = w[r] * sc;
+                if constexpr (R <= 2) {
+                    if (!A.bcgs) {  // MGS: (v_j, v_{j+1}), this thread's part
+                        double pv = 0.0;
+#pragma unroll
+                        for (int r = 0; r < R; r++)
+                            pv = fma(V[j * rpp + r * kBT + t], w[r] * sc, pv);
+                        P2[(j + 1) * kBT + t] = pv;
+                    }
+                }
                 if (flag == 3) {
                     claimed = 1;
                     break;
