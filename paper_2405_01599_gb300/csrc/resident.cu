@@ -99,8 +99,8 @@ __host__ __device__ inline ResLayout res_layout(int rpp, int lmax, int mmax, int
     L.g = take((size_t)(mmax + 1) * 8);
     L.y = take((size_t)mmax * 8);
     L.ea = take((size_t)lmax * rpp * 4);
-    // R <= 2: each thread's part of (v_{i-1}, v_i), formed once per basis vector
-    L.p2 = take(rpp <= 2 * 128 ? (size_t)(mmax + 1) * 128 * 8 : 0);
+    // R <= 4: each thread's part of (v_{i-1}, v_i), formed once per basis vector
+    L.p2 = take(rpp <= 4 * 128 ? (size_t)(mmax + 1) * 128 * 8 : 0);
     L.mb = take(2 * 8 + 4);  // two mbarriers, the abort flag
     L.total = o;
     return L;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
     double *g = reinterpret_cast<double *>(smem + L.g);
     double *yv = reinterpret_cast<double *>(smem + L.y);
     int *ea = reinterpret_cast<int *>(smem + L.ea);
-    double *P2 = reinterpret_cast<double *>(smem + L.p2);  // R <= 2 only
+    double *P2 = reinterpret_cast<double *>(smem + L.p2);  // R <= 4 only
     const unsigned rank = cluster_rank();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     Red<NCL> Rd;
@@ -537,13 +537,14 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     // fused MGS: pass i applies the projection on v_{i-1} and
                     // takes (w, v_i)
                     double hprev = 0.0;
-                    if constexpr (R <= 2) {
+                    if constexpr (R <= 4) {
                         // the thread's part of (w - h_{i-1} v_{i-1}, v_i) as
                         // (w, v_i) - h_{i-1} (v_{i-1}, v_i): both parts are
                         // formed while the previous exchange is in flight,
                         // so one FMA separates h_{i-1} from the next send
                         // (with more rows per thread that work outgrows the
-                        // exchange, and the direct form below is faster)
+                        // exchange, and the direct form below is faster:
+                        // measured at R = 8)
                         double p1 = 0.0, p2 = 0.0;
 #pragma unroll
                         for (int r = 0; r < R; r++) p1 = fma(w[r], V[r * kBT + t], p1);
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                 double *Vn = V + (j + 1) * rpp;
 #pragma unroll
                 for (int r = 0; r < R; r++) Vn[r * kBT + t] = w[r] * sc;
-                if constexpr (R <= 2) {
+                if constexpr (R <= 4) {
                     if (!A.bcgs) {  // MGS: (v_j, v_{j+1}), this thread's part
                         double pv = 0.0;
 #pragma unroll
