@@ -539,12 +539,13 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     double hprev = 0.0;
                     if constexpr (R <= 4) {
                         // the thread's part of (w - h_{i-1} v_{i-1}, v_i) as
-                        // (w, v_i) - h_{i-1} (v_{i-1}, v_i): both parts are
+                        // (w, v_i) - h_{i-1} (v_{i-1}, v_i): the first part is
                         // formed while the previous exchange is in flight,
-                        // so one FMA separates h_{i-1} from the next send
-                        // (with more rows per thread that work outgrows the
-                        // exchange, and the direct form below is faster:
-                        // measured at R = 8)
+                        // the second once when v_i was written, so one FMA
+                        // separates h_{i-1} from the next send (measured
+                        // faster than the direct form at 2 and 4 rows per
+                        // thread; at 8 the window's work would outgrow the
+                        // exchange, and the direct form below serves it)
                         double p1 = 0.0, p2 = 0.0;
 #pragma unroll
                         for (int r = 0; r < R; r++) p1 = fma(w[r], V[r * kBT + t], p1);
