@@ -139,17 +139,20 @@ def test_gmres_edge_cases(env, monkeypatch, path):
 
 @pytest.mark.parametrize("ncl,mat,m", [
     (2, "convdiff9", 23), (4, "convdiff9", 23), (8, "convdiff9", 23), (16, "convdiff9", 23),
-    (2, "poisson44", 10), (16, "poisson44", 10)])
+    (2, "poisson44", 10), (16, "poisson44", 10), (16, "poisson90", 30)])
 @pytest.mark.parametrize("ortho", ["mgs", "bcgs"])
 def test_gmres_resident_cluster_sizes(env, monkeypatch, ncl, mat, m, ortho):
     """The shared-memory path on each cluster size and rows-per-thread count
     (convdiff9, n = 729: 365 / 183 / 92 / 46 rows per CTA, 4 / 2 / 1 / 1 rows
     per thread; poisson44, n = 1936: 968 rows per CTA, 8 per thread, or 121;
-    the last CTA holds fewer rows than the others), both Gram-Schmidt forms,
-    against the oracle's GMRES with the same orthogonalisation."""
+    poisson90, n = 8100: 507 rows per CTA, 4 per thread, near the shared-
+    memory limit; the last CTA holds fewer rows than the others), both
+    Gram-Schmidt forms, against the oracle's GMRES with the same
+    orthogonalisation."""
     xb, dev = env
     monkeypatch.setenv("XB_RESIDENT_CL", str(ncl))
-    A = gen.convdiff3d(N=9) if mat == "convdiff9" else gen.poisson2d(44)
+    A = {"convdiff9": lambda: gen.convdiff3d(N=9), "poisson44": lambda: gen.poisson2d(44),
+         "poisson90": lambda: gen.poisson2d(90)}[mat]()
     oc = xb.ORTHO_MGS if ortho == "mgs" else xb.ORTHO_BCGS
     info, x, b = _solve(xb, dev, A, "gmres", m=m, tol=1e-10, ortho=oc, maxiter=20000)
     xo, io = oracle.gmres(A, b, m=m, tol=1e-10, maxiter=20000,
