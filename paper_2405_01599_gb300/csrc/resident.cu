@@ -314,18 +314,31 @@ __device__ __forceinline__ const double *mwait(Red<NCL> &R) {
     return R.ms + p * 4 * R.P;
 }
 
-// (A u)_row for the published vector u in shared buffer `buf` (local shared
-// address), row entries in storage order.
-__device__ __forceinline__ double row_spmv(const double *__restrict__ ev, const int *__restrict__ ea,
-                                           int len, int rpp, int l, unsigned buf) {
-    double s = 0.0;
-#pragma unroll 4
-    for (int k = 0; k < len; k++) {
-        const int e = ea[k * rpp + l];
-        const double u = ld_cluster(map_rank(buf + (unsigned)(e & 0xffff) * 8u, (unsigned)e >> 16));
-        s = fma(ev[k * rpp + l], u, s);
+// The thread's R rows at once, entry k of every row in one round, so their
+// gathers overlap; each row's sum keeps its storage order.
+template <int R>
+__device__ __forceinline__ void rows_spmv(const double *__restrict__ ev, const int *__restrict__ ea,
+                                          const int (&len)[R], int rpp, unsigned buf,
+                                          double (&s)[R]) {
+    int lmx = 0;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        s[r] = 0.0;
+        lmx = max(lmx, len[r]);
     }
-    return s;
+#pragma unroll 2
+    for (int k = 0; k < lmx; k++) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            if (k < len[r]) {
+                const int l = r * kBT + threadIdx.x;
+                const int e = ea[k * rpp + l];
+                const double u =
+                    ld_cluster(map_rank(buf + (unsigned)(e & 0xffff) * 8u, (unsigned)e >> 16));
+                s[r] = fma(ev[k * rpp + l], u, s[r]);
+            }
+        }
+    }
 }
 
 template <int R, int NCL>
@@ -420,9 +433,9 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
             cl_arrive();
             cl_wait();
             double rs[R];
+            rows_spmv<R>(ev, ea, len, rpp, wbuf[wb], rs);
 #pragma unroll
-            for (int r = 0; r < R; r++)
-                rs[r] = fma(-1.0, row_spmv(ev, ea, len[r], rpp, r * kBT + t, wbuf[wb]), bi[r]);
+            for (int r = 0; r < R; r++) rs[r] = fma(-1.0, rs[r], bi[r]);
             wb ^= 1;
             q4[0] = 0.0;
 #pragma unroll
@@ -471,9 +484,9 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
             int k = 0;
             for (int j = 0; j < m; j++) {
                 iters++;
+                rows_spmv<R>(ev, ea, len, rpp, wbuf[wb], w);
 #pragma unroll
-                for (int r = 0; r < R; r++)
-                    w[r] = row_spmv(ev, ea, len[r], rpp, r * kBT + t, wbuf[wb]) * sc;
+                for (int r = 0; r < R; r++) w[r] *= sc;
                 double len2 = 0.0, tt = 0.0;
                 // Givens rotations of the previous columns, applied as the
                 // column's entries arrive (while the next exchange is in
