@@ -628,8 +628,8 @@ __global__ void __launch_bounds__(kBT, 1) k_gmres_resident(const ResArgs A) {
                     if (hn2 <= 1e-28 * (len2 + hn2)) flag = 1;  // hn <= 1e-14 |column|
                     else if (fabs(gj) <= tol_g) flag = 3;
                 }
-                // thread 0's rotation, g and the column's entries (stored by
-                // the warps in turn) visible to the CTA before their next use
+                // thread 0's rotation, g, diagonal and raw column entries
+                // visible to the CTA before their next use
                 __syncthreads();
                 if (flag == 2) {
                     k = j;
